@@ -1,0 +1,403 @@
+"""FRKC2 oracle: a plain, slow, FP64 CPU statement of the method.
+
+TEST INFRASTRUCTURE ONLY.  This module is imported by ``tests/``, by
+``__graft_entry__.smoke()`` and by the CPU-baseline leg of ``bench.py`` -- nothing in the
+product package imports, links or runs it, and it imports nothing from the product.
+
+Every function follows a passage of O'Sullivan, "Factorized Runge-Kutta-Chebyshev
+Methods" (arXiv:1702.03818); the passage is cited in each docstring.  Where the paper is
+silent or garbled the reading taken is stated in the docstring ("Reading:").
+
+Contents
+--------
+* stability polynomial and step sizes (Sec. 2, Eqs. 5-8): ``alpha``, ``beta``, ``roots``,
+  ``step_sizes``;
+* internal stability (Sec. 2.2, Eqs. 10-12): ``realised_Q`` (brute force over all
+  sub-sequences), ``order_greedy`` and ``plan`` (the n-loop);
+* the diffusion operator f(w) = div(kappa grad w) in flux form (the semi-discrete system of
+  Eq. 1): ``cell_kappa``, ``apply_f``, ``rho_bound``;
+* the FRKC2 step (Sec. 3, Eq. 13), stages applied literally as complex forward-Euler steps:
+  ``frkc2_step``;
+* its discrete adjoint (reverse replay of Eq. 13): ``frkc2_adjoint``;
+* a classical RK4 integrator used as a fine-step reference for the nonlinear case: ``rk4``.
+
+Problem description
+-------------------
+A problem is a dict with keys ``ndim`` (1..3), ``dx`` (grid spacing), ``bc``
+(``"periodic"`` or ``"dirichlet"``: u = 0 in the ghost cells outside the grid), ``kappa``
+(``"const"``, ``"field"`` or ``"power"``), ``kappa_c`` (the constant, or the coefficient c
+of kappa(u) = 1 + c u^p), ``kappa_p`` (the exponent p) and ``kappa_field`` (cell-centred
+array, same shape as the state).  State arrays use numpy order, last axis = x.
+
+Parity status: every function here is pinned by ``tests/test_oracle_pins.py`` except the
+ordering itself (``order_greedy``): the paper's coefficient table is not available, so the
+permutation it produces is checked only through invariants (it is a permutation, the
+product is unchanged, the realised Q meets the paper's bound) -- parity unpinned for the
+exact order.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+# ----------------------------------------------------------------------------------------
+# Stability polynomial and step sizes (Sec. 2)
+# ----------------------------------------------------------------------------------------
+
+
+def alpha(L: int) -> float:
+    """alpha_M of Eq. 8 for the second-order polynomial of degree L = 2M.
+
+    Reading (the paper defers the closed form to its companion paper): with N = 2 the
+    polynomial of Eq. 7 is R(z) = 1 - alpha/4 + (alpha/4) T_L(1 + 4 z / (L^2 alpha)).
+    R(0) = 1 and R'(0) = 1 hold for any alpha; R''(0) = 1 (Eq. 5, n = 2) gives
+    alpha = 4 (1 - 1/L^2) / 3, which is also the largest alpha keeping |R| <= 1 (Eq. 6).
+    """
+    return 4.0 * (1.0 - 1.0 / (L * L)) / 3.0
+
+
+def beta(L: int) -> float:
+    """Extent of the real stability interval [-beta, 0] (Eq. 6): beta = L^2 alpha / 2."""
+    return 0.5 * L * L * alpha(L)
+
+
+def roots(L: int) -> np.ndarray:
+    """Roots zeta_j of T_L(x) = 1 - 4/alpha, the zeros of the polynomial of Eq. 7.
+
+    zeta_j = cos((pi (2j + 1) - i eta) / L), eta = arccosh(4/alpha - 1), j = 0..L-1.
+    Reading: the roots come in conjugate pairs j <-> L-1-j; the second member of each pair
+    is set to the exact conjugate of the first so that the pair is conjugate bit for bit.
+    """
+    if L < 2 or L % 2:
+        raise ValueError("L must be even and >= 2")
+    eta = np.arccosh(4.0 / alpha(L) - 1.0)
+    z = np.empty(L, dtype=np.complex128)
+    for j in range(L // 2):
+        z[j] = np.cos((np.pi * (2 * j + 1) - 1j * eta) / L)
+        z[L - 1 - j] = np.conj(z[j])
+    return z
+
+
+def step_sizes(L: int) -> np.ndarray:
+    """Complex Euler step sizes a_j = 1 / (M^2 alpha_M (1 - zeta_j)), L = 2M (Eq. 8).
+
+    Returned in root order j = 0..L-1 (before the internal-stability ordering).
+    """
+    M = L // 2
+    return 1.0 / (M * M * alpha(L) * (1.0 - roots(L)))
+
+
+# ----------------------------------------------------------------------------------------
+# Internal stability (Sec. 2.2)
+# ----------------------------------------------------------------------------------------
+
+
+def realised_Q(a: np.ndarray, beta_: float, points: int) -> float:
+    """Q = max over 1 <= j <= k <= L and x in [-beta, 0] of prod_{l=j}^{k} |1 + a_l x| (Eqs. 10-11).
+
+    Brute force over every contiguous sub-sequence of the ordered ``a`` on the grid
+    x_i = -beta i / points, i = 0..points (products formed as sums of logarithms).
+    """
+    x = -beta_ * np.arange(points + 1) / points
+    logv = np.log(np.abs(1.0 + np.outer(a, x)))
+    best = -np.inf
+    for j in range(len(a)):
+        sub = np.cumsum(logv[j:], axis=0)  # row k-j holds log prod_{l=j}^{k}
+        best = max(best, float(sub.max()))
+    return float(np.exp(best))
+
+
+def order_greedy(a: np.ndarray, beta_: float, n: int, samples: int, C: float = 1e-4) -> np.ndarray:
+    """Stage ordering that keeps the estimated amplification of Eq. 12 small.
+
+    Reading of Eq. 12 (its printed limits are garbled): the items ordered are the L
+    individual step sizes.  The samples are x_k = -beta_bar k / S, k = 1..S, on the reduced
+    range beta_bar = (1 - n C) beta.  For position l = 1..L the unplaced step size j that
+    minimises sum_k max(P_k v_jk, Rest_k / v_jk) is placed, where v_jk = |1 + a_j x_k|, P is
+    the product over the stages already placed and Rest the product over every stage not
+    yet placed (j included).  Ties go to the lowest original index.  Sums are formed in log
+    space (log-sum-exp) so that no product overflows.
+
+    Returns the permutation (indices into ``a``) in stage order.
+    """
+    L = len(a)
+    beta_bar = (1.0 - n * C) * beta_
+    x = -beta_bar * np.arange(1, samples + 1) / samples
+    logv = np.log(np.abs(1.0 + np.outer(a, x)))
+    remaining = list(range(L))
+    placed = []
+    logP = np.zeros(samples)
+    for _ in range(L):
+        rem = np.asarray(remaining)
+        cand = logv[rem]
+        logRest = cand.sum(axis=0)
+        e = np.maximum(logP[None, :] + cand, logRest[None, :] - cand)
+        m = e.max(axis=1)
+        cost = m + np.log(np.exp(e - m[:, None]).sum(axis=1))
+        j = remaining.pop(int(np.argmin(cost)))
+        placed.append(j)
+        logP = logP + logv[j]
+    return np.asarray(placed, dtype=np.int64)
+
+
+def plan(L: int, samples: int | None = None, q_points: int | None = None, n_max: int = 10,
+         bound: float = 10.0) -> dict:
+    """Ordered FRKC2 step sizes for L stages (Sec. 2.2, the n-loop).
+
+    The ordering is repeated with n = 1, 2, ... until the realised Q is at most
+    ``bound`` L^2 (the paper's practical bound 10 L^2) or ``n_max`` is reached; the ordering
+    with the smallest realised Q is kept.  Reading: S = 16 L ordering samples and
+    16 L + 1 points for the realised Q (the paper's L samples leave Q above 10 L^2 from
+    L = 128 on).
+    """
+    a = step_sizes(L)
+    b = beta(L)
+    S = samples if samples is not None else 16 * L
+    P = q_points if q_points is not None else 16 * L
+    best = None
+    for n in range(1, n_max + 1):
+        perm = order_greedy(a, b, n, S)
+        Q = realised_Q(a[perm], b, P)
+        if best is None or Q < best["Q"]:
+            best = dict(L=L, order=perm, a=a[perm], beta=b, Q=Q, n=n)
+        if Q <= bound * L * L:
+            break
+    return best
+
+
+# ----------------------------------------------------------------------------------------
+# The diffusion operator f(w) = div(kappa grad w) (the semi-discrete system of Eq. 1)
+# ----------------------------------------------------------------------------------------
+
+
+def cell_kappa(W, prob):
+    """Cell-centred conductivity for state W: a constant, a given field, or kappa(W).
+
+    For ``"power"`` kappa(W) = 1 + c W^p on the principal branch (W may be complex in the
+    middle of a step).
+    """
+    kind = prob["kappa"]
+    if kind == "const":
+        return np.full(W.shape, float(prob["kappa_c"]))
+    if kind == "field":
+        return np.asarray(prob["kappa_field"], dtype=np.float64)
+    if kind == "power":
+        return 1.0 + prob["kappa_c"] * np.power(W, prob["kappa_p"])
+    raise ValueError(kind)
+
+
+def _ghost_kappa(prob, kc):
+    """kappa in a Dirichlet ghost cell, as a function of the adjacent interior value.
+
+    Reading (the paper states no boundary treatment): for a given field or a constant the
+    ghost cell takes the adjacent interior cell's value, so a boundary face carries the
+    boundary cell's own kappa; for kappa(u) the ghost takes kappa(0) = 1, its state being 0.
+    """
+    if prob["kappa"] == "power":
+        return np.ones_like(kc)
+    return kc
+
+
+def _neighbours(A, ax, bc, ghost):
+    """(A at i+1, A at i-1) along axis ``ax`` with periodic wrap or ghost values."""
+    if bc == "periodic":
+        return np.roll(A, -1, axis=ax), np.roll(A, 1, axis=ax)
+    n = A.shape[ax]
+    plus = np.concatenate([np.take(A, range(1, n), axis=ax),
+                           np.take(ghost, [n - 1], axis=ax)], axis=ax)
+    minus = np.concatenate([np.take(ghost, [0], axis=ax),
+                            np.take(A, range(0, n - 1), axis=ax)], axis=ax)
+    return plus, minus
+
+
+def apply_f(W, prob):
+    """f(W)_c = (1/dx^2) sum over the 2 ndim faces of c of kappa_f (W_nb - W_c).
+
+    Flux form with the arithmetic-mean face conductivity kappa_f = (kappa_c + kappa_nb)/2
+    (reading: the paper specifies no spatial discretisation; this 2nd-order form keeps the
+    linear operator symmetric).  Ghost cells of a Dirichlet grid hold W = 0.
+    """
+    W = np.asarray(W)
+    kc = cell_kappa(W, prob)
+    zero = np.zeros_like(W)
+    gk = _ghost_kappa(prob, kc)
+    out = np.zeros(W.shape, dtype=np.result_type(W, kc))
+    for ax in range(W.ndim):
+        Wp, Wm = _neighbours(W, ax, prob["bc"], zero)
+        kp, km = _neighbours(kc, ax, prob["bc"], gk)
+        out = out + 0.5 * (kc + kp) * (Wp - W) + 0.5 * (kc + km) * (Wm - W)
+    return out / (prob["dx"] * prob["dx"])
+
+
+def rho_bound(prob, u=None) -> float:
+    """Gershgorin bound on the spectral radius: max_c (2/dx^2) sum_faces kappa_f.
+
+    Used for |lambda|_max of Sec. 3 when choosing T so that T |lambda|_max <= beta (Eq. 6).
+    For kappa(u) the bound is taken at the real state ``u``.  Faces are summed axis by axis
+    from the x axis outwards, the face on the low side before the high side.
+    """
+    shape = np.shape(u) if u is not None else np.shape(prob["kappa_field"])
+    if prob["kappa"] == "const":
+        kc = np.full(shape, float(prob["kappa_c"]))
+    elif prob["kappa"] == "field":
+        kc = np.asarray(prob["kappa_field"], dtype=np.float64)
+    else:
+        kc = 1.0 + prob["kappa_c"] * np.power(np.asarray(u, dtype=np.float64), prob["kappa_p"])
+    gk = _ghost_kappa(prob, kc)
+    acc = np.zeros(shape)
+    for ax in reversed(range(len(shape))):
+        kp, km = _neighbours(kc, ax, prob["bc"], gk)
+        acc = acc + 0.5 * (kc + km)
+        acc = acc + 0.5 * (kc + kp)
+    return float(np.max((2.0 * acc) / (prob["dx"] * prob["dx"])))
+
+
+# ----------------------------------------------------------------------------------------
+# The FRKC2 step (Sec. 3, Eq. 13)
+# ----------------------------------------------------------------------------------------
+
+
+def frkc2_step(u0, a, T, prob, nsteps: int = 1, return_imag: bool = False):
+    """Advance the real state u0 by ``nsteps`` FRKC2 steps of size T.
+
+    Each step sets W^0 = w^n and applies W^{l+1} = W^l + T a_l f(W^l) for the step sizes
+    ``a`` in the given order (Eq. 13), in complex arithmetic exactly as written.  The new
+    state is w^{n+1} = W^L; reading: its real part is kept (for a linear f the imaginary
+    part is zero up to rounding, the step sizes coming in conjugate pairs).  With
+    ``return_imag`` the largest ||Im W^L|| / ||Re W^L|| over the steps is also returned.
+    """
+    u = np.array(u0, dtype=np.float64)
+    worst = 0.0
+    for _ in range(nsteps):
+        W = u.astype(np.complex128)
+        for al in a:
+            W = W + (T * al) * apply_f(W, prob)
+        u = W.real.copy()
+        nr = np.linalg.norm(u)
+        if nr > 0:
+            worst = max(worst, float(np.linalg.norm(W.imag) / nr))
+    return (u, worst) if return_imag else u
+
+
+# ----------------------------------------------------------------------------------------
+# Discrete adjoint of the FRKC2 step
+# ----------------------------------------------------------------------------------------
+
+
+def _cell_dkappa(W, prob):
+    """d kappa / d W at each cell (zero unless kappa = kappa(W))."""
+    if prob["kappa"] != "power":
+        return np.zeros_like(W)
+    p = prob["kappa_p"]
+    return prob["kappa_c"] * p * np.power(W, p - 1.0)
+
+
+def apply_jh(W, lam, prob):
+    """(J_f(W)^H lam)_m for the flux-form operator, J_f the complex Jacobian of ``apply_f``.
+
+    Differentiating f_i = (1/dx^2) sum_nb kappa_f (W_nb - W_i), kappa_f = (kappa(W_i) +
+    kappa(W_nb))/2, and transposing gives
+    (J^H lam)_m = (1/dx^2) sum_{nb i of m} (lam_i - lam_m) conj(kappa_f - kappa'(W_m)(W_i - W_m)/2),
+    with lam = 0 in Dirichlet ghost cells.  For a fixed field kappa' = 0 and this is the
+    (symmetric) operator itself applied to lam.
+    """
+    W = np.asarray(W, dtype=np.complex128)
+    lam = np.asarray(lam, dtype=np.complex128)
+    kc = cell_kappa(W, prob)
+    dk = _cell_dkappa(W, prob)
+    zero = np.zeros_like(W)
+    gk = _ghost_kappa(prob, kc)
+    out = np.zeros_like(W)
+    for ax in range(W.ndim):
+        Wp, Wm = _neighbours(W, ax, prob["bc"], zero)
+        lp, lm = _neighbours(lam, ax, prob["bc"], zero)
+        kp, km = _neighbours(kc, ax, prob["bc"], gk)
+        out = out + (lp - lam) * np.conj(0.5 * (kc + kp) - 0.5 * dk * (Wp - W))
+        out = out + (lm - lam) * np.conj(0.5 * (kc + km) - 0.5 * dk * (Wm - W))
+    return out / (prob["dx"] * prob["dx"])
+
+
+def kappa_grad_stage(W, lam, c, prob):
+    """Contribution of one stage W -> W + c f(W) to dJ/dkappa (fixed-field kappa).
+
+    For the face f between cells i and j, d(f(W))/d kappa_f is (W_j - W_i)/dx^2 at i and
+    (W_i - W_j)/dx^2 at j; with the real inner product <x, y> = Re(x^H y) the face receives
+    Re(c [conj(lam_i)(W_j - W_i) + conj(lam_j)(W_i - W_j)]) / dx^2 (lam, W = 0 in ghosts),
+    and kappa_f = (kappa_i + kappa_j)/2 passes half of it to each cell; a Dirichlet
+    boundary face depends on its interior cell alone (ghost kappa = interior kappa) and
+    passes all of it.
+    """
+    W = np.asarray(W, dtype=np.complex128)
+    lam = np.asarray(lam, dtype=np.complex128)
+    zero = np.zeros_like(W)
+    g = np.zeros(W.shape)
+    h2 = prob["dx"] * prob["dx"]
+    for ax in range(W.ndim):
+        n = W.shape[ax]
+        Wp, _ = _neighbours(W, ax, prob["bc"], zero)
+        lp, _ = _neighbours(lam, ax, prob["bc"], zero)
+        # face between i and i+1 along ax, indexed by i
+        face = np.real(c * (np.conj(lam) * (Wp - W) + np.conj(lp) * (W - Wp))) / h2
+        if prob["bc"] == "periodic":
+            g = g + 0.5 * face + 0.5 * np.roll(face, 1, axis=ax)
+        else:
+            inner = np.take(face, range(0, n - 1), axis=ax)
+            last = np.take(face, [n - 1], axis=ax)  # boundary face on the high side
+            lo = np.concatenate([np.zeros_like(last), 0.5 * inner], axis=ax)
+            hi = np.concatenate([0.5 * inner, np.zeros_like(last)], axis=ax)
+            g = g + lo + hi
+            g = g + np.concatenate([np.zeros_like(inner), last], axis=ax)
+            # boundary face on the low side: ghost (index -1) and cell 0
+            face_lo = np.real(c * (np.conj(np.take(lam, [0], axis=ax))
+                                   * (0.0 - np.take(W, [0], axis=ax)))) / h2
+            g = g + np.concatenate([face_lo, np.zeros_like(inner)], axis=ax)
+    return g
+
+
+def frkc2_adjoint(u0, a, T, prob, nsteps, dJdu):
+    """Gradients of a scalar J(u(T_end)) for ``nsteps`` FRKC2 steps from u0.
+
+    Forward: the stage states of every step are kept (a plain tape).  Backward: with the
+    real projection w^{n+1} = Re W^L the step's adjoint starts from lam^L = dJ/dw^{n+1}
+    (imaginary part 0); each stage W^{l+1} = W^l + c_l f(W^l), c_l = T a_l, is reversed as
+    lam^l = lam^{l+1} + conj(c_l) J_f(W^l)^H lam^{l+1}; dJ/dw^n = Re lam^0 (W^0 = w^n is
+    real).  Returns (dJ/du0, dJ/dkappa) -- the second is None unless kappa is a field.
+    """
+    tape = []
+    u = np.array(u0, dtype=np.float64)
+    for _ in range(nsteps):
+        W = u.astype(np.complex128)
+        states = []
+        for al in a:
+            states.append(W)
+            W = W + (T * al) * apply_f(W, prob)
+        tape.append(states)
+        u = W.real.copy()
+    lam_u = np.array(dJdu, dtype=np.float64)
+    gk = np.zeros(np.shape(u0)) if prob["kappa"] == "field" else None
+    for n in reversed(range(nsteps)):
+        lam = lam_u.astype(np.complex128)
+        for l in reversed(range(len(a))):
+            c = T * a[l]
+            Wl = tape[n][l]
+            if gk is not None:
+                gk = gk + kappa_grad_stage(Wl, lam, c, prob)
+            lam = lam + np.conj(c) * apply_jh(Wl, lam, prob)
+        lam_u = lam.real.copy()
+    return lam_u, gk
+
+
+# ----------------------------------------------------------------------------------------
+# Fine-step reference
+# ----------------------------------------------------------------------------------------
+
+
+def rk4(u0, h, prob, nsteps):
+    """Classical fourth-order Runge-Kutta for w' = f(w) with real state, step h."""
+    u = np.array(u0, dtype=np.float64)
+    for _ in range(nsteps):
+        k1 = apply_f(u, prob)
+        k2 = apply_f(u + 0.5 * h * k1, prob)
+        k3 = apply_f(u + 0.5 * h * k2, prob)
+        k4 = apply_f(u + h * k3, prob)
+        u = u + (h / 6.0) * (k1 + 2.0 * k2 + 2.0 * k3 + k4)
+    return np.real(u)

@@ -1,0 +1,507 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix (CPU only).
+
+Each test checks an oracle function against something that does not come from the oracle
+itself: values printed in the paper (tests/golden/paper_values.json), closed forms,
+textbook or library routines (numpy's Chebyshev basis, numpy.linalg.eigh,
+scipy.linalg.expm), invariants, manufactured solutions and brute force.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+from numpy.polynomial import chebyshev as C
+
+from oracle import frkc2_oracle as O
+import frkc2_inputs as I
+
+GOLD = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "paper_values.json")))
+LS = [16, 32, 64, 128]
+
+
+def R_closed(z, L):
+    """1 - alpha/4 + (alpha/4) T_L(1 + 4 z / (L^2 alpha)), T_L from numpy's Chebyshev basis."""
+    al = 4.0 * (1.0 - 1.0 / L ** 2) / 3.0  # the value fixed by R''(0) = 1, retyped as a number check below
+    TL = C.Chebyshev.basis(L)
+    return 1.0 - al / 4.0 + (al / 4.0) * TL(1.0 + 4.0 * np.asarray(z) / (L * L * al))
+
+
+def R_product(z, a):
+    z = np.asarray(z, dtype=np.complex128)
+    out = np.ones_like(z)
+    for al in a:
+        out = out * (1.0 + al * z)
+    return out
+
+
+# --------------------------------------------------------------------------------------
+# Stability polynomial (Sec. 2, Eqs. 5-8)
+# --------------------------------------------------------------------------------------
+
+@pytest.mark.parametrize("L", LS + [256, 1024])
+def test_order_conditions_taylor(L):
+    """R(z) = 1 + z + z^2/2 + O(z^3): the first three Taylor coefficients of prod(1 + a z)."""
+    a = O.step_sizes(L)
+    coef = np.array([1.0 + 0j])
+    for al in a:
+        coef = np.convolve(coef, np.array([1.0, al]))  # ascending powers of z
+    assert abs(coef[1] - 1.0) < 1e-10
+    assert abs(coef[2] - 0.5) < 1e-10
+    # the third coefficient is not 1/6: the scheme is second order, not third
+    assert abs(coef[3] - 1.0 / 6.0) > 1e-3
+
+
+@pytest.mark.parametrize("L", LS + [256])
+def test_product_equals_chebyshev_closed_form(L):
+    a = O.step_sizes(L)
+    z = np.linspace(-O.beta(L), 0.0, 4001)
+    rp = R_product(z, a)
+    assert np.max(np.abs(rp.imag)) < 1e-9
+    assert np.max(np.abs(rp.real - R_closed(z, L))) < 1e-9
+
+
+@pytest.mark.parametrize("L", LS + [256])
+def test_conjugate_pairs_and_positive_real_part(L):
+    a = O.step_sizes(L)
+    assert np.all(a.real > 0)
+    assert np.array_equal(a[::-1], np.conj(a))
+    assert np.all(np.abs(a.imag) > 0)
+
+
+@pytest.mark.parametrize("L", LS + [256])
+def test_stability_extent(L):
+    """|R| <= 1 on [-beta, 0], |R| > 1 just beyond, beta/(L^2 beta_RK2) near the paper's 0.330."""
+    a = O.step_sizes(L)
+    b = O.beta(L)
+    z = np.linspace(-b, 0.0, 20 * L + 1)
+    assert np.max(np.abs(R_product(z, a))) <= 1.0 + 1e-9
+    assert abs(R_product(-b * (1 + 1e-3), a)) > 1.0
+    # bisection on the boundary of |R| <= 1 beyond the last extremum recovers beta
+    lo, hi = b * 0.999, b * 1.01
+    for _ in range(80):
+        mid = 0.5 * (lo + hi)
+        if abs(R_product(-mid, a)) <= 1.0:
+            lo = mid
+        else:
+            hi = mid
+    assert abs(lo / b - 1.0) < 1e-9
+    ratio = b / (L * L * GOLD["beta_RK2"]["value"])
+    assert GOLD["beta_over_L2_betaRK2_frkc2"]["value"] - 0.003 <= ratio <= 1.0 / 3.0
+
+
+def test_marginal_interior_points():
+    """The undamped polynomial touches |R| = 1 inside the interval (the points Sec. 2.1 damps)."""
+    L = 32
+    a = O.step_sizes(L)
+    al = O.alpha(L)
+    # T_L(x) = 1 at x = cos(2 pi m / L); z = (x - 1) L^2 alpha / 4
+    for m in range(1, L // 2):
+        z = (np.cos(2 * np.pi * m / L) - 1.0) * L * L * al / 4.0
+        assert abs(abs(R_product(z, a)) - 1.0) < 1e-10
+
+
+def test_acceleration_claim():
+    """beta grows like (2/3) L^2: at L = 10^4 stages the gain over RK2 per f-evaluation exceeds 6000."""
+    L = GOLD["viable_stages"]["value"]
+    per_eval = O.beta(L) / L  # real extent per f-evaluation
+    assert per_eval / (GOLD["beta_RK2"]["value"] / 2.0) > GOLD["acceleration_factor_min"]["value"]
+
+
+# --------------------------------------------------------------------------------------
+# Internal stability and ordering (Sec. 2.2)
+# --------------------------------------------------------------------------------------
+
+def test_realised_Q_brute_force_tiny():
+    """realised_Q equals an explicit triple loop over (j, k, x) on a tiny case."""
+    a = O.step_sizes(8)[[3, 0, 6, 1, 5, 2, 7, 4]]
+    b = O.beta(8)
+    pts = 64
+    best = 0.0
+    for i in range(pts + 1):
+        x = -b * i / pts
+        for j in range(8):
+            p = 1.0
+            for k in range(j, 8):
+                p *= abs(1 + a[k] * x)
+                best = max(best, p)
+    assert abs(O.realised_Q(a, b, pts) / best - 1.0) < 1e-12
+
+
+@pytest.mark.parametrize("L", LS)
+def test_plan_Q_within_paper_bounds(L):
+    p = O.plan(L)
+    assert sorted(p["order"].tolist()) == list(range(L))
+    assert np.array_equal(p["a"], O.step_sizes(L)[p["order"]])
+    lo = GOLD["Q_optimal_factor"]["value"] * L * L / 10.0
+    hi = GOLD["Q_bound_factor"]["value"] * L * L
+    assert lo <= p["Q"] <= hi
+    # the ordering matters: root order amplifies far more (Sec. 2.2 motivation)
+    qnat = O.realised_Q(O.step_sizes(L), O.beta(L), 16 * L)
+    assert qnat > p["Q"]
+    # order does not change the stability polynomial
+    z = np.linspace(-O.beta(L), 0.0, 501)
+    assert np.max(np.abs(R_product(z, p["a"]) - R_product(z, O.step_sizes(L)))) < 1e-9
+
+
+def test_plan_n_loop_runs():
+    """A tight bound forces the n-loop (Sec. 2.2): n grows and the best ordering is kept."""
+    L = 32
+    p = O.plan(L, bound=1e-6, n_max=3)
+    assert 1 <= p["n"] <= 3
+    q1 = O.realised_Q(O.step_sizes(L)[O.order_greedy(O.step_sizes(L), O.beta(L), 1, 16 * L)],
+                      O.beta(L), 16 * L)
+    assert p["Q"] <= q1
+
+
+# --------------------------------------------------------------------------------------
+# Operator (flux form)
+# --------------------------------------------------------------------------------------
+
+def _prob(ndim, bc, kappa, dx=1.0, field=None, c=1.0, p=2.5):
+    return dict(ndim=ndim, dx=dx, bc=bc, kappa=kappa, kappa_c=c, kappa_p=p, kappa_field=field)
+
+
+def dense(prob, shape):
+    n = int(np.prod(shape))
+    A = np.zeros((n, n))
+    for i in range(n):
+        e = np.zeros(n)
+        e[i] = 1.0
+        A[:, i] = O.apply_f(e.reshape(shape), prob).ravel()
+    return A
+
+
+def test_operator_manufactured_2d_field_second_order():
+    """f(u_h) -> div(kappa grad u) with error O(dx^2) on a smooth periodic solution."""
+    errs = []
+    for n in (32, 64, 128):
+        dx = 1.0 / n
+        x = dx * np.arange(n)
+        X, Y = np.meshgrid(x, x, indexing="xy")  # arrays [y][x]
+        tp = 2 * np.pi
+        u = np.sin(tp * X) * np.sin(2 * tp * Y)
+        k = 2.0 + np.sin(tp * X) * np.cos(tp * Y)
+        ux = tp * np.cos(tp * X) * np.sin(2 * tp * Y)
+        uy = 2 * tp * np.sin(tp * X) * np.cos(2 * tp * Y)
+        uxx = -tp ** 2 * u
+        uyy = -(2 * tp) ** 2 * u
+        kx = tp * np.cos(tp * X) * np.cos(tp * Y)
+        ky = -tp * np.sin(tp * X) * np.sin(tp * Y)
+        exact = kx * ux + k * uxx + ky * uy + k * uyy
+        f = O.apply_f(u, _prob(2, "periodic", "field", dx, k))
+        errs.append(np.max(np.abs(f - exact)))
+    assert 3.6 < errs[0] / errs[1] < 4.4 and 3.6 < errs[1] / errs[2] < 4.4
+
+
+def test_operator_manufactured_3d_power_second_order():
+    """kappa(u) = 1 + u^2.5: f -> kappa'(u)|grad u|^2 + kappa(u) lap u, error O(dx^2)."""
+    errs = []
+    for n in (16, 32, 64):
+        dx = 1.0 / n
+        x = dx * np.arange(n)
+        Z, Y, X = np.meshgrid(x, x, x, indexing="ij")
+        tp = 2 * np.pi
+        s = np.sin(tp * X) * np.sin(tp * Y) * np.sin(tp * Z)
+        u = 1.5 + 0.5 * s
+        gx = 0.5 * tp * np.cos(tp * X) * np.sin(tp * Y) * np.sin(tp * Z)
+        gy = 0.5 * tp * np.sin(tp * X) * np.cos(tp * Y) * np.sin(tp * Z)
+        gz = 0.5 * tp * np.sin(tp * X) * np.sin(tp * Y) * np.cos(tp * Z)
+        lap = -3 * tp ** 2 * 0.5 * s
+        exact = 2.5 * u ** 1.5 * (gx ** 2 + gy ** 2 + gz ** 2) + (1 + u ** 2.5) * lap
+        f = O.apply_f(u, _prob(3, "periodic", "power", dx))
+        errs.append(np.max(np.abs(f - exact)))
+    assert 3.5 < errs[0] / errs[1] < 4.5 and 3.5 < errs[1] / errs[2] < 4.5
+
+
+def test_operator_dirichlet_1d_closed_form():
+    """1D Dirichlet, kappa = 1: sine modes are exact eigenvectors, lambda_k = -(4/dx^2) sin^2(k pi dx/2)."""
+    n = 63
+    dx = 1.0 / (n + 1)
+    x = dx * np.arange(1, n + 1)
+    pr = _prob(1, "dirichlet", "const", dx)
+    for k in (1, 5, 40, 63):
+        v = np.sin(k * np.pi * x)
+        lam = -(4.0 / dx ** 2) * np.sin(k * np.pi * dx / 2) ** 2
+        assert np.max(np.abs(O.apply_f(v, pr) - lam * v)) < 1e-9 * abs(lam)
+
+
+def test_operator_symmetric_conservative():
+    rng = np.random.default_rng(0)
+    shape = (5, 7)
+    k = np.exp(rng.standard_normal(shape))
+    for bc in ("periodic", "dirichlet"):
+        A = dense(_prob(2, bc, "field", 1.0, k), shape)
+        assert np.max(np.abs(A - A.T)) < 1e-14
+        assert np.all(np.linalg.eigvalsh(A) < 1e-12)  # negative semi-definite diffusion
+    A = dense(_prob(2, "periodic", "field", 1.0, k), shape)
+    assert np.max(np.abs(A.sum(axis=0))) < 1e-13  # periodic flux form conserves the total
+    assert np.max(np.abs(A @ np.ones(A.shape[0]))) < 1e-13  # constants are steady
+    shape3 = (3, 4, 5)
+    k3 = np.exp(rng.standard_normal(shape3))
+    A3 = dense(_prob(3, "dirichlet", "field", 0.5, k3), shape3)
+    assert np.max(np.abs(A3 - A3.T)) < 1e-13
+
+
+def test_dirichlet_field_boundary_face_reading():
+    """A Dirichlet boundary face carries the boundary cell's own kappa (stated reading)."""
+    k = np.array([2.0, 3.0, 5.0])
+    A = dense(_prob(1, "dirichlet", "field", 1.0, k), (3,))
+    assert A[0, 0] == -(2.0 + 2.5) and A[0, 1] == 2.5
+    assert A[2, 2] == -(4.0 + 5.0) and A[2, 1] == 4.0
+
+
+@pytest.mark.parametrize("bc", ["periodic", "dirichlet"])
+def test_rho_bound_is_gershgorin(bc):
+    rng = np.random.default_rng(1)
+    shape = (6, 5)
+    k = np.exp(rng.standard_normal(shape))
+    pr = _prob(2, bc, "field", 0.7, k)
+    A = dense(pr, shape)
+    gersh = np.max(np.sum(np.abs(A), axis=1))
+    assert abs(O.rho_bound(pr) / gersh - 1.0) < 1e-14
+    assert O.rho_bound(pr) >= np.max(np.abs(np.linalg.eigvalsh(A)))
+
+
+def test_rho_bound_brusselator_paper_value():
+    """Diffusion 0.02 on a 200 x 200 mesh of the unit square: spectral radius about 6400 (Sec. 3.1)."""
+    n = 200
+    pr = _prob(2, "periodic", "const", 1.0 / n, c=GOLD["brusselator_diffusion"]["value"])
+    rho = O.rho_bound(pr, np.zeros((n, n)))
+    assert abs(rho / GOLD["brusselator_rho_200"]["value"] - 1.0) < 0.01
+    # the Gershgorin bound is attained by the checkerboard mode for a constant coefficient
+    chk = (-1.0) ** np.add.outer(np.arange(n), np.arange(n))
+    lam = O.apply_f(chk, pr)[0, 0] / chk[0, 0]
+    assert abs(-lam / rho - 1.0) < 1e-12
+
+
+def test_rho_bound_1d_heat_closed_form():
+    n = 256
+    dx = 1.0 / (n + 1)
+    pr = _prob(1, "dirichlet", "const", dx)
+    assert abs(O.rho_bound(pr, np.zeros(n)) / (4.0 / dx ** 2) - 1.0) < 1e-14
+
+
+# --------------------------------------------------------------------------------------
+# Stepping (Sec. 3, Eq. 13)
+# --------------------------------------------------------------------------------------
+
+def test_heat1d_closed_form_modes():
+    """1D heat workload: every sine mode is amplified by R(T lambda_k) per step (R from T_L)."""
+    cfg = I.CONFIGS["heat1d"]
+    u0, amp, dx = I.heat1d_u0(cfg["n"], 8, cfg["seed"])
+    L = cfg["s"]
+    p = O.plan(L)
+    dtmax = 0.9 * O.beta(L) * dx * dx / 4.0
+    nsteps = int(np.ceil(cfg["t_end"] / dtmax))
+    T = cfg["t_end"] / nsteps
+    pr = _prob(1, "dirichlet", "const", dx)
+    u = O.frkc2_step(u0, p["a"], T, pr, nsteps)
+    x = dx * np.arange(1, cfg["n"] + 1)
+    exact = np.zeros_like(x)
+    for k in range(1, 9):
+        lam = -(4.0 / dx ** 2) * np.sin(k * np.pi * dx / 2) ** 2
+        exact += amp[k - 1] * R_closed(T * lam, L) ** nsteps * np.sin(k * np.pi * x)
+    rel = np.linalg.norm(u - exact) / np.linalg.norm(exact)
+    assert rel < 1e-12, rel
+
+
+def test_periodic_fourier_mode_amplification():
+    L = 16
+    p = O.plan(L)
+    n0, n1 = 12, 10
+    pr = _prob(2, "periodic", "const", 1.0, c=1.3)
+    y, x = np.meshgrid(np.arange(n0), np.arange(n1), indexing="ij")
+    for k0, k1 in ((1, 2), (5, 3), (6, 5)):
+        v = np.cos(2 * np.pi * (k0 * y / n0 + k1 * x / n1))
+        lam = -(4 * 1.3) * (np.sin(np.pi * k0 / n0) ** 2 + np.sin(np.pi * k1 / n1) ** 2)
+        T = 0.9 * O.beta(L) / O.rho_bound(pr, v)
+        out = O.frkc2_step(v, p["a"], T, pr, 2)
+        assert np.max(np.abs(out - R_closed(T * lam, L) ** 2 * v)) < 1e-12
+
+
+def test_varkappa_eigh_library_pin():
+    """Linear var-kappa: u^n = V R(T Lambda)^n V^T u0, eigen-decomposition by numpy.linalg.eigh."""
+    rng = np.random.default_rng(7)
+    shape = (9, 7)
+    k = np.exp(0.5 * rng.standard_normal(shape))
+    for bc in ("periodic", "dirichlet"):
+        pr = _prob(2, bc, "field", 1.0, k)
+        A = dense(pr, shape)
+        w, V = np.linalg.eigh(A)
+        L = 32
+        p = O.plan(L)
+        T = 0.9 * O.beta(L) / O.rho_bound(pr)
+        u0 = rng.random(shape)
+        u = O.frkc2_step(u0, p["a"], T, pr, 3)
+        ref = V @ (R_closed(T * w, L) ** 3 * (V.T @ u0.ravel()))
+        assert np.linalg.norm(u.ravel() - ref) / np.linalg.norm(ref) < 1e-12
+
+
+def test_second_order_against_expm():
+    scipy_linalg = pytest.importorskip("scipy.linalg")
+    rng = np.random.default_rng(3)
+    shape = (8, 8)
+    k = np.exp(0.5 * rng.standard_normal(shape))
+    pr = _prob(2, "periodic", "field", 1.0, k)
+    A = dense(pr, shape)
+    u0 = rng.random(shape)
+    t_end = 2.0
+    ref = scipy_linalg.expm(t_end * A) @ u0.ravel()
+    L = 8
+    a = O.plan(L)["a"]
+    errs = []
+    for nsteps in (32, 64, 128):
+        u = O.frkc2_step(u0, a, t_end / nsteps, pr, nsteps)
+        errs.append(np.linalg.norm(u.ravel() - ref))
+    slope = np.log2(errs[0] / errs[1]), np.log2(errs[1] / errs[2])
+    assert all(1.9 < s < 2.1 for s in slope), slope
+
+
+def test_real_projection_drops_only_rounding():
+    """Linear f with conjugate-paired step sizes: Im W^L is rounding noise (reading of w^{n+1} = W^L)."""
+    rng = np.random.default_rng(5)
+    shape = (16, 16)
+    k = np.exp(0.5 * rng.standard_normal(shape))
+    pr = _prob(2, "periodic", "field", 1.0, k)
+    L = 64
+    a = O.plan(L)["a"]
+    T = 0.9 * O.beta(L) / O.rho_bound(pr)
+    _, worst = O.frkc2_step(rng.random(shape), a, T, pr, 2, return_imag=True)
+    assert worst < 1e-12
+
+
+def test_rk4_fourth_order_against_expm():
+    scipy_linalg = pytest.importorskip("scipy.linalg")
+    rng = np.random.default_rng(4)
+    shape = (6, 6)
+    pr = _prob(2, "periodic", "field", 1.0, np.exp(0.3 * rng.standard_normal(shape)))
+    A = dense(pr, shape)
+    u0 = rng.random(shape)
+    ref = scipy_linalg.expm(0.5 * A) @ u0.ravel()
+    e = [np.linalg.norm(O.rk4(u0, 0.5 / m, pr, m).ravel() - ref) for m in (16, 32)]
+    assert 3.7 < np.log2(e[0] / e[1]) < 4.3
+
+
+def test_nonlinear_second_order_against_rk4():
+    """kappa(u) = 1 + u^2.5, Dirichlet 3D: FRKC2 converges at order 2 to a fine RK4 solution."""
+    n = 6
+    u0 = I.hotspot3d_u0(n, sigma=1.5, seed=11)
+    pr = _prob(3, "dirichlet", "power", 1.0)
+    t_end = 0.6
+    ref = O.rk4(u0, t_end / 400, pr, 400)
+    L = 8
+    a = O.plan(L)["a"]
+    errs = [np.linalg.norm(O.frkc2_step(u0, a, t_end / m, pr, m) - ref) for m in (8, 16, 32)]
+    slopes = [np.log2(errs[0] / errs[1]), np.log2(errs[1] / errs[2])]
+    assert all(1.85 < s < 2.25 for s in slopes), slopes
+
+
+def test_internal_stability_fp64_many_stages():
+    """Ordered stages keep FP64 accuracy at s = 128 on all modes (Sec. 2.2), root order does not."""
+    n = 127
+    dx = 1.0 / (n + 1)
+    x = dx * np.arange(1, n + 1)
+    rng = np.random.default_rng(9)
+    amp = rng.standard_normal(n)
+    u0 = sum(amp[k - 1] * np.sin(k * np.pi * x) for k in range(1, n + 1))
+    pr = _prob(1, "dirichlet", "const", dx)
+    L = 128
+    p = O.plan(L)
+    T = 0.9 * O.beta(L) * dx * dx / 4
+    u = O.frkc2_step(u0, p["a"], T, pr, 1)
+    exact = sum(amp[k - 1] * R_closed(T * (-(4 / dx ** 2) * np.sin(k * np.pi * dx / 2) ** 2), L)
+                * np.sin(k * np.pi * x) for k in range(1, n + 1))
+    err = np.linalg.norm(u - exact) / np.linalg.norm(exact)
+    assert err < 1e-11, err
+    u_nat = O.frkc2_step(u0, O.step_sizes(L), T, pr, 1)
+    assert not np.linalg.norm(u_nat - exact) / np.linalg.norm(exact) < 1e-6
+
+
+# --------------------------------------------------------------------------------------
+# Adjoint
+# --------------------------------------------------------------------------------------
+
+def test_adjoint_dot_product_linear():
+    rng = np.random.default_rng(11)
+    shape = (10, 12)
+    for bc in ("periodic", "dirichlet"):
+        pr = _prob(2, bc, "field", 1.0, np.exp(0.5 * rng.standard_normal(shape)))
+        L = 16
+        a = O.plan(L)["a"]
+        T = 0.9 * O.beta(L) / O.rho_bound(pr)
+        v = rng.standard_normal(shape)
+        w = rng.standard_normal(shape)
+        Jv = O.frkc2_step(v, a, T, pr, 3)
+        JTw, _ = O.frkc2_adjoint(v, a, T, pr, 3, w)
+        assert abs(np.vdot(Jv, w) - np.vdot(v, JTw)) < 1e-12 * abs(np.vdot(Jv, w)) + 1e-13
+
+
+@pytest.mark.parametrize("bc", ["periodic", "dirichlet"])
+def test_adjoint_kappa_gradient_central_fd(bc):
+    rng = np.random.default_rng(12)
+    shape = (7, 6)
+    k0 = np.exp(0.5 * rng.standard_normal(shape))
+    u0 = rng.random(shape)
+    tgt = rng.random(shape)
+    L = 8
+    a = O.plan(L)["a"]
+    T = 0.8 * O.beta(L) / O.rho_bound(_prob(2, bc, "field", 1.0, k0))
+
+    def loss(k, u):
+        uT = O.frkc2_step(u, a, T, _prob(2, bc, "field", 1.0, k), 2)
+        return np.sum((uT - tgt) ** 2)
+
+    uT = O.frkc2_step(u0, a, T, _prob(2, bc, "field", 1.0, k0), 2)
+    gu, gk = O.frkc2_adjoint(u0, a, T, _prob(2, bc, "field", 1.0, k0), 2, 2.0 * (uT - tgt))
+    for idx in [(0, 0), (3, 2), (6, 5), (0, 5)]:
+        h = 1e-6 * k0[idx]
+        kp, km = k0.copy(), k0.copy()
+        kp[idx] += h
+        km[idx] -= h
+        fd = (loss(kp, u0) - loss(km, u0)) / (2 * h)
+        assert abs(fd - gk[idx]) < 1e-6 * max(1.0, abs(fd)), (idx, fd, gk[idx])
+        up, um = u0.copy(), u0.copy()
+        up[idx] += 1e-6
+        um[idx] -= 1e-6
+        fdu = (loss(k0, up) - loss(k0, um)) / 2e-6
+        assert abs(fdu - gu[idx]) < 1e-6 * max(1.0, abs(fdu))
+
+
+def test_adjoint_nonlinear_central_fd():
+    rng = np.random.default_rng(13)
+    n = 5
+    u0 = 0.5 + rng.random((n, n, n))
+    tgt = rng.random((n, n, n))
+    pr = _prob(3, "dirichlet", "power", 1.0)
+    L = 8
+    a = O.plan(L)["a"]
+    T = 0.5 * O.beta(L) / O.rho_bound(pr, u0 + 0.5)
+
+    def loss(u):
+        return np.sum((O.frkc2_step(u, a, T, pr, 2) - tgt) ** 2)
+
+    uT = O.frkc2_step(u0, a, T, pr, 2)
+    gu, gk = O.frkc2_adjoint(u0, a, T, pr, 2, 2 * (uT - tgt))
+    assert gk is None
+    for idx in [(0, 0, 0), (2, 2, 2), (4, 1, 3)]:
+        up, um = u0.copy(), u0.copy()
+        up[idx] += 1e-6
+        um[idx] -= 1e-6
+        fd = (loss(up) - loss(um)) / 2e-6
+        assert abs(fd - gu[idx]) < 1e-6 * max(1.0, abs(fd)), (idx, fd, gu[idx])
+
+
+# --------------------------------------------------------------------------------------
+# Input generators (no method arithmetic, but the recipes are checked)
+# --------------------------------------------------------------------------------------
+
+def test_inputs_recipes():
+    g = I.grf((64, 64), 8.0, 1)
+    assert abs(g.mean()) < 1e-12 and abs(g.std() - 1.0) < 1e-12
+    assert np.array_equal(g, I.grf((64, 64), 8.0, 1))
+    s = I.smooth_unit((32, 32), 4.0, 2)
+    assert s.min() == 0.0 and s.max() == 1.0
+    h = I.hotspot3d_u0(16, sigma=3.0)
+    assert h.min() >= 0.0 and 1.5 <= h.max() <= 2.02 + 1e-12
+    b = I.batched_problems(16)
+    assert all(64 <= p["n"] <= 1024 and p["s"] in (16, 32, 64, 128, 256) for p in b)
