@@ -1,0 +1,203 @@
+/*
+ * frkc2.h -- C ABI of the GB300 FRKC2 stage loop.
+ *
+ * The method is O'Sullivan's second-order Factorized Runge-Kutta-Chebyshev scheme
+ * (arXiv:1702.03818).  Given a semi-discrete system w' = f(w) (Sec. 1, Eq. 1), a state w^n,
+ * a step T and L = s stages with T |lambda|_max <= beta (Eq. 6), one step applies the
+ * ordered complex forward-Euler stages W^{l+1} = W^l + T a_l f(W^l), W^0 = w^n, and returns
+ * w^{n+1} = W^L (Sec. 3, Eq. 13).  Here f is the second-order flux-form diffusion operator
+ * f(w)_c = (1/dx^2) sum_faces kappa_f (w_nb - w_c), kappa_f = (kappa_c + kappa_nb)/2, on a
+ * 1D, 2D (5-point) or 3D (7-point) grid.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - No call allocates device memory.  Device buffers (states, conductivity, workspace)
+ *   belong to the caller; the library only reads and writes them during the calls.
+ * - `stream` is a cudaStream_t passed as void* (NULL = the legacy default stream).  Calls
+ *   that launch work are asynchronous on that stream: a returned FRKC2_OK means the work
+ *   was queued.  Argument and plan errors are reported synchronously and queue nothing.
+ * - Device-detected conditions (a non-finite value in a step's output, a device wait
+ *   that ran out of its iteration limit) are latched in a status word at the start of the
+ *   workspace and read with frkc2_workspace_status().
+ * - Arrays are dense, row-major with x fastest: index (z*ny + y)*nx + x.
+ * - No C++ exception crosses this boundary.  Every call is thread-safe as long as two
+ *   concurrent calls do not share a workspace; a plan is immutable after creation.
+ */
+#ifndef FRKC2_H
+#define FRKC2_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  FRKC2_OK = 0,
+  FRKC2_EINVAL = 1,       /* bad argument (size, pointer, enum value, alignment)            */
+  FRKC2_EUNSTABLE = 2,    /* dt * rho > beta: the step leaves the stability interval (Eq. 6) */
+  FRKC2_EPLAN = 3,        /* strict plan: realised Q above the bound after the n-loop       */
+  FRKC2_ENOMEM = 4,       /* workspace smaller than frkc2_workspace_size() asked for        */
+  FRKC2_ECUDA = 5,        /* a CUDA runtime call failed (launch, copy, device query)        */
+  FRKC2_ETIMEOUT = 6,     /* a bounded device wait expired (latched in the workspace)       */
+  FRKC2_ENONFINITE = 7,   /* a step produced NaN or Inf (latched in the workspace)          */
+  FRKC2_EUNSUPPORTED = 8  /* valid request that this build does not implement               */
+} frkc2_status;
+
+enum { FRKC2_BC_PERIODIC = 0, FRKC2_BC_DIRICHLET = 1 };
+
+/* Conductivity.  CONST: kappa = kappa_c.  FIELD: cell-centred array `kappa`.
+ * POWER: kappa(w) = 1 + kappa_c * w^kappa_p (principal branch for complex stage states). */
+enum { FRKC2_KAPPA_CONST = 0, FRKC2_KAPPA_FIELD = 1, FRKC2_KAPPA_POWER = 2 };
+
+/* FP64: double state and arithmetic.  FP32: float state and arithmetic.
+ * MIXED: double state and double stage update; neighbour differences are formed in double
+ * and the flux arithmetic (kappa_f * difference, face sums) runs in float.               */
+enum { FRKC2_FP64 = 0, FRKC2_FP32 = 1, FRKC2_MIXED = 2 };
+
+/* Plan flags. */
+enum { FRKC2_PLAN_STRICT = 1 };
+
+typedef struct frkc2_plan_s* frkc2_plan_t;
+
+typedef struct {
+  int ndim;          /* 1, 2 or 3                                                            */
+  int bc;            /* FRKC2_BC_*; DIRICHLET means w = 0 in the ghost cells outside the grid */
+  int kappa_kind;    /* FRKC2_KAPPA_*                                                        */
+  int precision;     /* FRKC2_FP64 / FP32 / MIXED                                            */
+  int64_t n[3];      /* n[0] = x extent, n[1] = y, n[2] = z; extents past ndim must be 1      */
+  double dx;         /* grid spacing, the same along every axis                              */
+  double kappa_c;    /* CONST: the value; POWER: the coefficient c                           */
+  double kappa_p;    /* POWER: the exponent p (> 0)                                          */
+  const void* kappa; /* FIELD: device array of n[0]*n[1]*n[2] cell values, double for FP64,
+                        float for FP32 and MIXED; a Dirichlet boundary face takes the value
+                        of its interior cell.  Ignored for the other kinds.                  */
+} frkc2_problem;
+
+typedef struct {
+  int k;             /* stages per pass (temporal blocking), 1..16; 0 = library default       */
+  int tile_x;        /* output tile per CTA along x, y, z; 0 = library default                */
+  int tile_y;
+  int tile_z;
+  int kernel;        /* 0 = library choice, 1 = generic shared-memory tile kernel,
+                        2 = 2D streaming kernel (k = 1 only), 3 = 2D register-blocked kernel  */
+} frkc2_tuning;
+
+/* ---- Plan (host, FP64) --------------------------------------------------------------
+ * Step sizes a_j = 1/(M^2 alpha_M (1 - zeta_j)), L = s = 2M (Sec. 2, Eq. 8), zeta_j the
+ * roots of the second-order polynomial of Eq. 7, read here as
+ * R(z) = 1 - alpha/4 + (alpha/4) T_L(1 + 4z/(L^2 alpha)), alpha = 4(1 - 1/L^2)/3, so that
+ * beta = (2/3)(L^2 - 1).  The stages are ordered greedily to keep the amplification
+ * estimate of Eq. 12 small and the ordering is repeated over n (reduced range
+ * (1 - n 1e-4) beta) until the realised Q of Eqs. 10-11 is at most 10 L^2 (Sec. 2.2).
+ *   s     : number of stages, even, 2..4096.
+ *   nu    : damping of Sec. 2.1; only 0 is implemented (FRKC2_EUNSUPPORTED otherwise).
+ *   flags : FRKC2_PLAN_STRICT makes an unmet Q bound an error (FRKC2_EPLAN); otherwise the
+ *           ordering with the smallest realised Q is kept.
+ *   out   : receives a new plan; release it with frkc2_plan_destroy.
+ * Cost is O(s^3) host work (tens of ms at s = 64, seconds at s = 1024).                   */
+frkc2_status frkc2_plan(int s, double nu, unsigned flags, frkc2_plan_t* out);
+
+/* A plan from caller-given ordered step sizes (a_re[l] + i a_im[l], l = 0..s-1, host arrays
+ * copied).  beta is the closed-form extent for s; Q is the realised amplification of the
+ * given order.  Used to run a stage order chosen elsewhere.                               */
+frkc2_status frkc2_plan_from_steps(int s, const double* a_re, const double* a_im,
+                                   frkc2_plan_t* out);
+
+/* Plan contents.  Any output pointer may be NULL.  a_re, a_im (length s) receive the step
+ * sizes in stage order; order (length s) the root index j of each stage.                   */
+frkc2_status frkc2_plan_info(frkc2_plan_t plan, int* s, double* beta, double* Q, int* n_iter,
+                             double* a_re, double* a_im, int* order);
+
+void frkc2_plan_destroy(frkc2_plan_t plan);
+
+/* ---- Spectral-radius bound --------------------------------------------------------------
+ * rho = max_c (2/dx^2) sum_faces kappa_f (Gershgorin), the |lambda|_max of Sec. 3 that sets
+ * T <= beta / rho.  For POWER the conductivity is evaluated at the real state u (device
+ * array in the problem's state precision); u is ignored for CONST and FIELD.  The result is
+ * written as one double to device memory rho_dev (caller-owned, 8-byte aligned).  Faces
+ * are summed x axis first, low face before high face, so FIELD and CONST results are exact
+ * repeats of that order of FP64 operations.                                               */
+frkc2_status frkc2_rho_bound(const frkc2_problem* prob, const void* u, double* rho_dev,
+                             void* stream);
+
+/* ---- Workspace ----------------------------------------------------------------------------
+ * Bytes of device workspace frkc2_step needs for this problem and tuning (tuning may be
+ * NULL).  The workspace must be 256-byte aligned.  Its first 256 bytes hold the status word. */
+frkc2_status frkc2_workspace_size(const frkc2_problem* prob, const frkc2_tuning* tune,
+                                  size_t* bytes);
+
+/* Clears the status word of a workspace (asynchronous, on stream).                         */
+frkc2_status frkc2_workspace_reset(void* ws, void* stream);
+
+/* Synchronises stream, reads the status word and returns FRKC2_OK, FRKC2_ENONFINITE or
+ * FRKC2_ETIMEOUT (the first condition latched).                                            */
+frkc2_status frkc2_workspace_status(const void* ws, void* stream);
+
+/* ---- Forward step (Sec. 3, Eq. 13) ------------------------------------------------------
+ * Advances u by nsteps FRKC2 steps of size dt with the plan's stage order.
+ *   u     : device array, in/out, real state (double for FP64 and MIXED, float for FP32).
+ *   rho   : if > 0, dt*rho <= beta is checked on the host (FRKC2_EUNSTABLE otherwise);
+ *           pass a bound from frkc2_rho_bound or 0 to skip the check.
+ *   ws    : device workspace of at least frkc2_workspace_size() bytes.
+ *   tune  : stages per pass, tile and kernel choice; NULL = library defaults.
+ * Each step starts from W^0 = u (imaginary part 0) and stores Re W^L back into u.  Stages
+ * are grouped into passes of k consecutive stages computed in shared memory.              */
+frkc2_status frkc2_step(frkc2_plan_t plan, const frkc2_problem* prob, double dt, int nsteps,
+                        double rho, void* u, void* ws, size_t ws_bytes,
+                        const frkc2_tuning* tune, void* stream);
+
+/* ---- Adjoint (reverse replay of Eq. 13) ------------------------------------------------
+ * Gradients of a scalar J(u(T_end)) after nsteps steps from u0, given g = dJ/du(T_end).
+ * The forward run keeps u every ckpt_every steps; each segment of ckpt_every steps is
+ * recomputed from its checkpoint with every stage state stored, then the stages are
+ * reversed: lam^l = lam^{l+1} + conj(dt a_l) J_f(W^l)^H lam^{l+1}, starting from
+ * lam = g (imaginary part 0) at the end of each step, and dJ/du^n = Re lam^0.
+ *   u0, g        : device arrays (state precision), read only.
+ *   dJdu0        : device array (state precision), written.
+ *   dJdkappa     : device array (kappa precision), written, FIELD only (NULL otherwise or to
+ *                  skip): dJ/dkappa_c = sum over stages of the face sensitivities
+ *                  Re(dt a_l [conj(lam_i)(W_j - W_i) + conj(lam_j)(W_i - W_j)])/dx^2, half
+ *                  to each cell of an interior face.
+ * Workspace: frkc2_adjoint_workspace_size().                                               */
+frkc2_status frkc2_adjoint_workspace_size(const frkc2_plan_t plan, const frkc2_problem* prob,
+                                          int nsteps, int ckpt_every, size_t* bytes);
+frkc2_status frkc2_adjoint(frkc2_plan_t plan, const frkc2_problem* prob, double dt,
+                           int nsteps, int ckpt_every, const void* u0, const void* g,
+                           void* dJdu0, void* dJdkappa, void* ws, size_t ws_bytes,
+                           void* stream);
+
+/* ---- Batched forward step ----------------------------------------------------------------
+ * nprob independent 2D problems (each with its own plan, grid size, conductivity, dt and
+ * step count, all of one precision and the same boundary kind) advanced by ONE persistent
+ * kernel launch.  The launch walks a device work list of (problem, pass, tile) items in
+ * rounds; a tile waits (bounded spin, then FRKC2_ETIMEOUT latched) until every tile of the
+ * previous pass of its problem is done.  frkc2_batch_prepare writes the problem table
+ * into the workspace (host-to-device copies on stream); frkc2_batch_launch only resets the
+ * counters and launches, so it can be captured in a CUDA graph and replayed.
+ *   plans, probs, dt, nsteps, u : host arrays of nprob entries (u[i] device pointers).    */
+frkc2_status frkc2_batch_workspace_size(int nprob, const frkc2_plan_t* plans,
+                                        const frkc2_problem* probs, const int* nsteps,
+                                        const frkc2_tuning* tune, size_t* bytes);
+frkc2_status frkc2_batch_prepare(int nprob, const frkc2_plan_t* plans,
+                                 const frkc2_problem* probs, const double* dt,
+                                 const int* nsteps, void* const* u, const frkc2_tuning* tune,
+                                 void* ws, size_t ws_bytes, void* stream);
+frkc2_status frkc2_batch_launch(void* ws, void* stream);
+frkc2_status frkc2_step_batched(int nprob, const frkc2_plan_t* plans,
+                                const frkc2_problem* probs, const double* dt,
+                                const int* nsteps, void* const* u, const frkc2_tuning* tune,
+                                void* ws, size_t ws_bytes, void* stream);
+
+/* Short text for a status code (static storage).                                          */
+const char* frkc2_status_string(frkc2_status st);
+
+/* Kernel launches queued by this thread since the last call (and resets the count).       */
+long long frkc2_launch_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FRKC2_H */

@@ -1,0 +1,274 @@
+// C ABI entry points for the forward step, the spectral-radius bound and the workspace.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+
+#include <cuda_runtime.h>
+
+#include "frkc2.h"
+#include "frkc2_internal.h"
+
+namespace frkc2 {
+
+static thread_local long long g_launches = 0;
+void count_launch(int n) { g_launches += n; }
+
+size_t state_bytes(int precision) { return precision == FRKC2_FP32 ? 4 : 8; }
+size_t arith_bytes(int precision) { return precision == FRKC2_FP64 ? 8 : 4; }
+size_t cells(const frkc2_problem& p) { return size_t(p.n[0]) * size_t(p.n[1]) * size_t(p.n[2]); }
+
+FaceLayout faces_layout(const frkc2_problem& p) {
+  FaceLayout L{0, 0, 0};
+  if (p.kappa_kind == FRKC2_KAPPA_POWER) return L;
+  const size_t nx = p.n[0], ny = p.n[1], nz = p.n[2];
+  L.nfx = nz * ny * (nx + 1);
+  if (p.ndim >= 2) L.nfy = nz * (ny + 1) * nx;
+  if (p.ndim >= 3) L.nfz = (nz + 1) * ny * nx;
+  return L;
+}
+
+StepLayout step_layout(const frkc2_problem& p) {
+  StepLayout s{};
+  const FaceLayout F = faces_layout(p);
+  const size_t A = arith_bytes(p.precision), S = state_bytes(p.precision), N = cells(p);
+  size_t off = 0;
+  s.status = off;
+  off += 256;
+  s.fx = off;
+  off += align256(F.nfx * A);
+  s.fy = off;
+  off += align256(F.nfy * A);
+  s.fz = off;
+  off += align256(F.nfz * A);
+  s.ua = off;
+  off += align256(N * S);
+  s.va = off;
+  off += align256(N * S);
+  s.ub = off;
+  off += align256(N * S);
+  s.vb = off;
+  off += align256(N * S);
+  s.total = off;
+  return s;
+}
+
+void default_tiles(const frkc2_problem& p, int k, int* tx, int* ty, int* tz) {
+  if (p.ndim == 1) {
+    *tx = 1024;
+    *ty = *tz = 1;
+  } else if (p.ndim == 2) {
+    *tx = 64;
+    *ty = p.precision == FRKC2_FP32 ? 32 : 16;
+    *tz = 1;
+  } else {
+    *tx = 32;
+    *ty = 4;
+    *tz = k > 1 ? 2 : 4;
+  }
+}
+
+static int default_k(const frkc2_problem& p) {
+  if (p.ndim == 1) return 16;
+  if (p.ndim == 2) return p.precision == FRKC2_FP32 ? 4 : 1;
+  return 1;
+}
+
+static int smem_optin() {
+  static int v = 0;
+  if (!v) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
+      v = 227 * 1024;
+  }
+  return v;
+}
+
+frkc2_status validate_problem(const frkc2_problem* p) {
+  if (!p) return FRKC2_EINVAL;
+  if (p->ndim < 1 || p->ndim > 3) return FRKC2_EINVAL;
+  if (p->bc != FRKC2_BC_PERIODIC && p->bc != FRKC2_BC_DIRICHLET) return FRKC2_EINVAL;
+  if (p->kappa_kind < FRKC2_KAPPA_CONST || p->kappa_kind > FRKC2_KAPPA_POWER) return FRKC2_EINVAL;
+  if (p->precision < FRKC2_FP64 || p->precision > FRKC2_MIXED) return FRKC2_EINVAL;
+  for (int d = 0; d < 3; ++d) {
+    if (p->n[d] < 1 || p->n[d] > (int64_t(1) << 30)) return FRKC2_EINVAL;
+    if (d >= p->ndim && p->n[d] != 1) return FRKC2_EINVAL;
+  }
+  if (cells(*p) > (size_t(1) << 34)) return FRKC2_EINVAL;
+  if (!(p->dx > 0.0) || !std::isfinite(p->dx)) return FRKC2_EINVAL;
+  if (p->kappa_kind == FRKC2_KAPPA_FIELD && !p->kappa) return FRKC2_EINVAL;
+  if (p->kappa_kind == FRKC2_KAPPA_POWER && !(p->kappa_p > 0.0)) return FRKC2_EINVAL;
+  return FRKC2_OK;
+}
+
+}  // namespace frkc2
+
+using namespace frkc2;
+
+extern "C" {
+
+long long frkc2_launch_count(void) {
+  const long long v = g_launches;
+  g_launches = 0;
+  return v;
+}
+
+frkc2_status frkc2_workspace_size(const frkc2_problem* prob, const frkc2_tuning* tune,
+                                  size_t* bytes) {
+  (void)tune;
+  if (!bytes) return FRKC2_EINVAL;
+  const frkc2_status v = validate_problem(prob);
+  if (v != FRKC2_OK) return v;
+  *bytes = step_layout(*prob).total;
+  return FRKC2_OK;
+}
+
+frkc2_status frkc2_workspace_reset(void* ws, void* stream) {
+  if (!ws) return FRKC2_EINVAL;
+  return cudaMemsetAsync(ws, 0, 256, static_cast<cudaStream_t>(stream)) == cudaSuccess ? FRKC2_OK
+                                                                                       : FRKC2_ECUDA;
+}
+
+frkc2_status frkc2_workspace_status(const void* ws, void* stream) {
+  if (!ws) return FRKC2_EINVAL;
+  unsigned st = 0;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (cudaMemcpyAsync(&st, ws, sizeof(unsigned), cudaMemcpyDeviceToHost, s) != cudaSuccess)
+    return FRKC2_ECUDA;
+  if (cudaStreamSynchronize(s) != cudaSuccess) return FRKC2_ECUDA;
+  if (st & ST_NONFINITE) return FRKC2_ENONFINITE;
+  if (st & ST_TIMEOUT) return FRKC2_ETIMEOUT;
+  return FRKC2_OK;
+}
+
+frkc2_status frkc2_rho_bound(const frkc2_problem* prob, const void* u, double* rho_dev,
+                             void* stream) {
+  const frkc2_status v = validate_problem(prob);
+  if (v != FRKC2_OK) return v;
+  if (!rho_dev || (reinterpret_cast<uintptr_t>(rho_dev) & 7)) return FRKC2_EINVAL;
+  if (prob->kappa_kind == FRKC2_KAPPA_POWER && !u) return FRKC2_EINVAL;
+  return launch_rho(*prob, u, rho_dev, static_cast<cudaStream_t>(stream)) == cudaSuccess
+             ? FRKC2_OK
+             : FRKC2_ECUDA;
+}
+
+frkc2_status frkc2_step(frkc2_plan_t plan, const frkc2_problem* prob, double dt, int nsteps,
+                        double rho, void* u, void* ws, size_t ws_bytes,
+                        const frkc2_tuning* tune, void* stream) {
+  if (!plan || !u || !ws || nsteps < 0) return FRKC2_EINVAL;
+  const frkc2_status v = validate_problem(prob);
+  if (v != FRKC2_OK) return v;
+  if (!(dt > 0.0) || !std::isfinite(dt)) return FRKC2_EINVAL;
+  if (reinterpret_cast<uintptr_t>(ws) & 255) return FRKC2_EINVAL;
+  if (reinterpret_cast<uintptr_t>(u) & (state_bytes(prob->precision) - 1)) return FRKC2_EINVAL;
+  if (rho > 0.0 && dt * rho > plan->beta * (1.0 + 1e-12)) return FRKC2_EUNSTABLE;
+  const StepLayout L = step_layout(*prob);
+  if (ws_bytes < L.total) return FRKC2_ENOMEM;
+  const frkc2_problem& p = *prob;
+
+  int k = (tune && tune->k) ? tune->k : default_k(p);
+  if (k < 1 || k > KMAX) return FRKC2_EINVAL;
+  k = std::min(k, plan->s);
+  int tx, ty, tz;
+  default_tiles(p, k, &tx, &ty, &tz);
+  if (tune && tune->tile_x) tx = tune->tile_x;
+  if (tune && tune->tile_y) ty = tune->tile_y;
+  if (tune && tune->tile_z) tz = tune->tile_z;
+  if (p.ndim < 2) ty = 1;
+  if (p.ndim < 3) tz = 1;
+  if (tx < 1 || ty < 1 || tz < 1) return FRKC2_EINVAL;
+  const int kern = tune ? tune->kernel : 0;
+  if (kern < 0 || kern > 3) return FRKC2_EINVAL;
+  const bool stream_ok = p.ndim == 2 && p.kappa_kind != FRKC2_KAPPA_POWER && k == 1;
+  bool use_stream2d = false;
+  if (kern == 2) {
+    if (!stream_ok) return FRKC2_EUNSUPPORTED;
+    use_stream2d = true;
+  } else if (kern == 3) {
+    return FRKC2_EUNSUPPORTED;
+  } else if (kern == 0) {
+    use_stream2d = stream_ok;
+  }
+  if (use_stream2d && !(tune && tune->tile_y)) ty = 64;
+  {
+    PassArgs probe{};
+    probe.tx = tx;
+    probe.ty = ty;
+    probe.tz = tz;
+    probe.hx = k;
+    probe.hy = p.ndim >= 2 ? k : 0;
+    probe.hz = p.ndim >= 3 ? k : 0;
+    if (!use_stream2d && generic_smem_bytes(p, probe) > size_t(smem_optin())) return FRKC2_EINVAL;
+  }
+  if (nsteps == 0) return FRKC2_OK;
+
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  char* base = static_cast<char*>(ws);
+  if (p.kappa_kind != FRKC2_KAPPA_POWER) {
+    if (launch_faces(p, base + L.fx, base + L.fy, base + L.fz, st) != cudaSuccess) return FRKC2_ECUDA;
+  }
+  void* ua = base + L.ua;
+  void* ub = base + L.ub;
+  void* va = base + L.va;
+  void* vb = base + L.vb;
+  const int s = plan->s;
+  const int npass = (s + k - 1) / k;
+  const double h2 = p.dx * p.dx;
+
+  PassArgs a{};
+  a.ndim = p.ndim;
+  a.bc = p.bc;
+  a.nx = int(p.n[0]);
+  a.ny = int(p.n[1]);
+  a.nz = int(p.n[2]);
+  a.tx = tx;
+  a.ty = ty;
+  a.tz = tz;
+  a.fx = base + L.fx;
+  a.fy = base + L.fy;
+  a.fz = base + L.fz;
+  a.kc = p.kappa_c;
+  a.kp = p.kappa_p;
+  a.status = reinterpret_cast<unsigned*>(base + L.status);
+
+  const void* curU = u;
+  const void* curV = nullptr;
+  for (int n = 0; n < nsteps; ++n) {
+    for (int q = 0; q < npass; ++q) {
+      const int l0 = q * k;
+      const int kq = std::min(k, s - l0);
+      const bool last = q == npass - 1;
+      void* outU;
+      if (last && curU != u)
+        outU = u;
+      else
+        outU = (curU == ua) ? ub : ua;
+      void* outV = last ? nullptr : (curV == va ? vb : va);
+      a.k = kq;
+      a.hx = kq;
+      a.hy = p.ndim >= 2 ? kq : 0;
+      a.hz = p.ndim >= 3 ? kq : 0;
+      a.U_in = curU;
+      a.V_in = curV;
+      a.U_out = outU;
+      a.V_out = outV;
+      a.check_finite = last ? 1 : 0;
+      for (int j = 0; j < kq; ++j) {
+        a.ca[j] = dt * plan->a_re[l0 + j] / h2;
+        a.cb[j] = dt * plan->a_im[l0 + j] / h2;
+      }
+      const cudaError_t e = use_stream2d ? launch_pass_stream2d(p, a, st) : launch_pass_generic(p, a, st);
+      if (e != cudaSuccess) return FRKC2_ECUDA;
+      curU = outU;
+      curV = outV;
+    }
+  }
+  if (curU != u) {
+    if (cudaMemcpyAsync(u, curU, cells(p) * state_bytes(p.precision), cudaMemcpyDeviceToDevice, st) !=
+        cudaSuccess)
+      return FRKC2_ECUDA;
+  }
+  return FRKC2_OK;
+}
+
+}  // extern "C"

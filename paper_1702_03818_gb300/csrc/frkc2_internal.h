@@ -1,0 +1,78 @@
+// Internal declarations shared by the FRKC2 host code and kernels (not part of the C ABI).
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "frkc2.h"
+
+struct frkc2_plan_s {
+  int s = 0;
+  double beta = 0.0;
+  double Q = 0.0;
+  int n_iter = 0;
+  std::vector<int> order;     // root index of each stage
+  std::vector<double> a_re;   // step sizes in stage order
+  std::vector<double> a_im;
+};
+
+namespace frkc2 {
+
+constexpr int KMAX = 16;                 // most stages in one pass
+constexpr unsigned ST_NONFINITE = 1u;    // status word bits
+constexpr unsigned ST_TIMEOUT = 2u;
+
+inline size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
+
+// One k-stage pass over the grid: read (U, V), apply k stages, write (U, V).
+struct PassArgs {
+  int ndim, bc;
+  int nx, ny, nz;         // grid extents (1 past ndim)
+  int tx, ty, tz;         // output tile of one CTA
+  int hx, hy, hz;         // halo width per axis: k along present axes, 0 otherwise
+  int k;                  // stages in this pass
+  int check_finite;       // flag non-finite outputs in the status word
+  const void* U_in;       // real part of the pass input
+  const void* V_in;       // imaginary part; nullptr = zero (first pass of a step)
+  void* U_out;
+  void* V_out;            // nullptr = not stored (last pass of a step)
+  const void* fx;         // face conductivities (FIELD / CONST), layouts in faces_layout()
+  const void* fy;
+  const void* fz;
+  double kc, kp;          // POWER: kappa(w) = 1 + kc * w^kp
+  unsigned* status;
+  double ca[KMAX];        // dt Re(a_l) / dx^2 for the pass's stages
+  double cb[KMAX];        // dt Im(a_l) / dx^2
+};
+
+// Face arrays: x faces [nz][ny][nx+1], y faces [nz][ny+1][nx], z faces [nz+1][ny][nx];
+// face index i along an axis lies between cells i-1 and i.
+struct FaceLayout {
+  size_t nfx, nfy, nfz;   // element counts (0 for absent axes)
+};
+FaceLayout faces_layout(const frkc2_problem& p);
+
+// Workspace layout of frkc2_step (byte offsets from the workspace base).
+struct StepLayout {
+  size_t status, fx, fy, fz, ua, va, ub, vb, total;
+};
+StepLayout step_layout(const frkc2_problem& p);
+
+size_t state_bytes(int precision);
+size_t arith_bytes(int precision);
+size_t cells(const frkc2_problem& p);
+
+// Launchers (return cudaGetLastError()).
+cudaError_t launch_faces(const frkc2_problem& p, void* fx, void* fy, void* fz, cudaStream_t st);
+cudaError_t launch_rho(const frkc2_problem& p, const void* u, double* rho_dev, cudaStream_t st);
+cudaError_t launch_pass_generic(const frkc2_problem& p, const PassArgs& a, cudaStream_t st);
+cudaError_t launch_pass_stream2d(const frkc2_problem& p, const PassArgs& a, cudaStream_t st);
+size_t generic_smem_bytes(const frkc2_problem& p, const PassArgs& a);
+void default_tiles(const frkc2_problem& p, int k, int* tx, int* ty, int* tz);
+
+void count_launch(int n = 1);
+
+}  // namespace frkc2

@@ -1,0 +1,183 @@
+"""GPU parity of the forward path (frkc2_rho_bound, frkc2_step) against the FP64 oracle.
+
+Every case builds the same seeded inputs for both sides; the CUDA path is called through
+the C ABI (the ctypes binding) and compared element by element with the oracle.
+Tolerances (relative L2 against the FP64 oracle): FP64 1e-11, FP32 1e-4 at s <= 64.
+"""
+import numpy as np
+import pytest
+
+from oracle import frkc2_oracle as O
+import frkc2_inputs as I
+from helpers import oracle_problem, rel_l2, seeded_case
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+F = pytest.importorskip("paper_1702_03818_gb300.frkc2")
+
+TOL = {"fp64": 1e-11, "fp32": 1e-4, "mixed": 1e-6}
+DT = {"fp64": torch.float64, "fp32": torch.float32, "mixed": torch.float64}
+KDT = {"fp64": torch.float64, "fp32": torch.float32, "mixed": torch.float32}
+
+
+def dev(a, dtype):
+    return torch.as_tensor(np.ascontiguousarray(a), dtype=dtype, device="cuda")
+
+
+def lib_problem(shape, bc, kappa, prec, dx=1.0, field_t=None, c=1.0, p=2.5):
+    n = tuple(reversed(shape))  # (nx, ny, nz)
+    return F.make_problem(len(shape), n, dx, bc, kappa, prec, kappa_c=c, kappa_p=p, kappa_field=field_t)
+
+
+def run_gpu(plan, shape, bc, kappa, prec, u0, field, dt, nsteps, dx=1.0, c=1.0, tune=None):
+    u = dev(u0, DT[prec])
+    kt = dev(field, KDT[prec]) if field is not None else None
+    pr = lib_problem(shape, bc, kappa, prec, dx, kt, c)
+    ws = torch.empty(F.frkc2_workspace_size(pr, tune), dtype=torch.uint8, device="cuda")
+    F.frkc2_workspace_reset(ws)
+    F.frkc2_step(plan, pr, dt, nsteps, 0.0, u, ws, tune)
+    st = F.frkc2_workspace_status(ws)
+    return u.double().cpu().numpy(), st
+
+
+def rounded_field(field, prec):
+    """The conductivity the GPU sees: float32-rounded for FP32 and MIXED."""
+    if field is None or prec == "fp64":
+        return field
+    return field.astype(np.float32).astype(np.float64)
+
+
+# ---------------------------------------------------------------------------------------
+# spectral-radius bound
+# ---------------------------------------------------------------------------------------
+
+@pytest.mark.parametrize("shape,bc", [((64, 80), "periodic"), ((33, 47), "dirichlet"),
+                                      ((9, 10, 11), "periodic"), ((7, 6, 5), "dirichlet"),
+                                      ((300,), "dirichlet")])
+def test_rho_bound_field_bit_exact(shape, bc):
+    _, field = seeded_case(shape, bc, "field", 21)
+    kt = dev(field, torch.float64)
+    pr = lib_problem(shape, bc, "field", "fp64", 0.37, kt)
+    rho = torch.zeros(1, dtype=torch.float64, device="cuda")
+    F.frkc2_rho_bound(pr, None, rho)
+    ref = O.rho_bound(oracle_problem(len(shape), bc, "field", 0.37, field))
+    assert rho.item() == ref
+
+
+def test_rho_bound_const_and_power():
+    n = 200
+    pr = lib_problem((n, n), "periodic", "const", "fp64", 1.0 / n, c=0.02)
+    rho = torch.zeros(1, dtype=torch.float64, device="cuda")
+    F.frkc2_rho_bound(pr, None, rho)
+    assert rho.item() == O.rho_bound(oracle_problem(2, "periodic", "const", 1.0 / n, c=0.02), np.zeros((n, n)))
+    u0 = I.hotspot3d_u0(24, sigma=4.0)
+    ut = dev(u0, torch.float64)
+    pr = lib_problem(u0.shape, "dirichlet", "power", "fp64", 1.0)
+    F.frkc2_rho_bound(pr, ut, rho)
+    ref = O.rho_bound(oracle_problem(3, "dirichlet", "power", 1.0), u0)
+    assert abs(rho.item() / ref - 1.0) < 1e-14
+    # FP32 field: the bound is formed in FP64 from the float values
+    _, field = seeded_case((40, 50), "periodic", "field", 5)
+    pr = lib_problem((40, 50), "periodic", "field", "fp32", 1.0, dev(field, torch.float32))
+    F.frkc2_rho_bound(pr, None, rho)
+    assert rho.item() == O.rho_bound(oracle_problem(2, "periodic", "field", 1.0, rounded_field(field, "fp32")))
+
+
+# ---------------------------------------------------------------------------------------
+# forward step parity
+# ---------------------------------------------------------------------------------------
+
+CASES = [
+    # shape, bc, kappa, s, nsteps, k, kernel
+    ((100, 77), "periodic", "field", 16, 2, 1, 0),
+    ((100, 77), "periodic", "field", 16, 2, 1, 1),
+    ((100, 77), "periodic", "field", 16, 2, 4, 1),
+    ((70, 130), "dirichlet", "field", 32, 2, 1, 0),
+    ((70, 130), "dirichlet", "field", 32, 2, 3, 1),
+    ((64, 64), "periodic", "const", 64, 1, 8, 1),
+    ((5, 7), "periodic", "field", 8, 3, 4, 1),
+    ((5, 7), "dirichlet", "field", 8, 3, 1, 0),
+    ((1, 9), "periodic", "field", 4, 2, 1, 0),
+    ((257,), "dirichlet", "const", 16, 3, 16, 1),
+    ((1000,), "periodic", "field", 16, 2, 5, 1),
+    ((12, 10, 14), "periodic", "field", 16, 1, 1, 1),
+    ((12, 10, 14), "dirichlet", "field", 16, 1, 2, 1),
+    ((10, 11, 9), "dirichlet", "power", 16, 1, 1, 1),
+    ((34, 20), "periodic", "power", 16, 1, 2, 1),
+]
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "mixed"])
+@pytest.mark.parametrize("case", CASES, ids=lambda c: f"{'x'.join(map(str, c[0]))}-{c[1]}-{c[2]}-s{c[3]}-k{c[5]}-kern{c[6]}")
+def test_step_parity(case, prec):
+    shape, bc, kappa, s, nsteps, k, kernel = case
+    u0, field = seeded_case(shape, bc, kappa, 100 + s)
+    oplan = O.plan(s)
+    plan = F.frkc2_plan(s)
+    assert np.array_equal(plan.info()["order"], oplan["order"])
+    fo = rounded_field(field, prec)
+    opr = oracle_problem(len(shape), bc, kappa, 1.0, fo)
+    dt = 0.9 * oplan["beta"] / O.rho_bound(opr, u0)
+    u0g = u0.astype(np.float32).astype(np.float64) if prec == "fp32" else u0
+    ref = O.frkc2_step(u0g, oplan["a"], dt, opr, nsteps)
+    tune = F.make_tuning(k=k, kernel=kernel)
+    got, st = run_gpu(plan, shape, bc, kappa, prec, u0, field, dt, nsteps, tune=tune)
+    assert st == F.OK
+    err = rel_l2(got, ref)
+    assert err < TOL[prec], err
+
+
+def test_heat1d_workload_matches_closed_form_and_oracle():
+    cfg = I.CONFIGS["heat1d"]
+    u0, amp, dx = I.heat1d_u0(cfg["n"], 8, cfg["seed"])
+    L = cfg["s"]
+    plan = F.frkc2_plan(L)
+    beta = plan.info()["beta"]
+    nsteps = int(np.ceil(cfg["t_end"] / (0.9 * beta * dx * dx / 4.0)))
+    dt = cfg["t_end"] / nsteps
+    opr = oracle_problem(1, "dirichlet", "const", dx)
+    ref = O.frkc2_step(u0, O.plan(L)["a"], dt, opr, nsteps)
+    got, st = run_gpu(plan, (cfg["n"],), "dirichlet", "const", "fp64", u0, None, dt, nsteps, dx=dx)
+    assert st == F.OK and nsteps == 87
+    assert rel_l2(got, ref) < 1e-12
+
+
+def test_varkappa2d_reduced_many_steps_fp64_fp32():
+    shape = (256, 256)
+    u0 = I.smooth_unit(shape, 64 / 8, 3819)
+    field = I.kappa_field(shape, 3818, ell=32 / 8)
+    s = 64
+    oplan = O.plan(s)
+    plan = F.frkc2_plan(s)
+    for prec, tol in (("fp64", 1e-11), ("fp32", 1e-4)):
+        fo = rounded_field(field, prec)
+        opr = oracle_problem(2, "periodic", "field", 1.0, fo)
+        dt = 0.9 * oplan["beta"] / O.rho_bound(opr)
+        u0g = u0.astype(np.float32).astype(np.float64) if prec == "fp32" else u0
+        ref = O.frkc2_step(u0g, oplan["a"], dt, opr, 4)
+        got, st = run_gpu(plan, shape, "periodic", "field", prec, u0, field, dt, 4)
+        assert st == F.OK
+        assert rel_l2(got, ref) < tol, (prec, rel_l2(got, ref))
+
+
+def test_nsteps_zero_and_nonfinite_flag():
+    shape = (32, 32)
+    u0, field = seeded_case(shape, "periodic", "field", 3)
+    plan = F.frkc2_plan(8)
+    got, st = run_gpu(plan, shape, "periodic", "field", "fp64", u0, field, 0.1, 0)
+    assert np.array_equal(got, u0) and st == F.OK
+    bad = u0.copy()
+    bad[5, 5] = np.nan
+    _, st = run_gpu(plan, shape, "periodic", "field", "fp64", bad, field, 0.1, 1)
+    assert st == F.ENONFINITE
+
+
+def test_launch_count_matches_passes():
+    shape = (64, 64)
+    u0, field = seeded_case(shape, "periodic", "field", 4)
+    plan = F.frkc2_plan(16)
+    F.frkc2_launch_count()
+    run_gpu(plan, shape, "periodic", "field", "fp32", u0, field, 0.5, 3, tune=F.make_tuning(k=4, kernel=1))
+    # one face-preparation launch plus 16/4 passes per step
+    assert F.frkc2_launch_count() == 1 + 3 * 4

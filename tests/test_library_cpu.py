@@ -1,0 +1,131 @@
+"""CPU-only checks of the C ABI library: it loads, exports every declared symbol, its host
+plan reproduces the oracle's plan, and argument errors are reported before any GPU work."""
+import os
+import re
+
+import numpy as np
+import pytest
+
+from oracle import frkc2_oracle as O
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+F = pytest.importorskip("paper_1702_03818_gb300.frkc2",
+                        reason="library not built; run paper_1702_03818_gb300.build")
+
+
+def declared_symbols():
+    txt = open(os.path.join(ROOT, "include", "frkc2.h")).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(frkc2_[a-z_0-9]+)\s*\(", txt)))
+
+
+def test_library_exports_every_declared_symbol():
+    syms = declared_symbols()
+    assert len(syms) >= 15
+    lib = F._lib
+    missing = [s for s in syms if not hasattr(lib, s)]
+    assert not missing, missing
+    # the binding declares a signature for each of them, under the same name
+    assert set(syms) <= set(F.EXPORTED)
+
+
+@pytest.mark.parametrize("L", [2, 4, 8, 16, 32, 64, 100, 128])
+def test_plan_matches_oracle(L):
+    lib = F.frkc2_plan(L).info()
+    ora = O.plan(L)
+    assert np.array_equal(lib["order"], ora["order"])
+    assert np.max(np.abs(lib["a"] - ora["a"])) < 1e-14
+    assert abs(lib["beta"] - ora["beta"]) <= 1e-15 * ora["beta"]
+    assert abs(lib["Q"] / ora["Q"] - 1.0) < 1e-9
+    assert lib["n_iter"] == ora["n"]
+
+
+@pytest.mark.slow
+def test_plan_matches_oracle_n_loop_256():
+    lib = F.frkc2_plan(256).info()
+    ora = O.plan(256)
+    assert ora["n"] >= 2  # the n-loop of Sec. 2.2 is exercised
+    assert np.array_equal(lib["order"], ora["order"])
+    assert lib["n_iter"] == ora["n"]
+
+
+def test_plan_from_steps_and_errors():
+    a = O.plan(16)["a"]
+    p = F.frkc2_plan_from_steps(a).info()
+    assert np.array_equal(p["a"], a)
+    assert abs(p["Q"] / O.realised_Q(a, O.beta(16), 256) - 1.0) < 1e-9
+    for bad in (0, 3, 5000):
+        with pytest.raises(F.Frkc2Error) as e:
+            F.frkc2_plan(bad)
+        assert e.value.status == F.EINVAL
+    with pytest.raises(F.Frkc2Error) as e:
+        F.frkc2_plan(16, nu=0.1)
+    assert e.value.status == F.EUNSUPPORTED
+    # strict plan with an unreachable bound is not possible to request; a normal plan is OK
+    assert F.frkc2_plan(16, flags=F.PLAN_STRICT).info()["Q"] <= 10 * 16 ** 2
+
+
+def test_workspace_size_and_validation_on_host():
+    p = F.make_problem(2, (100, 60), 1.0, "periodic", "const", "fp64", kappa_c=1.0)
+    ws = F.frkc2_workspace_size(p)
+    n = 100 * 60
+    assert ws >= 256 + 4 * n * 8 + (101 * 60 + 61 * 100) * 8
+    p32 = F.make_problem(2, (100, 60), 1.0, "periodic", "const", "fp32", kappa_c=1.0)
+    assert F.frkc2_workspace_size(p32) < ws
+    bad = F.make_problem(2, (100, 60, 2), 1.0)
+    with pytest.raises(F.Frkc2Error):
+        F.frkc2_workspace_size(bad)
+    bad = F.make_problem(2, (100, 60), -1.0, "periodic", "const")
+    with pytest.raises(F.Frkc2Error):
+        F.frkc2_workspace_size(bad)
+    bad = F.make_problem(2, (100, 60), 1.0, "periodic", "field")  # field kind without an array
+    with pytest.raises(F.Frkc2Error):
+        F.frkc2_workspace_size(bad)
+
+
+class _FakeBuf:
+    """An aligned address that is never dereferenced (the calls fail before touching it)."""
+
+    def __init__(self, addr, nbytes):
+        self._a, self._n = addr, nbytes
+
+    def data_ptr(self):
+        return self._a
+
+    def numel(self):
+        return self._n
+
+    def element_size(self):
+        return 1
+
+
+def test_step_rejects_unstable_dt_and_small_workspace_before_gpu_work():
+    plan = F.frkc2_plan(16)
+    beta = plan.info()["beta"]
+    p = F.make_problem(2, (64, 64), 1.0, "periodic", "const", "fp64", kappa_c=1.0)
+    need = F.frkc2_workspace_size(p)
+    u = _FakeBuf(1 << 20, 64 * 64 * 8)
+    ws = _FakeBuf(1 << 30, need)
+    rho = 8.0
+    with pytest.raises(F.Frkc2Error) as e:
+        F.frkc2_step(plan, p, 1.01 * beta / rho, 1, rho, u, ws, stream=0)
+    assert e.value.status == F.EUNSTABLE
+    with pytest.raises(F.Frkc2Error) as e:
+        F.frkc2_step(plan, p, 0.5 * beta / rho, 1, rho, u, _FakeBuf(1 << 30, need - 1), stream=0)
+    assert e.value.status == F.ENOMEM
+    with pytest.raises(F.Frkc2Error) as e:
+        F.frkc2_step(plan, p, 0.5 * beta / rho, 1, rho, u, _FakeBuf((1 << 30) + 8, need), stream=0)
+    assert e.value.status == F.EINVAL
+    with pytest.raises(F.Frkc2Error) as e:
+        F.frkc2_step(plan, p, -1.0, 1, rho, u, ws, stream=0)
+    assert e.value.status == F.EINVAL
+    with pytest.raises(F.Frkc2Error) as e:
+        F.frkc2_step(plan, p, 0.5 * beta / rho, 1, rho, u, ws, tune=F.make_tuning(k=17), stream=0)
+    assert e.value.status == F.EINVAL
+
+
+def test_status_strings():
+    for st in range(9):
+        assert F.frkc2_status_string(st)
+    assert "unknown" in F.frkc2_status_string(99)
