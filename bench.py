@@ -1,0 +1,409 @@
+#!/usr/bin/env python
+"""FRKC2 benchmark: cell-stage updates/s of the 2D variable-conductivity workload.
+
+Workload (one bench step = the whole job): 2048^2 periodic grid, kappa = exp(0.5 g) with g a
+unit Gaussian random field of correlation length 32 cells (seed 3818), u0 a smooth random
+field in [0, 1] (correlation length 64, seed 3819), FRKC2 with s = 64 stages, 100 steps of
+dt = 0.9 beta / rho.  A step runs every part of the path: the spectral-radius bound (kernel),
+dt from it, and frkc2_step over 100 x 64 stages.  The primary line is FP64; FP32 and MIXED
+runs of the same job are reported under "variants" with their errors.
+
+Timing: W untimed warm-up steps, then K timed steps, each bracketed by CUDA events on the
+launching stream; L2 is flushed (a 256 MiB write) between timed steps, outside the events.
+Under torchrun every rank runs its own replica (the job does not shard without a halo
+exchange), so scaling is weak and value = all ranks' cell-stages / the slowest rank's time.
+
+``--impl reference`` times the FP64 oracle (the CPU statement of the method) on the host on a
+bounded sample of the same workload, rank 0 only.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import frkc2_inputs as I  # noqa: E402
+
+CFG = I.CONFIGS["varkappa2d"]
+METRIC = "FRKC2 cell-stage updates/s (2D var-kappa 2048^2, s=64, 100 steps)"
+UNIT = "cell-stage/s"
+MEASURED_PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
+# FP64 pipe: 152 SMs x 2 FP64 instructions per clock x 2.07 GHz (1.259 TFLOP/s with FMA = 2)
+FP64_PEAK_TINST = 152 * 2 * 2.07e9 / 1e12
+FP64_INST_PER_CELL_STAGE = 18  # 2 x (2 differences + 2 face products + 3 sums) + 4 FMA updates
+# dram bytes per launch from one ncu capture of each pass kernel, keyed by the source hash of
+# the kernel file at capture time (the value is reported only while the source is unchanged)
+NCU_TRAFFIC = {}
+
+
+def kernel_source_hash(name: str) -> str:
+    path = os.path.join(ROOT, "paper_1702_03818_gb300", "csrc", name)
+    return hashlib.sha256(open(path, "rb").read()).hexdigest()[:16]
+
+
+def hbm_peak():
+    try:
+        return float(json.load(open(MEASURED_PEAKS))["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def inputs(n=None):
+    n = n or CFG["n"]
+    ell_u, ell_k = 64.0 * n / CFG["n"], 32.0 * n / CFG["n"]
+    u0 = I.smooth_unit((n, n), ell_u, CFG["u0_seed"])
+    kappa = I.kappa_field((n, n), CFG["kappa_seed"], ell=ell_k)
+    return u0, kappa
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join("/tmp", f"frkc2_clocks_{os.getpid()}.csv")
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = max(mx, float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def run_ours(args, rank, world, local_rank):
+    import torch
+    from paper_1702_03818_gb300 import frkc2 as F
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    stream = torch.cuda.current_stream()
+    s, nsteps, n = CFG["s"], CFG["steps"], CFG["n"]
+    u0_np, k_np = inputs()
+    plan = F.frkc2_plan(s)
+    beta = plan.info()["beta"]
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    cells = n * n
+    cell_stages = cells * s * nsteps
+
+    def setup(prec):
+        sd = torch.float32 if prec == "fp32" else torch.float64
+        kd = torch.float64 if prec == "fp64" else torch.float32
+        u0 = torch.as_tensor(u0_np, dtype=sd, device=dev)
+        kt = torch.as_tensor(k_np, dtype=kd, device=dev)
+        pr = F.make_problem(2, (n, n), 1.0, "periodic", "field", prec, kappa_field=kt)
+        ws = torch.empty(F.frkc2_workspace_size(pr), dtype=torch.uint8, device=dev)
+        F.frkc2_workspace_reset(ws)
+        return dict(u0=u0, u=u0.clone(), k=kt, pr=pr, ws=ws, rho=torch.zeros(1, dtype=torch.float64, device=dev))
+
+    def job(c):
+        F.frkc2_rho_bound(c["pr"], None, c["rho"])
+        rho = c["rho"].item()
+        dt = CFG["cfl"] * beta / rho
+        F.frkc2_step(plan, c["pr"], dt, nsteps, rho, c["u"], c["ws"])
+        return dt
+
+    def timed(prec, K, W, clocks=None):
+        c = setup(prec)
+        for _ in range(W):
+            c["u"].copy_(c["u0"])
+            job(c)
+        torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+        ms = []
+        launches = 0
+        if clocks:
+            clocks.start()
+        for _ in range(K):
+            c["u"].copy_(c["u0"])
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            F.frkc2_launch_count()
+            e0.record(stream)
+            job(c)
+            e1.record(stream)
+            launches += F.frkc2_launch_count()
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+        clk = clocks.stop() if clocks else None
+        assert F.frkc2_workspace_status(c["ws"]) == F.OK
+        return c, ms, launches, clk
+
+    def step_only_ms(c, reps=2):
+        """Event time of frkc2_step alone (the pass kernels and the face set-up kernel)."""
+        F.frkc2_rho_bound(c["pr"], None, c["rho"])
+        rho = c["rho"].item()
+        dt = CFG["cfl"] * beta / rho
+        out = []
+        for _ in range(reps):
+            c["u"].copy_(c["u0"])
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            F.frkc2_step(plan, c["pr"], dt, nsteps, rho, c["u"], c["ws"])
+            e1.record(stream)
+            e1.synchronize()
+            out.append(e0.elapsed_time(e1))
+        return float(np.mean(out))
+
+    clocks = Clocks(local_rank)
+    c64, ms, launches, clk = timed("fp64", args.steps, args.warmup, clocks)
+    total_ms = float(np.sum(ms))
+    # max over ranks of the timed region
+    if world > 1:
+        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = world * cell_stages * args.steps / (total_ms / 1e3)
+    u64 = c64["u"].double().cpu().numpy()
+
+    npass = nsteps * s  # k = 1 passes per step
+    step_ms = step_only_ms(c64)
+    launch_s = step_ms / 1e3 / npass
+    achieved_tinst = FP64_INST_PER_CELL_STAGE * cells / launch_s / 1e12
+    peak_hbm, peak_kind = hbm_peak()
+    # algorithmic bytes of the FP64 passes: read U, V, kappa and write U, V (8 B each);
+    # the first pass of a step reads no V, the last writes no V
+    bytes_step = cells * 8 * (s * 5 - 2)
+    hbm_gbs = bytes_step * nsteps / (step_ms / 1e3) / 1e9
+    roofline = {
+        "bound": "alu", "achieved": achieved_tinst, "peak": FP64_PEAK_TINST,
+        "unit": "Tinst/s (FP64 pipe)", "frac": achieved_tinst / FP64_PEAK_TINST,
+        "traffic": NCU_TRAFFIC.get(("pass_stream2d.cu", kernel_source_hash("pass_stream2d.cu"))),
+        "kernel": "k_stream2d<double,double,periodic>",
+        "hbm_achieved_gbs": hbm_gbs, "hbm_peak_gbs": peak_hbm, "hbm_peak_kind": peak_kind,
+        "hbm_frac": hbm_gbs / peak_hbm, "avg_launch_us": launch_s * 1e6,
+    }
+
+    variants = {}
+    if not args.no_variants:
+        for prec in ("fp32", "mixed"):
+            c, vms, _, _ = timed(prec, args.steps, max(3, args.warmup // 2))
+            v = cell_stages * args.steps / (np.sum(vms) / 1e3)
+            got = c["u"].double().cpu().numpy()
+            err = float(np.linalg.norm(got - u64) / np.linalg.norm(u64))
+            smsec = step_only_ms(c)
+            sbytes = 4 if prec == "fp32" else 8
+            kbytes = 8 if prec == "fp64" else 4
+            # default passes: k stages each; bytes per cell and pass as for FP64 with the
+            # state / kappa sizes of this precision
+            k = 4 if prec == "fp32" else 1
+            npv = (s + k - 1) // k
+            pass_bytes = cells * (npv * (4 * sbytes + kbytes) - 2 * sbytes)
+            g = pass_bytes * nsteps / (smsec / 1e3) / 1e9
+            variants[prec] = {
+                "value": v, "ms_per_step": float(np.mean(vms)), "k": k,
+                "speedup_vs_fp64": v / (cell_stages * args.steps / (float(np.sum(ms)) / 1e3)),
+                "rel_l2_vs_fp64_gpu_after_100_steps": err,
+                "roofline": {"bound": "hbm", "achieved": g, "peak": peak_hbm, "unit": "GB/s",
+                             "frac": g / peak_hbm, "peak_kind": peak_kind, "traffic": None},
+            }
+            del c
+
+    # e2e: host buffers, copies inside the timed region (primary precision)
+    e2e = None
+    if not args.no_e2e:
+        c = setup("fp64")
+        hu = torch.as_tensor(u0_np).pin_memory()
+        hk = torch.as_tensor(k_np).pin_memory()
+        hout = torch.empty_like(hu).pin_memory()
+        tms = []
+        for it in range(args.warmup + args.steps):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            c["u"].copy_(hu, non_blocking=True)
+            c["k"].copy_(hk, non_blocking=True)
+            job(c)
+            hout.copy_(c["u"], non_blocking=True)
+            e1.record(stream)
+            e1.synchronize()
+            if it >= args.warmup:
+                tms.append(e0.elapsed_time(e1))
+        e2e = {"value": cell_stages * len(tms) / (np.sum(tms) / 1e3), "unit": UNIT,
+               "h2d_bytes_per_step": hu.numel() * 8 + hk.numel() * 8,
+               "d2h_bytes_per_step": hout.numel() * 8,
+               "rel_l2_vs_device_run": float(np.linalg.norm(hout.numpy() - u64) / np.linalg.norm(u64))}
+        del c
+
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic (seeded GRF conductivity and initial state)",
+        "config": {"workload": "varkappa2d: 2D var-kappa diffusion 2048^2 periodic, FRKC2 s=64, 100 steps, FP64",
+                   "grid": [n, n], "s": s, "nsteps": nsteps, "cell_stages_per_step": cell_stages,
+                   "kernel": "k = 1 streaming pass (FP64)", "l2": "flushed between timed steps (256 MiB write)",
+                   "parallelism": f"replicas x{world}"},
+        "roofline": roofline,
+        "variants": variants,
+        "e2e": e2e,
+        "clocks": clk,
+        "gpu_launches": launches,
+    }
+    if rank == 0 and not args.no_cpu_baseline and world == 1:
+        out["cpu_baseline"] = cpu_baseline(args.cpu_stages)
+        if not args.no_variants:
+            out["error_vs_oracle"] = error_vs_oracle(torch, F, dev)
+    return out
+
+
+def cpu_baseline(stages: int):
+    from oracle import frkc2_oracle as O
+
+    u0, k = inputs()
+    pr = dict(ndim=2, dx=1.0, bc="periodic", kappa="field", kappa_c=1.0, kappa_p=2.5, kappa_field=k)
+    a = O.plan(CFG["s"])["a"][:stages]
+    dt = CFG["cfl"] * O.beta(CFG["s"]) / O.rho_bound(pr)
+    t = time.perf_counter()
+    O.frkc2_step(u0, a, dt, pr, 1)
+    el = time.perf_counter() - t
+    n = CFG["n"]
+    return {"value": n * n * stages / el, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"first {stages} of the 6400 stages of the 2048^2 FP64 job (numpy, one thread), {el:.1f} s"}
+
+
+def error_vs_oracle(torch, F, dev, n=1024):
+    """Relative L2 of one full FRKC2 step (s = 64) per precision against the FP64 oracle,
+    on a 1024^2 instance of the same recipe (the oracle takes ~8 s for it)."""
+    from oracle import frkc2_oracle as O
+
+    u0, k = inputs(n)
+    s = CFG["s"]
+    plan = F.frkc2_plan(s)
+    res = {}
+    for prec in ("fp64", "fp32", "mixed"):
+        kk = k if prec == "fp64" else k.astype(np.float32).astype(np.float64)
+        uu = u0 if prec != "fp32" else u0.astype(np.float32).astype(np.float64)
+        pr = dict(ndim=2, dx=1.0, bc="periodic", kappa="field", kappa_c=1.0, kappa_p=2.5, kappa_field=kk)
+        dt = CFG["cfl"] * O.beta(s) / O.rho_bound(pr)
+        ref = O.frkc2_step(uu, O.plan(s)["a"], dt, pr, 1)
+        sd = torch.float32 if prec == "fp32" else torch.float64
+        kd = torch.float64 if prec == "fp64" else torch.float32
+        u = torch.as_tensor(u0, dtype=sd, device=dev)
+        kt = torch.as_tensor(k, dtype=kd, device=dev)
+        lp = F.make_problem(2, (n, n), 1.0, "periodic", "field", prec, kappa_field=kt)
+        ws = torch.empty(F.frkc2_workspace_size(lp), dtype=torch.uint8, device=dev)
+        F.frkc2_workspace_reset(ws)
+        F.frkc2_step(plan, lp, dt, 1, 0.0, u, ws)
+        got = u.double().cpu().numpy()
+        res[prec] = float(np.linalg.norm(got - ref) / np.linalg.norm(ref))
+    res["sample"] = "one step (64 stages) on a 1024^2 instance of the recipe"
+    return res
+
+
+def run_reference(args, rank, world):
+    """The oracle timed on the host cores, each step a bounded sample of the workload."""
+    if rank != 0:
+        return None
+    from oracle import frkc2_oracle as O
+
+    u0, k = inputs()
+    pr = dict(ndim=2, dx=1.0, bc="periodic", kappa="field", kappa_c=1.0, kappa_p=2.5, kappa_field=k)
+    stages = args.cpu_stages
+    a = O.plan(CFG["s"])["a"][:stages]
+    dt = CFG["cfl"] * O.beta(CFG["s"]) / O.rho_bound(pr)
+    for _ in range(args.warmup):
+        O.frkc2_step(u0, a, dt, pr, 1)
+    times = []
+    for _ in range(args.steps):
+        t = time.perf_counter()
+        O.frkc2_step(u0, a, dt, pr, 1)
+        times.append(time.perf_counter() - t)
+    n = CFG["n"]
+    v = n * n * stages * len(times) / sum(times)
+    sample = f"each step: the first {stages} of the 6400 stages of the 2048^2 FP64 job (numpy, one thread)"
+    return {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / len(times),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (seeded GRF conductivity and initial state)",
+            "config": {"workload": "varkappa2d: 2D var-kappa diffusion 2048^2 periodic, FRKC2 s=64, 100 steps, FP64",
+                       "grid": [n, n], "s": CFG["s"], "sampled_stages_per_step": stages},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--cpu-stages", type=int, default=16)
+    ap.add_argument("--no-variants", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        out = run_reference(args, rank, world)
+        if out is not None:
+            print(json.dumps(out), flush=True)
+        return
+    if world > 1:
+        import torch
+        torch.cuda.set_device(local_rank)
+        torch.distributed.init_process_group("nccl")
+    out = run_ours(args, rank, world, local_rank)
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        import torch
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()
