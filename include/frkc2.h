@@ -148,6 +148,27 @@ frkc2_status frkc2_step(frkc2_plan_t plan, const frkc2_problem* prob, double dt,
                         double rho, void* u, void* ws, size_t ws_bytes,
                         const frkc2_tuning* tune, void* stream);
 
+/* ---- Forward step without a workspace -------------------------------------------------
+ * The paper has no counterpart: this is a service for callers that cannot allocate device
+ * memory -- for example a plugin whose host application owns every device allocation, or
+ * code running while the caller's allocator is locked -- and so cannot pass the workspace
+ * frkc2_step asks for.  Same arguments and result as frkc2_step with the default tuning,
+ * but the workspace is a fixed array of FRKC2_NOALLOC_SCRATCH_BYTES built into the library
+ * (every GPU that loads the library holds it until the process exits).  The call allocates
+ * nothing: no cudaMalloc, no cudaFree, no allocating library routine.
+ *   - Problems whose workspace (frkc2_workspace_size) exceeds the array are rejected with
+ *     FRKC2_ENOMEM before any work is queued (e.g. FP64 2D grids up to about 590^2 cells,
+ *     FP32 2D grids up to about 830^2 cells).
+ *   - The first call on a device looks up the array's device address (cudaGetSymbolAddress)
+ *     with that device current; make that first call before any stream capture.
+ *   - Every call shares the one array and it keeps the last call's contents; the call
+ *     clears the status word itself.  Calls whose work overlaps on the GPU (different
+ *     streams, or different host threads on the same device) race on the array: serialise
+ *     them.  The device status word is not returned: check the output for non-finite values. */
+#define FRKC2_NOALLOC_SCRATCH_BYTES ((size_t)16 << 20)
+frkc2_status frkc2_step_noalloc(frkc2_plan_t plan, const frkc2_problem* prob, double dt,
+                                int nsteps, double rho, void* u, void* stream);
+
 /* ---- Adjoint (reverse replay of Eq. 13) ------------------------------------------------
  * Gradients of a scalar J(u(T_end)) after nsteps steps from u0, given g = dJ/du(T_end).
  * The forward run keeps u every ckpt_every steps; each segment of ckpt_every steps is

@@ -51,6 +51,7 @@ _sig = {
     "frkc2_workspace_status": (C.c_int, [_P, _P]),
     "frkc2_step": (C.c_int, [_P, C.POINTER(frkc2_problem), C.c_double, C.c_int, C.c_double, _P, _P,
                              C.c_size_t, C.POINTER(frkc2_tuning), _P]),
+    "frkc2_step_noalloc": (C.c_int, [_P, C.POINTER(frkc2_problem), C.c_double, C.c_int, C.c_double, _P, _P]),
     "frkc2_adjoint_workspace_size": (C.c_int, [_P, C.POINTER(frkc2_problem), C.c_int, C.c_int,
                                                C.POINTER(C.c_size_t)]),
     "frkc2_adjoint": (C.c_int, [_P, C.POINTER(frkc2_problem), C.c_double, C.c_int, C.c_int, _P, _P, _P,
@@ -211,6 +212,15 @@ def frkc2_step(plan: Plan, prob: frkc2_problem, dt: float, nsteps: int, rho: flo
                            _ptr(ws), ws.numel() * ws.element_size(),
                            C.byref(tune) if tune is not None else None, _stream_ptr(stream)),
            "frkc2_step")
+
+
+def frkc2_step_noalloc(plan: Plan, prob: frkc2_problem, dt: float, nsteps: int, rho: float, u, stream=None):
+    """frkc2_step with the library's built-in scratch array instead of a caller workspace."""
+    _check(_lib.frkc2_step_noalloc(plan.handle, C.byref(prob), float(dt), int(nsteps), float(rho), _ptr(u),
+                                   _stream_ptr(stream)), "frkc2_step_noalloc")
+
+
+NOALLOC_SCRATCH_BYTES = 16 << 20
 
 
 def frkc2_adjoint_workspace_size(plan: Plan, prob: frkc2_problem, nsteps: int, ckpt_every: int) -> int:
