@@ -1,0 +1,50 @@
+"""torch.autograd wrapper: FRKC2 steps as a differentiable function of (u0, kappa).
+
+The forward runs ``frkc2_step``; the backward runs ``frkc2_adjoint`` (the discrete adjoint
+of the stage loop, with its own checkpoints every ``ckpt_every`` steps and per-segment stage
+recompute) and returns dJ/du0 and, for a conductivity field, dJ/dkappa.  Both run in the
+CUDA library; this module only allocates the workspaces and passes pointers.
+"""
+from __future__ import annotations
+
+import torch
+
+from . import frkc2 as F
+
+
+class FRKC2Steps(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, u0, kappa, plan, ndim, bc, precision, dx, dt, nsteps, ckpt_every):
+        n = tuple(reversed(u0.shape))
+        prob = F.make_problem(ndim, n, dx, bc, "field", precision, kappa_field=kappa)
+        u = u0.detach().clone().contiguous()
+        ws = torch.empty(F.frkc2_workspace_size(prob), dtype=torch.uint8, device=u0.device)
+        F.frkc2_workspace_reset(ws)
+        F.frkc2_step(plan, prob, dt, nsteps, 0.0, u, ws)
+        ctx.save_for_backward(u0.detach(), kappa.detach())
+        ctx.cfg = (plan, ndim, bc, precision, dx, dt, nsteps, ckpt_every)
+        return u
+
+    @staticmethod
+    def backward(ctx, g):
+        u0, kappa = ctx.saved_tensors
+        plan, ndim, bc, precision, dx, dt, nsteps, ckpt_every = ctx.cfg
+        n = tuple(reversed(u0.shape))
+        prob = F.make_problem(ndim, n, dx, bc, "field", precision, kappa_field=kappa)
+        ws = torch.empty(F.frkc2_adjoint_workspace_size(plan, prob, nsteps, ckpt_every),
+                         dtype=torch.uint8, device=u0.device)
+        du0 = torch.empty_like(u0)
+        dk = torch.empty_like(kappa) if ctx.needs_input_grad[1] else None
+        F.frkc2_adjoint(plan, prob, dt, nsteps, ckpt_every, u0, g.contiguous().to(u0.dtype), du0, dk, ws)
+        return du0, dk, None, None, None, None, None, None, None, None
+
+
+def frkc2_steps(u0, kappa, plan, dt, nsteps, bc="periodic", precision=None, dx=1.0, ckpt_every=8):
+    """Differentiable FRKC2 integration of div(kappa grad u) for a conductivity field.
+
+    u0, kappa: CUDA tensors of the grid shape (numpy order, last axis x); double for FP64,
+    float state and kappa for FP32, double state and float kappa for MIXED.
+    """
+    if precision is None:
+        precision = "fp64" if u0.dtype == torch.float64 else "fp32"
+    return FRKC2Steps.apply(u0, kappa, plan, u0.dim(), bc, precision, dx, dt, nsteps, ckpt_every)
