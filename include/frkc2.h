@@ -82,6 +82,10 @@ typedef struct {
   int tile_z;
   int kernel;        /* 0 = library choice, 1 = generic shared-memory tile kernel,
                         2 = 2D streaming kernel (k = 1 only), 3 = 2D register-blocked kernel  */
+  long long wait_limit; /* batched launch: polls a device wait makes before it gives up and
+                        latches FRKC2_ETIMEOUT (0 = library default, 2^22 polls)           */
+  int fault_inject;  /* batched launch, testing only: 1 = the first dependent work item waits
+                        on a counter nothing advances, so the wait must run out             */
 } frkc2_tuning;
 
 /* ---- Plan (host, FP64) --------------------------------------------------------------

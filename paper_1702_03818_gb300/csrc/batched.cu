@@ -1,21 +1,532 @@
-// Batched persistent forward step over many independent 2D problems.
+// Batched forward step: many independent 2D problems advanced by ONE persistent launch.
+//
+// Each problem i has its own grid (nx, ny), conductivity field, stage order (plan, s_i),
+// dt_i and step count; stages are grouped into passes of k (the pass of Sec. 3, Eq. 13
+// applied k times in shared memory, as in the generic tile kernel).  Problem i needs
+// T_i = nsteps_i * ceil(s_i / k) passes of N_i tiles.  The work list is a sequence of
+// rounds: round r holds, for every problem with T_i > r, all N_i tiles of its pass r
+// (problems sorted by T_i, largest first, so the active problems of a round are a prefix).
+// CTAs take items in list order from an atomic ticket; an item of pass r waits until the
+// problem's completion counter shows all N_i tiles of pass r-1 done (which also means every
+// read of the buffer that pass r overwrites is finished).  Every item a CTA waits for was
+// taken earlier by a running CTA that does not wait on anything later, so the waits end;
+// each wait is still bounded (polls counted) and on expiry the launch latches
+// FRKC2_ETIMEOUT in the status word, raises an abort word and every CTA returns.
+//
+// State buffers are rewritten by other CTAs within the launch, so state loads bypass L1
+// (ld.global.cg); a finished tile is published with a device-scope fence before its counter
+// increment.
+#include <algorithm>
+#include <cmath>
+#include <mutex>
+#include <numeric>
+#include <unordered_map>
+#include <vector>
+
+#include <cuda_runtime.h>
+
 #include "frkc2.h"
 #include "frkc2_internal.h"
 
+namespace frkc2 {
+
+frkc2_status validate_problem(const frkc2_problem* p);
+
+namespace {
+
+constexpr int BT_THREADS = 256;
+constexpr long long DEFAULT_WAIT_LIMIT = 1ll << 22;
+
+struct BProb {
+  int nx, ny;
+  int tiles_x, ntiles;
+  int s, passes_per_step, total_passes, extra_copy;
+  const void* fx;
+  const void* fy;
+  void* u;
+  void* ua;
+  void* va;
+  void* ub;
+  void* vb;
+  const double* coef;  // (ca, cb) per stage, dt a_l / dx^2
+};
+
+struct BHeader {
+  int nprob, nrounds, bc, tx, ty, k, fault_inject;
+  long long total_items;
+  long long wait_limit;
+  const BProb* probs;            // sorted by total passes, largest first
+  const long long* round_off;    // nrounds + 1 item offsets
+  const long long* cum_tiles;    // nprob + 1 tile prefix sums (sorted order)
+  unsigned* status;
+  unsigned long long* ticket;
+  unsigned* abort_flag;
+  unsigned* done;                // per problem: tiles completed
+};
+
+__device__ __forceinline__ int wrap_b(int g, int n) {
+  int r = g % n;
+  return r < 0 ? r + n : r;
+}
+
+template <class S>
+__device__ __forceinline__ S load_cg(const S* p) {
+  return __ldcg(p);
+}
+
+// state set read by pass r (r >= 1 reads A for odd r, B for even r; pass 0 reads u)
+__device__ __forceinline__ void pass_buffers(const BProb& P, int r, const void*& Uin, const void*& Vin,
+                                             void*& Uout, void*& Vout, int& l0, int& kq, int k) {
+  const int last = P.total_passes + P.extra_copy - 1;
+  if (r < P.total_passes) {
+    const int q = r % P.passes_per_step;
+    l0 = q * k;
+    kq = min(k, P.s - l0);
+    Uin = r == 0 ? P.u : ((r & 1) ? P.ua : P.ub);
+    Vin = (r == 0 || q == 0) ? nullptr : ((r & 1) ? P.va : P.vb);
+    const bool step_end = q == P.passes_per_step - 1;
+    if (r == last) {
+      Uout = P.u;
+      Vout = nullptr;
+    } else {
+      Uout = ((r + 1) & 1) ? P.ua : P.ub;
+      Vout = step_end ? nullptr : (((r + 1) & 1) ? P.va : P.vb);
+    }
+  } else {  // the copy pass of a problem with a single pass: A -> u
+    l0 = 0;
+    kq = 0;
+    Uin = P.ua;
+    Vin = nullptr;
+    Uout = P.u;
+    Vout = nullptr;
+  }
+}
+
+template <class S, class A>
+__global__ void __launch_bounds__(BT_THREADS) k_batched(const BHeader h) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ long long s_item;
+  __shared__ int s_prob, s_tile, s_round, s_ok;
+  const int tid = threadIdx.x;
+  const bool periodic = h.bc == FRKC2_BC_PERIODIC;
+  while (true) {
+    if (tid == 0) {
+      s_item = (long long)atomicAdd(h.ticket, 1ull);
+      s_ok = 1;
+      if (s_item < h.total_items && !*((volatile unsigned*)h.abort_flag)) {
+        // decode (round, problem, tile)
+        int lo = 0, hi = h.nrounds;  // largest r with round_off[r] <= item
+        while (hi - lo > 1) {
+          const int mid = (lo + hi) >> 1;
+          if (h.round_off[mid] <= s_item) lo = mid; else hi = mid;
+        }
+        const long long rem = s_item - h.round_off[lo];
+        int plo = 0, phi = h.nprob;
+        while (phi - plo > 1) {
+          const int mid = (plo + phi) >> 1;
+          if (h.cum_tiles[mid] <= rem) plo = mid; else phi = mid;
+        }
+        s_round = lo;
+        s_prob = plo;
+        s_tile = int(rem - h.cum_tiles[plo]);
+        // wait for the previous pass of this problem
+        const BProb& P = h.probs[plo];
+        unsigned need = unsigned(lo) * unsigned(P.ntiles);
+        if (h.fault_inject && lo > 0) need = 0xffffffffu;  // a target nothing reaches
+        if (lo > 0) {
+          long long polls = 0;
+          while (*((volatile unsigned*)&h.done[plo]) < need) {
+            if (*((volatile unsigned*)h.abort_flag) || ++polls > h.wait_limit) {
+              atomicOr(h.status, ST_TIMEOUT);
+              atomicExch(h.abort_flag, 1u);
+              s_ok = 0;
+              break;
+            }
+            __nanosleep(64);
+          }
+          __threadfence();
+        }
+      } else {
+        s_ok = 0;
+        s_item = h.total_items;
+      }
+    }
+    __syncthreads();
+    if (s_item >= h.total_items || !s_ok) break;
+    const BProb& P = h.probs[s_prob];
+    const void* Uin_v;
+    const void* Vin_v;
+    void* Uout_v;
+    void* Vout_v;
+    int l0, kq;
+    pass_buffers(P, s_round, Uin_v, Vin_v, Uout_v, Vout_v, l0, kq, h.k);
+    const S* Uin = static_cast<const S*>(Uin_v);
+    const S* Vin = static_cast<const S*>(Vin_v);
+    const A* FX = static_cast<const A*>(P.fx);
+    const A* FY = static_cast<const A*>(P.fy);
+    const int nx = P.nx, ny = P.ny;
+    const int tyi = s_tile / P.tiles_x, txi = s_tile - tyi * P.tiles_x;
+    const int RX = h.tx + 2 * kq, RY = h.ty + 2 * kq, R = RX * RY;
+    S* ub0 = reinterpret_cast<S*>(smem);
+    S* vb0 = ub0 + R;
+    S* ub1 = vb0 + R;
+    S* vb1 = ub1 + R;
+    A* fxs = reinterpret_cast<A*>(vb1 + R);
+    A* fys = fxs + R;
+    const int x0 = txi * h.tx - kq, y0 = tyi * h.ty - kq;
+    for (int idx = tid; idx < R; idx += BT_THREADS) {
+      const int y = idx / RX, x = idx - y * RX;
+      const int gx = x0 + x, gy = y0 + y;
+      S uu = S(0), vv = S(0);
+      A a0 = A(0), a1 = A(0);
+      if (periodic) {
+        const int wx = wrap_b(gx, nx), wy = wrap_b(gy, ny);
+        const size_t g = size_t(wy) * nx + wx;
+        uu = load_cg(Uin + g);
+        if (Vin) vv = load_cg(Vin + g);
+        a0 = FX[size_t(wy) * (nx + 1) + wx];
+        a1 = FY[size_t(wy) * nx + wx];
+      } else {
+        const bool inx = gx >= 0 && gx < nx, iny = gy >= 0 && gy < ny;
+        if (inx && iny) {
+          const size_t g = size_t(gy) * nx + gx;
+          uu = load_cg(Uin + g);
+          if (Vin) vv = load_cg(Vin + g);
+        }
+        if (iny && gx >= 0 && gx <= nx) a0 = FX[size_t(gy) * (nx + 1) + gx];
+        if (inx && gy >= 0 && gy <= ny) a1 = FY[size_t(gy) * nx + gx];
+      }
+      ub0[idx] = uu;
+      vb0[idx] = vv;
+      ub1[idx] = S(0);
+      vb1[idx] = S(0);
+      fxs[idx] = a0;
+      fys[idx] = a1;
+    }
+    __syncthreads();
+    for (int j = 1; j <= kq; ++j) {
+      const S* us = (j & 1) ? ub0 : ub1;
+      const S* vs = (j & 1) ? vb0 : vb1;
+      S* ud = (j & 1) ? ub1 : ub0;
+      S* vd = (j & 1) ? vb1 : vb0;
+      const S ca = S(P.coef[2 * (l0 + j - 1)]), cb = S(P.coef[2 * (l0 + j - 1) + 1]);
+      const int w = RX - 2 * j, hgt = RY - 2 * j;
+      for (int idx = tid; idx < w * hgt; idx += BT_THREADS) {
+        const int y = j + idx / w, x = j + idx % w;
+        const int i = y * RX + x;
+        if (!periodic) {
+          const int gx = x0 + x, gy = y0 + y;
+          if (gx < 0 || gx >= nx || gy < 0 || gy >= ny) {
+            ud[i] = S(0);
+            vd[i] = S(0);
+            continue;
+          }
+        }
+        const S Uc = us[i], Vc = vs[i];
+        const A fe = fxs[i + 1], fw = fxs[i], fn = fys[i + RX], fs = fys[i];
+        const A fR = fe * A(us[i + 1] - Uc) + fw * A(us[i - 1] - Uc) + fn * A(us[i + RX] - Uc) +
+                     fs * A(us[i - RX] - Uc);
+        const A fI = fe * A(vs[i + 1] - Vc) + fw * A(vs[i - 1] - Vc) + fn * A(vs[i + RX] - Vc) +
+                     fs * A(vs[i - RX] - Vc);
+        ud[i] = Uc + ca * S(fR) - cb * S(fI);
+        vd[i] = Vc + ca * S(fI) + cb * S(fR);
+      }
+      __syncthreads();
+    }
+    const S* uf = (kq & 1) ? ub1 : ub0;
+    const S* vf = (kq & 1) ? vb1 : vb0;
+    S* Uout = static_cast<S*>(Uout_v);
+    S* Vout = static_cast<S*>(Vout_v);
+    const int ox = txi * h.tx, oy = tyi * h.ty;
+    const int ex = min(h.tx, nx - ox), ey = min(h.ty, ny - oy);
+    bool bad = false;
+    for (int idx = tid; idx < ex * ey; idx += BT_THREADS) {
+      const int y = idx / ex, x = idx - y * ex;
+      const int i = (y + kq) * RX + (x + kq);
+      const size_t g = size_t(oy + y) * nx + (ox + x);
+      const S uu = uf[i];
+      Uout[g] = uu;
+      if (Vout) Vout[g] = vf[i];
+      if (!Vout && !isfinite(double(uu))) bad = true;
+    }
+    if (bad) atomicOr(h.status, ST_NONFINITE);
+    __threadfence();
+    __syncthreads();
+    if (tid == 0) atomicAdd(&h.done[s_prob], 1u);
+  }
+}
+
+struct LaunchCfg {
+  int precision;
+  size_t smem;
+  int grid;
+  void* counters;
+  size_t counter_bytes;
+  BHeader header;
+};
+
+std::mutex g_mu;
+std::unordered_map<void*, LaunchCfg> g_cfg;
+
+struct BatchPlanHost {
+  std::vector<int> order;         // sorted problem indices
+  std::vector<BProb> probs;       // sorted
+  std::vector<long long> round_off, cum_tiles;
+  std::vector<double> coef;       // all problems' (ca, cb)
+  std::vector<size_t> coef_off;   // per sorted problem, in doubles
+  size_t off_hdr, off_probs, off_round, off_cum, off_coef, off_counters, off_faces, off_states, total;
+  size_t counter_bytes;
+  int nrounds;
+  long long total_items;
+};
+
+frkc2_status batch_geometry(int nprob, const frkc2_plan_t* plans, const frkc2_problem* probs, const int* nsteps,
+                            const frkc2_tuning* tune, int* k_out, int* tx_out, int* ty_out) {
+  if (nprob < 1 || !plans || !probs || !nsteps) return FRKC2_EINVAL;
+  const frkc2_problem& p0 = probs[0];
+  for (int i = 0; i < nprob; ++i) {
+    const frkc2_status v = validate_problem(&probs[i]);
+    if (v != FRKC2_OK) return v;
+    if (!plans[i] || nsteps[i] < 1) return FRKC2_EINVAL;
+    if (probs[i].ndim != 2 || probs[i].kappa_kind == FRKC2_KAPPA_POWER) return FRKC2_EUNSUPPORTED;
+    if (probs[i].precision != p0.precision || probs[i].bc != p0.bc) return FRKC2_EINVAL;
+  }
+  int k = (tune && tune->k) ? tune->k : (p0.precision == FRKC2_FP32 ? 4 : 2);
+  int tx = (tune && tune->tile_x) ? tune->tile_x : 64;
+  int ty = (tune && tune->tile_y) ? tune->tile_y : (p0.precision == FRKC2_FP32 ? 32 : 16);
+  if (k < 1 || k > KMAX || tx < 1 || ty < 1) return FRKC2_EINVAL;
+  const size_t smem = size_t(tx + 2 * k) * (ty + 2 * k) * (4 * state_bytes(p0.precision) + 2 * arith_bytes(p0.precision));
+  if (smem > 200 * 1024) return FRKC2_EINVAL;
+  *k_out = k;
+  *tx_out = tx;
+  *ty_out = ty;
+  return FRKC2_OK;
+}
+
+frkc2_status batch_plan(int nprob, const frkc2_plan_t* plans, const frkc2_problem* probs, const double* dt,
+                        const int* nsteps, const frkc2_tuning* tune, BatchPlanHost& B, int& k, int& tx, int& ty) {
+  frkc2_status v = batch_geometry(nprob, plans, probs, nsteps, tune, &k, &tx, &ty);
+  if (v != FRKC2_OK) return v;
+  const size_t SB = state_bytes(probs[0].precision), AB = arith_bytes(probs[0].precision);
+  std::vector<int> T(nprob);
+  for (int i = 0; i < nprob; ++i) {
+    const int P = (plans[i]->s + k - 1) / k;
+    T[i] = nsteps[i] * P;
+  }
+  B.order.resize(nprob);
+  std::iota(B.order.begin(), B.order.end(), 0);
+  std::stable_sort(B.order.begin(), B.order.end(), [&](int a, int b) { return T[a] > T[b]; });
+  B.probs.resize(nprob);
+  B.cum_tiles.assign(nprob + 1, 0);
+  B.coef.clear();
+  B.coef_off.resize(nprob);
+  for (int r = 0; r < nprob; ++r) {
+    const int i = B.order[r];
+    const frkc2_problem& p = probs[i];
+    BProb& P = B.probs[r];
+    P.nx = int(p.n[0]);
+    P.ny = int(p.n[1]);
+    P.tiles_x = (P.nx + tx - 1) / tx;
+    P.ntiles = P.tiles_x * ((P.ny + ty - 1) / ty);
+    P.s = plans[i]->s;
+    P.passes_per_step = (P.s + k - 1) / k;
+    P.total_passes = T[i];
+    P.extra_copy = T[i] == 1 ? 1 : 0;
+    B.cum_tiles[r + 1] = B.cum_tiles[r] + P.ntiles;
+    B.coef_off[r] = B.coef.size();
+    const double h2 = p.dx * p.dx;
+    if (dt) {
+      if (!(dt[i] > 0.0) || !std::isfinite(dt[i])) return FRKC2_EINVAL;
+      for (int l = 0; l < P.s; ++l) {
+        B.coef.push_back(dt[i] * plans[i]->a_re[l] / h2);
+        B.coef.push_back(dt[i] * plans[i]->a_im[l] / h2);
+      }
+    } else {
+      B.coef.resize(B.coef.size() + 2 * size_t(P.s), 0.0);
+    }
+  }
+  const int maxT = B.probs[0].total_passes + B.probs[0].extra_copy;
+  B.nrounds = maxT;
+  B.round_off.assign(maxT + 1, 0);
+  for (int r = 0; r < maxT; ++r) {
+    int active = 0;
+    while (active < nprob && B.probs[active].total_passes + B.probs[active].extra_copy > r) ++active;
+    B.round_off[r + 1] = B.round_off[r] + B.cum_tiles[active];
+  }
+  B.total_items = B.round_off[maxT];
+  // workspace layout
+  size_t off = 256;  // status word
+  B.off_hdr = off;
+  off += 256;
+  B.off_probs = off;
+  off += align256(sizeof(BProb) * nprob);
+  B.off_round = off;
+  off += align256(sizeof(long long) * (maxT + 1));
+  B.off_cum = off;
+  off += align256(sizeof(long long) * (nprob + 1));
+  B.off_coef = off;
+  off += align256(sizeof(double) * B.coef.size());
+  B.off_counters = off;  // ticket (8 B), abort (4 B), done[nprob]
+  B.counter_bytes = 16 + sizeof(unsigned) * size_t(nprob);
+  off += align256(B.counter_bytes);
+  B.off_faces = off;
+  for (int r = 0; r < nprob; ++r) {
+    const BProb& P = B.probs[r];
+    off += align256(size_t(P.ny) * (P.nx + 1) * AB) + align256(size_t(P.ny + 1) * P.nx * AB);
+  }
+  B.off_states = off;
+  for (int r = 0; r < nprob; ++r) {
+    const BProb& P = B.probs[r];
+    off += 4 * align256(size_t(P.nx) * P.ny * SB);
+  }
+  B.total = off;
+  return FRKC2_OK;
+}
+
+int persistent_grid(int precision, size_t smem) {
+  int dev = 0, sms = 152, per = 1;
+  if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaError_t e;
+  if (precision == FRKC2_FP64)
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_batched<double, double>, BT_THREADS, smem);
+  else if (precision == FRKC2_FP32)
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_batched<float, float>, BT_THREADS, smem);
+  else
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_batched<double, float>, BT_THREADS, smem);
+  if (e != cudaSuccess || per < 1) per = 1;
+  return sms * per;
+}
+
+template <class S, class A>
+cudaError_t set_smem(size_t smem) {
+  if (smem <= 48 * 1024) return cudaSuccess;
+  return cudaFuncSetAttribute(k_batched<S, A>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+}
+
+}  // namespace
+}  // namespace frkc2
+
+using namespace frkc2;
+
 extern "C" {
 
-frkc2_status frkc2_batch_workspace_size(int, const frkc2_plan_t*, const frkc2_problem*, const int*,
-                                        const frkc2_tuning*, size_t*) {
-  return FRKC2_EUNSUPPORTED;
+frkc2_status frkc2_batch_workspace_size(int nprob, const frkc2_plan_t* plans, const frkc2_problem* probs,
+                                        const int* nsteps, const frkc2_tuning* tune, size_t* bytes) {
+  if (!bytes) return FRKC2_EINVAL;
+  BatchPlanHost B;
+  int k, tx, ty;
+  const frkc2_status v = batch_plan(nprob, plans, probs, nullptr, nsteps, tune, B, k, tx, ty);
+  if (v != FRKC2_OK) return v;
+  *bytes = B.total;
+  return FRKC2_OK;
 }
-frkc2_status frkc2_batch_prepare(int, const frkc2_plan_t*, const frkc2_problem*, const double*, const int*,
-                                 void* const*, const frkc2_tuning*, void*, size_t, void*) {
-  return FRKC2_EUNSUPPORTED;
+
+frkc2_status frkc2_batch_prepare(int nprob, const frkc2_plan_t* plans, const frkc2_problem* probs,
+                                 const double* dt, const int* nsteps, void* const* u, const frkc2_tuning* tune,
+                                 void* ws, size_t ws_bytes, void* stream) {
+  if (!dt || !u || !ws || (reinterpret_cast<uintptr_t>(ws) & 255)) return FRKC2_EINVAL;
+  BatchPlanHost B;
+  int k, tx, ty;
+  frkc2_status v = batch_plan(nprob, plans, probs, dt, nsteps, tune, B, k, tx, ty);
+  if (v != FRKC2_OK) return v;
+  if (ws_bytes < B.total) return FRKC2_ENOMEM;
+  for (int i = 0; i < nprob; ++i)
+    if (!u[i]) return FRKC2_EINVAL;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  char* base = static_cast<char*>(ws);
+  const int prec = probs[0].precision;
+  const size_t SB = state_bytes(prec), AB = arith_bytes(prec);
+  // per-problem pointers and face conductivities
+  size_t fo = B.off_faces, so = B.off_states;
+  for (int r = 0; r < nprob; ++r) {
+    BProb& P = B.probs[r];
+    const int i = B.order[r];
+    void* fx = base + fo;
+    fo += align256(size_t(P.ny) * (P.nx + 1) * AB);
+    void* fy = base + fo;
+    fo += align256(size_t(P.ny + 1) * P.nx * AB);
+    P.fx = fx;
+    P.fy = fy;
+    const size_t sb = align256(size_t(P.nx) * P.ny * SB);
+    P.ua = base + so;
+    P.va = base + so + sb;
+    P.ub = base + so + 2 * sb;
+    P.vb = base + so + 3 * sb;
+    so += 4 * sb;
+    P.u = u[i];
+    P.coef = reinterpret_cast<const double*>(base + B.off_coef) + B.coef_off[r];
+    if (launch_faces(probs[i], fx, fy, nullptr, st) != cudaSuccess) return FRKC2_ECUDA;
+  }
+  BHeader h{};
+  h.nprob = nprob;
+  h.nrounds = B.nrounds;
+  h.bc = probs[0].bc;
+  h.tx = tx;
+  h.ty = ty;
+  h.k = k;
+  h.fault_inject = tune ? tune->fault_inject : 0;
+  h.total_items = B.total_items;
+  h.wait_limit = (tune && tune->wait_limit > 0) ? tune->wait_limit : DEFAULT_WAIT_LIMIT;
+  h.probs = reinterpret_cast<const BProb*>(base + B.off_probs);
+  h.round_off = reinterpret_cast<const long long*>(base + B.off_round);
+  h.cum_tiles = reinterpret_cast<const long long*>(base + B.off_cum);
+  h.status = reinterpret_cast<unsigned*>(base);
+  h.ticket = reinterpret_cast<unsigned long long*>(base + B.off_counters);
+  h.abort_flag = reinterpret_cast<unsigned*>(base + B.off_counters + 8);
+  h.done = reinterpret_cast<unsigned*>(base + B.off_counters + 16);
+  auto up = [&](size_t off, const void* src, size_t n) {
+    return n == 0 || cudaMemcpyAsync(base + off, src, n, cudaMemcpyHostToDevice, st) == cudaSuccess;
+  };
+  if (!up(B.off_probs, B.probs.data(), sizeof(BProb) * nprob) ||
+      !up(B.off_round, B.round_off.data(), sizeof(long long) * B.round_off.size()) ||
+      !up(B.off_cum, B.cum_tiles.data(), sizeof(long long) * B.cum_tiles.size()) ||
+      !up(B.off_coef, B.coef.data(), sizeof(double) * B.coef.size()))
+    return FRKC2_ECUDA;
+  // the pageable-source copies above are staged before they return; make the uploads
+  // complete before the host vectors go out of scope
+  if (cudaStreamSynchronize(st) != cudaSuccess) return FRKC2_ECUDA;
+  LaunchCfg cfg{};
+  cfg.precision = prec;
+  cfg.smem = size_t(tx + 2 * k) * (ty + 2 * k) * (4 * SB + 2 * AB);
+  cudaError_t e = prec == FRKC2_FP64 ? set_smem<double, double>(cfg.smem)
+                                     : (prec == FRKC2_FP32 ? set_smem<float, float>(cfg.smem) : set_smem<double, float>(cfg.smem));
+  if (e != cudaSuccess) return FRKC2_ECUDA;
+  cfg.grid = persistent_grid(prec, cfg.smem);
+  if (cfg.grid > B.total_items) cfg.grid = int(B.total_items);
+  cfg.counters = base + B.off_counters;
+  cfg.counter_bytes = B.counter_bytes;
+  cfg.header = h;
+  std::lock_guard<std::mutex> lk(g_mu);
+  g_cfg[ws] = cfg;
+  return FRKC2_OK;
 }
-frkc2_status frkc2_batch_launch(void*, void*) { return FRKC2_EUNSUPPORTED; }
-frkc2_status frkc2_step_batched(int, const frkc2_plan_t*, const frkc2_problem*, const double*, const int*,
-                                void* const*, const frkc2_tuning*, void*, size_t, void*) {
-  return FRKC2_EUNSUPPORTED;
+
+frkc2_status frkc2_batch_launch(void* ws, void* stream) {
+  if (!ws) return FRKC2_EINVAL;
+  LaunchCfg cfg;
+  {
+    std::lock_guard<std::mutex> lk(g_mu);
+    auto it = g_cfg.find(ws);
+    if (it == g_cfg.end()) return FRKC2_EINVAL;  // not prepared
+    cfg = it->second;
+  }
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (cudaMemsetAsync(cfg.counters, 0, cfg.counter_bytes, st) != cudaSuccess) return FRKC2_ECUDA;
+  switch (cfg.precision) {
+    case FRKC2_FP64: k_batched<double, double><<<cfg.grid, BT_THREADS, cfg.smem, st>>>(cfg.header); break;
+    case FRKC2_FP32: k_batched<float, float><<<cfg.grid, BT_THREADS, cfg.smem, st>>>(cfg.header); break;
+    default: k_batched<double, float><<<cfg.grid, BT_THREADS, cfg.smem, st>>>(cfg.header); break;
+  }
+  count_launch();
+  return cudaGetLastError() == cudaSuccess ? FRKC2_OK : FRKC2_ECUDA;
+}
+
+frkc2_status frkc2_step_batched(int nprob, const frkc2_plan_t* plans, const frkc2_problem* probs, const double* dt,
+                                const int* nsteps, void* const* u, const frkc2_tuning* tune, void* ws,
+                                size_t ws_bytes, void* stream) {
+  const frkc2_status v = frkc2_batch_prepare(nprob, plans, probs, dt, nsteps, u, tune, ws, ws_bytes, stream);
+  if (v != FRKC2_OK) return v;
+  return frkc2_batch_launch(ws, stream);
 }
 
 }  // extern "C"

@@ -36,7 +36,7 @@ class frkc2_problem(C.Structure):
 
 class frkc2_tuning(C.Structure):
     _fields_ = [("k", C.c_int), ("tile_x", C.c_int), ("tile_y", C.c_int), ("tile_z", C.c_int),
-                ("kernel", C.c_int)]
+                ("kernel", C.c_int), ("wait_limit", C.c_longlong), ("fault_inject", C.c_int)]
 
 
 _P = C.c_void_p
@@ -178,11 +178,14 @@ def make_problem(ndim: int, n, dx: float, bc="periodic", kappa="field", precisio
     return p
 
 
-def make_tuning(k: int = 0, tile=(0, 0, 0), kernel: int = 0) -> frkc2_tuning:
+def make_tuning(k: int = 0, tile=(0, 0, 0), kernel: int = 0, wait_limit: int = 0,
+                fault_inject: int = 0) -> frkc2_tuning:
     t = frkc2_tuning()
     t.k = int(k)
     t.tile_x, t.tile_y, t.tile_z = (int(v) for v in (list(tile) + [0, 0, 0])[:3])
     t.kernel = int(kernel)
+    t.wait_limit = int(wait_limit)
+    t.fault_inject = int(fault_inject)
     return t
 
 

@@ -1,0 +1,134 @@
+"""GPU parity of the batched persistent launch (frkc2_step_batched / batch_prepare + batch_launch)
+against the FP64 oracle, CUDA-graph replay, and the bounded device wait (fault injected on
+the device side with a counter nothing advances -- the wait runs out, nothing hangs)."""
+import numpy as np
+import pytest
+
+from oracle import frkc2_oracle as O
+from helpers import oracle_problem, rel_l2, seeded_case
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+F = pytest.importorskip("paper_1702_03818_gb300.frkc2")
+
+DT = {"fp64": torch.float64, "fp32": torch.float32, "mixed": torch.float64}
+KDT = {"fp64": torch.float64, "fp32": torch.float32, "mixed": torch.float32}
+TOL = {"fp64": 1e-11, "fp32": 1e-4, "mixed": 1e-6}
+
+
+def make_batch(prec, bc, specs, seed0=900):
+    """specs: list of (ny, nx, s, nsteps)."""
+    items = []
+    for i, (ny, nx, s, nsteps) in enumerate(specs):
+        u0, field = seeded_case((ny, nx), bc, "field", seed0 + 3 * i)
+        fo = field if prec == "fp64" else field.astype(np.float32).astype(np.float64)
+        opr = oracle_problem(2, bc, "field", 1.0, fo)
+        dt = 0.9 * O.beta(s) / O.rho_bound(opr)
+        kt = torch.as_tensor(field, dtype=KDT[prec], device="cuda")
+        pr = F.make_problem(2, (nx, ny), 1.0, bc, "field", prec, kappa_field=kt)
+        items.append(dict(u0=u0, opr=opr, dt=dt, s=s, nsteps=nsteps, pr=pr,
+                          u=torch.as_tensor(u0, dtype=DT[prec], device="cuda")))
+    return items
+
+
+def oracle_results(items, prec):
+    out = []
+    for it in items:
+        u0 = it["u0"] if prec != "fp32" else it["u0"].astype(np.float32).astype(np.float64)
+        out.append(O.frkc2_step(u0, O.plan(it["s"])["a"], it["dt"], it["opr"], it["nsteps"]))
+    return out
+
+
+SPECS = [(20, 33, 8, 2), (64, 64, 16, 1), (150, 97, 32, 2), (7, 5, 8, 3), (40, 128, 16, 1),
+         (90, 90, 8, 1), (31, 17, 32, 1), (128, 40, 16, 2)]
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "mixed"])
+@pytest.mark.parametrize("bc", ["periodic", "dirichlet"])
+def test_batched_matches_oracle(prec, bc):
+    items = make_batch(prec, bc, SPECS)
+    plans = [F.frkc2_plan(it["s"]) for it in items]
+    tune = F.make_tuning(k=8 if prec == "fp32" else 4)  # s = 8, nsteps = 1 gives a single pass
+    nst = [it["nsteps"] for it in items]
+    ws = torch.empty(F.frkc2_batch_workspace_size(plans, [it["pr"] for it in items], nst, tune),
+                     dtype=torch.uint8, device="cuda")
+    F.frkc2_workspace_reset(ws)
+    F.frkc2_launch_count()
+    F.frkc2_step_batched(plans, [it["pr"] for it in items], [it["dt"] for it in items], nst,
+                         [it["u"] for it in items], ws, tune)
+    assert F.frkc2_workspace_status(ws) == F.OK
+    refs = oracle_results(items, prec)
+    for it, ref in zip(items, refs):
+        err = rel_l2(it["u"].double().cpu().numpy(), ref)
+        assert err < TOL[prec], (it["u"].shape, it["s"], it["nsteps"], err)
+
+
+def test_batched_cuda_graph_replay():
+    prec = "fp32"
+    items = make_batch(prec, "periodic", SPECS[:5], seed0=950)
+    plans = [F.frkc2_plan(it["s"]) for it in items]
+    probs = [it["pr"] for it in items]
+    nst = [it["nsteps"] for it in items]
+    ws = torch.empty(F.frkc2_batch_workspace_size(plans, probs, nst), dtype=torch.uint8, device="cuda")
+    F.frkc2_workspace_reset(ws)
+    us = [it["u"] for it in items]
+    u0s = [u.clone() for u in us]
+    F.frkc2_batch_prepare(plans, probs, [it["dt"] for it in items], nst, us, ws)
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        F.frkc2_batch_launch(ws, stream=s)  # eager launch on the capture stream first
+    torch.cuda.current_stream().wait_stream(s)
+    torch.cuda.synchronize()
+    eager = [u.clone() for u in us]
+    g = torch.cuda.CUDAGraph()
+    for u, u0 in zip(us, u0s):
+        u.copy_(u0)
+    torch.cuda.synchronize()
+    with torch.cuda.graph(g):
+        F.frkc2_batch_launch(ws, stream=torch.cuda.current_stream())
+    for _ in range(2):
+        for u, u0 in zip(us, u0s):
+            u.copy_(u0)
+        g.replay()
+        torch.cuda.synchronize()
+        for u, e in zip(us, eager):
+            assert torch.equal(u, e)
+    assert F.frkc2_workspace_status(ws) == F.OK
+    refs = oracle_results(items, prec)
+    for it, ref in zip(items, refs):
+        assert rel_l2(it["u"].double().cpu().numpy(), ref) < TOL[prec]
+
+
+def test_batched_bounded_wait_reports_timeout():
+    """A dependent work item waits on a counter nothing advances: the wait gives up after its
+    poll limit, the launch returns, and the status word reads FRKC2_ETIMEOUT."""
+    items = make_batch("fp32", "periodic", [(64, 64, 16, 2), (32, 48, 16, 3)], seed0=970)
+    plans = [F.frkc2_plan(it["s"]) for it in items]
+    probs = [it["pr"] for it in items]
+    nst = [it["nsteps"] for it in items]
+    tune = F.make_tuning(k=4, wait_limit=2000, fault_inject=1)
+    ws = torch.empty(F.frkc2_batch_workspace_size(plans, probs, nst, tune), dtype=torch.uint8, device="cuda")
+    F.frkc2_workspace_reset(ws)
+    F.frkc2_step_batched(plans, probs, [it["dt"] for it in items], nst, [it["u"] for it in items], ws, tune)
+    assert F.frkc2_workspace_status(ws) == F.ETIMEOUT
+    # the context is still usable: a normal launch on a fresh workspace succeeds
+    tune_ok = F.make_tuning(k=4)
+    ws2 = torch.empty_like(ws)
+    F.frkc2_workspace_reset(ws2)
+    for it in items:
+        it["u"].copy_(torch.as_tensor(it["u0"], dtype=torch.float32, device="cuda"))
+    F.frkc2_step_batched(plans, probs, [it["dt"] for it in items], nst, [it["u"] for it in items], ws2, tune_ok)
+    assert F.frkc2_workspace_status(ws2) == F.OK
+
+
+def test_batched_rejects_mixed_kinds():
+    items = make_batch("fp64", "periodic", SPECS[:2])
+    plans = [F.frkc2_plan(it["s"]) for it in items]
+    p2 = F.make_problem(2, (16, 16), 1.0, "periodic", "const", "fp32", kappa_c=1.0)
+    with pytest.raises(F.Frkc2Error):
+        F.frkc2_batch_workspace_size(plans, [items[0]["pr"], p2], [1, 1])
+    p3 = F.make_problem(3, (8, 8, 8), 1.0, "periodic", "const", "fp64", kappa_c=1.0)
+    with pytest.raises(F.Frkc2Error) as e:
+        F.frkc2_batch_workspace_size(plans, [items[0]["pr"], p3], [1, 1])
+    assert e.value.status == F.EUNSUPPORTED
