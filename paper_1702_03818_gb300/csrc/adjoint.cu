@@ -244,7 +244,7 @@ __global__ void k_store_grad(const double* __restrict__ acc, A* __restrict__ out
 }
 
 struct AdjLayout {
-  size_t status, fx, fy, fz, ckpt, tape, lam, dk, total;
+  size_t status, fx, fy, fz, fen, ckpt, tape, lam, dk, total;
   int nseg;
 };
 
@@ -261,6 +261,8 @@ AdjLayout adj_layout(const frkc2_problem& p, int s, int nsteps, int c) {
   off += align256(F.nfy * A);
   L.fz = off;
   off += align256(F.nfz * A);
+  L.fen = off;
+  if (p.ndim == 2 && p.kappa_kind != FRKC2_KAPPA_POWER) off += align256(face_pair_bytes(p));
   L.ckpt = off;  // nseg + 1 real states
   off += size_t(L.nseg + 1) * align256(N * S);
   L.tape = off;  // c steps x s stages x (U, V)
@@ -316,6 +318,8 @@ frkc2_status frkc2_adjoint(frkc2_plan_t plan, const frkc2_problem* prob, double 
 
   if (p.kappa_kind != FRKC2_KAPPA_POWER) {
     if (launch_faces(p, base + L.fx, base + L.fy, base + L.fz, st) != cudaSuccess) return FRKC2_ECUDA;
+    if (p.ndim == 2 && launch_face_pairs(p, base + L.fx, base + L.fy, base + L.fen, st) != cudaSuccess)
+      return FRKC2_ECUDA;
   }
   if (dJdkappa && cudaMemsetAsync(base + L.dk, 0, N * sizeof(double), st) != cudaSuccess) return FRKC2_ECUDA;
   auto ckpt = [&](int j) { return base + L.ckpt + size_t(j) * slot; };
@@ -366,9 +370,11 @@ frkc2_status frkc2_adjoint(frkc2_plan_t plan, const frkc2_problem* prob, double 
           a.V_out = nullptr;
         }
         a.check_finite = l + 1 == s;
+        a.in_mode = l == 0 ? PASS_IO_REAL : PASS_IO_PLANAR;
+        a.out_mode = l + 1 < s ? PASS_IO_PLANAR : PASS_IO_REAL;
         a.ca[0] = dt * plan->a_re[l] / h2;
         a.cb[0] = dt * plan->a_im[l] / h2;
-        const cudaError_t e = stream2d ? launch_pass_stream2d(p, a, st) : launch_pass_generic(p, a, st);
+        const cudaError_t e = stream2d ? launch_pass_stream2d(p, a, base + L.fen, st) : launch_pass_generic(p, a, st);
         if (e != cudaSuccess) return false;
       }
     }

@@ -40,6 +40,8 @@ StepLayout step_layout(const frkc2_problem& p) {
   off += align256(F.nfy * A);
   s.fz = off;
   off += align256(F.nfz * A);
+  s.fen = off;  // face pairs of the 2D streaming pass
+  if (p.ndim == 2 && p.kappa_kind != FRKC2_KAPPA_POWER) off += align256(face_pair_bytes(p));
   s.ua = off;
   off += align256(N * S);
   s.va = off;
@@ -69,7 +71,7 @@ void default_tiles(const frkc2_problem& p, int k, int* tx, int* ty, int* tz) {
 
 static int default_k(const frkc2_problem& p) {
   if (p.ndim == 1) return 16;
-  if (p.ndim == 2) return p.precision == FRKC2_FP32 ? 4 : 1;
+  if (p.ndim == 2) return (p.precision == FRKC2_FP32 && p.kappa_kind != FRKC2_KAPPA_POWER) ? 8 : 1;
   return 1;
 }
 
@@ -180,14 +182,19 @@ frkc2_status frkc2_step(frkc2_plan_t plan, const frkc2_problem* prob, double dt,
   const int kern = tune ? tune->kernel : 0;
   if (kern < 0 || kern > 3) return FRKC2_EINVAL;
   const bool stream_ok = p.ndim == 2 && p.kappa_kind != FRKC2_KAPPA_POWER && k == 1;
-  bool use_stream2d = false;
+  const bool tb_ok = tb2d_supported(p, k);
+  bool use_stream2d = false, use_tb = false;
   if (kern == 2) {
     if (!stream_ok) return FRKC2_EUNSUPPORTED;
     use_stream2d = true;
   } else if (kern == 3) {
-    return FRKC2_EUNSUPPORTED;
+    if (!tb_ok) return FRKC2_EUNSUPPORTED;
+    use_tb = true;
   } else if (kern == 0) {
-    use_stream2d = stream_ok;
+    if (tb_ok && k > 1)
+      use_tb = true;
+    else
+      use_stream2d = stream_ok;
   }
   if (use_stream2d && !(tune && tune->tile_y)) ty = 64;
   {
@@ -198,7 +205,7 @@ frkc2_status frkc2_step(frkc2_plan_t plan, const frkc2_problem* prob, double dt,
     probe.hx = k;
     probe.hy = p.ndim >= 2 ? k : 0;
     probe.hz = p.ndim >= 3 ? k : 0;
-    if (!use_stream2d && generic_smem_bytes(p, probe) > size_t(smem_optin())) return FRKC2_EINVAL;
+    if (!use_stream2d && !use_tb && generic_smem_bytes(p, probe) > size_t(smem_optin())) return FRKC2_EINVAL;
   }
   if (nsteps == 0) return FRKC2_OK;
 
@@ -233,6 +240,31 @@ frkc2_status frkc2_step(frkc2_plan_t plan, const frkc2_problem* prob, double dt,
 
   const void* curU = u;
   const void* curV = nullptr;
+  if (use_stream2d) {
+    // interleaved complex state between passes: W buffers at ua (with va) and ub (with vb)
+    if (launch_face_pairs(p, base + L.fx, base + L.fy, base + L.fen, st) != cudaSuccess) return FRKC2_ECUDA;
+    a.k = 1;
+    a.hx = a.hy = 1;
+    a.hz = 0;
+    for (int n = 0; n < nsteps; ++n) {
+      for (int l = 0; l < s; ++l) {
+        const bool first = l == 0, last = l == s - 1;
+        a.U_in = first ? u : curU;
+        a.V_in = nullptr;
+        a.in_mode = first ? PASS_IO_REAL : PASS_IO_COMPLEX;
+        void* outW = (curU == ua) ? ub : ua;
+        a.U_out = last ? u : outW;
+        a.V_out = nullptr;
+        a.out_mode = last ? PASS_IO_REAL : PASS_IO_COMPLEX;
+        a.check_finite = last ? 1 : 0;
+        a.ca[0] = dt * plan->a_re[l] / h2;
+        a.cb[0] = dt * plan->a_im[l] / h2;
+        if (launch_pass_stream2d(p, a, base + L.fen, st) != cudaSuccess) return FRKC2_ECUDA;
+        curU = last ? u : outW;
+      }
+    }
+    return FRKC2_OK;
+  }
   for (int n = 0; n < nsteps; ++n) {
     for (int q = 0; q < npass; ++q) {
       const int l0 = q * k;
@@ -257,7 +289,7 @@ frkc2_status frkc2_step(frkc2_plan_t plan, const frkc2_problem* prob, double dt,
         a.ca[j] = dt * plan->a_re[l0 + j] / h2;
         a.cb[j] = dt * plan->a_im[l0 + j] / h2;
       }
-      const cudaError_t e = use_stream2d ? launch_pass_stream2d(p, a, st) : launch_pass_generic(p, a, st);
+      const cudaError_t e = use_tb ? launch_pass_tb2d(p, a, st) : launch_pass_generic(p, a, st);
       if (e != cudaSuccess) return FRKC2_ECUDA;
       curU = outU;
       curV = outV;

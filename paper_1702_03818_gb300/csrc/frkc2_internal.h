@@ -25,6 +25,12 @@ constexpr int KMAX = 16;                 // most stages in one pass
 constexpr unsigned ST_NONFINITE = 1u;    // status word bits
 constexpr unsigned ST_TIMEOUT = 2u;
 
+// state layouts a pass reads or writes (the streaming pass honours them; the tile kernels
+// always use planar U, V)
+constexpr int PASS_IO_REAL = 0;     // U only (imaginary part zero on input, dropped on output)
+constexpr int PASS_IO_PLANAR = 1;   // separate U and V arrays
+constexpr int PASS_IO_COMPLEX = 2;  // one interleaved (U, V) array at U_in / U_out
+
 inline size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
 
 // One k-stage pass over the grid: read (U, V), apply k stages, write (U, V).
@@ -35,6 +41,7 @@ struct PassArgs {
   int hx, hy, hz;         // halo width per axis: k along present axes, 0 otherwise
   int k;                  // stages in this pass
   int check_finite;       // flag non-finite outputs in the status word
+  int in_mode, out_mode;  // PASS_IO_* (streaming pass only)
   const void* U_in;       // real part of the pass input
   const void* V_in;       // imaginary part; nullptr = zero (first pass of a step)
   void* U_out;
@@ -57,7 +64,7 @@ FaceLayout faces_layout(const frkc2_problem& p);
 
 // Workspace layout of frkc2_step (byte offsets from the workspace base).
 struct StepLayout {
-  size_t status, fx, fy, fz, ua, va, ub, vb, total;
+  size_t status, fx, fy, fz, fen, ua, va, ub, vb, total;
 };
 StepLayout step_layout(const frkc2_problem& p);
 
@@ -69,7 +76,11 @@ size_t cells(const frkc2_problem& p);
 cudaError_t launch_faces(const frkc2_problem& p, void* fx, void* fy, void* fz, cudaStream_t st);
 cudaError_t launch_rho(const frkc2_problem& p, const void* u, double* rho_dev, cudaStream_t st);
 cudaError_t launch_pass_generic(const frkc2_problem& p, const PassArgs& a, cudaStream_t st);
-cudaError_t launch_pass_stream2d(const frkc2_problem& p, const PassArgs& a, cudaStream_t st);
+cudaError_t launch_pass_stream2d(const frkc2_problem& p, const PassArgs& a, const void* fen, cudaStream_t st);
+size_t face_pair_bytes(const frkc2_problem& p);
+cudaError_t launch_face_pairs(const frkc2_problem& p, const void* fx, const void* fy, void* out, cudaStream_t st);
+cudaError_t launch_pass_tb2d(const frkc2_problem& p, const PassArgs& a, cudaStream_t st);
+bool tb2d_supported(const frkc2_problem& p, int k);
 size_t generic_smem_bytes(const frkc2_problem& p, const PassArgs& a);
 void default_tiles(const frkc2_problem& p, int k, int* tx, int* ty, int* tz);
 

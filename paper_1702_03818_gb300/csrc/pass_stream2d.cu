@@ -3,16 +3,25 @@
 //
 // Each warp owns 31 consecutive columns plus one halo lane on the low-x side and walks rows
 // upward.  Every face flux kappa_f (W_nb - W_c) is computed once and used by both cells of
-// the face: the x flux of a lane's east face reaches the next lane through a warp shuffle
-// (the halo lane supplies the chunk's west edge), and the y flux of a cell's north face is
-// carried in registers as the next row's south flux.  Per cell and stage this leaves 2
+// the face: the x flux through a lane's east face reaches the next lane through a warp
+// shuffle (the halo lane supplies the chunk's west edge), and the y flux through a cell's
+// north face is carried in registers to the next row.  Per cell and stage this leaves 2
 // differences, 2 products and 3 sums for each of U and V plus 4 fused multiply-adds for the
 // complex update -- 18 floating-point instructions, which is what bounds the FP64 path on
 // GB300 (its FP64 pipe issues 2 lanes per clock per SM, far below its memory system).
+// Fluxes are combined by subtraction, never by an explicit negation.
+//
+// Memory: the stage state between passes is stored interleaved (U, V) so one 16-byte (FP64)
+// load brings a cell's complex value, and each cell's east and north face conductivities
+// are read as one pair from a face-pair array; a step's first pass reads the real state and
+// its last pass writes it.  Planar (U, V) input and output are also accepted (the adjoint's
+// stage tape uses them).
 //
 // Work split: the grid is persistent (every CTA resident) and the (column chunk, row)
 // pairs, chunk-major, are cut into one contiguous range per warp, so every SM gets the same
 // number of cell updates.  A range that crosses into the next chunk restarts the stream.
+#include <algorithm>
+
 #include <cuda_runtime.h>
 
 #include "frkc2_internal.h"
@@ -25,6 +34,10 @@ constexpr int ST_WARPS = ST_THREADS / 32;
 constexpr int ST_COLS = 31;  // output columns per warp
 constexpr int ST_MIN_BLOCKS = 6;
 
+template <class T> struct Vec2;
+template <> struct Vec2<double> { using type = double2; };
+template <> struct Vec2<float> { using type = float2; };
+
 __device__ __forceinline__ bool nonfinite_bits(double v) {
   return (__double2hiint(v) & 0x7ff00000) == 0x7ff00000;
 }
@@ -34,19 +47,23 @@ __device__ __forceinline__ bool nonfinite_bits(float v) {
 
 template <class S, class A, bool PERIODIC>
 __global__ void __launch_bounds__(ST_THREADS, ST_MIN_BLOCKS)
-    k_stream2d(const PassArgs p, int ncolw, long long total, long long nwarps_grid) {
+    k_stream2d(const PassArgs p, const void* __restrict__ fen_v, int ncolw, long long total,
+               long long nwarps_grid) {
+  using S2 = typename Vec2<S>::type;
+  using A2 = typename Vec2<A>::type;
   const int lane = threadIdx.x & 31;
   const long long gw = (long long)blockIdx.x * ST_WARPS + (threadIdx.x >> 5);
   const int nx = p.nx, ny = p.ny;
   long long idx = gw * total / nwarps_grid;
   const long long end = (gw + 1) * total / nwarps_grid;
-  const S* __restrict__ U = static_cast<const S*>(p.U_in);
-  const S* __restrict__ V = static_cast<const S*>(p.V_in);
-  const A* __restrict__ FX = static_cast<const A*>(p.fx);
-  const A* __restrict__ FY = static_cast<const A*>(p.fy);
+  const A2* __restrict__ FEN = static_cast<const A2*>(fen_v);  // [(ny+1)][(nx+1)], index (y+1, x+1)
+  const int in_mode = p.in_mode, out_mode = p.out_mode;
+  const S* __restrict__ Ur = static_cast<const S*>(p.U_in);
+  const S* __restrict__ Vr = static_cast<const S*>(p.V_in);
+  const S2* __restrict__ Wi = static_cast<const S2*>(p.U_in);
   S* __restrict__ Uo = static_cast<S*>(p.U_out);
   S* __restrict__ Vo = static_cast<S*>(p.V_out);
-  const bool hasV = V != nullptr;
+  S2* __restrict__ Wo = static_cast<S2*>(p.U_out);
   const S ca = S(p.ca[0]), cb = S(p.cb[0]);
   bool bad = false;
 
@@ -57,7 +74,7 @@ __global__ void __launch_bounds__(ST_THREADS, ST_MIN_BLOCKS)
     idx += y1 - y0;
     const int x = wcol * ST_COLS + lane - 1;
 
-    // column read by this lane, and whether it holds a real cell
+    // column read by this lane (wrapped when periodic) and whether it holds a real cell
     int xr;
     bool xin;
     if (PERIODIC) {
@@ -67,9 +84,6 @@ __global__ void __launch_bounds__(ST_THREADS, ST_MIN_BLOCKS)
       xr = x;
       xin = x >= 0 && x < nx;
     }
-    // east face of the lane's cell: face index xr + 1 (x faces have nx + 1 entries per row)
-    const bool has_east_face = PERIODIC ? true : (x >= -1 && x < nx);
-    const int xe_face = PERIODIC ? xr + 1 : x + 1;
     // lane 31 reads its east neighbour itself
     int xeast;
     bool eastin;
@@ -80,68 +94,110 @@ __global__ void __launch_bounds__(ST_THREADS, ST_MIN_BLOCKS)
       xeast = x + 1;
       eastin = xeast >= 0 && xeast < nx;
     }
+    // the lane's face-pair column (x = -1 is the Dirichlet west boundary, column 0)
+    const bool has_faces = PERIODIC || (x >= -1 && x < nx);
+    const int fcol = (PERIODIC ? xr : x) + 1;
     const bool out_ok = lane >= 1 && x >= 0 && x < nx;
 
-    auto load = [&](const S* __restrict__ P, int yy, int xx, bool inx) -> S {
+    auto load = [&](int yy, int xx, bool inx) -> S2 {
+      S2 w;
+      w.x = S(0);
+      w.y = S(0);
+      int yw = yy;
       if (PERIODIC) {
-        const int yw = yy < 0 ? yy + ny : (yy >= ny ? yy - ny : yy);
-        return P[size_t(yw) * nx + xx];
+        yw = yy < 0 ? yy + ny : (yy >= ny ? yy - ny : yy);
+      } else if (!(inx && yy >= 0 && yy < ny)) {
+        return w;
       }
-      return (inx && yy >= 0 && yy < ny) ? P[size_t(yy) * nx + xx] : S(0);
+      const size_t g = size_t(yw) * nx + xx;
+      if (in_mode == PASS_IO_COMPLEX) {
+        w = __ldg(Wi + g);
+      } else {
+        w.x = __ldg(Ur + g);
+        if (in_mode == PASS_IO_PLANAR) w.y = __ldg(Vr + g);
+      }
+      return w;
     };
-    // y face j (between rows j-1 and j) of this lane's column
-    auto yface = [&](int j) -> A {
-      if (PERIODIC) return FY[size_t(j) * nx + xr];
-      return xin ? FY[size_t(j) * nx + xr] : A(0);
+    // face pair (east face, north face) of the cell in row yy of this lane's column
+    auto faces = [&](int yy) -> A2 {
+      A2 f;
+      f.x = A(0);
+      f.y = A(0);
+      if (PERIODIC) yy = yy < 0 ? yy + ny : (yy >= ny ? yy - ny : yy);
+      if (!has_faces) return f;
+      return __ldg(FEN + size_t(yy + 1) * (nx + 1) + fcol);
     };
 
-    // prime the stream: the cell row y0 and the flux through its south face
-    S Uc = load(U, y0, xr, xin);
-    S Vc = hasV ? load(V, y0, xr, xin) : S(0);
-    A FsU, FsV;
+    // prime the stream: row y0 and the flux into row y0 - 1 through its north face
+    S2 Wc = load(y0, xr, xin);
+    A PnU, PnV;
     {
-      const S Us = load(U, y0 - 1, xr, xin);
-      const S Vs = hasV ? load(V, y0 - 1, xr, xin) : S(0);
-      const A ks = yface(y0);
-      FsU = ks * A(Us - Uc);
-      FsV = ks * A(Vs - Vc);
+      const S2 Ws = load(y0 - 1, xr, xin);
+      const A ks = faces(y0 - 1).y;
+      PnU = ks * A(Wc.x - Ws.x);
+      PnV = ks * A(Wc.y - Ws.y);
     }
+#pragma unroll 2
     for (int y = y0; y < y1; ++y) {
-      const S Un = load(U, y + 1, xr, xin);
-      const S Vn = hasV ? load(V, y + 1, xr, xin) : S(0);
-      const A kn = yface(y + 1);
-      const A ke = has_east_face ? FX[size_t(y) * (nx + 1) + xe_face] : A(0);
-      S Ue = __shfl_down_sync(0xffffffffu, Uc, 1);
-      S Ve = __shfl_down_sync(0xffffffffu, Vc, 1);
+      const S2 Wn = load(y + 1, xr, xin);
+      const A2 f = faces(y);
+      S Ue = __shfl_down_sync(0xffffffffu, Wc.x, 1);
+      S Ve = __shfl_down_sync(0xffffffffu, Wc.y, 1);
       if (lane == 31) {
-        Ue = load(U, y, xeast, eastin);
-        Ve = hasV ? load(V, y, xeast, eastin) : S(0);
+        const S2 We = load(y, xeast, eastin);
+        Ue = We.x;
+        Ve = We.y;
       }
-      const A FnU = kn * A(Un - Uc), FnV = kn * A(Vn - Vc);
-      const A FeU = ke * A(Ue - Uc), FeV = ke * A(Ve - Vc);
-      const A FwU = -__shfl_up_sync(0xffffffffu, FeU, 1);
-      const A FwV = -__shfl_up_sync(0xffffffffu, FeV, 1);
-      const A fU = (FeU + FwU) + (FnU + FsU);
-      const A fV = (FeV + FwV) + (FnV + FsV);
-      const S un = Uc + ca * S(fU) - cb * S(fV);
-      const S vn = Vc + ca * S(fV) + cb * S(fU);
+      // fluxes into this cell through its east and north faces
+      const A FeU = f.x * A(Ue - Wc.x), FeV = f.x * A(Ve - Wc.y);
+      const A FnU = f.y * A(Wn.x - Wc.x), FnV = f.y * A(Wn.y - Wc.y);
+      // through the west face: minus the west neighbour's east flux; through the south
+      // face: minus the north flux of the row below
+      const A wU = __shfl_up_sync(0xffffffffu, FeU, 1);
+      const A wV = __shfl_up_sync(0xffffffffu, FeV, 1);
+      const A fU = (FeU - wU) + (FnU - PnU);
+      const A fV = (FeV - wV) + (FnV - PnV);
+      const S un = Wc.x + ca * S(fU) - cb * S(fV);
+      const S vn = Wc.y + ca * S(fV) + cb * S(fU);
       if (out_ok) {
         const size_t g = size_t(y) * nx + x;
-        Uo[g] = un;
-        if (Vo) Vo[g] = vn;
+        if (out_mode == PASS_IO_COMPLEX) {
+          S2 w;
+          w.x = un;
+          w.y = vn;
+          Wo[g] = w;
+        } else {
+          Uo[g] = un;
+          if (out_mode == PASS_IO_PLANAR) Vo[g] = vn;
+        }
         if (p.check_finite) bad |= nonfinite_bits(un);
       }
-      FsU = -FnU;
-      FsV = -FnV;
-      Uc = Un;
-      Vc = Vn;
+      PnU = FnU;
+      PnV = FnV;
+      Wc = Wn;
     }
   }
   if (bad) atomicOr(p.status, ST_NONFINITE);
 }
 
+// Face pairs for the streaming pass: FEN(y, x) = (x face x+1 of row y, y face y+1 of column x)
+// for y, x in [-1, n), stored at ((y+1)(nx+1) + x+1); entries with no such face are 0.
+template <class A>
+__global__ void k_face_pairs(const A* __restrict__ fx, const A* __restrict__ fy, void* out, int nx, int ny) {
+  using A2 = typename Vec2<A>::type;
+  A2* F = static_cast<A2*>(out);
+  const size_t total = size_t(ny + 1) * (nx + 1);
+  for (size_t t = blockIdx.x * size_t(blockDim.x) + threadIdx.x; t < total; t += size_t(gridDim.x) * blockDim.x) {
+    const int y = int(t / (nx + 1)) - 1, x = int(t % (nx + 1)) - 1;
+    A2 v;
+    v.x = y >= 0 ? fx[size_t(y) * (nx + 1) + (x + 1)] : A(0);
+    v.y = x >= 0 ? fy[size_t(y + 1) * nx + x] : A(0);
+    F[t] = v;
+  }
+}
+
 template <class S, class A, bool PERIODIC>
-cudaError_t launch_t(const PassArgs& a, cudaStream_t st) {
+cudaError_t launch_t(const PassArgs& a, const void* fen, cudaStream_t st) {
   static int blocks_per_sm = 0, sms = 0;
   auto kern = k_stream2d<S, A, PERIODIC>;
   if (!blocks_per_sm) {
@@ -157,23 +213,40 @@ cudaError_t launch_t(const PassArgs& a, cudaStream_t st) {
   long long grid = (long long)sms * blocks_per_sm;
   const long long max_useful = (total + ST_WARPS - 1) / ST_WARPS;
   if (grid > max_useful) grid = max_useful;
-  kern<<<unsigned(grid), ST_THREADS, 0, st>>>(a, ncolw, total, grid * ST_WARPS);
+  kern<<<unsigned(grid), ST_THREADS, 0, st>>>(a, fen, ncolw, total, grid * ST_WARPS);
   count_launch();
   return cudaGetLastError();
 }
 
 template <class S, class A>
-cudaError_t launch_s(const PassArgs& a, cudaStream_t st) {
-  return a.bc == FRKC2_BC_PERIODIC ? launch_t<S, A, true>(a, st) : launch_t<S, A, false>(a, st);
+cudaError_t launch_s(const PassArgs& a, const void* fen, cudaStream_t st) {
+  return a.bc == FRKC2_BC_PERIODIC ? launch_t<S, A, true>(a, fen, st) : launch_t<S, A, false>(a, fen, st);
 }
 
 }  // namespace
 
-cudaError_t launch_pass_stream2d(const frkc2_problem& p, const PassArgs& a, cudaStream_t st) {
+size_t face_pair_bytes(const frkc2_problem& p) {
+  return size_t(p.n[1] + 1) * size_t(p.n[0] + 1) * 2 * arith_bytes(p.precision);
+}
+
+cudaError_t launch_face_pairs(const frkc2_problem& p, const void* fx, const void* fy, void* out, cudaStream_t st) {
+  const int nx = int(p.n[0]), ny = int(p.n[1]);
+  const size_t total = size_t(ny + 1) * (nx + 1);
+  const int threads = 256;
+  const int blocks = int(std::min<size_t>((total + threads - 1) / threads, 152 * 16));
+  if (p.precision == FRKC2_FP64)
+    k_face_pairs<double><<<blocks, threads, 0, st>>>(static_cast<const double*>(fx), static_cast<const double*>(fy), out, nx, ny);
+  else
+    k_face_pairs<float><<<blocks, threads, 0, st>>>(static_cast<const float*>(fx), static_cast<const float*>(fy), out, nx, ny);
+  count_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pass_stream2d(const frkc2_problem& p, const PassArgs& a, const void* fen, cudaStream_t st) {
   switch (p.precision) {
-    case FRKC2_FP64: return launch_s<double, double>(a, st);
-    case FRKC2_FP32: return launch_s<float, float>(a, st);
-    default: return launch_s<double, float>(a, st);
+    case FRKC2_FP64: return launch_s<double, double>(a, fen, st);
+    case FRKC2_FP32: return launch_s<float, float>(a, fen, st);
+    default: return launch_s<double, float>(a, fen, st);
   }
 }
 

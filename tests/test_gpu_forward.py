@@ -181,3 +181,41 @@ def test_launch_count_matches_passes():
     run_gpu(plan, shape, "periodic", "field", "fp32", u0, field, 0.5, 3, tune=F.make_tuning(k=4, kernel=1))
     # one face-preparation launch plus 16/4 passes per step
     assert F.frkc2_launch_count() == 1 + 3 * 4
+
+
+TB_CASES = [
+    # shape, bc, kappa, s, nsteps, k
+    ((100, 77), "periodic", "field", 16, 2, 4),
+    ((100, 77), "periodic", "field", 16, 2, 1),
+    ((200, 130), "dirichlet", "field", 32, 2, 3),
+    ((64, 64), "periodic", "const", 64, 1, 8),
+    ((9, 13), "periodic", "field", 8, 3, 2),
+    ((9, 13), "dirichlet", "field", 8, 3, 8),
+    ((130, 300), "periodic", "field", 16, 1, 16),
+    ((57, 200), "dirichlet", "const", 32, 2, 5),
+]
+
+
+@pytest.mark.parametrize("case", TB_CASES, ids=lambda c: f"{'x'.join(map(str, c[0]))}-{c[1]}-{c[2]}-k{c[5]}")
+def test_step_parity_fp32_temporal_blocking(case):
+    """The FP32 register/shared-memory temporally blocked kernel (kernel 3)."""
+    shape, bc, kappa, s, nsteps, k = case
+    u0, field = seeded_case(shape, bc, kappa, 300 + s)
+    oplan = O.plan(s)
+    plan = F.frkc2_plan(s)
+    fo = rounded_field(field, "fp32")
+    opr = oracle_problem(2, bc, kappa, 1.0, fo)
+    dt = 0.9 * oplan["beta"] / O.rho_bound(opr, u0)
+    ref = O.frkc2_step(u0.astype(np.float32).astype(np.float64), oplan["a"], dt, opr, nsteps)
+    got, st = run_gpu(plan, shape, bc, kappa, "fp32", u0, field, dt, nsteps, tune=F.make_tuning(k=k, kernel=3))
+    assert st == F.OK
+    assert rel_l2(got, ref) < TOL["fp32"], rel_l2(got, ref)
+
+
+def test_tb_kernel_rejects_unsupported():
+    shape = (32, 32)
+    u0, field = seeded_case(shape, "periodic", "field", 5)
+    plan = F.frkc2_plan(8)
+    with pytest.raises(F.Frkc2Error) as e:
+        run_gpu(plan, shape, "periodic", "field", "fp64", u0, field, 0.1, 1, tune=F.make_tuning(k=4, kernel=3))
+    assert e.value.status == F.EUNSUPPORTED
