@@ -56,8 +56,8 @@ enum { FRKC2_KAPPA_CONST = 0, FRKC2_KAPPA_FIELD = 1, FRKC2_KAPPA_POWER = 2 };
  * and the flux arithmetic (kappa_f * difference, face sums) runs in float.               */
 enum { FRKC2_FP64 = 0, FRKC2_FP32 = 1, FRKC2_MIXED = 2 };
 
-/* Plan flags. */
-enum { FRKC2_PLAN_STRICT = 1 };
+/* Plan flags: STRICT makes an unmet Q bound an error; GREEDY / LEBEDEV force one ordering. */
+enum { FRKC2_PLAN_STRICT = 1, FRKC2_PLAN_GREEDY = 2, FRKC2_PLAN_LEBEDEV = 4 };
 
 typedef struct frkc2_plan_s* frkc2_plan_t;
 
@@ -92,15 +92,21 @@ typedef struct {
  * Step sizes a_j = 1/(M^2 alpha_M (1 - zeta_j)), L = s = 2M (Sec. 2, Eq. 8), zeta_j the
  * roots of the second-order polynomial of Eq. 7, read here as
  * R(z) = 1 - alpha/4 + (alpha/4) T_L(1 + 4z/(L^2 alpha)), alpha = 4(1 - 1/L^2)/3, so that
- * beta = (2/3)(L^2 - 1).  The stages are ordered greedily to keep the amplification
- * estimate of Eq. 12 small and the ordering is repeated over n (reduced range
- * (1 - n 1e-4) beta) until the realised Q of Eqs. 10-11 is at most 10 L^2 (Sec. 2.2).
+ * beta = (2/3)(L^2 - 1).  Stage order (Sec. 2.2): for s <= 256 the stages are ordered
+ * greedily to keep the amplification estimate of Eq. 12 small, repeated over n (reduced
+ * range (1 - n 1e-4) beta) until the realised Q of Eqs. 10-11 is at most 10 L^2; for
+ * s > 256 the upper-half roots are taken in Lebedev-Finogenov order followed by their
+ * conjugates in the same order (for s a power of two its realised Q equals the largest
+ * single factor, the least any order can reach), with the greedy n-loop as well if that
+ * order misses 10 L^2; the smaller realised Q wins.
  *   s     : number of stages, even, 2..4096.
  *   nu    : damping of Sec. 2.1; only 0 is implemented (FRKC2_EUNSUPPORTED otherwise).
  *   flags : FRKC2_PLAN_STRICT makes an unmet Q bound an error (FRKC2_EPLAN); otherwise the
- *           ordering with the smallest realised Q is kept.
+ *           ordering with the smallest realised Q is kept.  FRKC2_PLAN_GREEDY or
+ *           FRKC2_PLAN_LEBEDEV use that ordering alone (both together: FRKC2_EINVAL).
  *   out   : receives a new plan; release it with frkc2_plan_destroy.
- * Cost is O(s^3) host work (tens of ms at s = 64, seconds at s = 1024).                   */
+ * Cost: the greedy is O(s^3) host work (tens of ms at s = 64, about 1 s at s = 256); the
+ * Lebedev-Finogenov order costs O(s^2) (about 0.2 s at s = 1024).                          */
 frkc2_status frkc2_plan(int s, double nu, unsigned flags, frkc2_plan_t* out);
 
 /* A plan from caller-given ordered step sizes (a_re[l] + i a_im[l], l = 0..s-1, host arrays

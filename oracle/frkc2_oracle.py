@@ -13,7 +13,7 @@ Contents
 * stability polynomial and step sizes (Sec. 2, Eqs. 5-8): ``alpha``, ``beta``, ``roots``,
   ``step_sizes``;
 * internal stability (Sec. 2.2, Eqs. 10-12): ``realised_Q`` (brute force over all
-  sub-sequences), ``order_greedy`` and ``plan`` (the n-loop);
+  sub-sequences), ``order_greedy``, ``order_lebedev`` and ``plan`` (the n-loop);
 * the diffusion operator f(w) = div(kappa grad w) in flux form (the semi-discrete system of
   Eq. 1): ``cell_kappa``, ``apply_f``, ``rho_bound``;
 * the FRKC2 step (Sec. 3, Eq. 13), stages applied literally as complex forward-Euler steps:
@@ -30,10 +30,10 @@ of kappa(u) = 1 + c u^p), ``kappa_p`` (the exponent p) and ``kappa_field`` (cell
 array, same shape as the state).  State arrays use numpy order, last axis = x.
 
 Parity status: every function here is pinned by ``tests/test_oracle_pins.py`` except the
-ordering itself (``order_greedy``): the paper's coefficient table is not available, so the
-permutation it produces is checked only through invariants (it is a permutation, the
+greedy ordering itself (``order_greedy``): the paper's coefficient table is not available,
+so the permutation it produces is checked only through invariants (it is a permutation, the
 product is unchanged, the realised Q meets the paper's bound) -- parity unpinned for the
-exact order.
+exact greedy order.  ``order_lebedev`` is pinned by the lower bound it attains.
 """
 from __future__ import annotations
 
@@ -139,28 +139,69 @@ def order_greedy(a: np.ndarray, beta_: float, n: int, samples: int, C: float = 1
     return np.asarray(placed, dtype=np.int64)
 
 
+def lebedev_permutation(m: int) -> list:
+    """Lebedev-Finogenov recursive permutation of 0..m-1 (the ordering idea of Sec. 2.2).
+
+    P(1) = (0); P(2q) interleaves each entry v of P(q) with its mirror 2q - 1 - v;
+    P(2q + 1) = P(2q) followed by 2q.
+    """
+    if m == 1:
+        return [0]
+    if m % 2 == 0:
+        out = []
+        for v in lebedev_permutation(m // 2):
+            out += [v, m - 1 - v]
+        return out
+    return lebedev_permutation(m - 1) + [m - 1]
+
+
+def order_lebedev(L: int) -> np.ndarray:
+    """Stage order: the L/2 roots of the upper half (j < L/2) in Lebedev-Finogenov order, then
+    their conjugates (j -> L-1-j) in the same order.
+
+    On the real axis |1 + a_j x| = |1 + conj(a_j) x|, so the second half repeats the magnitudes
+    of the first; reading for large L (see ``plan``).
+    """
+    h = np.asarray(lebedev_permutation(L // 2), dtype=np.int64)
+    return np.concatenate([h, L - 1 - h])
+
+
 def plan(L: int, samples: int | None = None, q_points: int | None = None, n_max: int = 10,
-         bound: float = 10.0) -> dict:
+         bound: float = 10.0, method: str = "auto") -> dict:
     """Ordered FRKC2 step sizes for L stages (Sec. 2.2, the n-loop).
 
-    The ordering is repeated with n = 1, 2, ... until the realised Q is at most
-    ``bound`` L^2 (the paper's practical bound 10 L^2) or ``n_max`` is reached; the ordering
-    with the smallest realised Q is kept.  Reading: S = 16 L ordering samples and
+    ``greedy``: the ordering of Eq. 12 is repeated with n = 1, 2, ... until the realised Q is
+    at most ``bound`` L^2 (the paper's practical bound 10 L^2) or ``n_max`` is reached; the
+    ordering with the smallest realised Q is kept.  Reading: S = 16 L ordering samples and
     16 L + 1 points for the realised Q (the paper's L samples leave Q above 10 L^2 from
     L = 128 on).
+    ``lebedev``: ``order_lebedev``.
+    ``auto`` (reading): the greedy n-loop for L <= 256, where it meets the bound; above that
+    the Lebedev-Finogenov order, and the greedy n-loop as well only if that order misses the
+    bound (the smaller realised Q is kept).
     """
     a = step_sizes(L)
     b = beta(L)
     S = samples if samples is not None else 16 * L
     P = q_points if q_points is not None else 16 * L
     best = None
-    for n in range(1, n_max + 1):
-        perm = order_greedy(a, b, n, S)
+
+    def consider(perm, n):
+        nonlocal best
         Q = realised_Q(a[perm], b, P)
         if best is None or Q < best["Q"]:
-            best = dict(L=L, order=perm, a=a[perm], beta=b, Q=Q, n=n)
-        if Q <= bound * L * L:
-            break
+            best = dict(L=L, order=np.asarray(perm), a=a[perm], beta=b, Q=Q, n=n)
+        return Q
+
+    run_greedy = method == "greedy" or (method == "auto" and L <= 256)
+    if method == "lebedev" or (method == "auto" and L > 256):
+        q = consider(order_lebedev(L), 0)
+        if method == "auto" and q > bound * L * L:
+            run_greedy = True
+    if run_greedy:
+        for n in range(1, n_max + 1):
+            if consider(order_greedy(a, b, n, S), n) <= bound * L * L:
+                break
     return best
 
 

@@ -80,51 +80,58 @@ __device__ __forceinline__ double cell_kappa_real(const RhoArgs& a, const T* F, 
   return __dadd_rn(1.0, __dmul_rn(a.c, pow(double(F[g]), a.p)));
 }
 
-// rho = max_c (2 acc_c)/(dx*dx), acc_c = sum of face values, x axis first, low face first.
+// rho = max_c (2 acc_c)/(dx*dx), acc_c = sum of face values (kappa_c + kappa_nb)/2, x axis
+// first, low face first.  Halving and doubling are exact, so 2 acc_c equals the same running
+// sum of the unhalved pair sums (kappa_c + kappa_nb); and rounding is monotonic, so the
+// maximum may be taken before the one division by dx*dx, done once per block.
+// Each warp takes whole rows (fixed y, z) and its lanes walk x, so no index is divided.
 template <class T>
 __global__ void k_rho(const RhoArgs a) {
   const T* F = static_cast<const T*>(a.field);
   const bool periodic = a.bc == FRKC2_BC_PERIODIC;
-  const size_t N = size_t(a.nx) * a.ny * a.nz;
+  const int nx = a.nx, ny = a.ny, nz = a.nz;
+  const size_t sy = size_t(nx), sz = size_t(nx) * ny;
   const double h2 = __dmul_rn(a.dx, a.dx);
-  double best = 0.0;
-  for (size_t g = blockIdx.x * size_t(blockDim.x) + threadIdx.x; g < N;
-       g += size_t(gridDim.x) * blockDim.x) {
-    const int x = int(g % a.nx);
-    const int y = int((g / a.nx) % a.ny);
-    const int z = int(g / (size_t(a.nx) * a.ny));
-    const double kc = cell_kappa_real<T>(a, F, g);
-    double acc = 0.0;
-    const int n3[3] = {a.nx, a.ny, a.nz};
-    const int c3[3] = {x, y, z};
-    const size_t s3[3] = {1, size_t(a.nx), size_t(a.nx) * a.ny};
-    for (int d = 0; d < a.ndim; ++d) {
-      for (int side = 0; side < 2; ++side) {
-        const int nbc = side ? c3[d] + 1 : c3[d] - 1;
-        double kn;
-        if (nbc >= 0 && nbc < n3[d]) {
-          kn = cell_kappa_real<T>(a, F, side ? g + s3[d] : g - s3[d]);
-        } else if (periodic) {
-          const size_t gw = side ? g - size_t(n3[d] - 1) * s3[d] : g + size_t(n3[d] - 1) * s3[d];
-          kn = cell_kappa_real<T>(a, F, gw);
-        } else {
-          kn = a.kind == FRKC2_KAPPA_POWER ? 1.0 : kc;
-        }
-        acc = __dadd_rn(acc, __dmul_rn(0.5, __dadd_rn(kc, kn)));
+  const int lane = threadIdx.x & 31;
+  const long long warp = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const long long nwarps = (long long)gridDim.x * (blockDim.x >> 5);
+  const long long rows = (long long)ny * nz;
+  // the neighbour's conductivity, or the ghost value when it lies outside a Dirichlet grid
+  auto nb = [&](double kc, size_t g, int c, int n, size_t stride, int side) -> double {
+    const int q = side ? c + 1 : c - 1;
+    if (q >= 0 && q < n) return cell_kappa_real<T>(a, F, side ? g + stride : g - stride);
+    if (periodic) return cell_kappa_real<T>(a, F, side ? g - size_t(n - 1) * stride : g + size_t(n - 1) * stride);
+    return a.kind == FRKC2_KAPPA_POWER ? 1.0 : kc;
+  };
+  double best2 = 0.0;  // max of 2 acc_c
+  for (long long r = warp; r < rows; r += nwarps) {
+    const int y = int(r % ny), z = int(r / ny);
+    const size_t row0 = size_t(r) * nx;
+    for (int x = lane; x < nx; x += 32) {
+      const size_t g = row0 + x;
+      const double kc = cell_kappa_real<T>(a, F, g);
+      double acc2 = __dadd_rn(kc, nb(kc, g, x, nx, 1, 0));
+      acc2 = __dadd_rn(acc2, __dadd_rn(kc, nb(kc, g, x, nx, 1, 1)));
+      if (a.ndim >= 2) {
+        acc2 = __dadd_rn(acc2, __dadd_rn(kc, nb(kc, g, y, ny, sy, 0)));
+        acc2 = __dadd_rn(acc2, __dadd_rn(kc, nb(kc, g, y, ny, sy, 1)));
       }
+      if (a.ndim >= 3) {
+        acc2 = __dadd_rn(acc2, __dadd_rn(kc, nb(kc, g, z, nz, sz, 0)));
+        acc2 = __dadd_rn(acc2, __dadd_rn(kc, nb(kc, g, z, nz, sz, 1)));
+      }
+      best2 = (acc2 > best2 || acc2 != acc2) ? acc2 : best2;
     }
-    const double v = __ddiv_rn(__dmul_rn(2.0, acc), h2);
-    best = (v > best || v != v) ? v : best;
   }
   // block max, then one atomic per block on the bit pattern (non-negative doubles, and NaN,
   // order like their bits read as unsigned integers)
-  unsigned long long bits = static_cast<unsigned long long>(__double_as_longlong(best));
+  unsigned long long bits = static_cast<unsigned long long>(__double_as_longlong(best2));
   for (int o = 16; o > 0; o >>= 1) {
     const unsigned long long other = __shfl_xor_sync(0xffffffffu, bits, o);
     bits = other > bits ? other : bits;
   }
   __shared__ unsigned long long warp_best[32];
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int w = threadIdx.x >> 5;
   if (lane == 0) warp_best[w] = bits;
   __syncthreads();
   if (w == 0) {
@@ -133,7 +140,11 @@ __global__ void k_rho(const RhoArgs a) {
       const unsigned long long other = __shfl_xor_sync(0xffffffffu, bits, o);
       bits = other > bits ? other : bits;
     }
-    if (lane == 0) atomicMax(reinterpret_cast<unsigned long long*>(a.out), bits);
+    if (lane == 0) {
+      const double v = __ddiv_rn(__longlong_as_double(static_cast<long long>(bits)), h2);
+      atomicMax(reinterpret_cast<unsigned long long*>(a.out),
+                static_cast<unsigned long long>(__double_as_longlong(v)));
+    }
   }
 }
 
@@ -166,15 +177,14 @@ cudaError_t launch_rho(const frkc2_problem& p, const void* u, double* rho_dev, c
   if (e != cudaSuccess) return e;
   RhoArgs a{p.ndim, p.bc, p.kappa_kind, int(p.n[0]), int(p.n[1]), int(p.n[2]), p.kappa_c,
             p.kappa_p, p.dx, p.kappa_kind == FRKC2_KAPPA_POWER ? u : p.kappa, rho_dev};
-  const size_t N = cells(p);
   const int threads = 256;
   // the field is read in the state precision for POWER and the kappa precision otherwise
   const bool dbl = p.kappa_kind == FRKC2_KAPPA_POWER ? state_bytes(p.precision) == 8
                                                      : arith_bytes(p.precision) == 8;
   if (dbl)
-    k_rho<double><<<grid_for(N, threads), threads, 0, st>>>(a);
+    k_rho<double><<<grid_for(size_t(p.n[1]) * p.n[2] * 32, threads), threads, 0, st>>>(a);
   else
-    k_rho<float><<<grid_for(N, threads), threads, 0, st>>>(a);
+    k_rho<float><<<grid_for(size_t(p.n[1]) * p.n[2] * 32, threads), threads, 0, st>>>(a);
   count_launch();
   return cudaGetLastError();
 }

@@ -139,6 +139,31 @@ double realised_Q(const std::vector<cplx>& a, double beta, int P) {
   return std::exp(*std::max_element(best.begin(), best.end()));
 }
 
+// Lebedev-Finogenov recursive permutation of 0..m-1: P(1) = (0); P(2q) interleaves each v of
+// P(q) with 2q-1-v; P(2q+1) = P(2q) followed by 2q.
+std::vector<int> lebedev_permutation(int m) {
+  if (m == 1) return {0};
+  std::vector<int> out;
+  if (m % 2 == 0) {
+    for (int v : lebedev_permutation(m / 2)) {
+      out.push_back(v);
+      out.push_back(m - 1 - v);
+    }
+    return out;
+  }
+  out = lebedev_permutation(m - 1);
+  out.push_back(m - 1);
+  return out;
+}
+
+// The upper-half roots (j < L/2) in Lebedev-Finogenov order, then their conjugates L-1-j in
+// the same order.
+std::vector<int> order_lebedev(int L) {
+  std::vector<int> h = lebedev_permutation(L / 2), out(h);
+  for (int v : h) out.push_back(L - 1 - v);
+  return out;
+}
+
 }  // namespace
 
 extern "C" {
@@ -155,8 +180,7 @@ frkc2_status frkc2_plan(int s, double nu, unsigned flags, frkc2_plan_t* out) {
   std::vector<int> best_order;
   double best_Q = std::numeric_limits<double>::infinity();
   int best_n = 0;
-  for (int n = 1; n <= n_max; ++n) {
-    std::vector<int> ord = order_greedy(a, beta, n, S);
+  auto consider = [&](const std::vector<int>& ord, int n) {
     std::vector<cplx> ao(L);
     for (int l = 0; l < L; ++l) ao[l] = a[ord[l]];
     const double Q = realised_Q(ao, beta, P);
@@ -165,7 +189,18 @@ frkc2_status frkc2_plan(int s, double nu, unsigned flags, frkc2_plan_t* out) {
       best_order = ord;
       best_n = n;
     }
-    if (Q <= bound) break;
+    return Q;
+  };
+  const bool force_greedy = flags & FRKC2_PLAN_GREEDY, force_lebedev = flags & FRKC2_PLAN_LEBEDEV;
+  if (force_greedy && force_lebedev) return FRKC2_EINVAL;
+  bool run_greedy = force_greedy || (!force_lebedev && L <= 256);
+  if (force_lebedev || (!force_greedy && L > 256)) {
+    const double q = consider(order_lebedev(L), 0);
+    if (!force_lebedev && q > bound) run_greedy = true;
+  }
+  if (run_greedy) {
+    for (int n = 1; n <= n_max; ++n)
+      if (consider(order_greedy(a, beta, n, S), n) <= bound) break;
   }
   if ((flags & FRKC2_PLAN_STRICT) && best_Q > bound) return FRKC2_EPLAN;
   frkc2_plan_s* p = new (std::nothrow) frkc2_plan_s;

@@ -129,3 +129,23 @@ def test_status_strings():
     for st in range(9):
         assert F.frkc2_status_string(st)
     assert "unknown" in F.frkc2_status_string(99)
+
+
+@pytest.mark.parametrize("L", [16, 64, 100, 128])
+def test_plan_lebedev_flag_matches_oracle(L):
+    lib = F.frkc2_plan(L, flags=F.PLAN_LEBEDEV).info()
+    ora = O.plan(L, method="lebedev")
+    assert np.array_equal(lib["order"], ora["order"])
+    assert lib["n_iter"] == 0
+    assert abs(lib["Q"] / ora["Q"] - 1.0) < 1e-9
+
+
+def test_plan_auto_large_s_matches_oracle():
+    lib = F.frkc2_plan(512).info()
+    ora = O.plan(512, q_points=1024)
+    assert np.array_equal(lib["order"], ora["order"])
+    assert lib["Q"] <= 10 * 512 ** 2
+    with pytest.raises(F.Frkc2Error):
+        F.frkc2_plan(16, flags=F.PLAN_GREEDY | F.PLAN_LEBEDEV)
+    g = F.frkc2_plan(16, flags=F.PLAN_GREEDY).info()
+    assert np.array_equal(g["order"], O.plan(16, method="greedy")["order"])

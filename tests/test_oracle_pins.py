@@ -505,3 +505,35 @@ def test_inputs_recipes():
     assert h.min() >= 0.0 and 1.5 <= h.max() <= 2.02 + 1e-12
     b = I.batched_problems(16)
     assert all(64 <= p["n"] <= 1024 and p["s"] in (16, 32, 64, 128, 256) for p in b)
+
+
+@pytest.mark.parametrize("L", [8, 16, 64, 128, 256])
+def test_lebedev_order_reaches_single_factor_lower_bound(L):
+    """Any order's Q is at least the largest single factor max_l max_x |1 + a_l x|; the
+    Lebedev-Finogenov half-then-conjugates order attains it for L a power of two."""
+    a = O.step_sizes(L)
+    b = O.beta(L)
+    pts = 8 * L
+    perm = O.order_lebedev(L)
+    assert sorted(perm.tolist()) == list(range(L))
+    x = -b * np.arange(pts + 1) / pts
+    single = float(np.max(np.abs(1.0 + np.outer(a, x))))
+    q = O.realised_Q(a[perm], b, pts)
+    assert abs(q / single - 1.0) < 1e-12
+    assert q < GOLD["Q_optimal_factor"]["value"] * L * L
+
+
+def test_lebedev_permutation_recursion():
+    assert O.lebedev_permutation(1) == [0]
+    assert O.lebedev_permutation(2) == [0, 1]
+    assert O.lebedev_permutation(4) == [0, 3, 1, 2]
+    assert O.lebedev_permutation(8) == [0, 7, 3, 4, 1, 6, 2, 5]
+    assert O.lebedev_permutation(5) == [0, 3, 1, 2, 4]
+    for m in range(1, 40):
+        assert sorted(O.lebedev_permutation(m)) == list(range(m))
+
+
+def test_plan_auto_uses_lebedev_above_256():
+    p = O.plan(512, q_points=1024)
+    assert p["n"] == 0 and np.array_equal(p["order"], O.order_lebedev(512))
+    assert p["Q"] <= 10 * 512 ** 2
