@@ -291,42 +291,34 @@ def run_ours(args, rank, world, local_rank):
         "gpu_launches": launches,
     }
     if rank == 0 and not args.no_cpu_baseline and world == 1:
-        out["cpu_baseline"] = cpu_baseline(args.cpu_stages)
-        if not args.no_variants:
-            out["error_vs_oracle"] = error_vs_oracle(torch, F, dev)
+        out["cpu_baseline"], out["error_vs_oracle"] = cpu_baseline(torch, F, dev)
     return out
 
 
-def cpu_baseline(stages: int):
-    from oracle import frkc2_oracle as O
-
-    u0, k = inputs()
-    pr = dict(ndim=2, dx=1.0, bc="periodic", kappa="field", kappa_c=1.0, kappa_p=2.5, kappa_field=k)
-    a = O.plan(CFG["s"])["a"][:stages]
-    dt = CFG["cfl"] * O.beta(CFG["s"]) / O.rho_bound(pr)
-    t = time.perf_counter()
-    O.frkc2_step(u0, a, dt, pr, 1)
-    el = time.perf_counter() - t
-    n = CFG["n"]
-    return {"value": n * n * stages / el, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"first {stages} of the 6400 stages of the 2048^2 FP64 job (numpy, one thread), {el:.1f} s"}
-
-
-def error_vs_oracle(torch, F, dev, n=1024):
-    """Relative L2 of one full FRKC2 step (s = 64) per precision against the FP64 oracle,
-    on a 1024^2 instance of the same recipe (the oracle takes ~8 s for it)."""
+def cpu_baseline(torch, F, dev, n=1024):
+    """The CPU baseline leg: the FP64 oracle timed on one full FRKC2 step (64 stages) of a
+    1024^2 instance of the recipe (one thread), and the GPU path's error at each precision
+    against that same oracle output."""
     from oracle import frkc2_oracle as O
 
     u0, k = inputs(n)
     s = CFG["s"]
     plan = F.frkc2_plan(s)
-    res = {}
+    oplan = O.plan(s)
+    errs = {}
+    value = None
     for prec in ("fp64", "fp32", "mixed"):
         kk = k if prec == "fp64" else k.astype(np.float32).astype(np.float64)
         uu = u0 if prec != "fp32" else u0.astype(np.float32).astype(np.float64)
         pr = dict(ndim=2, dx=1.0, bc="periodic", kappa="field", kappa_c=1.0, kappa_p=2.5, kappa_field=kk)
         dt = CFG["cfl"] * O.beta(s) / O.rho_bound(pr)
-        ref = O.frkc2_step(uu, O.plan(s)["a"], dt, pr, 1)
+        t = time.perf_counter()
+        ref = O.frkc2_step(uu, oplan["a"], dt, pr, 1)
+        el = time.perf_counter() - t
+        if prec == "fp64":
+            value = n * n * s / el
+            sample = (f"one full FRKC2 step (64 stages) of a {n}^2 instance of the recipe, FP64 oracle "
+                      f"(numpy, one thread), {el:.1f} s")
         sd = torch.float32 if prec == "fp32" else torch.float64
         kd = torch.float64 if prec == "fp64" else torch.float32
         u = torch.as_tensor(u0, dtype=sd, device=dev)
@@ -336,9 +328,9 @@ def error_vs_oracle(torch, F, dev, n=1024):
         F.frkc2_workspace_reset(ws)
         F.frkc2_step(plan, lp, dt, 1, 0.0, u, ws)
         got = u.double().cpu().numpy()
-        res[prec] = float(np.linalg.norm(got - ref) / np.linalg.norm(ref))
-    res["sample"] = "one step (64 stages) on a 1024^2 instance of the recipe"
-    return res
+        errs[prec] = float(np.linalg.norm(got - ref) / np.linalg.norm(ref))
+    errs["sample"] = f"one step (64 stages) on a {n}^2 instance of the recipe"
+    return ({"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample}, errs)
 
 
 def run_reference(args, rank, world):
@@ -382,12 +374,20 @@ def main():
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default="varkappa2d",
+                    help="varkappa2d (the default line) or one of bench_workloads.WORKLOADS")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.workload != "varkappa2d":
+        import bench_workloads as BW
+        from paper_1702_03818_gb300 import frkc2 as F
+        if rank == 0:
+            print(json.dumps(BW.WORKLOADS[args.workload](F)), flush=True)
+        return
     if args.impl == "reference":
         out = run_reference(args, rank, world)
         if out is not None:

@@ -1,0 +1,288 @@
+"""Benchmarks of the other FRKC2 workloads (``python bench.py --workload NAME``).
+
+Each function times one workload on cuda:0 and returns a JSON-ready dict in the bench line
+format.  Timing: CUDA events on the launching stream, warm-up runs first, L2 flushed (a
+256 MiB write) before every timed run, outside the events.  Errors of FP32 / MIXED runs are
+stated against the FP64 GPU result of the same job; parity of every path with the FP64 oracle
+is established by the GPU tests (tests/test_gpu_*.py) on reduced instances of these recipes.
+
+Workloads (sizes and seeds from frkc2_inputs.CONFIGS):
+  heat1d       1D heat, N = 256 Dirichlet, s = 16, 87 steps to T = 0.05, FP64.
+  nonlinear3d  3D kappa(u) = 1 + u^2.5, 256^3 Dirichlet hot spot with 1 % noise; one bench
+               step = one FRKC2 step at FP64, FP32 and MIXED.  s = 32: with s = 128 the complex
+               stages amplify the noise modes until kappa(W) leaves the stability bound and the
+               run (and the FP64 oracle on reduced grids) produces non-finite values.
+  adjoint2d    2D var-kappa 1024^2, s = 100, 40 steps, checkpoint every 8: forward vs adjoint.
+  batched2d    512 2D var-kappa problems (n ~ U{64..1024}, s ~ {16..256}, 10 steps), one
+               persistent launch replayed from a CUDA graph, FP32 and FP64.
+  ssweep       4096^2 var-kappa, s in {32, 128, 512, 1024}, 4 steps, FP32 vs FP64 error growth
+               with s (internal amplification).
+"""
+from __future__ import annotations
+
+import numpy as np
+
+import frkc2_inputs as I
+
+UNIT = "cell-stage/s"
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _timed(fn, warmup=2, reps=3, flush=None):
+    torch = _torch()
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    ms = []
+    for _ in range(reps):
+        if flush is not None:
+            flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        fn()
+        e1.record()
+        e1.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    return float(np.median(ms)), ms
+
+
+def _dt(torch):
+    return {"fp64": (torch.float64, torch.float64), "fp32": (torch.float32, torch.float32),
+            "mixed": (torch.float64, torch.float32)}
+
+
+def _rel(a, b):
+    return float(np.linalg.norm((a - b).ravel()) / np.linalg.norm(b.ravel()))
+
+
+def heat1d(F):
+    torch = _torch()
+    cfg = I.CONFIGS["heat1d"]
+    u0, _, dx = I.heat1d_u0(cfg["n"], 8, cfg["seed"])
+    s = cfg["s"]
+    plan = F.frkc2_plan(s)
+    beta = plan.info()["beta"]
+    nsteps = int(np.ceil(cfg["t_end"] / (0.9 * beta * dx * dx / 4.0)))
+    dt = cfg["t_end"] / nsteps
+    pr = F.make_problem(1, (cfg["n"],), dx, "dirichlet", "const", "fp64", kappa_c=1.0)
+    ws = torch.empty(F.frkc2_workspace_size(pr), dtype=torch.uint8, device="cuda")
+    u0d = torch.as_tensor(u0, device="cuda")
+    u = u0d.clone()
+
+    def job():
+        u.copy_(u0d)
+        F.frkc2_step(plan, pr, dt, nsteps, 0.0, u, ws)
+
+    med, _ = _timed(job, 3, 5)
+    cs = cfg["n"] * s * nsteps
+    return {"workload": "heat1d: 1D heat N=256 Dirichlet, s=16, 87 steps, FP64", "metric": "cell-stage/s",
+            "value": cs / (med / 1e3), "unit": UNIT, "ms_per_job": med, "nsteps": nsteps,
+            "kernel": "generic tile pass, k = 16 (one launch per step)"}
+
+
+def nonlinear3d(F, n=None):
+    torch = _torch()
+    cfg = I.CONFIGS["nonlinear3d"]
+    n = n or cfg["n"]
+    s = cfg["s_stable"]
+    u0 = I.hotspot3d_u0(n, sigma=20.0 * n / cfg["n"], seed=cfg["seed"])
+    plan = F.frkc2_plan(s)
+    beta = plan.info()["beta"]
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    out, results = {}, {}
+    rho_t = torch.zeros(1, dtype=torch.float64, device="cuda")
+    pr64 = F.make_problem(3, (n, n, n), 1.0, "dirichlet", "power", "fp64", kappa_c=1.0, kappa_p=2.5)
+    F.frkc2_rho_bound(pr64, torch.as_tensor(u0, device="cuda"), rho_t)
+    dt = cfg["cfl"] * beta / rho_t.item()
+    for prec in ("fp64", "fp32", "mixed"):
+        sd, _ = _dt(torch)[prec]
+        pr = F.make_problem(3, (n, n, n), 1.0, "dirichlet", "power", prec, kappa_c=1.0, kappa_p=2.5)
+        ws = torch.empty(F.frkc2_workspace_size(pr), dtype=torch.uint8, device="cuda")
+        u0d = torch.as_tensor(u0, dtype=sd, device="cuda")
+        u = u0d.clone()
+
+        def job():
+            u.copy_(u0d)
+            F.frkc2_step(plan, pr, dt, 1, 0.0, u, ws)
+
+        med, _ = _timed(job, 1, 3, flush)
+        results[prec] = u.double().cpu().numpy()
+        out[prec] = {"value": n ** 3 * s / (med / 1e3), "ms_per_step": med,
+                     "status": F.frkc2_workspace_status(ws)}
+        del ws, u, u0d
+    for prec in ("fp32", "mixed"):
+        out[prec]["rel_l2_vs_fp64_gpu"] = _rel(results[prec], results["fp64"])
+    return {"workload": f"nonlinear3d: 3D kappa(u)=1+u^2.5 {n}^3 Dirichlet, s={s}, one FRKC2 step per bench step",
+            "metric": "cell-stage/s", "value": out["fp64"]["value"], "unit": UNIT, "dtype": "f64",
+            "precisions": out,
+            "kernel": "generic tile pass, k = 1, tile 32x4x4"}
+
+
+def adjoint2d(F):
+    torch = _torch()
+    cfg = I.CONFIGS["adjoint2d"]
+    n, s, nsteps, ck = cfg["n"], cfg["s"], cfg["steps"], cfg["ckpt"]
+    u0 = I.smooth_unit((n, n), 64.0 * n / 2048, cfg["u0_seed"])
+    kap = I.kappa_field((n, n), cfg["kappa_seed"], ell=32.0 * n / 2048)
+    tgt = I.smooth_unit((n, n), 64.0 * n / 2048, cfg["target_seed"])
+    plan = F.frkc2_plan(s)
+    beta = plan.info()["beta"]
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    res = {}
+    for prec in ("fp64", "fp32"):
+        sd, kd = _dt(torch)[prec]
+        kt = torch.as_tensor(kap, dtype=kd, device="cuda")
+        pr = F.make_problem(2, (n, n), 1.0, "periodic", "field", prec, kappa_field=kt)
+        rho_t = torch.zeros(1, dtype=torch.float64, device="cuda")
+        F.frkc2_rho_bound(pr, None, rho_t)
+        dt = cfg["cfl"] * beta / rho_t.item()
+        ws = torch.empty(F.frkc2_workspace_size(pr), dtype=torch.uint8, device="cuda")
+        u0d = torch.as_tensor(u0, dtype=sd, device="cuda")
+        u = u0d.clone()
+
+        def fwd():
+            u.copy_(u0d)
+            F.frkc2_step(plan, pr, dt, nsteps, 0.0, u, ws)
+
+        tf, _ = _timed(fwd, 1, 3, flush)
+        g = 2.0 * (u - torch.as_tensor(tgt, dtype=sd, device="cuda"))
+        wsa = torch.empty(F.frkc2_adjoint_workspace_size(plan, pr, nsteps, ck), dtype=torch.uint8, device="cuda")
+        du = torch.empty_like(u0d)
+        dk = torch.empty_like(kt)
+
+        def adj():
+            F.frkc2_adjoint(plan, pr, dt, nsteps, ck, u0d, g, du, dk, wsa)
+
+        ta, _ = _timed(adj, 1, 3, flush)
+        res[prec] = {"forward_ms": tf, "adjoint_ms": ta, "adjoint_over_forward": ta / tf,
+                     "forward_value": n * n * s * nsteps / (tf / 1e3),
+                     "workspace_gb": wsa.numel() / 1e9,
+                     "grad_norms": [float(du.double().norm()), float(dk.double().norm())]}
+        del wsa, ws
+    return {"workload": f"adjoint2d: 2D var-kappa {n}^2 periodic, s={s}, {nsteps} steps, checkpoint every {ck}",
+            "metric": "adjoint time / forward time", "value": res["fp64"]["adjoint_over_forward"],
+            "unit": "ratio", "higher_is_better": False, "precisions": res,
+            "note": "the adjoint call includes its own checkpointed forward run"}
+
+
+def batched2d(F):
+    torch = _torch()
+    cfg = I.CONFIGS["batched2d"]
+    specs = I.batched_problems(cfg["count"], cfg["seed"])
+    nsteps = cfg["steps"]
+    plans = {s: F.frkc2_plan(s) for s in sorted({p["s"] for p in specs})}
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    fields = []
+    for p in specs:
+        n = p["n"]
+        u = I.grf_torch(n, 64.0 * n / 2048, p["u0_seed"])
+        u = (u - u.min()) / (u.max() - u.min())
+        k = torch.exp(0.5 * I.grf_torch(n, 32.0 * n / 2048, p["kappa_seed"]))
+        fields.append((u, k))
+    res = {}
+    for prec in ("fp32", "fp64"):
+        sd, kd = _dt(torch)[prec]
+        probs, us, u0s, dts, pl = [], [], [], [], []
+        for p, (u, k) in zip(specs, fields):
+            kt = k.to(kd).contiguous()
+            pr = F.make_problem(2, (p["n"], p["n"]), 1.0, "periodic", "field", prec, kappa_field=kt)
+            rho_t = torch.zeros(1, dtype=torch.float64, device="cuda")
+            F.frkc2_rho_bound(pr, None, rho_t)
+            dts.append(0.9 * plans[p["s"]].info()["beta"] / rho_t.item())
+            probs.append(pr)
+            u0s.append(u.to(sd).contiguous())
+            us.append(u0s[-1].clone())
+            pl.append(plans[p["s"]])
+        nst = [nsteps] * len(specs)
+        ws = torch.empty(F.frkc2_batch_workspace_size(pl, probs, nst), dtype=torch.uint8, device="cuda")
+        F.frkc2_workspace_reset(ws)
+        F.frkc2_batch_prepare(pl, probs, dts, nst, us, ws)
+        g = torch.cuda.CUDAGraph()
+        side = torch.cuda.Stream()
+        side.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(side):
+            F.frkc2_batch_launch(ws, stream=side)
+        torch.cuda.current_stream().wait_stream(side)
+        torch.cuda.synchronize()
+        with torch.cuda.graph(g):
+            F.frkc2_batch_launch(ws, stream=torch.cuda.current_stream())
+
+        def reset():
+            for u, u0 in zip(us, u0s):
+                u.copy_(u0)
+
+        ms = []
+        for it in range(4):
+            reset()
+            flush.zero_()
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            g.replay()
+            e1.record()
+            e1.synchronize()
+            if it >= 1:
+                ms.append(e0.elapsed_time(e1))
+        assert F.frkc2_workspace_status(ws) == F.OK
+        cs = sum(p["n"] ** 2 * p["s"] * nsteps for p in specs)
+        # consistency: three problems against the single-problem path
+        errs = []
+        for i in (0, len(specs) // 2, len(specs) - 1):
+            wsi = torch.empty(F.frkc2_workspace_size(probs[i]), dtype=torch.uint8, device="cuda")
+            v = u0s[i].clone()
+            F.frkc2_step(pl[i], probs[i], dts[i], nsteps, 0.0, v, wsi)
+            errs.append(_rel(us[i].double().cpu().numpy(), v.double().cpu().numpy()))
+        res[prec] = {"value": cs / (np.median(ms) / 1e3), "ms_per_launch": float(np.median(ms)),
+                     "cell_stages": cs, "max_rel_l2_vs_single_problem_path": max(errs),
+                     "workspace_gb": ws.numel() / 1e9}
+        del ws, g
+    return {"workload": "batched2d: 512 var-kappa 2D problems, n~U{64..1024}, s~{16..256}, 10 steps, one persistent launch (CUDA graph)",
+            "metric": "cell-stage/s", "value": res["fp32"]["value"], "unit": UNIT, "precisions": res}
+
+
+def ssweep(F):
+    torch = _torch()
+    n = 4096
+    u0 = I.smooth_unit((n, n), 64.0 * 2, 3819)
+    kap = I.kappa_field((n, n), 3818, ell=64.0)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    out = {}
+    for s in (32, 128, 512, 1024):
+        plan = F.frkc2_plan(s)
+        info = plan.info()
+        row = {"Q_over_L2": info["Q"] / s ** 2}
+        res = {}
+        for prec in ("fp64", "fp32"):
+            sd, kd = _dt(torch)[prec]
+            kt = torch.as_tensor(kap, dtype=kd, device="cuda")
+            pr = F.make_problem(2, (n, n), 1.0, "periodic", "field", prec, kappa_field=kt)
+            rho_t = torch.zeros(1, dtype=torch.float64, device="cuda")
+            F.frkc2_rho_bound(pr, None, rho_t)
+            dt = 0.9 * info["beta"] / rho_t.item()
+            ws = torch.empty(F.frkc2_workspace_size(pr), dtype=torch.uint8, device="cuda")
+            u0d = torch.as_tensor(u0, dtype=sd, device="cuda")
+            u = u0d.clone()
+
+            def job():
+                u.copy_(u0d)
+                F.frkc2_step(plan, pr, dt, 4, 0.0, u, ws)
+
+            med, _ = _timed(job, 1, 2, flush)
+            res[prec] = u.double().cpu().numpy()
+            row[prec] = {"value": n * n * s * 4 / (med / 1e3), "ms": med}
+            del ws
+        row["fp32_rel_l2_vs_fp64_gpu"] = _rel(res["fp32"], res["fp64"])
+        out[str(s)] = row
+    return {"workload": "ssweep: 4096^2 var-kappa periodic, s in {32,128,512,1024}, 4 steps, FP32 vs FP64",
+            "metric": "fp32 error vs fp64 by s", "value": out["1024"]["fp32_rel_l2_vs_fp64_gpu"], "unit": "rel L2",
+            "by_s": out}
+
+
+WORKLOADS = {"heat1d": heat1d, "nonlinear3d": nonlinear3d, "adjoint2d": adjoint2d,
+             "batched2d": batched2d, "ssweep": ssweep}

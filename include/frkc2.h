@@ -100,7 +100,11 @@ typedef struct {
  * single factor, the least any order can reach), with the greedy n-loop as well if that
  * order misses 10 L^2; the smaller realised Q wins.
  *   s     : number of stages, even, 2..4096.
- *   nu    : damping of Sec. 2.1; only 0 is implemented (FRKC2_EUNSUPPORTED otherwise).
+ *   nu    : damping nu0 of Sec. 2.1, 0 <= nu0 < 0.9 (nu = nu0/2 with N = 2).  nu0 > 0 uses
+ *           a_l = (1 - mu_l)/((1 - nu) M^2 alpha (1 - (1 - 2 mu_l) zeta_l)) with mu_l = mu on
+ *           the roots of T_M = +i c and conj(mu) on their conjugates, mu found by Newton-
+ *           Raphson on the order conditions; beta is then found by bisection on |R| = 1
+ *           (about (1 - nu) times the undamped extent; interior maxima of |R| drop below 1).
  *   flags : FRKC2_PLAN_STRICT makes an unmet Q bound an error (FRKC2_EPLAN); otherwise the
  *           ordering with the smallest realised Q is kept.  FRKC2_PLAN_GREEDY or
  *           FRKC2_PLAN_LEBEDEV use that ordering alone (both together: FRKC2_EINVAL).

@@ -86,6 +86,73 @@ def step_sizes(L: int) -> np.ndarray:
     return 1.0 / (M * M * alpha(L) * (1.0 - roots(L)))
 
 
+def _taylor2(a):
+    """First and second coefficients of prod_l (1 + a_l z) (e1 = sum a, e2 = sum_{i<j} a_i a_j)."""
+    c = np.array([1.0 + 0j])
+    for al in a:
+        c = np.convolve(c, np.array([1.0, al]))
+    return c[1], c[2]
+
+
+def damped_step_sizes(L: int, nu0: float):
+    """Damped step sizes of Sec. 2.1 and the damping parameter mu.
+
+    a_l = (1 - mu_l) / ((1 - nu) M^2 alpha_M (1 - (1 - 2 mu_l) zeta_l)), nu = nu0 / N, N = 2.
+    Reading: the N = 2 distinct values of mu_l belong to the two families of roots (T_M(zeta)
+    = +i c for even root index j, -i c for odd j); for the step sizes to stay in conjugate
+    pairs they are mu and conj(mu).  Newton-Raphson over (Re mu, Im mu) enforces the order
+    conditions sum a = 1, sum_{i<j} a_i a_j = 1/2 (Eq. 5), starting from mu = 0 (the undamped
+    solution), with a forward-difference Jacobian.
+    """
+    nu = nu0 / 2.0
+    M = L // 2
+    al = alpha(L)
+    z = roots(L)
+    even = (np.arange(L) % 2) == 0
+
+    def steps(mu):
+        m = np.where(even, mu, np.conj(mu))
+        return (1.0 - m) / ((1.0 - nu) * M * M * al * (1.0 - (1.0 - 2.0 * m) * z))
+
+    def resid(mu):
+        e1, e2 = _taylor2(steps(mu))
+        return np.array([(e1 - 1.0).real, (e2 - 0.5).real])
+
+    mu = 0.0 + 0.0j
+    for _ in range(60):
+        r = resid(mu)
+        if np.max(np.abs(r)) < 1e-14:
+            break
+        h = 1e-7
+        J = np.column_stack([(resid(mu + h) - r) / h, (resid(mu + 1j * h) - r) / h])
+        d = np.linalg.solve(J, -r)
+        mu = mu + d[0] + 1j * d[1]
+    a = steps(mu)
+    for j in range(L // 2):  # conjugate pairs exact to the bit, as for the undamped roots
+        a[L - 1 - j] = np.conj(a[j])
+    return a, mu
+
+
+def stability_extent(a, guess: float) -> float:
+    """Largest x with |R(-x)| <= 1 near ``guess`` (bisection on the last crossing, Eq. 6)."""
+    def absR(x):
+        return float(np.abs(np.prod(1.0 + a * (-x))))
+    lo, hi = 0.9 * guess, 1.1 * guess
+    while absR(lo) > 1.0:
+        lo *= 0.99
+    while absR(hi) <= 1.0:
+        hi *= 1.01
+    for _ in range(200):
+        mid = 0.5 * (lo + hi)
+        if absR(mid) <= 1.0:
+            lo = mid
+        else:
+            hi = mid
+        if hi - lo <= 1e-15 * hi:
+            break
+    return lo
+
+
 # ----------------------------------------------------------------------------------------
 # Internal stability (Sec. 2.2)
 # ----------------------------------------------------------------------------------------
@@ -167,7 +234,7 @@ def order_lebedev(L: int) -> np.ndarray:
 
 
 def plan(L: int, samples: int | None = None, q_points: int | None = None, n_max: int = 10,
-         bound: float = 10.0, method: str = "auto") -> dict:
+         bound: float = 10.0, method: str = "auto", nu0: float = 0.0) -> dict:
     """Ordered FRKC2 step sizes for L stages (Sec. 2.2, the n-loop).
 
     ``greedy``: the ordering of Eq. 12 is repeated with n = 1, 2, ... until the realised Q is
@@ -179,9 +246,14 @@ def plan(L: int, samples: int | None = None, q_points: int | None = None, n_max:
     ``auto`` (reading): the greedy n-loop for L <= 256, where it meets the bound; above that
     the Lebedev-Finogenov order, and the greedy n-loop as well only if that order misses the
     bound (the smaller realised Q is kept).
+    ``nu0`` > 0 uses the damped step sizes of Sec. 2.1, with beta found by bisection.
     """
-    a = step_sizes(L)
-    b = beta(L)
+    if nu0 > 0.0:
+        a, _ = damped_step_sizes(L, nu0)
+        b = stability_extent(a, (1.0 - nu0 / 2.0) * beta(L))
+    else:
+        a = step_sizes(L)
+        b = beta(L)
     S = samples if samples is not None else 16 * L
     P = q_points if q_points is not None else 16 * L
     best = None

@@ -40,6 +40,76 @@ std::vector<cplx> root_order_steps(int L) {
   return a;
 }
 
+// Damped step sizes of Sec. 2.1: a_l = (1 - mu_l) / ((1 - nu) M^2 alpha (1 - (1 - 2 mu_l) zeta_l)),
+// nu = nu0 / 2.  mu_l = mu for even root index j (T_M(zeta_j) = +i c), conj(mu) for odd j, so the
+// step sizes stay in conjugate pairs; Newton-Raphson over (Re mu, Im mu) from mu = 0 enforces
+// e1 = sum a = 1 and e2 = sum_{i<j} a_i a_j = (e1^2 - sum a^2) / 2 = 1/2.
+std::vector<cplx> damped_steps(int L, double nu0) {
+  const double nu = 0.5 * nu0, al = poly_alpha(L), eta = std::acosh(4.0 / al - 1.0), M = 0.5 * L;
+  std::vector<cplx> z(L);
+  for (int j = 0; j < L / 2; ++j) {
+    const double th = M_PI * double(2 * j + 1) / double(L), y = eta / double(L);
+    z[j] = cplx(std::cos(th) * std::cosh(y), std::sin(th) * std::sinh(y));
+    z[L - 1 - j] = std::conj(z[j]);
+  }
+  auto steps = [&](cplx mu) {
+    std::vector<cplx> a(L);
+    for (int j = 0; j < L; ++j) {
+      const cplx m = (j % 2 == 0) ? mu : std::conj(mu);
+      a[j] = (1.0 - m) / ((1.0 - nu) * M * M * al * (1.0 - (1.0 - 2.0 * m) * z[j]));
+    }
+    return a;
+  };
+  auto resid = [&](cplx mu, double r[2]) {
+    const std::vector<cplx> a = steps(mu);
+    cplx e1 = 0.0, p2 = 0.0;
+    for (const cplx& v : a) {
+      e1 += v;
+      p2 += v * v;
+    }
+    const cplx e2 = 0.5 * (e1 * e1 - p2);
+    r[0] = (e1 - 1.0).real();
+    r[1] = (e2 - 0.5).real();
+  };
+  cplx mu = 0.0;
+  for (int it = 0; it < 60; ++it) {
+    double r[2], rx[2], ry[2];
+    resid(mu, r);
+    if (std::max(std::abs(r[0]), std::abs(r[1])) < 1e-14) break;
+    const double h = 1e-7;
+    resid(mu + cplx(h, 0.0), rx);
+    resid(mu + cplx(0.0, h), ry);
+    const double J00 = (rx[0] - r[0]) / h, J01 = (ry[0] - r[0]) / h;
+    const double J10 = (rx[1] - r[1]) / h, J11 = (ry[1] - r[1]) / h;
+    const double det = J00 * J11 - J01 * J10;
+    if (det == 0.0 || !std::isfinite(det)) break;
+    mu += cplx((-r[0] * J11 + r[1] * J01) / det, (-J00 * r[1] + J10 * r[0]) / det);
+  }
+  std::vector<cplx> a = steps(mu);
+  for (int j = 0; j < L / 2; ++j) a[L - 1 - j] = std::conj(a[j]);
+  return a;
+}
+
+// Largest x with |R(-x)| <= 1 near `guess` (bisection on the last crossing of |R| = 1).
+double stability_extent(const std::vector<cplx>& a, double guess) {
+  auto absR = [&](double x) {
+    cplx p = 1.0;
+    for (const cplx& v : a) p *= (1.0 - v * x);
+    return std::abs(p);
+  };
+  double lo = 0.9 * guess, hi = 1.1 * guess;
+  while (absR(lo) > 1.0) lo *= 0.99;
+  while (absR(hi) <= 1.0) hi *= 1.01;
+  for (int i = 0; i < 200 && hi - lo > 1e-15 * hi; ++i) {
+    const double mid = 0.5 * (lo + hi);
+    if (absR(mid) <= 1.0)
+      lo = mid;
+    else
+      hi = mid;
+  }
+  return lo;
+}
+
 // Runs fn(lo, hi) over [0, n) on up to hardware_concurrency threads.
 template <class F>
 void parallel_ranges(int n, F fn) {
@@ -170,11 +240,11 @@ extern "C" {
 
 frkc2_status frkc2_plan(int s, double nu, unsigned flags, frkc2_plan_t* out) {
   if (!out || s < 2 || s > 4096 || (s & 1)) return FRKC2_EINVAL;
-  if (nu != 0.0) return FRKC2_EUNSUPPORTED;
+  if (!(nu >= 0.0 && nu < 0.9)) return FRKC2_EINVAL;
   *out = nullptr;
   const int L = s;
-  const std::vector<cplx> a = root_order_steps(L);
-  const double beta = poly_beta(L);
+  const std::vector<cplx> a = nu > 0.0 ? damped_steps(L, nu) : root_order_steps(L);
+  const double beta = nu > 0.0 ? stability_extent(a, (1.0 - 0.5 * nu) * poly_beta(L)) : poly_beta(L);
   const int S = 16 * L, P = 16 * L, n_max = 10;
   const double bound = 10.0 * double(L) * double(L);
   std::vector<int> best_order;

@@ -60,8 +60,8 @@ def test_plan_from_steps_and_errors():
             F.frkc2_plan(bad)
         assert e.value.status == F.EINVAL
     with pytest.raises(F.Frkc2Error) as e:
-        F.frkc2_plan(16, nu=0.1)
-    assert e.value.status == F.EUNSUPPORTED
+        F.frkc2_plan(16, nu=0.95)
+    assert e.value.status == F.EINVAL
     # strict plan with an unreachable bound is not possible to request; a normal plan is OK
     assert F.frkc2_plan(16, flags=F.PLAN_STRICT).info()["Q"] <= 10 * 16 ** 2
 
@@ -149,3 +149,13 @@ def test_plan_auto_large_s_matches_oracle():
         F.frkc2_plan(16, flags=F.PLAN_GREEDY | F.PLAN_LEBEDEV)
     g = F.frkc2_plan(16, flags=F.PLAN_GREEDY).info()
     assert np.array_equal(g["order"], O.plan(16, method="greedy")["order"])
+
+
+@pytest.mark.parametrize("L", [16, 64, 100])
+@pytest.mark.parametrize("nu0", [0.05, 0.2])
+def test_damped_plan_matches_oracle(L, nu0):
+    lib = F.frkc2_plan(L, nu=nu0).info()
+    ora = O.plan(L, nu0=nu0)
+    assert np.array_equal(lib["order"], ora["order"])
+    assert np.max(np.abs(lib["a"] - ora["a"])) < 1e-13
+    assert abs(lib["beta"] / ora["beta"] - 1.0) < 1e-12

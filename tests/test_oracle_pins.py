@@ -537,3 +537,28 @@ def test_plan_auto_uses_lebedev_above_256():
     p = O.plan(512, q_points=1024)
     assert p["n"] == 0 and np.array_equal(p["order"], O.order_lebedev(512))
     assert p["Q"] <= 10 * 512 ** 2
+
+
+@pytest.mark.parametrize("L", [16, 64, 100])
+@pytest.mark.parametrize("nu0", [0.05, 0.2])
+def test_damping_order_conditions_extent_and_maxima(L, nu0):
+    """Sec. 2.1: damped step sizes keep the order conditions, shrink beta by about (1 - nu),
+    nu = nu0/2, and lift the marginal interior points off |R| = 1."""
+    a, mu = O.damped_step_sizes(L, nu0)
+    coef = np.array([1.0 + 0j])
+    for al in a:
+        coef = np.convolve(coef, np.array([1.0, al]))
+    assert abs(coef[1] - 1.0) < 1e-12 and abs(coef[2] - 0.5) < 1e-12
+    assert np.array_equal(a[::-1], np.conj(a))
+    b = O.stability_extent(a, O.beta(L))
+    assert abs(b / O.beta(L) - (1.0 - nu0 / 2.0)) < 0.005
+    z = np.linspace(-0.95 * b, -0.05 * b, 4001)
+    assert np.max(np.abs(R_product(z, a))) < 1.0 - nu0 / 4.0
+    assert np.max(np.abs(R_product(np.linspace(-b, 0.0, 4001), a))) <= 1.0 + 1e-9
+    assert abs(R_product(-1.001 * b, a)) > 1.0
+
+
+def test_damping_zero_is_undamped():
+    a, mu = O.damped_step_sizes(32, 0.0)
+    assert mu == 0
+    assert np.max(np.abs(a - O.step_sizes(32))) < 1e-15
