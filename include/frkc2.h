@@ -203,6 +203,19 @@ frkc2_status frkc2_adjoint(frkc2_plan_t plan, const frkc2_problem* prob, double 
                            void* dJdu0, void* dJdkappa, void* ws, size_t ws_bytes,
                            void* stream);
 
+/* The two halves of frkc2_adjoint, for callers (such as an autodiff framework) that run the
+ * forward integration first and ask for gradients later.  frkc2_adjoint_forward integrates
+ * from u0, keeps the checkpoints and the last segment's stage tape in ws, and writes u(T_end)
+ * to uT (device array, may be NULL).  frkc2_adjoint_backward then takes g = dJ/du(T_end) and
+ * writes dJdu0 / dJdkappa; it must get the same plan, problem, dt, nsteps, ckpt_every and
+ * workspace as the forward call, with the workspace untouched in between.               */
+frkc2_status frkc2_adjoint_forward(frkc2_plan_t plan, const frkc2_problem* prob, double dt,
+                                   int nsteps, int ckpt_every, const void* u0, void* uT,
+                                   void* ws, size_t ws_bytes, void* stream);
+frkc2_status frkc2_adjoint_backward(frkc2_plan_t plan, const frkc2_problem* prob, double dt,
+                                    int nsteps, int ckpt_every, const void* g, void* dJdu0,
+                                    void* dJdkappa, void* ws, size_t ws_bytes, void* stream);
+
 /* ---- Batched forward step ----------------------------------------------------------------
  * nprob independent 2D problems (each with its own plan, grid size, conductivity, dt and
  * step count, all of one precision and the same boundary kind) advanced by ONE persistent

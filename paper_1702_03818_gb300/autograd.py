@@ -1,8 +1,9 @@
 """torch.autograd wrapper: FRKC2 steps as a differentiable function of (u0, kappa).
 
-The forward runs ``frkc2_step``; the backward runs ``frkc2_adjoint`` (the discrete adjoint
-of the stage loop, with its own checkpoints every ``ckpt_every`` steps and per-segment stage
-recompute) and returns dJ/du0 and, for a conductivity field, dJ/dkappa.  Both run in the
+The forward runs ``frkc2_adjoint_forward`` (the integration, keeping a checkpoint every
+``ckpt_every`` steps and the last segment's stage tape in a workspace saved for backward);
+the backward runs ``frkc2_adjoint_backward`` (per-segment stage recompute and the reverse
+stage replay) and returns dJ/du0 and, for a conductivity field, dJ/dkappa.  Both run in the
 CUDA library; this module only allocates the workspaces and passes pointers.
 """
 from __future__ import annotations
@@ -16,26 +17,32 @@ class FRKC2Steps(torch.autograd.Function):
     @staticmethod
     def forward(ctx, u0, kappa, plan, ndim, bc, precision, dx, dt, nsteps, ckpt_every):
         n = tuple(reversed(u0.shape))
+        u0 = u0.detach().contiguous()
+        kappa = kappa.detach().contiguous()
         prob = F.make_problem(ndim, n, dx, bc, "field", precision, kappa_field=kappa)
-        u = u0.detach().clone().contiguous()
-        ws = torch.empty(F.frkc2_workspace_size(prob), dtype=torch.uint8, device=u0.device)
+        ws = torch.empty(F.frkc2_adjoint_workspace_size(plan, prob, nsteps, ckpt_every),
+                         dtype=torch.uint8, device=u0.device)
         F.frkc2_workspace_reset(ws)
-        F.frkc2_step(plan, prob, dt, nsteps, 0.0, u, ws)
-        ctx.save_for_backward(u0.detach(), kappa.detach())
+        u = torch.empty_like(u0)
+        F.frkc2_adjoint_forward(plan, prob, dt, nsteps, ckpt_every, u0, u, ws)
+        ctx.save_for_backward(kappa)
+        ctx.ws = ws
+        ctx.shape = u0.shape
+        ctx.state_dtype = u0.dtype
         ctx.cfg = (plan, ndim, bc, precision, dx, dt, nsteps, ckpt_every)
         return u
 
     @staticmethod
     def backward(ctx, g):
-        u0, kappa = ctx.saved_tensors
+        (kappa,) = ctx.saved_tensors
         plan, ndim, bc, precision, dx, dt, nsteps, ckpt_every = ctx.cfg
-        n = tuple(reversed(u0.shape))
+        n = tuple(reversed(ctx.shape))
         prob = F.make_problem(ndim, n, dx, bc, "field", precision, kappa_field=kappa)
-        ws = torch.empty(F.frkc2_adjoint_workspace_size(plan, prob, nsteps, ckpt_every),
-                         dtype=torch.uint8, device=u0.device)
-        du0 = torch.empty_like(u0)
+        du0 = torch.empty(ctx.shape, dtype=ctx.state_dtype, device=kappa.device)
         dk = torch.empty_like(kappa) if ctx.needs_input_grad[1] else None
-        F.frkc2_adjoint(plan, prob, dt, nsteps, ckpt_every, u0, g.contiguous().to(u0.dtype), du0, dk, ws)
+        F.frkc2_adjoint_backward(plan, prob, dt, nsteps, ckpt_every, g.contiguous().to(ctx.state_dtype),
+                                 du0, dk, ctx.ws)
+        ctx.ws = None
         return du0, dk, None, None, None, None, None, None, None, None
 
 

@@ -12,7 +12,9 @@
 // Driver: the forward run keeps the state every ckpt_every steps; each segment of steps is
 // recomputed from its checkpoint with every stage state written to a tape in the workspace,
 // then the segment's stages are reversed (last step first, last stage first).  The last
-// segment's tape is still in place after the forward run and is not recomputed.
+// segment's tape is still in place after the forward run and is not recomputed.  2D problems
+// with a fixed conductivity use the streaming kernels with the tape and lambda stored
+// interleaved (U, V); the others use the tile kernels with planar U, V.
 #include <algorithm>
 #include <cmath>
 
@@ -275,6 +277,215 @@ AdjLayout adj_layout(const frkc2_problem& p, int s, int nsteps, int c) {
   return L;
 }
 
+
+// Shared state of one adjoint computation (forward with checkpoints, then backward).
+struct AdjCtx {
+  const frkc2_plan_s* plan;
+  const frkc2_problem* p;
+  double dt, h2;
+  int nsteps, c, s;
+  AdjLayout L;
+  char* base;
+  cudaStream_t st;
+  size_t N, SB, slot;
+  bool stream2d;  // 2D fixed conductivity: streaming kernels, interleaved tape and lambda
+  int tx, ty, tz;
+  char* ckpt(int j) const { return base + L.ckpt + size_t(j) * slot; }
+  char* tape(int q, int l) const { return base + L.tape + (size_t(q) * s + l) * 2 * slot; }
+  // W^0 of step q of segment j: the checkpoint for the first step, else tape slot 0
+  char* w0(int j, int q) const { return q == 0 ? ckpt(j) : tape(q, 0); }
+};
+
+frkc2_status adj_setup(AdjCtx& C, frkc2_plan_t plan, const frkc2_problem* prob, double dt, int nsteps,
+                       int ckpt_every, void* ws, size_t ws_bytes, void* stream) {
+  if (!plan || !ws || nsteps < 1 || ckpt_every < 1) return FRKC2_EINVAL;
+  const frkc2_status v = validate_problem(prob);
+  if (v != FRKC2_OK) return v;
+  if (!(dt > 0.0) || !std::isfinite(dt)) return FRKC2_EINVAL;
+  if (reinterpret_cast<uintptr_t>(ws) & 255) return FRKC2_EINVAL;
+  const frkc2_problem& p = *prob;
+  C.plan = plan;
+  C.p = prob;
+  C.dt = dt;
+  C.h2 = p.dx * p.dx;
+  C.nsteps = nsteps;
+  C.s = plan->s;
+  C.c = std::min(ckpt_every, nsteps);
+  C.L = adj_layout(p, C.s, nsteps, C.c);
+  if (ws_bytes < C.L.total) return FRKC2_ENOMEM;
+  C.base = static_cast<char*>(ws);
+  C.st = static_cast<cudaStream_t>(stream);
+  C.N = cells(p);
+  C.SB = state_bytes(p.precision);
+  C.slot = align256(C.N * C.SB);
+  C.stream2d = p.ndim == 2 && p.kappa_kind != FRKC2_KAPPA_POWER;
+  default_tiles(p, 1, &C.tx, &C.ty, &C.tz);
+  if (p.ndim < 2) C.ty = 1;
+  if (p.ndim < 3) C.tz = 1;
+  if (!C.stream2d && adj_smem_bytes(p, C.tx, C.ty, C.tz) > 200 * 1024) return FRKC2_EINVAL;
+  return FRKC2_OK;
+}
+
+// Recompute segment j from its checkpoint, every stage state to the tape; the segment's final
+// state goes to checkpoint j + 1.
+bool run_segment(const AdjCtx& C, int j) {
+  const frkc2_problem& p = *C.p;
+  PassArgs a{};
+  a.ndim = p.ndim;
+  a.bc = p.bc;
+  a.nx = int(p.n[0]);
+  a.ny = int(p.n[1]);
+  a.nz = int(p.n[2]);
+  a.tx = C.tx;
+  a.ty = C.ty;
+  a.tz = C.tz;
+  a.k = 1;
+  a.hx = 1;
+  a.hy = p.ndim >= 2 ? 1 : 0;
+  a.hz = p.ndim >= 3 ? 1 : 0;
+  a.fx = C.base + C.L.fx;
+  a.fy = C.base + C.L.fy;
+  a.fz = C.base + C.L.fz;
+  a.kc = p.kappa_c;
+  a.kp = p.kappa_p;
+  a.status = reinterpret_cast<unsigned*>(C.base + C.L.status);
+  const int n0 = j * C.c, m = std::min(C.c, C.nsteps - n0);
+  for (int q = 0; q < m; ++q) {
+    for (int l = 0; l < C.s; ++l) {
+      const bool last = l + 1 == C.s;
+      char* in = l == 0 ? C.w0(j, q) : C.tape(q, l);
+      char* out = !last ? C.tape(q, l + 1) : (q + 1 < m ? C.tape(q + 1, 0) : C.ckpt(j + 1));
+      a.U_in = in;
+      a.U_out = out;
+      a.check_finite = last;
+      a.ca[0] = C.dt * C.plan->a_re[l] / C.h2;
+      a.cb[0] = C.dt * C.plan->a_im[l] / C.h2;
+      cudaError_t e;
+      if (C.stream2d) {
+        a.V_in = nullptr;
+        a.V_out = nullptr;
+        a.in_mode = l == 0 ? PASS_IO_REAL : PASS_IO_COMPLEX;
+        a.out_mode = last ? PASS_IO_REAL : PASS_IO_COMPLEX;
+        e = launch_pass_stream2d(p, a, C.base + C.L.fen, C.st);
+      } else {
+        a.V_in = l == 0 ? nullptr : in + C.slot;
+        a.V_out = last ? nullptr : out + C.slot;
+        e = launch_pass_generic(p, a, C.st);
+      }
+      if (e != cudaSuccess) return false;
+    }
+  }
+  return true;
+}
+
+frkc2_status adj_forward(const AdjCtx& C, const void* u0) {
+  const frkc2_problem& p = *C.p;
+  if (p.kappa_kind != FRKC2_KAPPA_POWER) {
+    if (launch_faces(p, C.base + C.L.fx, C.base + C.L.fy, C.base + C.L.fz, C.st) != cudaSuccess) return FRKC2_ECUDA;
+    if (p.ndim == 2 && launch_face_pairs(p, C.base + C.L.fx, C.base + C.L.fy, C.base + C.L.fen, C.st) != cudaSuccess)
+      return FRKC2_ECUDA;
+  }
+  if (cudaMemcpyAsync(C.ckpt(0), u0, C.N * C.SB, cudaMemcpyDeviceToDevice, C.st) != cudaSuccess) return FRKC2_ECUDA;
+  for (int j = 0; j < C.L.nseg; ++j)
+    if (!run_segment(C, j)) return FRKC2_ECUDA;
+  return FRKC2_OK;
+}
+
+frkc2_status adj_backward(const AdjCtx& C, const void* g, void* dJdu0, void* dJdkappa) {
+  const frkc2_problem& p = *C.p;
+  double* dk = dJdkappa ? reinterpret_cast<double*>(C.base + C.L.dk) : nullptr;
+  if (dk && cudaMemsetAsync(dk, 0, C.N * sizeof(double), C.st) != cudaSuccess) return FRKC2_ECUDA;
+  char* lam[2] = {C.base + C.L.lam, C.base + C.L.lam + 2 * C.slot};  // each: U then V (planar) or (U,V) pairs
+  int cur = 0;
+  bool lam_real_input = true;  // g itself for the last step
+  const void* lam_src = g;
+  AdjArgs b{};
+  b.ndim = p.ndim;
+  b.bc = p.bc;
+  b.nx = int(p.n[0]);
+  b.ny = int(p.n[1]);
+  b.nz = int(p.n[2]);
+  b.tx = C.tx;
+  b.ty = C.ty;
+  b.tz = C.tz;
+  b.fx = C.base + C.L.fx;
+  b.fy = C.base + C.L.fy;
+  b.fz = C.base + C.L.fz;
+  b.dk = dk;
+  b.kc = p.kappa_c;
+  b.kp = p.kappa_p;
+  AdjStreamArgs sa{};
+  sa.nx = int(p.n[0]);
+  sa.ny = int(p.n[1]);
+  sa.fen = C.base + C.L.fen;
+  sa.dk = dk;
+  for (int j = C.L.nseg - 1; j >= 0; --j) {
+    if (j != C.L.nseg - 1 && !run_segment(C, j)) return FRKC2_ECUDA;
+    const int m = std::min(C.c, C.nsteps - j * C.c);
+    for (int q = m - 1; q >= 0; --q) {
+      // the step output is Re W^L: the adjoint of a step starts from a real lambda
+      for (int l = C.s - 1; l >= 0; --l) {
+        const bool first = l == C.s - 1;
+        char* W = l == 0 ? C.w0(j, q) : C.tape(q, l);
+        const double ca = C.dt * C.plan->a_re[l] / C.h2, cb = C.dt * C.plan->a_im[l] / C.h2;
+        cudaError_t e;
+        if (C.stream2d) {
+          sa.W = W;
+          sa.w_complex = l == 0 ? 0 : 1;
+          if (first) {
+            sa.L_in = lam_src;
+            sa.l_complex = lam_real_input ? 0 : 2;  // 2: real part of an interleaved buffer
+          } else {
+            sa.L_in = lam[cur];
+            sa.l_complex = 1;
+          }
+          sa.L_out = lam[cur ^ 1];
+          sa.ca = ca;
+          sa.cb = cb;
+          e = launch_adj_stream2d(p, sa, C.st);
+        } else {
+          b.WU = W;
+          b.WV = l == 0 ? nullptr : W + C.slot;
+          if (first) {
+            b.LU_in = lam_src;
+            b.LV_in = nullptr;
+          } else {
+            b.LU_in = lam[cur];
+            b.LV_in = lam[cur] + C.slot;
+          }
+          b.LU_out = lam[cur ^ 1];
+          b.LV_out = lam[cur ^ 1] + C.slot;
+          b.ca = ca;
+          b.cb = cb;
+          e = launch_adj(p, b, C.st);
+        }
+        if (e != cudaSuccess) return FRKC2_ECUDA;
+        cur ^= 1;
+      }
+      lam_src = lam[cur];
+      lam_real_input = false;
+    }
+  }
+  // dJ/du0 = Re lam^0
+  if (C.stream2d) {
+    if (cudaMemcpy2DAsync(dJdu0, C.SB, lam[cur], 2 * C.SB, C.SB, C.N, cudaMemcpyDeviceToDevice, C.st) != cudaSuccess)
+      return FRKC2_ECUDA;
+  } else {
+    if (cudaMemcpyAsync(dJdu0, lam[cur], C.N * C.SB, cudaMemcpyDeviceToDevice, C.st) != cudaSuccess)
+      return FRKC2_ECUDA;
+  }
+  if (dJdkappa) {
+    const int threads = 256, blocks = int(std::min<size_t>((C.N + threads - 1) / threads, 4096));
+    if (p.precision == FRKC2_FP64)
+      k_store_grad<double><<<blocks, threads, 0, C.st>>>(dk, static_cast<double*>(dJdkappa), C.N);
+    else
+      k_store_grad<float><<<blocks, threads, 0, C.st>>>(dk, static_cast<float*>(dJdkappa), C.N);
+    count_launch();
+    if (cudaGetLastError() != cudaSuccess) return FRKC2_ECUDA;
+  }
+  return FRKC2_OK;
+}
+
 }  // namespace
 }  // namespace frkc2
 
@@ -287,156 +498,47 @@ frkc2_status frkc2_adjoint_workspace_size(const frkc2_plan_t plan, const frkc2_p
   if (!plan || !bytes || nsteps < 0 || ckpt_every < 1) return FRKC2_EINVAL;
   const frkc2_status v = validate_problem(prob);
   if (v != FRKC2_OK) return v;
-  *bytes = adj_layout(*prob, plan->s, std::max(nsteps, 1), ckpt_every).total;
+  const int n = std::max(nsteps, 1);
+  *bytes = adj_layout(*prob, plan->s, n, std::min(ckpt_every, n)).total;
   return FRKC2_OK;
+}
+
+frkc2_status frkc2_adjoint_forward(frkc2_plan_t plan, const frkc2_problem* prob, double dt, int nsteps,
+                                   int ckpt_every, const void* u0, void* uT, void* ws, size_t ws_bytes,
+                                   void* stream) {
+  if (!u0) return FRKC2_EINVAL;
+  AdjCtx C;
+  frkc2_status v = adj_setup(C, plan, prob, dt, nsteps, ckpt_every, ws, ws_bytes, stream);
+  if (v != FRKC2_OK) return v;
+  v = adj_forward(C, u0);
+  if (v != FRKC2_OK) return v;
+  if (uT && cudaMemcpyAsync(uT, C.ckpt(C.L.nseg), C.N * C.SB, cudaMemcpyDeviceToDevice, C.st) != cudaSuccess)
+    return FRKC2_ECUDA;
+  return FRKC2_OK;
+}
+
+frkc2_status frkc2_adjoint_backward(frkc2_plan_t plan, const frkc2_problem* prob, double dt, int nsteps,
+                                    int ckpt_every, const void* g, void* dJdu0, void* dJdkappa, void* ws,
+                                    size_t ws_bytes, void* stream) {
+  if (!g || !dJdu0) return FRKC2_EINVAL;
+  if (dJdkappa && (!prob || prob->kappa_kind != FRKC2_KAPPA_FIELD)) return FRKC2_EINVAL;
+  AdjCtx C;
+  const frkc2_status v = adj_setup(C, plan, prob, dt, nsteps, ckpt_every, ws, ws_bytes, stream);
+  if (v != FRKC2_OK) return v;
+  return adj_backward(C, g, dJdu0, dJdkappa);
 }
 
 frkc2_status frkc2_adjoint(frkc2_plan_t plan, const frkc2_problem* prob, double dt, int nsteps, int ckpt_every,
                            const void* u0, const void* g, void* dJdu0, void* dJdkappa, void* ws, size_t ws_bytes,
                            void* stream) {
-  if (!plan || !u0 || !g || !dJdu0 || !ws || nsteps < 1 || ckpt_every < 1) return FRKC2_EINVAL;
-  const frkc2_status v = validate_problem(prob);
+  if (!u0 || !g || !dJdu0) return FRKC2_EINVAL;
+  if (dJdkappa && (!prob || prob->kappa_kind != FRKC2_KAPPA_FIELD)) return FRKC2_EINVAL;
+  AdjCtx C;
+  frkc2_status v = adj_setup(C, plan, prob, dt, nsteps, ckpt_every, ws, ws_bytes, stream);
   if (v != FRKC2_OK) return v;
-  const frkc2_problem& p = *prob;
-  if (dJdkappa && p.kappa_kind != FRKC2_KAPPA_FIELD) return FRKC2_EINVAL;
-  if (!(dt > 0.0) || !std::isfinite(dt)) return FRKC2_EINVAL;
-  if (reinterpret_cast<uintptr_t>(ws) & 255) return FRKC2_EINVAL;
-  const int s = plan->s;
-  const int c = std::min(ckpt_every, nsteps);
-  const AdjLayout L = adj_layout(p, s, nsteps, c);
-  if (ws_bytes < L.total) return FRKC2_ENOMEM;
-  cudaStream_t st = static_cast<cudaStream_t>(stream);
-  char* base = static_cast<char*>(ws);
-  const size_t N = cells(p), SB = state_bytes(p.precision), slot = align256(N * SB);
-  const double h2 = p.dx * p.dx;
-
-  int tx, ty, tz;
-  default_tiles(p, 1, &tx, &ty, &tz);
-  if (p.ndim < 2) ty = 1;
-  if (p.ndim < 3) tz = 1;
-  if (adj_smem_bytes(p, tx, ty, tz) > 200 * 1024) return FRKC2_EINVAL;
-
-  if (p.kappa_kind != FRKC2_KAPPA_POWER) {
-    if (launch_faces(p, base + L.fx, base + L.fy, base + L.fz, st) != cudaSuccess) return FRKC2_ECUDA;
-    if (p.ndim == 2 && launch_face_pairs(p, base + L.fx, base + L.fy, base + L.fen, st) != cudaSuccess)
-      return FRKC2_ECUDA;
-  }
-  if (dJdkappa && cudaMemsetAsync(base + L.dk, 0, N * sizeof(double), st) != cudaSuccess) return FRKC2_ECUDA;
-  auto ckpt = [&](int j) { return base + L.ckpt + size_t(j) * slot; };
-  auto tapeU = [&](int n, int l) { return base + L.tape + (size_t(n) * s + l) * 2 * slot; };
-  auto tapeV = [&](int n, int l) { return tapeU(n, l) + slot; };
-  if (cudaMemcpyAsync(ckpt(0), u0, N * SB, cudaMemcpyDeviceToDevice, st) != cudaSuccess) return FRKC2_ECUDA;
-
-  // forward pass arguments (k = 1 stages)
-  PassArgs a{};
-  a.ndim = p.ndim;
-  a.bc = p.bc;
-  a.nx = int(p.n[0]);
-  a.ny = int(p.n[1]);
-  a.nz = int(p.n[2]);
-  a.tx = tx;
-  a.ty = ty;
-  a.tz = tz;
-  a.k = 1;
-  a.hx = 1;
-  a.hy = p.ndim >= 2 ? 1 : 0;
-  a.hz = p.ndim >= 3 ? 1 : 0;
-  a.fx = base + L.fx;
-  a.fy = base + L.fy;
-  a.fz = base + L.fz;
-  a.kc = p.kappa_c;
-  a.kp = p.kappa_p;
-  a.status = reinterpret_cast<unsigned*>(base + L.status);
-  const bool stream2d = p.ndim == 2 && p.kappa_kind != FRKC2_KAPPA_POWER;
-
-  // recompute segment j: every stage state of its steps goes to the tape; the segment's final
-  // state goes to checkpoint j+1
-  auto run_segment = [&](int j) -> bool {
-    const int n0 = j * c, m = std::min(c, nsteps - n0);
-    for (int q = 0; q < m; ++q) {
-      for (int l = 0; l < s; ++l) {
-        a.U_in = l == 0 ? (q == 0 ? static_cast<const void*>(ckpt(j)) : tapeU(q, 0)) : tapeU(q, l);
-        a.V_in = l == 0 ? nullptr : tapeV(q, l);
-        if (l == 0 && q == 0) {
-          // stage 0 of the segment reads the checkpoint; keep a copy of it in the tape slot
-          if (cudaMemcpyAsync(tapeU(0, 0), ckpt(j), N * SB, cudaMemcpyDeviceToDevice, st) != cudaSuccess) return false;
-          a.U_in = tapeU(0, 0);
-        }
-        if (l + 1 < s) {
-          a.U_out = tapeU(q, l + 1);
-          a.V_out = tapeV(q, l + 1);
-        } else {
-          a.U_out = q + 1 < m ? static_cast<void*>(tapeU(q + 1, 0)) : static_cast<void*>(ckpt(j + 1));
-          a.V_out = nullptr;
-        }
-        a.check_finite = l + 1 == s;
-        a.in_mode = l == 0 ? PASS_IO_REAL : PASS_IO_PLANAR;
-        a.out_mode = l + 1 < s ? PASS_IO_PLANAR : PASS_IO_REAL;
-        a.ca[0] = dt * plan->a_re[l] / h2;
-        a.cb[0] = dt * plan->a_im[l] / h2;
-        const cudaError_t e = stream2d ? launch_pass_stream2d(p, a, base + L.fen, st) : launch_pass_generic(p, a, st);
-        if (e != cudaSuccess) return false;
-      }
-    }
-    return true;
-  };
-
-  for (int j = 0; j < L.nseg; ++j)
-    if (!run_segment(j)) return FRKC2_ECUDA;
-
-  // backward
-  char* lam[2][2] = {{base + L.lam, base + L.lam + slot}, {base + L.lam + 2 * slot, base + L.lam + 3 * slot}};
-  if (cudaMemcpyAsync(lam[0][0], g, N * SB, cudaMemcpyDeviceToDevice, st) != cudaSuccess) return FRKC2_ECUDA;
-  int cur = 0;
-  bool lam_v_zero = true;
-  AdjArgs b{};
-  b.ndim = p.ndim;
-  b.bc = p.bc;
-  b.nx = a.nx;
-  b.ny = a.ny;
-  b.nz = a.nz;
-  b.tx = tx;
-  b.ty = ty;
-  b.tz = tz;
-  b.fx = a.fx;
-  b.fy = a.fy;
-  b.fz = a.fz;
-  b.dk = dJdkappa ? reinterpret_cast<double*>(base + L.dk) : nullptr;
-  b.kc = p.kappa_c;
-  b.kp = p.kappa_p;
-  for (int j = L.nseg - 1; j >= 0; --j) {
-    if (j != L.nseg - 1 && !run_segment(j)) return FRKC2_ECUDA;
-    const int m = std::min(c, nsteps - j * c);
-    for (int q = m - 1; q >= 0; --q) {
-      lam_v_zero = true;  // the step output is Re W^L: its adjoint has zero imaginary part
-      for (int l = s - 1; l >= 0; --l) {
-        b.WU = tapeU(q, l);
-        b.WV = l == 0 ? nullptr : tapeV(q, l);
-        b.LU_in = lam[cur][0];
-        b.LV_in = lam_v_zero ? nullptr : lam[cur][1];
-        b.LU_out = lam[cur ^ 1][0];
-        b.LV_out = lam[cur ^ 1][1];
-        b.ca = dt * plan->a_re[l] / h2;
-        b.cb = dt * plan->a_im[l] / h2;
-        if (launch_adj(p, b, st) != cudaSuccess) return FRKC2_ECUDA;
-        cur ^= 1;
-        lam_v_zero = false;
-      }
-    }
-  }
-  if (cudaMemcpyAsync(dJdu0, lam[cur][0], N * SB, cudaMemcpyDeviceToDevice, st) != cudaSuccess) return FRKC2_ECUDA;
-  if (dJdkappa) {
-    const int threads = 256, blocks = int(std::min<size_t>((N + threads - 1) / threads, 4096));
-    if (p.precision == FRKC2_FP64)
-      k_store_grad<double><<<blocks, threads, 0, st>>>(reinterpret_cast<double*>(base + L.dk),
-                                                       static_cast<double*>(dJdkappa), N);
-    else
-      k_store_grad<float><<<blocks, threads, 0, st>>>(reinterpret_cast<double*>(base + L.dk),
-                                                      static_cast<float*>(dJdkappa), N);
-    count_launch();
-    if (cudaGetLastError() != cudaSuccess) return FRKC2_ECUDA;
-  }
-  return FRKC2_OK;
+  v = adj_forward(C, u0);
+  if (v != FRKC2_OK) return v;
+  return adj_backward(C, g, dJdu0, dJdkappa);
 }
 
 }  // extern "C"

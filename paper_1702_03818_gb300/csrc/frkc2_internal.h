@@ -84,6 +84,20 @@ bool tb2d_supported(const frkc2_problem& p, int k);
 size_t generic_smem_bytes(const frkc2_problem& p, const PassArgs& a);
 void default_tiles(const frkc2_problem& p, int k, int* tx, int* ty, int* tz);
 
+// One streamed 2D adjoint stage (fixed conductivity).
+struct AdjStreamArgs {
+  int nx, ny;
+  const void* fen;    // face pairs
+  const void* W;      // stage state W^l
+  int w_complex;      // 0: real array (imaginary part 0), 1: interleaved (U, V)
+  const void* L_in;   // lam^{l+1}
+  int l_complex;      // 0: real array, 1: interleaved, 2: real part of an interleaved array
+  void* L_out;        // lam^l, interleaved
+  double* dk;         // dJ/dkappa accumulator or nullptr
+  double ca, cb;      // dt a_l / dx^2
+};
+cudaError_t launch_adj_stream2d(const frkc2_problem& p, const AdjStreamArgs& a, cudaStream_t st);
+
 void count_launch(int n = 1);
 
 }  // namespace frkc2

@@ -56,6 +56,10 @@ _sig = {
                                                C.POINTER(C.c_size_t)]),
     "frkc2_adjoint": (C.c_int, [_P, C.POINTER(frkc2_problem), C.c_double, C.c_int, C.c_int, _P, _P, _P,
                                 _P, _P, C.c_size_t, _P]),
+    "frkc2_adjoint_forward": (C.c_int, [_P, C.POINTER(frkc2_problem), C.c_double, C.c_int, C.c_int, _P, _P,
+                                        _P, C.c_size_t, _P]),
+    "frkc2_adjoint_backward": (C.c_int, [_P, C.POINTER(frkc2_problem), C.c_double, C.c_int, C.c_int, _P, _P,
+                                         _P, _P, C.c_size_t, _P]),
     "frkc2_batch_workspace_size": (C.c_int, [C.c_int, _P, C.POINTER(frkc2_problem), _P,
                                              C.POINTER(frkc2_tuning), C.POINTER(C.c_size_t)]),
     "frkc2_batch_prepare": (C.c_int, [C.c_int, _P, C.POINTER(frkc2_problem), _P, _P, _P,
@@ -238,6 +242,21 @@ def frkc2_adjoint(plan: Plan, prob: frkc2_problem, dt: float, nsteps: int, ckpt_
     _check(_lib.frkc2_adjoint(plan.handle, C.byref(prob), float(dt), int(nsteps), int(ckpt_every),
                               _ptr(u0), _ptr(g), _ptr(dJdu0), _ptr(dJdkappa), _ptr(ws),
                               ws.numel() * ws.element_size(), _stream_ptr(stream)), "frkc2_adjoint")
+
+
+def frkc2_adjoint_forward(plan: Plan, prob: frkc2_problem, dt: float, nsteps: int, ckpt_every: int, u0, uT,
+                          ws, stream=None):
+    _check(_lib.frkc2_adjoint_forward(plan.handle, C.byref(prob), float(dt), int(nsteps), int(ckpt_every),
+                                      _ptr(u0), _ptr(uT), _ptr(ws), ws.numel() * ws.element_size(),
+                                      _stream_ptr(stream)), "frkc2_adjoint_forward")
+
+
+def frkc2_adjoint_backward(plan: Plan, prob: frkc2_problem, dt: float, nsteps: int, ckpt_every: int, g,
+                           dJdu0, dJdkappa, ws, stream=None):
+    _check(_lib.frkc2_adjoint_backward(plan.handle, C.byref(prob), float(dt), int(nsteps), int(ckpt_every),
+                                       _ptr(g), _ptr(dJdu0), _ptr(dJdkappa), _ptr(ws),
+                                       ws.numel() * ws.element_size(), _stream_ptr(stream)),
+           "frkc2_adjoint_backward")
 
 
 def _batch_arrays(plans, probs, dt, nsteps, u):

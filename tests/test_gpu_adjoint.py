@@ -136,3 +136,27 @@ def test_autograd_wrapper():
     ref_u, ref_k = O.frkc2_adjoint(u0, oplan["a"], dt, opr, nsteps, 2 * uT)
     assert rel_l2(u.grad.cpu().numpy(), ref_u) < 1e-10
     assert rel_l2(k.grad.cpu().numpy(), ref_k) < 1e-10
+
+
+@pytest.mark.parametrize("shape,bc", [((50, 44), "periodic"), ((33, 41), "dirichlet")])
+def test_split_forward_backward_equals_combined(shape, bc):
+    u0, field = seeded_case(shape, bc, "field", 61)
+    s, nsteps, ck = 16, 5, 2
+    plan = F.frkc2_plan(s)
+    dt = 0.8 * O.beta(s) / O.rho_bound(oracle_problem(2, bc, "field", 1.0, field))
+    kt = dev(field, torch.float64)
+    pr = F.make_problem(2, tuple(reversed(shape)), 1.0, bc, "field", "fp64", kappa_field=kt)
+    ws = torch.empty(F.frkc2_adjoint_workspace_size(plan, pr, nsteps, ck), dtype=torch.uint8, device="cuda")
+    u0d = dev(u0, torch.float64)
+    uT = torch.empty_like(u0d)
+    F.frkc2_adjoint_forward(plan, pr, dt, nsteps, ck, u0d, uT, ws)
+    ref_uT = gpu_forward(plan, shape, bc, "field", "fp64", u0, field, dt, nsteps)
+    assert rel_l2(uT.cpu().numpy(), ref_uT) < 1e-13
+    g = np.random.default_rng(62).standard_normal(shape)
+    du = torch.empty_like(u0d)
+    dk = torch.empty_like(kt)
+    F.frkc2_adjoint_backward(plan, pr, dt, nsteps, ck, dev(g, torch.float64), du, dk, ws)
+    du2, dk2 = gpu_adjoint(plan, shape, bc, "field", "fp64", u0, field, dt, nsteps, ck, g)
+    assert np.array_equal(du.cpu().numpy(), du2) and np.array_equal(dk.cpu().numpy(), dk2)
+    ref_u, ref_k = O.frkc2_adjoint(u0, O.plan(s)["a"], dt, oracle_problem(2, bc, "field", 1.0, field), nsteps, g)
+    assert rel_l2(du2, ref_u) < 1e-10 and rel_l2(dk2, ref_k) < 1e-10
