@@ -42,7 +42,10 @@ FP64_PEAK_TINST = 152 * 2 * 2.07e9 / 1e12
 FP64_INST_PER_CELL_STAGE = 18  # 2 x (2 differences + 2 face products + 3 sums) + 4 FMA updates
 # dram bytes per launch from one ncu capture of each pass kernel, keyed by the source hash of
 # the kernel file at capture time (the value is reported only while the source is unchanged)
-NCU_TRAFFIC = {}
+NCU_TRAFFIC = {
+    # profiles/stream2d_fp64_varkappa2d_2048.md: an intermediate pass, read 152.7 MB + write 50.0 MB
+    ("pass_stream2d.cu", "8bfbed348f174b59"): 202.7e6,
+}
 
 
 def kernel_source_hash(name: str) -> str:
@@ -218,6 +221,7 @@ def run_ours(args, rank, world, local_rank):
         "bound": "alu", "achieved": achieved_tinst, "peak": FP64_PEAK_TINST,
         "unit": "Tinst/s (FP64 pipe)", "frac": achieved_tinst / FP64_PEAK_TINST,
         "traffic": NCU_TRAFFIC.get(("pass_stream2d.cu", kernel_source_hash("pass_stream2d.cu"))),
+        "algorithmic_bytes_per_launch": 40 * cells,
         "kernel": "k_stream2d<double,double,periodic>",
         "hbm_achieved_gbs": hbm_gbs, "hbm_peak_gbs": peak_hbm, "hbm_peak_kind": peak_kind,
         "hbm_frac": hbm_gbs / peak_hbm, "avg_launch_us": launch_s * 1e6,
@@ -386,7 +390,11 @@ def main():
         import bench_workloads as BW
         from paper_1702_03818_gb300 import frkc2 as F
         if rank == 0:
-            print(json.dumps(BW.WORKLOADS[args.workload](F)), flush=True)
+            if args.workload.startswith("profile:"):
+                out = BW.profile_case(F, args.workload.split(":", 1)[1])
+            else:
+                out = BW.WORKLOADS[args.workload](F)
+            print(json.dumps(out), flush=True)
         return
     if args.impl == "reference":
         out = run_reference(args, rank, world)
