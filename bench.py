@@ -154,8 +154,8 @@ def run_ours(args, rank, world, local_rank):
             c["u"].copy_(c["u0"])
             job(c)
         torch.cuda.synchronize()
-        if world > 1:
-            torch.distributed.barrier()
+        from paper_1702_03818_gb300 import dist as D
+        D.barrier(dev)
         ms = []
         launches = 0
         if clocks:
@@ -173,8 +173,7 @@ def run_ours(args, rank, world, local_rank):
             e1.synchronize()
             ms.append(e0.elapsed_time(e1))
         torch.cuda.synchronize()
-        if world > 1:
-            torch.distributed.barrier()
+        D.barrier(dev)
         clk = clocks.stop() if clocks else None
         assert F.frkc2_workspace_status(c["ws"]) == F.OK
         return c, ms, launches, clk
@@ -201,10 +200,8 @@ def run_ours(args, rank, world, local_rank):
     c64, ms, launches, clk = timed("fp64", args.steps, args.warmup, clocks)
     total_ms = float(np.sum(ms))
     # max over ranks of the timed region
-    if world > 1:
-        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
+    from paper_1702_03818_gb300 import dist as D
+    total_ms = D.max_over_ranks(total_ms, dev)
     value = world * cell_stages * args.steps / (total_ms / 1e3)
     u64 = c64["u"].double().cpu().numpy()
 
