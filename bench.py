@@ -141,18 +141,18 @@ def run_ours(args, rank, world, local_rank):
         F.frkc2_workspace_reset(ws)
         return dict(u0=u0, u=u0.clone(), k=kt, pr=pr, ws=ws, rho=torch.zeros(1, dtype=torch.float64, device=dev))
 
-    def job(c):
+    def job(c, pl=None):
         F.frkc2_rho_bound(c["pr"], None, c["rho"])
         rho = c["rho"].item()
         dt = CFG["cfl"] * beta / rho
-        F.frkc2_step(plan, c["pr"], dt, nsteps, rho, c["u"], c["ws"])
+        F.frkc2_step(pl or plan, c["pr"], dt, nsteps, rho, c["u"], c["ws"])
         return dt
 
-    def timed(prec, K, W, clocks=None):
+    def timed(prec, K, W, clocks=None, pl=None):
         c = setup(prec)
         for _ in range(W):
             c["u"].copy_(c["u0"])
-            job(c)
+            job(c, pl)
         torch.cuda.synchronize()
         from paper_1702_03818_gb300 import dist as D
         D.barrier(dev)
@@ -167,7 +167,7 @@ def run_ours(args, rank, world, local_rank):
             e1 = torch.cuda.Event(enable_timing=True)
             F.frkc2_launch_count()
             e0.record(stream)
-            job(c)
+            job(c, pl)
             e1.record(stream)
             launches += F.frkc2_launch_count()
             e1.synchronize()
@@ -178,8 +178,8 @@ def run_ours(args, rank, world, local_rank):
         assert F.frkc2_workspace_status(c["ws"]) == F.OK
         return c, ms, launches, clk
 
-    def step_only_ms(c, reps=2):
-        """Event time of frkc2_step alone (the pass kernels and the face set-up kernel)."""
+    def step_only_ms(c, reps=2, pl=None):
+        """Event time of frkc2_step alone (the pass kernels and the face set-up kernels)."""
         F.frkc2_rho_bound(c["pr"], None, c["rho"])
         rho = c["rho"].item()
         dt = CFG["cfl"] * beta / rho
@@ -190,7 +190,7 @@ def run_ours(args, rank, world, local_rank):
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            F.frkc2_step(plan, c["pr"], dt, nsteps, rho, c["u"], c["ws"])
+            F.frkc2_step(pl or plan, c["pr"], dt, nsteps, rho, c["u"], c["ws"])
             e1.record(stream)
             e1.synchronize()
             out.append(e0.elapsed_time(e1))
@@ -248,6 +248,22 @@ def run_ours(args, rank, world, local_rank):
                              "frac": g / peak_hbm, "peak_kind": peak_kind, "traffic": None},
             }
             del c
+        # FP64 with conjugate pairs in adjacent stages, each pair applied to the real state
+        plan_p = F.frkc2_plan(s, flags=F.PLAN_PAIRED)
+        c, vms, _, _ = timed("fp64", args.steps, max(3, args.warmup // 2), pl=plan_p)
+        v = cell_stages * args.steps / (np.sum(vms) / 1e3)
+        got = c["u"].double().cpu().numpy()
+        smsec = step_only_ms(c, pl=plan_p)
+        ach = 8.5 * cells * s * nsteps / (smsec / 1e3) / 1e12
+        variants["fp64_paired"] = {
+            "value": v, "ms_per_step": float(np.mean(vms)), "plan": "FRKC2_PLAN_PAIRED (Lebedev pairs, Q ~ 0.12 L^4)",
+            "speedup_vs_fp64": v / (cell_stages * args.steps / (float(np.sum(ms)) / 1e3)),
+            "rel_l2_vs_fp64_gpu_after_100_steps": float(np.linalg.norm(got - u64) / np.linalg.norm(u64)),
+            "roofline": {"bound": "alu", "achieved": ach, "peak": FP64_PEAK_TINST,
+                         "unit": "Tinst/s (FP64 pipe)", "frac": ach / FP64_PEAK_TINST,
+                         "inst_per_cell_stage": 8.5, "traffic": None},
+        }
+        del c
 
     # e2e: host buffers, copies inside the timed region (primary precision)
     e2e = None
@@ -330,6 +346,17 @@ def cpu_baseline(torch, F, dev, n=1024):
         F.frkc2_step(plan, lp, dt, 1, 0.0, u, ws)
         got = u.double().cpu().numpy()
         errs[prec] = float(np.linalg.norm(got - ref) / np.linalg.norm(ref))
+    # the paired variant against the oracle's complex stages in the same (paired) order
+    pplan = F.frkc2_plan(s, flags=F.PLAN_PAIRED)
+    opl = O.plan(s, method="paired")
+    pr = dict(ndim=2, dx=1.0, bc="periodic", kappa="field", kappa_c=1.0, kappa_p=2.5, kappa_field=k)
+    dt = CFG["cfl"] * O.beta(s) / O.rho_bound(pr)
+    ref = O.frkc2_step(u0, opl["a"], dt, pr, 1)
+    u = torch.as_tensor(u0, dtype=torch.float64, device=dev)
+    lp = F.make_problem(2, (n, n), 1.0, "periodic", "field", "fp64", kappa_field=torch.as_tensor(k, device=dev))
+    ws = torch.empty(F.frkc2_workspace_size(lp), dtype=torch.uint8, device=dev)
+    F.frkc2_step(pplan, lp, dt, 1, 0.0, u, ws)
+    errs["fp64_paired"] = float(np.linalg.norm(u.cpu().numpy() - ref) / np.linalg.norm(ref))
     errs["sample"] = f"one step (64 stages) on a {n}^2 instance of the recipe"
     return ({"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample}, errs)
 

@@ -233,6 +233,35 @@ def order_lebedev(L: int) -> np.ndarray:
     return np.concatenate([h, L - 1 - h])
 
 
+def order_paired(L: int) -> np.ndarray:
+    """Stage order with each conjugate pair adjacent: for the upper-half roots j in
+    Lebedev-Finogenov order, the stages j then L-1-j.  Two adjacent conjugate stages act on a
+    real state as the real quadratic factor 1 + 2 Re(a) z + |a|^2 z^2 (the pairs "taken in
+    conjugate pairs and evaluated in real arithmetic"); any such order has Q >= the largest
+    quadratic factor (about 0.12 L^4)."""
+    h = np.asarray(lebedev_permutation(L // 2), dtype=np.int64)
+    return np.stack([h, L - 1 - h], axis=1).ravel()
+
+
+def frkc2_step_paired(u0, a, T, prob, nsteps: int = 1):
+    """The FRKC2 step with the stages applied pair by pair in real arithmetic.
+
+    For adjacent stages (a, conj(a)) and a linear f, (1 + T a f)(1 + T conj(a) f) w =
+    w + 2 T Re(a) f(w) + T^2 |a|^2 f(f(w)); with alpha = Re a, beta = Im a this is evaluated
+    as Y = w + T alpha f(w), w' = w + T (alpha - beta^2/alpha) f(w) + T (|a|^2/alpha) f(Y).
+    ``a`` must list each pair as two consecutive entries (``order_paired``).
+    """
+    u = np.array(u0, dtype=np.float64)
+    a = np.asarray(a)
+    for _ in range(nsteps):
+        for p in range(len(a) // 2):
+            al, be = a[2 * p].real, a[2 * p].imag
+            fw = apply_f(u, prob)
+            Y = u + T * al * fw
+            u = u + T * (al - be * be / al) * fw + T * ((al * al + be * be) / al) * apply_f(Y, prob)
+    return u
+
+
 def plan(L: int, samples: int | None = None, q_points: int | None = None, n_max: int = 10,
          bound: float = 10.0, method: str = "auto", nu0: float = 0.0) -> dict:
     """Ordered FRKC2 step sizes for L stages (Sec. 2.2, the n-loop).
@@ -246,6 +275,7 @@ def plan(L: int, samples: int | None = None, q_points: int | None = None, n_max:
     ``auto`` (reading): the greedy n-loop for L <= 256, where it meets the bound; above that
     the Lebedev-Finogenov order, and the greedy n-loop as well only if that order misses the
     bound (the smaller realised Q is kept).
+    ``paired``: ``order_paired`` (conjugates adjacent, for real-arithmetic pair stages).
     ``nu0`` > 0 uses the damped step sizes of Sec. 2.1, with beta found by bisection.
     """
     if nu0 > 0.0:
@@ -265,6 +295,9 @@ def plan(L: int, samples: int | None = None, q_points: int | None = None, n_max:
             best = dict(L=L, order=np.asarray(perm), a=a[perm], beta=b, Q=Q, n=n)
         return Q
 
+    if method == "paired":
+        consider(order_paired(L), 0)
+        return best
     run_greedy = method == "greedy" or (method == "auto" and L <= 256)
     if method == "lebedev" or (method == "auto" and L > 256):
         q = consider(order_lebedev(L), 0)

@@ -180,11 +180,17 @@ frkc2_status frkc2_step(frkc2_plan_t plan, const frkc2_problem* prob, double dt,
   if (p.ndim < 3) tz = 1;
   if (tx < 1 || ty < 1 || tz < 1) return FRKC2_EINVAL;
   const int kern = tune ? tune->kernel : 0;
-  if (kern < 0 || kern > 3) return FRKC2_EINVAL;
+  if (kern < 0 || kern > 4) return FRKC2_EINVAL;
   const bool stream_ok = p.ndim == 2 && p.kappa_kind != FRKC2_KAPPA_POWER && k == 1;
   const bool tb_ok = tb2d_supported(p, k);
-  bool use_stream2d = false, use_tb = false;
-  if (kern == 2) {
+  const bool paired_ok = plan->paired && p.ndim == 2 && p.kappa_kind != FRKC2_KAPPA_POWER;
+  bool use_stream2d = false, use_tb = false, use_paired = false;
+  if (kern == 4) {
+    if (!paired_ok) return FRKC2_EUNSUPPORTED;
+    use_paired = true;
+  } else if (kern == 0 && paired_ok && !(tune && tune->k)) {
+    use_paired = true;
+  } else if (kern == 2) {
     if (!stream_ok) return FRKC2_EUNSUPPORTED;
     use_stream2d = true;
   } else if (kern == 3) {
@@ -205,7 +211,8 @@ frkc2_status frkc2_step(frkc2_plan_t plan, const frkc2_problem* prob, double dt,
     probe.hx = k;
     probe.hy = p.ndim >= 2 ? k : 0;
     probe.hz = p.ndim >= 3 ? k : 0;
-    if (!use_stream2d && !use_tb && generic_smem_bytes(p, probe) > size_t(smem_optin())) return FRKC2_EINVAL;
+    if (!use_stream2d && !use_tb && !use_paired && generic_smem_bytes(p, probe) > size_t(smem_optin()))
+      return FRKC2_EINVAL;
   }
   if (nsteps == 0) return FRKC2_OK;
 
@@ -240,6 +247,31 @@ frkc2_status frkc2_step(frkc2_plan_t plan, const frkc2_problem* prob, double dt,
 
   const void* curU = u;
   const void* curV = nullptr;
+  if (use_paired) {
+    // real state throughout; each pass applies one conjugate pair (stages 2q, 2q+1)
+    if (launch_face_pairs(p, base + L.fx, base + L.fy, base + L.fen, st) != cudaSuccess) return FRKC2_ECUDA;
+    const int npair = s / 2;
+    for (int n = 0; n < nsteps; ++n) {
+      for (int q = 0; q < npair; ++q) {
+        const bool last = n == nsteps - 1 && q == npair - 1;
+        void* out = (last && curU != u) ? u : (curU == ua ? ub : ua);
+        const double al = plan->a_re[2 * q], be = plan->a_im[2 * q];
+        a.U_in = curU;
+        a.U_out = out;
+        a.V_in = a.V_out = nullptr;
+        a.check_finite = q == npair - 1;
+        a.ca[0] = dt * al / h2;
+        a.ca[1] = dt * (al - be * be / al) / h2;
+        a.cb[0] = dt * ((al * al + be * be) / al) / h2;
+        if (launch_pass_paired2d(p, a, base + L.fen, st) != cudaSuccess) return FRKC2_ECUDA;
+        curU = out;
+      }
+    }
+    if (curU != u &&
+        cudaMemcpyAsync(u, curU, cells(p) * state_bytes(p.precision), cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+      return FRKC2_ECUDA;
+    return FRKC2_OK;
+  }
   if (use_stream2d) {
     // interleaved complex state between passes: W buffers at ua (with va) and ub (with vb)
     if (launch_face_pairs(p, base + L.fx, base + L.fy, base + L.fen, st) != cudaSuccess) return FRKC2_ECUDA;

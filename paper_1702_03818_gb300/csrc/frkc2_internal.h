@@ -17,6 +17,7 @@ struct frkc2_plan_s {
   std::vector<int> order;     // root index of each stage
   std::vector<double> a_re;   // step sizes in stage order
   std::vector<double> a_im;
+  bool paired = false;        // conjugates adjacent: stages 2p, 2p+1 form one real pair
 };
 
 namespace frkc2 {
@@ -80,6 +81,7 @@ cudaError_t launch_pass_stream2d(const frkc2_problem& p, const PassArgs& a, cons
 size_t face_pair_bytes(const frkc2_problem& p);
 cudaError_t launch_face_pairs(const frkc2_problem& p, const void* fx, const void* fy, void* out, cudaStream_t st);
 cudaError_t launch_pass_tb2d(const frkc2_problem& p, const PassArgs& a, cudaStream_t st);
+cudaError_t launch_pass_paired2d(const frkc2_problem& p, const PassArgs& a, const void* fen, cudaStream_t st);
 bool tb2d_supported(const frkc2_problem& p, int k);
 size_t generic_smem_bytes(const frkc2_problem& p, const PassArgs& a);
 void default_tiles(const frkc2_problem& p, int k, int* tx, int* ty, int* tz);

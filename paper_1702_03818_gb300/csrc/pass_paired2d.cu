@@ -1,0 +1,185 @@
+// 2D pass applying one conjugate pair of stages in real arithmetic (fixed conductivity).
+//
+// Two adjacent stages with step sizes a and conj(a) (Sec. 3, Eq. 13) act on a real state w of a
+// linear problem as the real quadratic factor (1 + T a f)(1 + T conj(a) f) w =
+// w + 2 T alpha f(w) + T^2 |a|^2 f(f(w)), alpha = Re a, beta = Im a, evaluated here as
+//   Y = w + cy f(w),   w' = w + c1 f(w) + c2 f(Y),
+//   cy = T alpha / dx^2,  c1 = T (alpha - beta^2/alpha) / dx^2,  c2 = T (|a|^2/alpha) / dx^2
+// (f here without the 1/dx^2, which the coefficients carry).  The state stays real: 8 bytes
+// per cell in FP64 instead of 16, and 17 floating-point instructions per pair (two
+// flux-shared stencils, 1 + 2 fused multiply-adds) instead of 2 x 18 for two complex stages.
+//
+// Streaming layout: a warp owns 32 consecutive columns, outputs 29 of them (lanes 2..30), and
+// walks rows upward.  At row y it reads w(y+2), forms f(w) and Y for row y+1 and f(Y) and w'
+// for row y; x-neighbours come by shuffle (lane 31 reads its east neighbour itself), the
+// north fluxes of f(w) and f(Y) are carried to the next row.  Same persistent, balanced work
+// split as the complex streaming pass.
+#include <algorithm>
+
+#include <cuda_runtime.h>
+
+#include "frkc2_internal.h"
+
+namespace frkc2 {
+namespace {
+
+constexpr int PR_THREADS = 256;
+constexpr int PR_WARPS = PR_THREADS / 32;
+constexpr int PR_COLS = 29;  // output columns per warp (lanes 2..30)
+
+template <class T> struct P2t;
+template <> struct P2t<double> { using type = double2; };
+template <> struct P2t<float> { using type = float2; };
+
+__device__ __forceinline__ bool bad_bits(double v) { return (__double2hiint(v) & 0x7ff00000) == 0x7ff00000; }
+__device__ __forceinline__ bool bad_bits(float v) { return (__float_as_uint(v) & 0x7f800000u) == 0x7f800000u; }
+
+template <class S, class A, bool PERIODIC>
+__global__ void __launch_bounds__(PR_THREADS, 4)
+    k_paired2d(const PassArgs p, const void* __restrict__ fen_v, long long total, long long nwarps_grid) {
+  using A2 = typename P2t<A>::type;
+  const int lane = threadIdx.x & 31;
+  const long long gw = (long long)blockIdx.x * PR_WARPS + (threadIdx.x >> 5);
+  const int nx = p.nx, ny = p.ny;
+  long long idx = gw * total / nwarps_grid;
+  const long long end = (gw + 1) * total / nwarps_grid;
+  const A2* __restrict__ FEN = static_cast<const A2*>(fen_v);
+  const S* __restrict__ W = static_cast<const S*>(p.U_in);
+  S* __restrict__ Wo = static_cast<S*>(p.U_out);
+  const S cy = S(p.ca[0]), c1 = S(p.ca[1]), c2 = S(p.cb[0]);
+  bool bad = false;
+
+  while (idx < end) {  // warp-uniform
+    const int wcol = int(idx / ny);
+    const int y0 = int(idx - (long long)wcol * ny);
+    const int y1 = int(min((long long)ny, (long long)y0 + (end - idx)));
+    idx += y1 - y0;
+    const int x = wcol * PR_COLS + lane - 2;
+    int xr;
+    bool xin;
+    if (PERIODIC) {
+      xr = ((x % nx) + nx) % nx;
+      xin = true;
+    } else {
+      xr = x;
+      xin = x >= 0 && x < nx;
+    }
+    int xeast;
+    bool eastin;
+    if (PERIODIC) {
+      xeast = xr + 1 == nx ? 0 : xr + 1;
+      eastin = true;
+    } else {
+      xeast = x + 1;
+      eastin = xeast >= 0 && xeast < nx;
+    }
+    const bool has_faces = PERIODIC || (x >= -1 && x < nx);
+    const int fcol = (PERIODIC ? xr : x) + 1;
+    const bool out_ok = lane >= 2 && lane <= 30 && x >= 0 && x < nx;
+
+    auto wrapy = [&](int yy) { return PERIODIC ? (yy < 0 ? yy + ny : (yy >= ny ? yy - ny : yy)) : yy; };
+    auto ld = [&](int yy, int xx, bool inx) -> S {
+      if (!PERIODIC && !(inx && yy >= 0 && yy < ny)) return S(0);
+      return __ldg(W + size_t(wrapy(yy)) * nx + xx);
+    };
+    auto faces = [&](int yy) -> A2 {
+      A2 f;
+      f.x = A(0);
+      f.y = A(0);
+      if (!has_faces) return f;
+      return __ldg(FEN + size_t(wrapy(yy) + 1) * (nx + 1) + fcol);
+    };
+    auto cell_in = [&](int yy) { return PERIODIC || (xin && yy >= 0 && yy < ny); };
+    // f along x for one row: east flux by this lane, west flux from lane - 1
+    auto xflux = [&](S wc, S we, A ke) -> A {
+      const A Fe = ke * A(we - wc);
+      const A Fw = __shfl_up_sync(0xffffffffu, Fe, 1);
+      return Fe - Fw;
+    };
+    auto east_of = [&](S wc, int yy) -> S {
+      S e = __shfl_down_sync(0xffffffffu, wc, 1);
+      if (lane == 31) e = ld(yy, xeast, eastin);
+      return e;
+    };
+
+    // prologue: rows y0-2 .. y0+1 of w; f(w) and Y of rows y0-1, y0; north fluxes
+    const S wm2 = ld(y0 - 2, xr, xin), wm1 = ld(y0 - 1, xr, xin), w0 = ld(y0, xr, xin), w1 = ld(y0 + 1, xr, xin);
+    const A2 fm2 = faces(y0 - 2), fm1 = faces(y0 - 1), f0 = faces(y0);
+    // north flux of w through the faces below rows y0-1, y0, y0+1
+    const A FnWm2 = fm2.y * A(wm1 - wm2);
+    const A FnWm1 = fm1.y * A(w0 - wm1);
+    const A FnW0 = f0.y * A(w1 - w0);
+    const A fWm1 = xflux(wm1, east_of(wm1, y0 - 1), fm1.x) + (FnWm1 - FnWm2);
+    A fW0 = xflux(w0, east_of(w0, y0), f0.x) + (FnW0 - FnWm1);
+    const S Ym1 = cell_in(y0 - 1) ? wm1 + cy * S(fWm1) : S(0);
+    S Y0 = cell_in(y0) ? w0 + cy * S(fW0) : S(0);
+    A FnYm1 = fm1.y * A(Y0 - Ym1);  // north flux of Y into row y0-1
+    // rolling registers for row y (= current output row)
+    S wc = w0, wn = w1;
+    A FnWc = FnW0;  // north flux of w at row y
+    A2 fc = f0;     // faces of row y
+    S Yc = Y0;
+
+    for (int y = y0; y < y1; ++y) {
+      // row y+1: f(w) and Y
+      const S wnn = ld(y + 2, xr, xin);
+      const A2 fn = faces(y + 1);
+      const A FnWn = fn.y * A(wnn - wn);
+      const A fWn = xflux(wn, east_of(wn, y + 1), fn.x) + (FnWn - FnWc);
+      const S Yn = cell_in(y + 1) ? wn + cy * S(fWn) : S(0);
+      // row y: f(Y) and the new state
+      const A FnYc = fc.y * A(Yn - Yc);
+      // (lane 31 has no east neighbour for Y; its f(Y) is not an output)
+      const A fY = xflux(Yc, __shfl_down_sync(0xffffffffu, Yc, 1), fc.x) + (FnYc - FnYm1);
+      const S wnew = wc + c1 * S(fW0) + c2 * S(fY);
+      if (out_ok) {
+        Wo[size_t(y) * nx + x] = wnew;
+        if (p.check_finite) bad |= bad_bits(wnew);
+      }
+      // roll
+      FnYm1 = FnYc;
+      fW0 = fWn;
+      FnWc = FnWn;
+      Yc = Yn;
+      wc = wn;
+      wn = wnn;
+      fc = fn;
+    }
+  }
+  if (bad) atomicOr(p.status, ST_NONFINITE);
+}
+
+template <class S, class A, bool PERIODIC>
+cudaError_t launch_t(const PassArgs& a, const void* fen, cudaStream_t st) {
+  static int blocks_per_sm = 0, sms = 0;
+  auto kern = k_paired2d<S, A, PERIODIC>;
+  if (!blocks_per_sm) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, kern, PR_THREADS, 0);
+    if (e != cudaSuccess) return e;
+    if (blocks_per_sm < 1) blocks_per_sm = 1;
+  }
+  const int ncolw = (a.nx + PR_COLS - 1) / PR_COLS;
+  const long long total = (long long)ncolw * a.ny;
+  long long grid = (long long)sms * blocks_per_sm;
+  const long long max_useful = (total + PR_WARPS - 1) / PR_WARPS;
+  if (grid > max_useful) grid = max_useful;
+  kern<<<unsigned(grid), PR_THREADS, 0, st>>>(a, fen, total, grid * PR_WARPS);
+  count_launch();
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_pass_paired2d(const frkc2_problem& p, const PassArgs& a, const void* fen, cudaStream_t st) {
+  const bool per = p.bc == FRKC2_BC_PERIODIC;
+  switch (p.precision) {
+    case FRKC2_FP64: return per ? launch_t<double, double, true>(a, fen, st) : launch_t<double, double, false>(a, fen, st);
+    case FRKC2_FP32: return per ? launch_t<float, float, true>(a, fen, st) : launch_t<float, float, false>(a, fen, st);
+    default: return per ? launch_t<double, float, true>(a, fen, st) : launch_t<double, float, false>(a, fen, st);
+  }
+}
+
+}  // namespace frkc2

@@ -32,7 +32,13 @@ namespace {
 constexpr int ST_THREADS = 256;
 constexpr int ST_WARPS = ST_THREADS / 32;
 constexpr int ST_COLS = 31;  // output columns per warp
-constexpr int ST_MIN_BLOCKS = 6;
+#ifndef FRKC2_STREAM_MIN_BLOCKS
+#define FRKC2_STREAM_MIN_BLOCKS 6
+#endif
+#ifndef FRKC2_STREAM_PREFETCH
+#define FRKC2_STREAM_PREFETCH 0
+#endif
+constexpr int ST_MIN_BLOCKS = FRKC2_STREAM_MIN_BLOCKS;  // CTAs per SM the register budget allows
 
 template <class T> struct Vec2;
 template <> struct Vec2<double> { using type = double2; };
@@ -137,8 +143,25 @@ __global__ void __launch_bounds__(ST_THREADS, ST_MIN_BLOCKS)
       PnU = ks * A(Wc.x - Ws.x);
       PnV = ks * A(Wc.y - Ws.y);
     }
+#if FRKC2_STREAM_PREFETCH
+    // loads for row y+1 are issued one iteration ahead of their use
+    S2 Wn = load(y0 + 1, xr, xin);
+    A2 f = faces(y0);
+    S2 Wen = lane == 31 ? load(y0, xeast, eastin) : Wc;
+#endif
 #pragma unroll 2
     for (int y = y0; y < y1; ++y) {
+#if FRKC2_STREAM_PREFETCH
+      const S2 Wnn = load(y + 2, xr, xin);
+      const A2 fnext = faces(y + 1);
+      const S2 Wenn = lane == 31 ? load(y + 1, xeast, eastin) : Wn;
+      S Ue = __shfl_down_sync(0xffffffffu, Wc.x, 1);
+      S Ve = __shfl_down_sync(0xffffffffu, Wc.y, 1);
+      if (lane == 31) {
+        Ue = Wen.x;
+        Ve = Wen.y;
+      }
+#else
       const S2 Wn = load(y + 1, xr, xin);
       const A2 f = faces(y);
       S Ue = __shfl_down_sync(0xffffffffu, Wc.x, 1);
@@ -148,6 +171,7 @@ __global__ void __launch_bounds__(ST_THREADS, ST_MIN_BLOCKS)
         Ue = We.x;
         Ve = We.y;
       }
+#endif
       // fluxes into this cell through its east and north faces
       const A FeU = f.x * A(Ue - Wc.x), FeV = f.x * A(Ve - Wc.y);
       const A FnU = f.y * A(Wn.x - Wc.x), FnV = f.y * A(Wn.y - Wc.y);
@@ -175,6 +199,11 @@ __global__ void __launch_bounds__(ST_THREADS, ST_MIN_BLOCKS)
       PnU = FnU;
       PnV = FnV;
       Wc = Wn;
+#if FRKC2_STREAM_PREFETCH
+      Wn = Wnn;
+      f = fnext;
+      Wen = Wenn;
+#endif
     }
   }
   if (bad) atomicOr(p.status, ST_NONFINITE);

@@ -234,6 +234,17 @@ std::vector<int> order_lebedev(int L) {
   return out;
 }
 
+// Each conjugate pair adjacent: for j of the upper half in Lebedev-Finogenov order, the
+// stages j then L-1-j.
+std::vector<int> order_paired(int L) {
+  std::vector<int> out;
+  for (int v : lebedev_permutation(L / 2)) {
+    out.push_back(v);
+    out.push_back(L - 1 - v);
+  }
+  return out;
+}
+
 }  // namespace
 
 extern "C" {
@@ -262,9 +273,11 @@ frkc2_status frkc2_plan(int s, double nu, unsigned flags, frkc2_plan_t* out) {
     return Q;
   };
   const bool force_greedy = flags & FRKC2_PLAN_GREEDY, force_lebedev = flags & FRKC2_PLAN_LEBEDEV;
-  if (force_greedy && force_lebedev) return FRKC2_EINVAL;
-  bool run_greedy = force_greedy || (!force_lebedev && L <= 256);
-  if (force_lebedev || (!force_greedy && L > 256)) {
+  const bool paired = flags & FRKC2_PLAN_PAIRED;
+  if (int(force_greedy) + int(force_lebedev) + int(paired) > 1) return FRKC2_EINVAL;
+  if (paired) consider(order_paired(L), 0);
+  bool run_greedy = !paired && (force_greedy || (!force_lebedev && L <= 256));
+  if (!paired && (force_lebedev || (!force_greedy && L > 256))) {
     const double q = consider(order_lebedev(L), 0);
     if (!force_lebedev && q > bound) run_greedy = true;
   }
@@ -280,6 +293,7 @@ frkc2_status frkc2_plan(int s, double nu, unsigned flags, frkc2_plan_t* out) {
   p->Q = best_Q;
   p->n_iter = best_n;
   p->order = best_order;
+  p->paired = paired;
   p->a_re.resize(L);
   p->a_im.resize(L);
   for (int l = 0; l < L; ++l) {

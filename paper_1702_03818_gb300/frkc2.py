@@ -22,7 +22,7 @@ OK, EINVAL, EUNSTABLE, EPLAN, ENOMEM, ECUDA, ETIMEOUT, ENONFINITE, EUNSUPPORTED 
 BC_PERIODIC, BC_DIRICHLET = 0, 1
 KAPPA_CONST, KAPPA_FIELD, KAPPA_POWER = 0, 1, 2
 FP64, FP32, MIXED = 0, 1, 2
-PLAN_STRICT, PLAN_GREEDY, PLAN_LEBEDEV = 1, 2, 4
+PLAN_STRICT, PLAN_GREEDY, PLAN_LEBEDEV, PLAN_PAIRED = 1, 2, 4, 8
 PRECISION = {"fp64": FP64, "fp32": FP32, "mixed": MIXED}
 BC = {"periodic": BC_PERIODIC, "dirichlet": BC_DIRICHLET}
 KAPPA = {"const": KAPPA_CONST, "field": KAPPA_FIELD, "power": KAPPA_POWER}

@@ -219,3 +219,48 @@ def test_tb_kernel_rejects_unsupported():
     with pytest.raises(F.Frkc2Error) as e:
         run_gpu(plan, shape, "periodic", "field", "fp64", u0, field, 0.1, 1, tune=F.make_tuning(k=4, kernel=3))
     assert e.value.status == F.EUNSUPPORTED
+
+
+PAIRED_CASES = [
+    # shape, bc, kappa, s, nsteps
+    ((100, 77), "periodic", "field", 16, 3),
+    ((70, 130), "dirichlet", "field", 32, 2),
+    ((64, 64), "periodic", "const", 8, 2),
+    ((5, 7), "periodic", "field", 8, 2),
+    ((9, 40), "dirichlet", "field", 4, 3),
+    ((257, 33), "periodic", "field", 64, 1),
+]
+
+
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-11), ("mixed", 1e-6), ("fp32", 5e-4)])
+@pytest.mark.parametrize("case", PAIRED_CASES, ids=lambda c: f"{'x'.join(map(str, c[0]))}-{c[1]}-{c[2]}-s{c[3]}")
+def test_step_parity_paired_real_pairs(case, prec, tol):
+    """Conjugate pairs in adjacent stages applied to the real state (kernel 4) against the
+    oracle's literal complex stages in the same order."""
+    shape, bc, kappa, s, nsteps = case
+    u0, field = seeded_case(shape, bc, kappa, 600 + s)
+    oplan = O.plan(s, method="paired")
+    plan = F.frkc2_plan(s, flags=F.PLAN_PAIRED)
+    assert np.array_equal(plan.info()["order"], oplan["order"])
+    fo = rounded_field(field, prec)
+    opr = oracle_problem(2, bc, kappa, 1.0, fo)
+    dt = 0.9 * oplan["beta"] / O.rho_bound(opr, u0)
+    u0g = u0.astype(np.float32).astype(np.float64) if prec == "fp32" else u0
+    ref = O.frkc2_step(u0g, oplan["a"], dt, opr, nsteps)
+    got, st = run_gpu(plan, shape, bc, kappa, prec, u0, field, dt, nsteps, tune=F.make_tuning(kernel=4))
+    assert st == F.OK
+    assert rel_l2(got, ref) < tol, rel_l2(got, ref)
+    # the oracle's own real pair form agrees with its complex stages
+    assert rel_l2(O.frkc2_step_paired(u0g, oplan["a"], dt, opr, nsteps), ref) < 1e-12
+
+
+def test_paired_plan_on_3d_runs_as_complex_stages():
+    shape = (9, 10, 11)
+    u0, field = seeded_case(shape, "periodic", "field", 77)
+    oplan = O.plan(8, method="paired")
+    plan = F.frkc2_plan(8, flags=F.PLAN_PAIRED)
+    opr = oracle_problem(3, "periodic", "field", 1.0, field)
+    dt = 0.9 * oplan["beta"] / O.rho_bound(opr)
+    ref = O.frkc2_step(u0, oplan["a"], dt, opr, 2)
+    got, st = run_gpu(plan, shape, "periodic", "field", "fp64", u0, field, dt, 2)
+    assert st == F.OK and rel_l2(got, ref) < 1e-11

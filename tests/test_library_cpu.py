@@ -159,3 +159,13 @@ def test_damped_plan_matches_oracle(L, nu0):
     assert np.array_equal(lib["order"], ora["order"])
     assert np.max(np.abs(lib["a"] - ora["a"])) < 1e-13
     assert abs(lib["beta"] / ora["beta"] - 1.0) < 1e-12
+
+
+@pytest.mark.parametrize("L", [8, 16, 64, 100])
+def test_paired_plan_matches_oracle(L):
+    lib = F.frkc2_plan(L, flags=F.PLAN_PAIRED).info()
+    ora = O.plan(L, method="paired")
+    assert np.array_equal(lib["order"], ora["order"])
+    a = lib["a"]
+    assert np.array_equal(a[1::2], np.conj(a[0::2]))
+    assert abs(lib["Q"] / ora["Q"] - 1.0) < 1e-9

@@ -562,3 +562,20 @@ def test_damping_zero_is_undamped():
     a, mu = O.damped_step_sizes(32, 0.0)
     assert mu == 0
     assert np.max(np.abs(a - O.step_sizes(32))) < 1e-15
+
+
+@pytest.mark.parametrize("L", [8, 32, 64])
+def test_paired_order_quadratic_factor_bound(L):
+    """With conjugates adjacent every pair is a real quadratic factor; Q is at least the largest
+    of them (about 0.12 L^4) and the paired order attains it for L a power of two."""
+    a = O.step_sizes(L)
+    perm = O.order_paired(L)
+    ap = a[perm]
+    assert np.array_equal(ap[1::2], np.conj(ap[0::2]))
+    b = O.beta(L)
+    pts = 8 * L
+    x = -b * np.arange(pts + 1) / pts
+    quad = float(np.max(np.abs((1 + np.outer(ap[0::2], x)) * (1 + np.outer(ap[1::2], x)))))
+    q = O.realised_Q(ap, b, pts)
+    assert abs(q / quad - 1.0) < 1e-12
+    assert 0.1 < q / L ** 4 < 0.13
