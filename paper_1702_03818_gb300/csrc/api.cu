@@ -320,6 +320,8 @@ frkc2_status frkc2_step(frkc2_plan_t plan, const frkc2_problem* prob, double dt,
       for (int j = 0; j < kq; ++j) {
         a.ca[j] = dt * plan->a_re[l0 + j] / h2;
         a.cb[j] = dt * plan->a_im[l0 + j] / h2;
+        a.caf[j] = float(a.ca[j]);
+        a.cbf[j] = float(a.cb[j]);
       }
       const cudaError_t e = use_tb ? launch_pass_tb2d(p, a, st) : launch_pass_generic(p, a, st);
       if (e != cudaSuccess) return FRKC2_ECUDA;

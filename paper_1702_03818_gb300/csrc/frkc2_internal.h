@@ -54,6 +54,8 @@ struct PassArgs {
   unsigned* status;
   double ca[KMAX];        // dt Re(a_l) / dx^2 for the pass's stages
   double cb[KMAX];        // dt Im(a_l) / dx^2
+  float caf[KMAX];        // the same, rounded to float once on the host
+  float cbf[KMAX];
 };
 
 // Face arrays: x faces [nz][ny][nx+1], y faces [nz][ny+1][nx], z faces [nz+1][ny][nx];

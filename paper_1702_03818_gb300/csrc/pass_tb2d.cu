@@ -1,10 +1,11 @@
 // 2D temporally blocked pass for FP32 (fixed conductivity): k stages of Sec. 3, Eq. 13 per
 // HBM round trip, the stages computed in shared memory and registers.
 //
-// A CTA of 16 x 16 threads owns a 64 x 64 region: its output tile (64 - 2k)^2 plus a k-cell
-// halo (recomputed redundantly).  Every stage updates every region cell; values near the
-// region edge go stale one cell per stage, which never reaches the output tile.  Thread
-// (tx, ty) owns the 4 x 4 cells at columns 4tx..4tx+3, rows 4ty..4ty+3:
+// A CTA of 16 x (64/PY) threads owns a 64 x 64 region: its output tile (64 - 2k)^2 plus a
+// k-cell halo (recomputed redundantly).  Every stage updates every region cell; values near
+// the region edge go stale one cell per stage, which never reaches the output tile.  Thread
+// (tx, ty) owns the 4 x PY cells at columns 4tx..4tx+3, rows PY ty..PY ty+PY-1 (PY = 2 gives
+// 512-thread CTAs and twice the resident warps of PY = 4, for the same shared memory):
 //   - the state ping-pongs between two shared buffers; a thread reads its rows as float4,
 //     walking up its 4 rows with the row below and above in registers;
 //   - the x neighbours beyond its 4 columns come from the adjacent threads by 16-lane
@@ -22,7 +23,11 @@ namespace {
 
 constexpr int TB_R = 64;          // region edge (cells)
 constexpr int TB_ROWS = TB_R + 2; // shared rows: region rows at 1..64, zero rows 0 and 65
-constexpr int TB_THREADS = 256;
+#ifndef FRKC2_TB_PY
+#define FRKC2_TB_PY 4
+#endif
+constexpr int TB_PY = FRKC2_TB_PY;          // rows per thread
+constexpr int TB_THREADS = 16 * (TB_R / TB_PY);
 
 __device__ __forceinline__ int wrap_t(int g, int n) {
   if (g >= 0 && g < n) return g;
@@ -34,6 +39,7 @@ __device__ __forceinline__ int wrap_t(int g, int n) {
 
 template <bool PERIODIC>
 __global__ void __launch_bounds__(TB_THREADS, 2) k_tb2d_f32(const PassArgs p) {
+  constexpr int PY = TB_PY;
   extern __shared__ __align__(16) float tb_smem[];
   float* Ub[2] = {tb_smem, tb_smem + 2 * TB_ROWS * TB_R};
   float* Vb[2] = {tb_smem + TB_ROWS * TB_R, tb_smem + 3 * TB_ROWS * TB_R};
@@ -49,25 +55,29 @@ __global__ void __launch_bounds__(TB_THREADS, 2) k_tb2d_f32(const PassArgs p) {
 
   // wrapped (periodic) or raw (Dirichlet) grid rows / columns of the thread's 5 rows and
   // 5 columns (the fifth is the next row / column, for the north and east faces)
-  int gyr[5], gxc[5];
-  bool yin[5], xin[5];
+  int gyr[PY + 1], gxc[5];
+  bool yin[PY + 1], xin[5];
 #pragma unroll
   for (int i = 0; i < 5; ++i) {
-    const int gy = y0 + 4 * ty + i, gx = x0 + 4 * tx + i;
-    gyr[i] = PERIODIC ? wrap_t(gy, ny) : gy;
+    const int gx = x0 + 4 * tx + i;
     gxc[i] = PERIODIC ? wrap_t(gx, nx) : gx;
-    yin[i] = gy >= 0 && gy < ny;
     xin[i] = gx >= 0 && gx < nx;
+  }
+#pragma unroll
+  for (int i = 0; i <= PY; ++i) {
+    const int gy = y0 + PY * ty + i;
+    gyr[i] = PERIODIC ? wrap_t(gy, ny) : gy;
+    yin[i] = gy >= 0 && gy < ny;
   }
   // faces in registers: fx[r][c] = west face of cell c (c = 4 is the east face of cell 3),
   // fy[r][c] = south face of row r (r = 4 is the north face of row 3)
-  float fx[4][5], fy[5][4];
+  float fx[PY][5], fy[PY + 1][4];
   unsigned inside = 0;  // Dirichlet: bit r*4+c set if the cell lies in the grid
 #pragma unroll
-  for (int r = 0; r < 5; ++r) {
+  for (int r = 0; r <= PY; ++r) {
 #pragma unroll
     for (int c = 0; c < 5; ++c) {
-      if (r < 4) {
+      if (r < PY) {
         float v = 0.f;
         if (PERIODIC) {
           // face index of the west face of the wrapped column (face nx equals face 0)
@@ -85,13 +95,13 @@ __global__ void __launch_bounds__(TB_THREADS, 2) k_tb2d_f32(const PassArgs p) {
           v = FY[size_t(gyr[r]) * nx + gxc[c]];
         }
         fy[r][c] = v;
-        if (r < 4 && xin[c] && yin[r]) inside |= 1u << (r * 4 + c);
+        if (r < PY && xin[c] && yin[r]) inside |= 1u << (r * 4 + c);
       }
     }
   }
   // state into buffer 0; zero the border rows of both buffers
 #pragma unroll
-  for (int r = 0; r < 4; ++r) {
+  for (int r = 0; r < PY; ++r) {
     float u4[4], v4[4];
 #pragma unroll
     for (int c = 0; c < 4; ++c) {
@@ -104,7 +114,7 @@ __global__ void __launch_bounds__(TB_THREADS, 2) k_tb2d_f32(const PassArgs p) {
       u4[c] = uu;
       v4[c] = vv;
     }
-    const int row = 4 * ty + r + 1;
+    const int row = PY * ty + r + 1;
     *reinterpret_cast<float4*>(&Ub[0][row * TB_R + 4 * tx]) = make_float4(u4[0], u4[1], u4[2], u4[3]);
     *reinterpret_cast<float4*>(&Vb[0][row * TB_R + 4 * tx]) = make_float4(v4[0], v4[1], v4[2], v4[3]);
   }
@@ -125,8 +135,8 @@ __global__ void __launch_bounds__(TB_THREADS, 2) k_tb2d_f32(const PassArgs p) {
     const float* vs = Vb[j & 1];
     float* ud = Ub[(j + 1) & 1];
     float* vd = Vb[(j + 1) & 1];
-    const float ca = float(p.ca[j]), cb = float(p.cb[j]);
-    const int base = 4 * ty * TB_R + 4 * tx;  // shared row 4ty (region row 4ty - 1)
+    const float ca = p.caf[j], cb = p.cbf[j];
+    const int base = PY * ty * TB_R + 4 * tx;  // shared row PY ty (region row PY ty - 1)
     float4 s4 = *reinterpret_cast<const float4*>(&us[base]);
     float4 t4 = *reinterpret_cast<const float4*>(&vs[base]);
     float cu[4], cv[4];
@@ -147,7 +157,7 @@ __global__ void __launch_bounds__(TB_THREADS, 2) k_tb2d_f32(const PassArgs p) {
       }
     }
 #pragma unroll
-    for (int r = 0; r < 4; ++r) {
+    for (int r = 0; r < PY; ++r) {
       const float4 a = *reinterpret_cast<const float4*>(&us[base + (r + 2) * TB_R]);
       const float4 b = *reinterpret_cast<const float4*>(&vs[base + (r + 2) * TB_R]);
       const float nu[4] = {a.x, a.y, a.z, a.w}, nv[4] = {b.x, b.y, b.z, b.w};
@@ -200,8 +210,8 @@ __global__ void __launch_bounds__(TB_THREADS, 2) k_tb2d_f32(const PassArgs p) {
   float* __restrict__ Vo = static_cast<float*>(p.V_out);
   bool bad = false;
 #pragma unroll
-  for (int r = 0; r < 4; ++r) {
-    const int ry = 4 * ty + r;
+  for (int r = 0; r < PY; ++r) {
+    const int ry = PY * ty + r;
     const int gy = y0 + ry;
     if (ry < k || ry >= TB_R - k || gy >= ny) continue;
 #pragma unroll
