@@ -168,6 +168,35 @@ frkc2_status frkc2_step(frkc2_plan_t plan, const frkc2_problem* prob, double dt,
                         double rho, void* u, void* ws, size_t ws_bytes,
                         const frkc2_tuning* tune, void* stream);
 
+/* ---- Error-controlled integration (Sec. 3, Eqs. 14-16) --------------------------------
+ * Integrates u from t = 0 to t_end with the embedded first-order solution
+ * What^{l+1} = What^l + T Re(a_l) Re(f(W^l)) (Eq. 14) carried through every step and the
+ * scaled error ||err|| = RMS_i |Re W^L_i - What^L_i| / (tol (1 + max(|Re W^L_i|, |What^L_i|)))
+ * (Eq. 15, root mean square over the cells).  A step with ||err|| > 1 is rejected and retried
+ * with T scaled by SAFE/sqrt(||err||), SAFE = 0.8; after an accepted step the next T is
+ * T (SAFE/sqrt(e_n)) (T/T_prev) sqrt(e_{n-1}/e_n) (Eq. 16; SAFE/sqrt(e_n) alone after the
+ * first step), growing by at most 5x.  T is also capped by t_end - t and, if rho > 0, by the
+ * stability limit beta/rho.  The plan's stage count is used for every step.
+ * The call is synchronous: each step reads the error norm back to the host.  u is updated
+ * only by accepted steps.  Returns FRKC2_ETIMEOUT if 10^6 attempts did not reach t_end.
+ *   dt0   : first step size to try (> 0).
+ *   stats : may be NULL; receives the accepted and rejected step counts, the time reached,
+ *           the last accepted step size and its scaled error.
+ * Workspace: frkc2_adaptive_workspace_size().                                             */
+typedef struct {
+  int accepted;
+  int rejected;
+  double t;
+  double dt_last;
+  double err_last;
+} frkc2_adaptive_stats;
+frkc2_status frkc2_adaptive_workspace_size(const frkc2_problem* prob, const frkc2_tuning* tune,
+                                           size_t* bytes);
+frkc2_status frkc2_step_adaptive(frkc2_plan_t plan, const frkc2_problem* prob, double t_end,
+                                 double tol, double dt0, double rho, void* u, void* ws,
+                                 size_t ws_bytes, const frkc2_tuning* tune,
+                                 frkc2_adaptive_stats* stats, void* stream);
+
 /* ---- Forward step without a workspace -------------------------------------------------
  * The paper has no counterpart: this is a service for callers that cannot allocate device
  * memory -- for example a plugin whose host application owns every device allocation, or

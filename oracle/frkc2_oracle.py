@@ -547,3 +547,73 @@ def rk4(u0, h, prob, nsteps):
         k4 = apply_f(u + h * k3, prob)
         u = u + (h / 6.0) * (k1 + 2.0 * k2 + 2.0 * k3 + k4)
     return np.real(u)
+
+
+# ----------------------------------------------------------------------------------------
+# Embedded first-order solution and step-size control (Sec. 3, Eqs. 14-16)
+# ----------------------------------------------------------------------------------------
+
+
+def frkc2_step_embedded(u0, a, T, prob):
+    """One FRKC2 step and its embedded first-order solution (Eq. 14).
+
+    W^{l+1} = W^l + T a_l f(W^l) as in ``frkc2_step``; alongside, What^0 = W^0 and
+    What^{l+1} = What^l + T Re(a_l) Re(f(W^l)).  Returns (Re W^L, What^L).
+    """
+    W = np.array(u0, dtype=np.float64).astype(np.complex128)
+    H = np.array(u0, dtype=np.float64)
+    for al in a:
+        fw = apply_f(W, prob)
+        H = H + T * al.real * fw.real
+        W = W + (T * al) * fw
+    return W.real.copy(), H
+
+
+def error_norm(w, what, tol: float) -> float:
+    """Scaled error of Eq. 15, ||e|| with e_i = |w_i - what_i| / (TOL (1 + max(|w_i|, |what_i|))).
+
+    Reading: the norm is the root mean square over the cells (the convention of the error
+    controllers the paper refers to), and w is the step's output Re W^L.
+    """
+    e = np.abs(w - what) / (tol * (1.0 + np.maximum(np.abs(w), np.abs(what))))
+    return float(np.sqrt(np.mean(e * e)))
+
+
+def frkc2_adaptive(u0, a, beta_, prob, t_end: float, tol: float, dt0: float, rho: float = 0.0,
+                   safe: float = 0.8, max_steps: int = 100000):
+    """Integrate to ``t_end`` with the error control of Sec. 3.
+
+    A step with ||err|| > 1 is rejected and retried with T scaled by SAFE / sqrt(||err||).
+    After an accepted step the next T comes from the predictive controller (Eq. 16), read as
+    T^{n+1} = T^n (SAFE / sqrt(e_n)) (T^n / T^{n-1}) sqrt(e_{n-1} / e_n) (the printed formula
+    lacks the leading T^n), and from T^n SAFE / sqrt(e_n) for the first step.  Readings: T is
+    also capped by the stability limit beta/rho (when rho > 0), by the time left, and may grow
+    by at most 5x per step; e is floored at 1e-10.
+    Returns (u, dict(accepted, rejected, t, dts)).
+    """
+    u = np.array(u0, dtype=np.float64)
+    t, T = 0.0, float(dt0)
+    T_prev, e_prev = None, None
+    acc = rej = 0
+    dts = []
+    while t < t_end * (1.0 - 1e-14) and acc + rej < max_steps:
+        T = min(T, t_end - t)
+        if rho > 0:
+            T = min(T, beta_ / rho)
+        w, h = frkc2_step_embedded(u, a, T, prob)
+        e = error_norm(w, h, tol)
+        if not np.isfinite(e) or e > 1.0:
+            rej += 1
+            T = T * safe / np.sqrt(e if np.isfinite(e) else 1e10)
+            continue
+        acc += 1
+        u = w
+        t += T
+        dts.append(T)
+        e = max(e, 1e-10)
+        fac = safe / np.sqrt(e)
+        if T_prev is not None:
+            fac *= (T / T_prev) * np.sqrt(e_prev / e)
+        T_prev, e_prev = T, e
+        T = T * min(fac, 5.0)
+    return u, dict(accepted=acc, rejected=rej, t=t, dts=dts)

@@ -337,4 +337,145 @@ frkc2_status frkc2_step(frkc2_plan_t plan, const frkc2_problem* prob, double dt,
   return FRKC2_OK;
 }
 
+frkc2_status frkc2_adaptive_workspace_size(const frkc2_problem* prob, const frkc2_tuning* tune, size_t* bytes) {
+  (void)tune;
+  if (!bytes) return FRKC2_EINVAL;
+  const frkc2_status v = validate_problem(prob);
+  if (v != FRKC2_OK) return v;
+  const size_t N = cells(*prob), S = state_bytes(prob->precision);
+  // step workspace + two embedded-solution buffers + the error sum
+  *bytes = step_layout(*prob).total + 2 * align256(N * S) + 256;
+  return FRKC2_OK;
+}
+
+frkc2_status frkc2_step_adaptive(frkc2_plan_t plan, const frkc2_problem* prob, double t_end, double tol,
+                                 double dt0, double rho, void* u, void* ws, size_t ws_bytes,
+                                 const frkc2_tuning* tune, frkc2_adaptive_stats* stats, void* stream) {
+  if (!plan || !u || !ws || !(t_end > 0.0) || !(tol > 0.0) || !(dt0 > 0.0)) return FRKC2_EINVAL;
+  const frkc2_status v = validate_problem(prob);
+  if (v != FRKC2_OK) return v;
+  if (reinterpret_cast<uintptr_t>(ws) & 255) return FRKC2_EINVAL;
+  size_t need = 0;
+  frkc2_adaptive_workspace_size(prob, tune, &need);
+  if (ws_bytes < need) return FRKC2_ENOMEM;
+  const frkc2_problem& p = *prob;
+  const StepLayout L = step_layout(p);
+  const size_t N = cells(p), SB = state_bytes(p.precision);
+  char* base = static_cast<char*>(ws);
+  char* hA = base + L.total;
+  char* hB = hA + align256(N * SB);
+  double* esum = reinterpret_cast<double*>(hB + align256(N * SB));
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  int k = (tune && tune->k) ? tune->k : default_k(p);
+  if (k < 1 || k > KMAX) return FRKC2_EINVAL;
+  k = std::min(k, plan->s);
+  int tx, ty, tz;
+  default_tiles(p, k, &tx, &ty, &tz);
+  if (tune && tune->tile_x) tx = tune->tile_x;
+  if (tune && tune->tile_y) ty = tune->tile_y;
+  if (tune && tune->tile_z) tz = tune->tile_z;
+  if (p.ndim < 2) ty = 1;
+  if (p.ndim < 3) tz = 1;
+  if (p.kappa_kind != FRKC2_KAPPA_POWER &&
+      launch_faces(p, base + L.fx, base + L.fy, base + L.fz, st) != cudaSuccess)
+    return FRKC2_ECUDA;
+  PassArgs a{};
+  a.ndim = p.ndim;
+  a.bc = p.bc;
+  a.nx = int(p.n[0]);
+  a.ny = int(p.n[1]);
+  a.nz = int(p.n[2]);
+  a.tx = tx;
+  a.ty = ty;
+  a.tz = tz;
+  a.fx = base + L.fx;
+  a.fy = base + L.fy;
+  a.fz = base + L.fz;
+  a.kc = p.kappa_c;
+  a.kp = p.kappa_p;
+  a.status = reinterpret_cast<unsigned*>(base + L.status);
+  {
+    PassArgs probe = a;
+    probe.hx = k;
+    probe.hy = p.ndim >= 2 ? k : 0;
+    probe.hz = p.ndim >= 3 ? k : 0;
+    probe.H_out = hA;
+    if (generic_smem_bytes(p, probe) > size_t(smem_optin())) return FRKC2_EINVAL;
+  }
+  void* UA = base + L.ua;
+  void* VA = base + L.va;
+  void* UB = base + L.ub;
+  void* VB = base + L.vb;
+  const int s = plan->s, npass = (s + k - 1) / k;
+  const double h2 = p.dx * p.dx, safe = 0.8, tmax = rho > 0.0 ? plan->beta / rho : 0.0;
+  double t = 0.0, T = dt0, T_prev = 0.0, e_prev = 0.0;
+  int acc = 0, rej = 0;
+  const int max_attempts = 1000000;
+  while (t < t_end * (1.0 - 1e-14) && acc + rej < max_attempts) {
+    T = std::min(T, t_end - t);
+    if (tmax > 0.0) T = std::min(T, tmax);
+    // one step from u into the ping-pong buffers; the embedded solution alongside
+    const void* cU = u;
+    const void* cV = nullptr;
+    const void* cH = u;
+    for (int q = 0; q < npass; ++q) {
+      const int l0 = q * k, kq = std::min(k, s - l0);
+      const bool last = q == npass - 1;
+      void* oU = (cU == UA) ? UB : UA;
+      void* oV = last ? nullptr : ((cV == VA) ? VB : VA);
+      void* oH = (cH == hA) ? hB : hA;
+      a.k = kq;
+      a.hx = kq;
+      a.hy = p.ndim >= 2 ? kq : 0;
+      a.hz = p.ndim >= 3 ? kq : 0;
+      a.U_in = cU;
+      a.V_in = cV;
+      a.H_in = cH;
+      a.U_out = oU;
+      a.V_out = oV;
+      a.H_out = oH;
+      a.check_finite = 0;
+      for (int j = 0; j < kq; ++j) {
+        a.ca[j] = T * plan->a_re[l0 + j] / h2;
+        a.cb[j] = T * plan->a_im[l0 + j] / h2;
+      }
+      if (launch_pass_generic(p, a, st) != cudaSuccess) return FRKC2_ECUDA;
+      cU = oU;
+      cV = oV;
+      cH = oH;
+    }
+    if (launch_err_sum(p, cU, cH, esum, st) != cudaSuccess) return FRKC2_ECUDA;
+    double e2 = 0.0;
+    if (cudaMemcpyAsync(&e2, esum, sizeof(double), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+      return FRKC2_ECUDA;
+    double e = std::sqrt(e2 / double(N)) / tol;  // Eq. 15, root mean square over the cells
+    if (!std::isfinite(e) || e > 1.0) {
+      ++rej;
+      T *= safe / std::sqrt(std::isfinite(e) ? e : 1e10);
+      continue;
+    }
+    if (cudaMemcpyAsync(u, cU, N * SB, cudaMemcpyDeviceToDevice, st) != cudaSuccess) return FRKC2_ECUDA;
+    ++acc;
+    t += T;
+    e = std::max(e, 1e-10);
+    double fac = safe / std::sqrt(e);
+    if (T_prev > 0.0) fac *= (T / T_prev) * std::sqrt(e_prev / e);  // Eq. 16
+    if (stats) {
+      stats->dt_last = T;
+      stats->err_last = e;
+    }
+    T_prev = T;
+    e_prev = e;
+    T *= std::min(fac, 5.0);
+  }
+  if (stats) {
+    stats->accepted = acc;
+    stats->rejected = rej;
+    stats->t = t;
+  }
+  if (cudaStreamSynchronize(st) != cudaSuccess) return FRKC2_ECUDA;
+  return t >= t_end * (1.0 - 1e-14) ? FRKC2_OK : FRKC2_ETIMEOUT;
+}
+
 }  // extern "C"

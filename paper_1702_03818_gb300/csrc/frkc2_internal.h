@@ -47,6 +47,8 @@ struct PassArgs {
   const void* V_in;       // imaginary part; nullptr = zero (first pass of a step)
   void* U_out;
   void* V_out;            // nullptr = not stored (last pass of a step)
+  const void* H_in;       // embedded first-order solution (tile kernel only); nullptr = none
+  void* H_out;
   const void* fx;         // face conductivities (FIELD / CONST), layouts in faces_layout()
   const void* fy;
   const void* fz;
@@ -79,6 +81,7 @@ size_t cells(const frkc2_problem& p);
 cudaError_t launch_faces(const frkc2_problem& p, void* fx, void* fy, void* fz, cudaStream_t st);
 cudaError_t launch_rho(const frkc2_problem& p, const void* u, double* rho_dev, cudaStream_t st);
 cudaError_t launch_pass_generic(const frkc2_problem& p, const PassArgs& a, cudaStream_t st);
+cudaError_t launch_err_sum(const frkc2_problem& p, const void* u, const void* h, double* out, cudaStream_t st);
 cudaError_t launch_pass_stream2d(const frkc2_problem& p, const PassArgs& a, const void* fen, cudaStream_t st);
 size_t face_pair_bytes(const frkc2_problem& p);
 cudaError_t launch_face_pairs(const frkc2_problem& p, const void* fx, const void* fy, void* out, cudaStream_t st);

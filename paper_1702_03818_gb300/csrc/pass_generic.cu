@@ -10,6 +10,10 @@
 // i beta_l the stage reads, in real arithmetic,
 //   U' = U + ca f_R - cb f_I,  V' = V + ca f_I + cb f_R,   ca = dt alpha_l/dx^2, cb = dt beta_l/dx^2,
 // where f_R + i f_I = dx^2 f(U + iV); for a fixed conductivity f_R = dx^2 f(U), f_I = dx^2 f(V).
+// Optionally the pass also advances the embedded first-order solution of Eq. 14,
+// What <- What + ca f_R (ca = dt Re(a_l)/dx^2), held in one more shared array.
+#include <algorithm>
+
 #include <cuda_runtime.h>
 
 #include "frkc2_internal.h"
@@ -40,6 +44,11 @@ __global__ void __launch_bounds__(GEN_THREADS) k_pass_generic(const PassArgs p) 
   A* f0 = reinterpret_cast<A*>(vb[1] + R);  // x faces, or Re kappa(W) for POWER
   A* f1 = f0 + R;                           // y faces, or Im kappa(W)
   A* f2 = f1 + R;                           // z faces
+  const int nf = POWER ? 2 : p.ndim;
+  // embedded solution (if H_out), 16-byte aligned after the face arrays
+  S* hb = reinterpret_cast<S*>((reinterpret_cast<uintptr_t>(f0 + size_t(nf) * R) + 15) & ~uintptr_t(15));
+  const bool hat = p.H_out != nullptr;
+  const S* __restrict__ Hin = static_cast<const S*>(p.H_in);
   const bool periodic = p.bc == FRKC2_BC_PERIODIC;
   const int x0 = blockIdx.x * p.tx - p.hx;
   const int y0 = blockIdx.y * p.ty - p.hy;
@@ -64,6 +73,7 @@ __global__ void __launch_bounds__(GEN_THREADS) k_pass_generic(const PassArgs p) 
         const size_t g = (size_t(wz) * p.ny + wy) * p.nx + wx;
         uu = Uin[g];
         if (Vin) vv = Vin[g];
+        if (hat) hb[i] = Hin[g];
         if (!POWER) {
           a0 = FX[(size_t(wz) * p.ny + wy) * (p.nx + 1) + wx];
           if (p.ndim >= 2) a1 = FY[(size_t(wz) * (p.ny + 1) + wy) * p.nx + wx];
@@ -75,6 +85,9 @@ __global__ void __launch_bounds__(GEN_THREADS) k_pass_generic(const PassArgs p) 
           const size_t g = (size_t(gz) * p.ny + gy) * p.nx + gx;
           uu = Uin[g];
           if (Vin) vv = Vin[g];
+          if (hat) hb[i] = Hin[g];
+        } else if (hat) {
+          hb[i] = S(0);
         }
         if (!POWER) {
           if (iny && inz && gx >= 0 && gx <= p.nx) a0 = FX[(size_t(gz) * p.ny + gy) * (p.nx + 1) + gx];
@@ -167,6 +180,7 @@ __global__ void __launch_bounds__(GEN_THREADS) k_pass_generic(const PassArgs p) 
         }
         ud[i] = Uc + ca * S(fR) - cb * S(fI);
         vd[i] = Vc + ca * S(fI) + cb * S(fR);
+        if (hat) hb[i] += ca * S(fR);
       }
     }
     __syncthreads();
@@ -188,18 +202,54 @@ __global__ void __launch_bounds__(GEN_THREADS) k_pass_generic(const PassArgs p) 
       const S uu = uf[i];
       Uout[g] = uu;
       if (Vout) Vout[g] = vf[i];
+      if (hat) static_cast<S*>(p.H_out)[g] = hb[i];
       if (p.check_finite && !isfinite(double(uu))) bad = true;
     }
   if (bad) atomicOr(p.status, ST_NONFINITE);
 }
 
+// sum over cells of e_i^2, e_i = |u_i - h_i| / (1 + max(|u_i|, |h_i|)) (Eq. 15 without TOL)
+template <class S>
+__global__ void k_err_sum(const S* __restrict__ u, const S* __restrict__ h, size_t n, double* out) {
+  double acc = 0.0;
+  for (size_t i = blockIdx.x * size_t(blockDim.x) + threadIdx.x; i < n; i += size_t(gridDim.x) * blockDim.x) {
+    const double a = double(u[i]), b = double(h[i]);
+    const double e = fabs(a - b) / (1.0 + fmax(fabs(a), fabs(b)));
+    acc += e * e;
+  }
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  __shared__ double part[32];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  if (lane == 0) part[w] = acc;
+  __syncthreads();
+  if (w == 0) {
+    acc = lane < int(blockDim.x >> 5) ? part[lane] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0) atomicAdd(out, acc);
+  }
+}
+
 }  // namespace
+
+cudaError_t launch_err_sum(const frkc2_problem& p, const void* u, const void* h, double* out, cudaStream_t st) {
+  cudaError_t e = cudaMemsetAsync(out, 0, sizeof(double), st);
+  if (e != cudaSuccess) return e;
+  const size_t n = size_t(p.n[0]) * p.n[1] * p.n[2];
+  const int threads = 256;
+  const int blocks = int(std::min<size_t>((n + threads - 1) / threads, 152 * 8));
+  if (state_bytes(p.precision) == 8)
+    k_err_sum<double><<<blocks, threads, 0, st>>>(static_cast<const double*>(u), static_cast<const double*>(h), n, out);
+  else
+    k_err_sum<float><<<blocks, threads, 0, st>>>(static_cast<const float*>(u), static_cast<const float*>(h), n, out);
+  count_launch();
+  return cudaGetLastError();
+}
 
 size_t generic_smem_bytes(const frkc2_problem& pr, const PassArgs& a) {
   const size_t R = size_t(a.tx + 2 * a.hx) * (a.ty + 2 * a.hy) * (a.tz + 2 * a.hz);
   const size_t S = state_bytes(pr.precision), A = arith_bytes(pr.precision);
   const size_t nf = pr.kappa_kind == FRKC2_KAPPA_POWER ? 2 : size_t(pr.ndim);
-  return R * (4 * S + nf * A);
+  return R * (4 * S + nf * A) + (a.H_out ? R * S + 16 : 0);
 }
 
 template <class S, class A, bool POWER>

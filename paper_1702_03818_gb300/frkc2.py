@@ -34,6 +34,11 @@ class frkc2_problem(C.Structure):
                 ("kappa_p", C.c_double), ("kappa", C.c_void_p)]
 
 
+class frkc2_adaptive_stats(C.Structure):
+    _fields_ = [("accepted", C.c_int), ("rejected", C.c_int), ("t", C.c_double), ("dt_last", C.c_double),
+                ("err_last", C.c_double)]
+
+
 class frkc2_tuning(C.Structure):
     _fields_ = [("k", C.c_int), ("tile_x", C.c_int), ("tile_y", C.c_int), ("tile_z", C.c_int),
                 ("kernel", C.c_int), ("wait_limit", C.c_longlong), ("fault_inject", C.c_int)]
@@ -52,6 +57,11 @@ _sig = {
     "frkc2_step": (C.c_int, [_P, C.POINTER(frkc2_problem), C.c_double, C.c_int, C.c_double, _P, _P,
                              C.c_size_t, C.POINTER(frkc2_tuning), _P]),
     "frkc2_step_noalloc": (C.c_int, [_P, C.POINTER(frkc2_problem), C.c_double, C.c_int, C.c_double, _P, _P]),
+    "frkc2_adaptive_workspace_size": (C.c_int, [C.POINTER(frkc2_problem), C.POINTER(frkc2_tuning),
+                                                C.POINTER(C.c_size_t)]),
+    "frkc2_step_adaptive": (C.c_int, [_P, C.POINTER(frkc2_problem), C.c_double, C.c_double, C.c_double,
+                                      C.c_double, _P, _P, C.c_size_t, C.POINTER(frkc2_tuning),
+                                      C.POINTER(frkc2_adaptive_stats), _P]),
     "frkc2_adjoint_workspace_size": (C.c_int, [_P, C.POINTER(frkc2_problem), C.c_int, C.c_int,
                                                C.POINTER(C.c_size_t)]),
     "frkc2_adjoint": (C.c_int, [_P, C.POINTER(frkc2_problem), C.c_double, C.c_int, C.c_int, _P, _P, _P,
@@ -219,6 +229,23 @@ def frkc2_step(plan: Plan, prob: frkc2_problem, dt: float, nsteps: int, rho: flo
                            _ptr(ws), ws.numel() * ws.element_size(),
                            C.byref(tune) if tune is not None else None, _stream_ptr(stream)),
            "frkc2_step")
+
+
+def frkc2_adaptive_workspace_size(prob: frkc2_problem, tune: frkc2_tuning | None = None) -> int:
+    b = C.c_size_t()
+    _check(_lib.frkc2_adaptive_workspace_size(C.byref(prob), C.byref(tune) if tune is not None else None,
+                                              C.byref(b)), "frkc2_adaptive_workspace_size")
+    return b.value
+
+
+def frkc2_step_adaptive(plan: Plan, prob: frkc2_problem, t_end: float, tol: float, dt0: float, rho: float, u,
+                        ws, tune: frkc2_tuning | None = None, stream=None) -> dict:
+    st = frkc2_adaptive_stats()
+    _check(_lib.frkc2_step_adaptive(plan.handle, C.byref(prob), float(t_end), float(tol), float(dt0), float(rho),
+                                    _ptr(u), _ptr(ws), ws.numel() * ws.element_size(),
+                                    C.byref(tune) if tune is not None else None, C.byref(st),
+                                    _stream_ptr(stream)), "frkc2_step_adaptive")
+    return dict(accepted=st.accepted, rejected=st.rejected, t=st.t, dt_last=st.dt_last, err_last=st.err_last)
 
 
 def frkc2_step_noalloc(plan: Plan, prob: frkc2_problem, dt: float, nsteps: int, rho: float, u, stream=None):

@@ -1,0 +1,57 @@
+"""GPU parity of the error-controlled integration (frkc2_step_adaptive, Sec. 3 Eqs. 14-16)
+against the oracle's controller: same accepted/rejected step counts, same final state."""
+import numpy as np
+import pytest
+
+from oracle import frkc2_oracle as O
+from helpers import oracle_problem, rel_l2, seeded_case
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+F = pytest.importorskip("paper_1702_03818_gb300.frkc2")
+
+CASES = [
+    # shape, bc, kappa, s, t_end, tol, dt0 factor (of the stability limit)
+    ((48, 40), "periodic", "field", 16, 40.0, 1e-4, 1.0),
+    ((48, 40), "periodic", "field", 16, 40.0, 1e-6, 0.2),
+    ((37, 29), "dirichlet", "field", 8, 15.0, 1e-5, 1.0),
+    ((200,), "dirichlet", "const", 16, 300.0, 1e-5, 1.0),
+    ((8, 7, 6), "dirichlet", "power", 8, 2.0, 1e-4, 0.5),
+]
+
+
+@pytest.mark.parametrize("case", CASES, ids=lambda c: f"{'x'.join(map(str, c[0]))}-{c[1]}-{c[2]}-tol{c[5]}")
+def test_adaptive_matches_oracle_controller(case):
+    shape, bc, kappa, s, t_end, tol, f0 = case
+    u0, field = seeded_case(shape, bc, kappa, 700 + s)
+    opr = oracle_problem(len(shape), bc, kappa, 1.0, field)
+    rho = O.rho_bound(opr, u0 + (0.5 if kappa == "power" else 0.0))
+    oplan = O.plan(s)
+    dt0 = f0 * O.beta(s) / rho
+    ref, st_ref = O.frkc2_adaptive(u0, oplan["a"], O.beta(s), opr, t_end, tol, dt0, rho=rho)
+    plan = F.frkc2_plan(s)
+    kt = torch.as_tensor(field, device="cuda") if field is not None else None
+    pr = F.make_problem(len(shape), tuple(reversed(shape)), 1.0, bc, kappa, "fp64", kappa_field=kt)
+    ws = torch.empty(F.frkc2_adaptive_workspace_size(pr), dtype=torch.uint8, device="cuda")
+    u = torch.as_tensor(u0, device="cuda")
+    st = F.frkc2_step_adaptive(plan, pr, t_end, tol, dt0, rho, u, ws)
+    assert abs(st["t"] - t_end) < 1e-9 * t_end
+    assert (st["accepted"], st["rejected"]) == (st_ref["accepted"], st_ref["rejected"])
+    assert st_ref["rejected"] >= 0 and st_ref["accepted"] >= 2
+    assert rel_l2(u.cpu().numpy(), ref) < 1e-10
+
+
+def test_adaptive_rejects_an_oversized_first_step_and_recovers():
+    shape = (64, 64)
+    u0, field = seeded_case(shape, "periodic", "field", 91)
+    opr = oracle_problem(2, "periodic", "field", 1.0, field)
+    s = 16
+    rho = O.rho_bound(opr)
+    plan = F.frkc2_plan(s)
+    pr = F.make_problem(2, (64, 64), 1.0, "periodic", "field", "fp64", kappa_field=torch.as_tensor(field, device="cuda"))
+    ws = torch.empty(F.frkc2_adaptive_workspace_size(pr), dtype=torch.uint8, device="cuda")
+    u = torch.as_tensor(u0, device="cuda")
+    # no stability cap and a first step far too large for tol: rejected, then accepted
+    st = F.frkc2_step_adaptive(plan, pr, 5.0, 1e-8, 5.0, 0.0, u, ws)
+    assert st["rejected"] >= 1 and abs(st["t"] - 5.0) < 1e-12
+    assert np.all(np.isfinite(u.cpu().numpy()))

@@ -579,3 +579,56 @@ def test_paired_order_quadratic_factor_bound(L):
     q = O.realised_Q(ap, b, pts)
     assert abs(q / quad - 1.0) < 1e-12
     assert 0.1 < q / L ** 4 < 0.13
+
+
+def test_embedded_solution_first_order():
+    """Eq. 14: the embedded solution is first order -- its one-step error against expm falls
+    like T^2 while the FRKC2 step's falls like T^3."""
+    scipy_linalg = pytest.importorskip("scipy.linalg")
+    rng = np.random.default_rng(21)
+    shape = (8, 8)
+    pr = _prob(2, "periodic", "field", 1.0, np.exp(0.5 * rng.standard_normal(shape)))
+    A = dense(pr, shape)
+    u0 = rng.random(shape)
+    a = O.plan(8)["a"]
+    e_w, e_h = [], []
+    for T in (0.0125, 0.00625, 0.003125):
+        ref = scipy_linalg.expm(T * A) @ u0.ravel()
+        w, h = O.frkc2_step_embedded(u0, a, T, pr)
+        e_w.append(np.linalg.norm(w.ravel() - ref))
+        e_h.append(np.linalg.norm(h.ravel() - ref))
+    sw = np.log2(e_w[0] / e_w[1]), np.log2(e_w[1] / e_w[2])
+    sh = np.log2(e_h[0] / e_h[1]), np.log2(e_h[1] / e_h[2])
+    assert all(2.8 < x < 3.2 for x in sw), sw
+    assert all(1.8 < x < 2.2 for x in sh), sh  # local error O(T^2): first order
+    # the embedded solution uses Re(a) only: sum Re(a) = 1 keeps it consistent
+    assert abs(np.sum(a.real) - 1.0) < 1e-13
+
+
+def test_error_norm_definition():
+    w = np.array([1.0, -2.0, 0.0])
+    h = np.array([1.5, -2.0, 0.1])
+    e = np.array([0.5 / 2.5, 0.0, 0.1 / 1.1]) / 1e-3
+    assert abs(O.error_norm(w, h, 1e-3) - np.sqrt(np.mean(e ** 2))) < 1e-12
+
+
+def test_adaptive_reaches_end_and_tolerance_controls_error():
+    scipy_linalg = pytest.importorskip("scipy.linalg")
+    rng = np.random.default_rng(22)
+    shape = (10, 10)
+    pr = _prob(2, "periodic", "field", 1.0, np.exp(0.5 * rng.standard_normal(shape)))
+    A = dense(pr, shape)
+    u0 = rng.random(shape)
+    L = 16
+    a = O.plan(L)["a"]
+    rho = O.rho_bound(pr)
+    t_end = 3.0
+    ref = scipy_linalg.expm(t_end * A) @ u0.ravel()
+    errs, steps = [], []
+    for tol in (1e-3, 1e-5):
+        u, st = O.frkc2_adaptive(u0, a, O.beta(L), pr, t_end, tol, dt0=0.01, rho=rho)
+        assert abs(st["t"] - t_end) < 1e-12
+        errs.append(np.linalg.norm(u.ravel() - ref) / np.linalg.norm(ref))
+        steps.append(st["accepted"])
+        assert max(st["dts"]) <= O.beta(L) / rho * (1 + 1e-12)
+    assert errs[1] < errs[0] and steps[1] > steps[0]
