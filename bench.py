@@ -43,8 +43,9 @@ FP64_INST_PER_CELL_STAGE = 18  # 2 x (2 differences + 2 face products + 3 sums) 
 # dram bytes per launch from one ncu capture of each pass kernel, keyed by the source hash of
 # the kernel file at capture time (the value is reported only while the source is unchanged)
 NCU_TRAFFIC = {
-    # profiles/stream2d_fp64_varkappa2d_2048.md: an intermediate pass, read 152.7 MB + write 50.0 MB
-    ("pass_stream2d.cu", "8bfbed348f174b59"): 202.7e6,
+    # profiles/stream2d_fp64_varkappa2d_2048.md: two intermediate passes, mean of
+    # (152.3 + 48.8) MB and (152.1 + 45.9) MB
+    ("pass_stream2d.cu", "ede11c5105c5b133"): 199.5e6,
 }
 
 
