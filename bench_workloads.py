@@ -17,6 +17,9 @@ Workloads (sizes and seeds from frkc2_inputs.CONFIGS):
                persistent launch replayed from a CUDA graph, FP32 and FP64.
   ssweep       4096^2 var-kappa, s in {32, 128, 512, 1024}, 4 steps, FP32 vs FP64 error growth
                with s (internal amplification).
+  bruss2d      the paper's Brusselator (Sec. 3.1): 200^2 periodic, s = 16, dt = 0.9 beta/rho, to
+               t = 1, FP64 and FP32, persistent launch vs one launch per stage; plus 2048^2,
+               s = 64, 10 steps for throughput against the FP64-pipe and HBM rooflines.
 """
 from __future__ import annotations
 
@@ -310,8 +313,82 @@ def ssweep(F):
             "by_s": out}
 
 
+BRUSS_INST_PER_CELL_STAGE = 41  # 4 Laplacians (4 each), v^2 and v^2 w (8), 4 rhs (9), 4 updates (8)
+BRUSS_BYTES_PER_CELL_STAGE = {"fp64": 64, "fp32": 32}  # 4 state values read and written
+FP64_PEAK_TINST = 152 * 2 * 2.07e9 / 1e12
+
+
+def bruss2d(F, hbm_peak_gbs: float = 6787.2):
+    torch = _torch()
+    cfg = I.CONFIGS["bruss2d"]
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    sd = {"fp64": torch.float64, "fp32": torch.float32}
+    out = {}
+
+    def case(n, s, nsteps_or_tend, label):
+        dx = 1.0 / n
+        v0, w0 = I.bruss_u0(n, n, dx)
+        plan = F.frkc2_plan(s)
+        beta = plan.info()["beta"]
+        res, rows = {}, {}
+        for prec in ("fp64", "fp32"):
+            pr = F.make_bruss_problem(n, dx=dx, bc=cfg["bc"], precision=prec, D=cfg["D"], A=cfg["A"], B=cfg["B"])
+            ws = torch.empty(F.frkc2_bruss_workspace_size(pr), dtype=torch.uint8, device="cuda")
+            F.frkc2_workspace_reset(ws)
+            v0d = torch.as_tensor(v0, dtype=sd[prec], device="cuda")
+            w0d = torch.as_tensor(w0, dtype=sd[prec], device="cuda")
+            rho_t = torch.zeros(1, dtype=torch.float64, device="cuda")
+            F.frkc2_bruss_rho_bound(pr, v0d, w0d, rho_t, ws)
+            rho = rho_t.item()
+            if label == "paper":
+                nsteps = int(np.ceil(nsteps_or_tend / (cfg["cfl"] * beta / rho)))
+                dt = nsteps_or_tend / nsteps
+            else:
+                nsteps = nsteps_or_tend
+                dt = cfg["cfl"] * beta / rho
+            v, w = v0d.clone(), w0d.clone()
+            row = {"rho_bound": rho, "dt": dt, "nsteps": nsteps}
+            for kern, name in ((1, "persistent"), (2, "per_stage")):
+                t = F.make_tuning(kernel=kern)
+
+                def job():
+                    v.copy_(v0d)
+                    w.copy_(w0d)
+                    F.frkc2_bruss_step(plan, pr, dt, nsteps, 0.0, v, w, ws, t)
+
+                F.frkc2_launch_count()
+                med, _ = _timed(job, 2, 5, flush)
+                launches = F.frkc2_launch_count() // 7
+                cs = n * n * s * nsteps
+                r = {"value": cs / (med / 1e3), "ms_per_job": med, "launches_per_job": launches}
+                if prec == "fp64":
+                    tinst = cs * BRUSS_INST_PER_CELL_STAGE / (med / 1e3) / 1e12
+                    r["roofline"] = {"bound": "alu", "achieved": tinst, "peak": FP64_PEAK_TINST,
+                                     "unit": "Tinst/s (FP64 pipe)", "frac": tinst / FP64_PEAK_TINST}
+                else:
+                    gbs = cs * BRUSS_BYTES_PER_CELL_STAGE[prec] / (med / 1e3) / 1e9
+                    r["roofline"] = {"bound": "hbm", "achieved": gbs, "peak": hbm_peak_gbs, "unit": "GB/s",
+                                     "frac": gbs / hbm_peak_gbs,
+                                     "note": "L2-resident state" if n * n * 32 * 2 < 100e6 else "state larger than L2"}
+                row[name] = r
+            row["status"] = F.frkc2_workspace_status(ws)
+            res[prec] = (v.double().cpu().numpy(), w.double().cpu().numpy())
+            rows[prec] = row
+            del ws
+        rows["fp32_rel_l2_vs_fp64_gpu"] = max(_rel(res["fp32"][0], res["fp64"][0]), _rel(res["fp32"][1], res["fp64"][1]))
+        return rows
+
+    out["paper_200"] = case(cfg["n"], cfg["s"], cfg["t_end"], "paper")
+    out["large_2048"] = case(cfg["n_large"], cfg["s_large"], cfg["steps_large"], "large")
+    big = out["large_2048"]["fp64"]["persistent"]
+    return {"workload": f"bruss2d: Brusselator D=0.02, A=1, B=3 periodic; 200^2 s={cfg['s']} to t={cfg['t_end']}, "
+                        f"and 2048^2 s={cfg['s_large']} {cfg['steps_large']} steps",
+            "metric": "cell-stage/s", "value": big["value"], "unit": UNIT, "dtype": "f64", "cases": out,
+            "kernel": "k_bruss2d: persistent cooperative launch, grid barrier between stages"}
+
+
 WORKLOADS = {"heat1d": heat1d, "nonlinear3d": nonlinear3d, "adjoint2d": adjoint2d,
-             "batched2d": batched2d, "ssweep": ssweep}
+             "batched2d": batched2d, "ssweep": ssweep, "bruss2d": bruss2d}
 
 
 def profile_case(F, name: str):
@@ -378,6 +455,19 @@ def profile_case(F, name: str):
         for _ in range(2):
             v = u.clone()
             F.frkc2_step(plan, pr, dt, 1, 0.0, v, ws)
+    elif name == "bruss":  # FP64 Brusselator persistent launch, 2048^2, s = 16, 1 step
+        n, s = 2048, 16
+        v0, w0 = I.bruss_u0(n, n, 1.0 / n)
+        plan = F.frkc2_plan(s)
+        pr = F.make_bruss_problem(n, precision="fp64")
+        ws = torch.empty(F.frkc2_bruss_workspace_size(pr), dtype=torch.uint8, device="cuda")
+        F.frkc2_workspace_reset(ws)
+        v, w = torch.as_tensor(v0, device="cuda"), torch.as_tensor(w0, device="cuda")
+        rho = torch.zeros(1, dtype=torch.float64, device="cuda")
+        F.frkc2_bruss_rho_bound(pr, v, w, rho, ws)
+        dt = 0.9 * plan.info()["beta"] / rho.item()
+        for _ in range(2):
+            F.frkc2_bruss_step(plan, pr, dt, 1, 0.0, v, w, ws)
     else:
         raise ValueError(name)
     torch.cuda.synchronize()

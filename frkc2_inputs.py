@@ -24,6 +24,7 @@ import numpy as np
 __all__ = [
     "grf", "grf_torch", "smooth_unit", "kappa_field", "heat1d_u0", "hotspot3d_u0", "batched_problems",
     "CONFIGS",
+    "bruss_u0",
 ]
 
 
@@ -42,6 +43,16 @@ def grf(shape, ell: float, seed: int) -> np.ndarray:
     g -= g.mean()
     sd = g.std()
     return g / sd if sd > 0 else g
+
+
+def bruss_u0(nx: int, ny: int, dx: float):
+    """The Brusselator initial state of Sec. 3.1 (Eq. 17): v = 1 + sin(2 pi x),
+    w = 3 + cos(2 pi y) at grid points x = i dx, y = j dx; arrays of shape (ny, nx)."""
+    x = np.arange(nx) * dx
+    y = np.arange(ny) * dx
+    v = np.broadcast_to(1.0 + np.sin(2.0 * np.pi * x)[None, :], (ny, nx)).copy()
+    w = np.broadcast_to(3.0 + np.cos(2.0 * np.pi * y)[:, None], (ny, nx)).copy()
+    return v, w
 
 
 def grf_torch(n: int, ell: float, seed: int, device="cuda"):
@@ -125,4 +136,8 @@ CONFIGS = {
     "adjoint2d": dict(ndim=2, n=1024, bc="periodic", kappa="field", s=100, steps=40, ckpt=8,
                       kappa_seed=3818, u0_seed=3819, target_seed=4040, cfl=0.9),
     "batched2d": dict(count=512, seed=512, steps=10),
+    # the paper's Brusselator demonstration: D = 0.02, A = 1, B = 3 on the unit square, 200^2;
+    # end time and boundaries unstated (read: t = 1, periodic); plus a 2048^2 throughput case
+    "bruss2d": dict(n=200, bc="periodic", D=0.02, A=1.0, B=3.0, s=16, t_end=1.0, cfl=0.9,
+                    n_large=2048, s_large=64, steps_large=10),
 }

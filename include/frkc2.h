@@ -45,7 +45,9 @@ typedef enum {
   FRKC2_EUNSUPPORTED = 8  /* valid request that this build does not implement               */
 } frkc2_status;
 
-enum { FRKC2_BC_PERIODIC = 0, FRKC2_BC_DIRICHLET = 1 };
+/* NEUMANN (zero flux: the ghost cell repeats its boundary cell) is taken by the Brusselator
+ * entry points only; the diffusion entry points reject it.                                 */
+enum { FRKC2_BC_PERIODIC = 0, FRKC2_BC_DIRICHLET = 1, FRKC2_BC_NEUMANN = 2 };
 
 /* Conductivity.  CONST: kappa = kappa_c.  FIELD: cell-centred array `kappa`.
  * POWER: kappa(w) = 1 + kappa_c * w^kappa_p (principal branch for complex stage states). */
@@ -272,6 +274,48 @@ frkc2_status frkc2_step_batched(int nprob, const frkc2_plan_t* plans,
                                 const frkc2_problem* probs, const double* dt,
                                 const int* nsteps, void* const* u, const frkc2_tuning* tune,
                                 void* ws, size_t ws_bytes, void* stream);
+
+/* ---- Brusselator reaction-diffusion (Sec. 3.1, Eq. 17) ------------------------------------
+ * The paper's demonstration system, two species on a 2D grid with the 5-point Laplacian:
+ *   v' = D Lap v + A - (B + 1) v + v^2 w,    w' = D Lap w + B v - v^2 w
+ * (the paper's values: D = 0.02, A = 1, B = 3, unit square, spectral radius about 6400 on
+ * 200 x 200).  A step applies the plan's ordered complex stages W^{l+1} = W^l + dt a_l f(W^l)
+ * (Eq. 13) to the pair (v, w) in complex arithmetic and stores Re W^L; the paper states no
+ * boundary condition: PERIODIC and NEUMANN are offered.                                    */
+typedef struct {
+  int bc;            /* FRKC2_BC_PERIODIC or FRKC2_BC_NEUMANN                                */
+  int precision;     /* FRKC2_FP64 or FRKC2_FP32 (state and arithmetic); MIXED: EUNSUPPORTED */
+  int64_t nx, ny;    /* grid extents (x fastest), 1..2^30 each                               */
+  double dx;         /* grid spacing                                                         */
+  double D;          /* diffusion coefficient (>= 0)                                         */
+  double A, B;       /* reaction constants                                                   */
+} frkc2_bruss_problem;
+
+/* Workspace bytes for frkc2_bruss_step and frkc2_bruss_rho_bound: 256 bytes of status and
+ * barrier words, then two complex stage states (4 planes of nx*ny values each).            */
+frkc2_status frkc2_bruss_workspace_size(const frkc2_bruss_problem* prob, size_t* bytes);
+
+/* Gershgorin bound on the spectral radius of the Jacobian of f at the real state (v, w):
+ *   rho = 8 D/dx^2 + max_cells max(|2 v w - (B+1)| + v^2, |B - 2 v w| + v^2),
+ * formed in FP64 in that order (p = v w, q = v v), written as one double to rho_dev (device,
+ * 8-byte aligned).  v, w: device arrays of the problem's precision, read only.             */
+frkc2_status frkc2_bruss_rho_bound(const frkc2_bruss_problem* prob, const void* v,
+                                   const void* w, double* rho_dev, void* ws, size_t ws_bytes,
+                                   void* stream);
+
+/* Advances (v, w) by nsteps FRKC2 steps of size dt (in place; v and w distinct device arrays
+ * of the problem's precision).  rho > 0: dt*rho <= beta is checked (FRKC2_EUNSTABLE).
+ * tune->kernel: 0 or 1 = one persistent cooperative launch for every stage of every step,
+ * the CTAs meeting at a device-wide barrier between stages (a plan of more than 1024 stages
+ * takes one launch per 1024 stages of each step); 2 = one launch per stage.  The barrier
+ * waits are bounded by tune->wait_limit polls (0 = 2^22); on expiry FRKC2_ETIMEOUT is latched
+ * in the workspace and the launch returns early (the state is then unspecified).
+ * tune->fault_inject = 1 (testing only, persistent form) makes the first barrier wait for a
+ * count that nothing reaches.  A non-finite value in a step's output latches FRKC2_ENONFINITE.
+ * Memory: 4 state reads and writes per cell-stage (32 bytes in FP32, 64 in FP64).          */
+frkc2_status frkc2_bruss_step(frkc2_plan_t plan, const frkc2_bruss_problem* prob, double dt,
+                              int nsteps, double rho, void* v, void* w, void* ws,
+                              size_t ws_bytes, const frkc2_tuning* tune, void* stream);
 
 /* Short text for a status code (static storage).                                          */
 const char* frkc2_status_string(frkc2_status st);

@@ -10,9 +10,9 @@ Brusselator on the unit square,
     v_t = D (v_xx + v_yy) + A - (B + 1) v + v^2 w,
     w_t = D (w_xx + w_yy) + B v - v^2 w,
 
-with the paper's values D = 0.02, A = 1, B = 3 (equilibrium v = A, w = B / A) and the
-initial state v = 1 + sin(2 pi x), w = 3 + cos(2 pi y).  Space is discretised with the
-5-point Laplacian on an nx-by-ny grid of spacing dx.  The FRKC2 step applies the ordered
+with the paper's values D = 0.02, A = 1, B = 3 (equilibrium v = A, w = B / A); the paper's
+initial state v = 1 + sin(2 pi x), w = 3 + cos(2 pi y) is an input (``frkc2_inputs.bruss_u0``).
+Space is discretised with the 5-point Laplacian on an nx-by-ny grid of spacing dx.  The FRKC2 step applies the ordered
 complex forward-Euler stages of Eq. 13 to the pair (v, w) in complex arithmetic; the
 reaction terms are polynomials, so their complex evaluation is unambiguous.
 
@@ -42,16 +42,6 @@ def problem(n: int | tuple, bc: str = "periodic", D: float = PAPER_D, A: float =
     ny, nx = (n, n) if np.isscalar(n) else n
     return {"ny": int(ny), "nx": int(nx), "bc": bc, "D": float(D), "A": float(A), "B": float(B),
             "dx": float(dx) if dx is not None else 1.0 / nx}
-
-
-def initial_state(prob: dict):
-    """The paper's initial perturbation of the equilibrium (Eq. 17): v = 1 + sin(2 pi x),
-    w = 3 + cos(2 pi y), with x = i dx and y = j dx."""
-    x = np.arange(prob["nx"]) * prob["dx"]
-    y = np.arange(prob["ny"]) * prob["dx"]
-    v = np.broadcast_to(1.0 + np.sin(2.0 * np.pi * x)[None, :], (prob["ny"], prob["nx"])).copy()
-    w = np.broadcast_to(3.0 + np.cos(2.0 * np.pi * y)[:, None], (prob["ny"], prob["nx"])).copy()
-    return v, w
 
 
 def laplacian(u, prob):

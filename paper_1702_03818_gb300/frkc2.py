@@ -19,12 +19,12 @@ if not os.path.exists(_LIB_PATH):
 _lib = C.CDLL(_LIB_PATH)
 
 OK, EINVAL, EUNSTABLE, EPLAN, ENOMEM, ECUDA, ETIMEOUT, ENONFINITE, EUNSUPPORTED = range(9)
-BC_PERIODIC, BC_DIRICHLET = 0, 1
+BC_PERIODIC, BC_DIRICHLET, BC_NEUMANN = 0, 1, 2
 KAPPA_CONST, KAPPA_FIELD, KAPPA_POWER = 0, 1, 2
 FP64, FP32, MIXED = 0, 1, 2
 PLAN_STRICT, PLAN_GREEDY, PLAN_LEBEDEV, PLAN_PAIRED = 1, 2, 4, 8
 PRECISION = {"fp64": FP64, "fp32": FP32, "mixed": MIXED}
-BC = {"periodic": BC_PERIODIC, "dirichlet": BC_DIRICHLET}
+BC = {"periodic": BC_PERIODIC, "dirichlet": BC_DIRICHLET, "neumann": BC_NEUMANN}
 KAPPA = {"const": KAPPA_CONST, "field": KAPPA_FIELD, "power": KAPPA_POWER}
 
 
@@ -32,6 +32,11 @@ class frkc2_problem(C.Structure):
     _fields_ = [("ndim", C.c_int), ("bc", C.c_int), ("kappa_kind", C.c_int), ("precision", C.c_int),
                 ("n", C.c_int64 * 3), ("dx", C.c_double), ("kappa_c", C.c_double),
                 ("kappa_p", C.c_double), ("kappa", C.c_void_p)]
+
+
+class frkc2_bruss_problem(C.Structure):
+    _fields_ = [("bc", C.c_int), ("precision", C.c_int), ("nx", C.c_int64), ("ny", C.c_int64),
+                ("dx", C.c_double), ("D", C.c_double), ("A", C.c_double), ("B", C.c_double)]
 
 
 class frkc2_adaptive_stats(C.Structure):
@@ -77,6 +82,10 @@ _sig = {
     "frkc2_batch_launch": (C.c_int, [_P, _P]),
     "frkc2_step_batched": (C.c_int, [C.c_int, _P, C.POINTER(frkc2_problem), _P, _P, _P,
                                      C.POINTER(frkc2_tuning), _P, C.c_size_t, _P]),
+    "frkc2_bruss_workspace_size": (C.c_int, [C.POINTER(frkc2_bruss_problem), C.POINTER(C.c_size_t)]),
+    "frkc2_bruss_rho_bound": (C.c_int, [C.POINTER(frkc2_bruss_problem), _P, _P, _P, _P, C.c_size_t, _P]),
+    "frkc2_bruss_step": (C.c_int, [_P, C.POINTER(frkc2_bruss_problem), C.c_double, C.c_int, C.c_double, _P, _P,
+                                   _P, C.c_size_t, C.POINTER(frkc2_tuning), _P]),
     "frkc2_status_string": (C.c_char_p, [C.c_int]),
     "frkc2_launch_count": (C.c_longlong, []),
 }
@@ -320,6 +329,39 @@ def frkc2_step_batched(plans, probs, dt, nsteps, u, ws, tune: frkc2_tuning | Non
     _check(_lib.frkc2_step_batched(n, ph, pa, da, na, ua, C.byref(tune) if tune is not None else None,
                                    _ptr(ws), ws.numel() * ws.element_size(), _stream_ptr(stream)),
            "frkc2_step_batched")
+
+
+def make_bruss_problem(n, dx: float | None = None, bc="periodic", precision="fp64", D: float = 0.02,
+                       A: float = 1.0, B: float = 3.0) -> frkc2_bruss_problem:
+    """Fill a ``frkc2_bruss_problem``; ``n`` = (nx, ny) or one side; dx defaults to 1/nx."""
+    nx, ny = (n, n) if isinstance(n, int) else (int(n[0]), int(n[1]))
+    p = frkc2_bruss_problem()
+    p.bc = BC[bc] if isinstance(bc, str) else int(bc)
+    p.precision = PRECISION[precision] if isinstance(precision, str) else int(precision)
+    p.nx, p.ny = int(nx), int(ny)
+    p.dx = float(dx) if dx is not None else 1.0 / nx
+    p.D, p.A, p.B = float(D), float(A), float(B)
+    return p
+
+
+def frkc2_bruss_workspace_size(prob: frkc2_bruss_problem) -> int:
+    b = C.c_size_t()
+    _check(_lib.frkc2_bruss_workspace_size(C.byref(prob), C.byref(b)), "frkc2_bruss_workspace_size")
+    return b.value
+
+
+def frkc2_bruss_rho_bound(prob: frkc2_bruss_problem, v, w, rho_dev, ws, stream=None):
+    _check(_lib.frkc2_bruss_rho_bound(C.byref(prob), _ptr(v), _ptr(w), _ptr(rho_dev), _ptr(ws),
+                                      ws.numel() * ws.element_size(), _stream_ptr(stream)),
+           "frkc2_bruss_rho_bound")
+
+
+def frkc2_bruss_step(plan: Plan, prob: frkc2_bruss_problem, dt: float, nsteps: int, rho: float, v, w, ws,
+                     tune: frkc2_tuning | None = None, stream=None):
+    _check(_lib.frkc2_bruss_step(plan.handle, C.byref(prob), float(dt), int(nsteps), float(rho), _ptr(v), _ptr(w),
+                                 _ptr(ws), ws.numel() * ws.element_size(),
+                                 C.byref(tune) if tune is not None else None, _stream_ptr(stream)),
+           "frkc2_bruss_step")
 
 
 def library_path() -> str:

@@ -169,3 +169,46 @@ def test_paired_plan_matches_oracle(L):
     a = lib["a"]
     assert np.array_equal(a[1::2], np.conj(a[0::2]))
     assert abs(lib["Q"] / ora["Q"] - 1.0) < 1e-9
+
+
+def test_bruss_workspace_size_and_validation_on_host():
+    p = F.make_bruss_problem((200, 120), precision="fp64")
+    plane = ((200 * 120 * 8 + 255) // 256) * 256
+    assert F.frkc2_bruss_workspace_size(p) == 256 + 8 * plane
+    p32 = F.make_bruss_problem(64, precision="fp32")
+    assert F.frkc2_bruss_workspace_size(p32) == 256 + 8 * (64 * 64 * 4)
+    for bad, st in [(dict(bc="dirichlet"), F.EINVAL), (dict(precision="mixed"), F.EUNSUPPORTED),
+                    (dict(D=-1.0), F.EINVAL), (dict(dx=0.0), F.EINVAL)]:
+        kw = dict(n=32)
+        kw.update(bad)
+        with pytest.raises(F.Frkc2Error) as e:
+            F.frkc2_bruss_workspace_size(F.make_bruss_problem(**kw))
+        assert e.value.status == st
+    with pytest.raises(F.Frkc2Error) as e:
+        F.frkc2_bruss_workspace_size(F.make_bruss_problem((0, 5), dx=0.1))
+    assert e.value.status == F.EINVAL
+
+
+def test_bruss_step_rejects_before_gpu_work():
+    plan = F.frkc2_plan(16)
+    beta = F.frkc2_plan_info(plan)["beta"]
+    p = F.make_bruss_problem(64)
+    need = F.frkc2_bruss_workspace_size(p)
+    v, w, ws = _FakeBuf(1 << 20, 64 * 64 * 8), _FakeBuf(1 << 24, 64 * 64 * 8), _FakeBuf(1 << 30, need)
+    rho = 6400.0
+    cases = [
+        (dict(dt=1.01 * beta / rho), F.EUNSTABLE),
+        (dict(dt=0.0), F.EINVAL),
+        (dict(ws=_FakeBuf(1 << 30, need - 1)), F.ENOMEM),
+        (dict(ws=_FakeBuf((1 << 30) + 64, need)), F.EINVAL),
+        (dict(w=v), F.EINVAL),
+        (dict(v=_FakeBuf((1 << 20) + 4, 8)), F.EINVAL),
+        (dict(tune=F.make_tuning(kernel=3)), F.EINVAL),
+        (dict(tune=F.make_tuning(kernel=2, fault_inject=1)), F.EINVAL),
+    ]
+    for over, st in cases:
+        kw = dict(dt=0.5 * beta / rho, v=v, w=w, ws=ws, tune=None)
+        kw.update(over)
+        with pytest.raises(F.Frkc2Error) as e:
+            F.frkc2_bruss_step(plan, p, kw["dt"], 1, rho, kw["v"], kw["w"], kw["ws"], kw["tune"], stream=0)
+        assert e.value.status == st, (over, e.value.status)

@@ -8,6 +8,7 @@ import os
 import numpy as np
 import pytest
 
+import frkc2_inputs as I
 from oracle import brusselator as BR
 from oracle import frkc2_oracle as O
 
@@ -140,8 +141,7 @@ def test_rho_bound_covers_dense_spectrum():
 
 
 def test_paper_initial_state():
-    pr = BR.problem(8)
-    v, w = BR.initial_state(pr)
+    v, w = I.bruss_u0(8, 8, 1.0 / 8)
     assert np.allclose(v[3], 1.0 + np.sin(2 * np.pi * np.arange(8) / 8))
     assert np.allclose(w[:, 5], 3.0 + np.cos(2 * np.pi * np.arange(8) / 8))
 
@@ -150,7 +150,7 @@ def test_second_order_convergence():
     """FRKC2 steps of the full nonlinear system converge at second order in T to a fine RK4
     solution (paper's initial state, 12 x 12 periodic grid, t = 0.4)."""
     pr = BR.problem(12)
-    v0, w0 = BR.initial_state(pr)
+    v0, w0 = I.bruss_u0(12, 12, pr["dx"])
     t_end = 0.4
     vr, wr = BR.rk4(v0, w0, t_end / 800, pr, 800)
     a = O.plan(6)["a"]
