@@ -39,13 +39,13 @@ UNIT = "cell-stage/s"
 MEASURED_PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
 # FP64 pipe: 152 SMs x 2 FP64 instructions per clock x 2.07 GHz (1.259 TFLOP/s with FMA = 2)
 FP64_PEAK_TINST = 152 * 2 * 2.07e9 / 1e12
-FP64_INST_PER_CELL_STAGE = 18  # 2 x (2 differences + 2 face products + 3 sums) + 4 FMA updates
+FP64_INST_PER_CELL_STAGE = 16  # 2 x (2 differences + 1 product + 3 multiply-adds) + 4 FMA updates
 # dram bytes per launch from one ncu capture of each pass kernel, keyed by the source hash of
 # the kernel file at capture time (the value is reported only while the source is unchanged)
 NCU_TRAFFIC = {
     # profiles/stream2d_fp64_varkappa2d_2048.md: two intermediate passes, mean of
-    # (152.3 + 48.8) MB and (152.1 + 45.9) MB
-    ("pass_stream2d.cu", "ede11c5105c5b133"): 199.5e6,
+    # (153.2 + 40.5) MB and (152.7 + 37.5) MB
+    ("pass_stream2d.cu", "a7019e6b6e0ef96d"): 191.9e6,
 }
 
 
@@ -255,14 +255,14 @@ def run_ours(args, rank, world, local_rank):
         v = cell_stages * args.steps / (np.sum(vms) / 1e3)
         got = c["u"].double().cpu().numpy()
         smsec = step_only_ms(c, pl=plan_p)
-        ach = 8.5 * cells * s * nsteps / (smsec / 1e3) / 1e12
+        ach = 7.5 * cells * s * nsteps / (smsec / 1e3) / 1e12
         variants["fp64_paired"] = {
             "value": v, "ms_per_step": float(np.mean(vms)), "plan": "FRKC2_PLAN_PAIRED (Lebedev pairs, Q ~ 0.12 L^4)",
             "speedup_vs_fp64": v / (cell_stages * args.steps / (float(np.sum(ms)) / 1e3)),
             "rel_l2_vs_fp64_gpu_after_100_steps": float(np.linalg.norm(got - u64) / np.linalg.norm(u64)),
             "roofline": {"bound": "alu", "achieved": ach, "peak": FP64_PEAK_TINST,
                          "unit": "Tinst/s (FP64 pipe)", "frac": ach / FP64_PEAK_TINST,
-                         "inst_per_cell_stage": 8.5, "traffic": None},
+                         "inst_per_cell_stage": 7.5, "traffic": None},
         }
         del c
 

@@ -3,10 +3,16 @@
 // and, for a conductivity field, the face sensitivities
 //   G_f = Re(c_l conj(lam_m - lam_i)(W_i - W_m)) / dx^2
 // of every face, added to dJ/dkappa of its two cells with weight 1/2 (1 for a Dirichlet
-// boundary face).  Same layout as the forward streaming pass: a warp owns 31 columns plus a
-// west halo lane and walks rows upward; each face's lambda difference, lambda flux, W
-// difference and sensitivity are formed once (x faces shared by shuffle, y faces carried
-// to the next row).  lam and the stage state W^l are read interleaved (U, V).
+// boundary face).  A warp owns 30 columns plus a halo lane on each side and walks rows
+// upward; each face's lambda difference and sensitivity are formed once (x faces shared by
+// shuffle, y faces carried to the next row), and A lam = k_e d_e - k_w d_w + k_n d_n - k_s d_s
+// takes one product and three fused multiply-adds per component.  Each cell forms
+// Y = -(c/2) W^l once (in the state precision), so a face's sensitivity share is
+// Re(conj(lam_m - lam_i)(Y_m - Y_i)): two differences and one multiply-add, the face weight
+// 1/2 folded into Y (a Dirichlet boundary face, weight 1, counts twice).  Per cell-stage: 4
+// lambda differences, 4 for Y, 2 x (2 differences + 2) for the sensitivities, 8 for A lam,
+// 4 for the update and 4 for the dJ/dkappa sum -- 32 floating-point instructions.  lam and
+// the stage state W^l are read interleaved (U, V).
 #include <algorithm>
 
 #include <cuda_runtime.h>
@@ -18,14 +24,21 @@ namespace {
 
 constexpr int AS_THREADS = 256;
 constexpr int AS_WARPS = AS_THREADS / 32;
-constexpr int AS_COLS = 31;
+constexpr int AS_COLS = 30;  // output columns per warp: lanes 1..30 (lanes 0 and 31 are halos)
+#ifndef FRKC2_ADJ_MIN_BLOCKS
+#define FRKC2_ADJ_MIN_BLOCKS 3
+#endif
+#ifndef FRKC2_ADJ_UNROLL
+#define FRKC2_ADJ_UNROLL 2
+#endif
+constexpr int AS_UNROLL = FRKC2_ADJ_UNROLL;
 
 template <class T> struct V2t;
 template <> struct V2t<double> { using type = double2; };
 template <> struct V2t<float> { using type = float2; };
 
 template <class S, class A, bool PERIODIC>
-__global__ void __launch_bounds__(AS_THREADS, 4)
+__global__ void __launch_bounds__(AS_THREADS, FRKC2_ADJ_MIN_BLOCKS)
     k_adj_stream2d(const AdjStreamArgs p, long long total, long long nwarps_grid) {
   using S2 = typename V2t<S>::type;
   using A2 = typename V2t<A>::type;
@@ -42,7 +55,7 @@ __global__ void __launch_bounds__(AS_THREADS, 4)
   S2* __restrict__ Lout = static_cast<S2*>(p.L_out);
   double* __restrict__ dk = p.dk;
   const S ca = S(p.ca), cb = S(p.cb);
-  const A cad = A(p.ca), cbd = A(p.cb);
+  const S hr = S(0.5 * p.ca), hi = S(0.5 * p.cb);  // c/2: each face gives half to each cell
 
   while (idx < end) {
     const int wcol = int(idx / ny);
@@ -59,30 +72,21 @@ __global__ void __launch_bounds__(AS_THREADS, 4)
       xr = x;
       xin = x >= 0 && x < nx;
     }
-    int xeast;
-    bool eastin;
-    if (PERIODIC) {
-      xeast = xr + 1 == nx ? 0 : xr + 1;
-      eastin = true;
-    } else {
-      xeast = x + 1;
-      eastin = xeast >= 0 && xeast < nx;
-    }
     const bool has_faces = PERIODIC || (x >= -1 && x < nx);
     const int fcol = (PERIODIC ? xr : x) + 1;
-    const bool out_ok = lane >= 1 && x >= 0 && x < nx;
+    const bool out_ok = lane >= 1 && lane <= 30 && x >= 0 && x < nx;
     // Dirichlet: a boundary face passes all of its sensitivity to its interior cell
-    const A wW = (!PERIODIC && x == 0) ? A(1) : A(0.5);
-    const A wE = (!PERIODIC && x == nx - 1) ? A(1) : A(0.5);
+    const bool bW = !PERIODIC && x == 0;
+    const bool bE = !PERIODIC && x == nx - 1;
 
     auto wrapy = [&](int yy) { return PERIODIC ? (yy < 0 ? yy + ny : (yy >= ny ? yy - ny : yy)) : yy; };
-    auto ld = [&](const S2* __restrict__ P2, const S* __restrict__ P1, int cplx, int yy, int xx, bool inx) -> S2 {
+    auto ld = [&](const S2* __restrict__ P2, const S* __restrict__ P1, int cplx, int yy) -> S2 {
       S2 w;
       w.x = S(0);
       w.y = S(0);
       const int yw = wrapy(yy);
-      if (!PERIODIC && !(inx && yy >= 0 && yy < ny)) return w;
-      const size_t g = size_t(yw) * nx + xx;
+      if (!PERIODIC && !(xin && yy >= 0 && yy < ny)) return w;
+      const size_t g = size_t(yw) * nx + xr;
       if (cplx == 1) {
         w = __ldg(P2 + g);
       } else if (cplx == 2) {
@@ -100,65 +104,49 @@ __global__ void __launch_bounds__(AS_THREADS, 4)
       if (!has_faces) return f;
       return __ldg(FEN + size_t(yy + 1) * (nx + 1) + fcol);
     };
+    // Y = -(c/2) W: a face's sensitivity is then Re(conj(lam_m - lam_i)(Y_m - Y_i))
+    auto yof = [&](S2 w) -> S2 {
+      S2 y;
+      y.x = hi * w.y - hr * w.x;
+      y.y = -(hi * w.x) - hr * w.y;
+      return y;
+    };
 
-    // prime: row y0 and its south face (lambda flux and sensitivity through it)
-    S2 Lc = ld(Lin, Lr, p.l_complex, y0, xr, xin);
-    S2 Wc = ld(Wc2, Wr, p.w_complex, y0, xr, xin);
-    A PnU, PnV;      // lambda flux into row y0-1 through its north face
+    // prime: row y0 and its south face (lambda difference, conductivity and sensitivity)
+    S2 Lc = ld(Lin, Lr, p.l_complex, y0);
+    S2 Yc = yof(ld(Wc2, Wr, p.w_complex, y0));
+    A dSr, dSi, ks;  // lambda difference across the south face of row y0, and that face
     A Gs;            // sensitivity of the south face of row y0
     {
-      const S2 Ls = ld(Lin, Lr, p.l_complex, y0 - 1, xr, xin);
-      const S2 Ws = ld(Wc2, Wr, p.w_complex, y0 - 1, xr, xin);
-      const A ks = faces(y0 - 1).y;
-      const A dlr = A(Lc.x - Ls.x), dli = A(Lc.y - Ls.y);
-      PnU = ks * dlr;
-      PnV = ks * dli;
-      const A dWr = A(Wc.x - Ws.x), dWi = A(Wc.y - Ws.y);
-      const A zr = dlr * dWr + dli * dWi;
-      const A zi = dlr * dWi - dli * dWr;
-      Gs = cbd * zi - cad * zr;
+      const S2 Ls = ld(Lin, Lr, p.l_complex, y0 - 1);
+      const S2 Ys = yof(ld(Wc2, Wr, p.w_complex, y0 - 1));
+      ks = faces(y0 - 1).y;
+      dSr = A(Lc.x - Ls.x);
+      dSi = A(Lc.y - Ls.y);
+      Gs = dSr * A(Yc.x - Ys.x) + dSi * A(Yc.y - Ys.y);
     }
+#pragma unroll AS_UNROLL
     for (int y = y0; y < y1; ++y) {
-      const S2 Ln = ld(Lin, Lr, p.l_complex, y + 1, xr, xin);
-      const S2 Wn = ld(Wc2, Wr, p.w_complex, y + 1, xr, xin);
+      const S2 Ln = ld(Lin, Lr, p.l_complex, y + 1);
+      const S2 Yn = yof(ld(Wc2, Wr, p.w_complex, y + 1));
       const A2 f = faces(y);
-      S Le_r = __shfl_down_sync(0xffffffffu, Lc.x, 1);
-      S Le_i = __shfl_down_sync(0xffffffffu, Lc.y, 1);
-      S We_r = __shfl_down_sync(0xffffffffu, Wc.x, 1);
-      S We_i = __shfl_down_sync(0xffffffffu, Wc.y, 1);
-      if (lane == 31) {
-        const S2 Le = ld(Lin, Lr, p.l_complex, y, xeast, eastin);
-        const S2 We = ld(Wc2, Wr, p.w_complex, y, xeast, eastin);
-        Le_r = Le.x;
-        Le_i = Le.y;
-        We_r = We.x;
-        We_i = We.y;
-      }
-      // east face: lambda difference, flux, W difference, sensitivity
+      // east face (lane 31 is a halo: its east values are not used)
+      const S Le_r = __shfl_down_sync(0xffffffffu, Lc.x, 1);
+      const S Le_i = __shfl_down_sync(0xffffffffu, Lc.y, 1);
+      const S Ye_r = __shfl_down_sync(0xffffffffu, Yc.x, 1);
+      const S Ye_i = __shfl_down_sync(0xffffffffu, Yc.y, 1);
       const A dEr = A(Le_r - Lc.x), dEi = A(Le_i - Lc.y);
-      const A FeU = f.x * dEr, FeV = f.x * dEi;
-      A Ge;
-      {
-        const A dWr = A(We_r - Wc.x), dWi = A(We_i - Wc.y);
-        const A zr = dEr * dWr + dEi * dWi;
-        const A zi = dEr * dWi - dEi * dWr;
-        Ge = cbd * zi - cad * zr;
-      }
+      const A Ge = dEr * A(Ye_r - Yc.x) + dEi * A(Ye_i - Yc.y);
       // north face
       const A dNr = A(Ln.x - Lc.x), dNi = A(Ln.y - Lc.y);
-      const A FnU = f.y * dNr, FnV = f.y * dNi;
-      A Gn;
-      {
-        const A dWr = A(Wn.x - Wc.x), dWi = A(Wn.y - Wc.y);
-        const A zr = dNr * dWr + dNi * dWi;
-        const A zi = dNr * dWi - dNi * dWr;
-        Gn = cbd * zi - cad * zr;
-      }
-      const A wU = __shfl_up_sync(0xffffffffu, FeU, 1);
-      const A wV = __shfl_up_sync(0xffffffffu, FeV, 1);
+      const A Gn = dNr * A(Yn.x - Yc.x) + dNi * A(Yn.y - Yc.y);
+      // west face from lane - 1
+      const A dWr = __shfl_up_sync(0xffffffffu, dEr, 1);
+      const A dWi = __shfl_up_sync(0xffffffffu, dEi, 1);
+      const A kw = __shfl_up_sync(0xffffffffu, f.x, 1);
       const A Gw = __shfl_up_sync(0xffffffffu, Ge, 1);
-      const A fU = (FeU - wU) + (FnU - PnU);
-      const A fV = (FeV - wV) + (FnV - PnV);
+      const A fU = f.y * dNr - ks * dSr - kw * dWr + f.x * dEr;
+      const A fV = f.y * dNi - ks * dSi - kw * dWi + f.x * dEi;
       if (out_ok) {
         const size_t g = size_t(y) * nx + x;
         S2 o;
@@ -166,16 +154,22 @@ __global__ void __launch_bounds__(AS_THREADS, 4)
         o.y = Lc.y + ca * S(fV) - cb * S(fU);
         Lout[g] = o;
         if (dk) {
-          const A wS = (!PERIODIC && y == 0) ? A(1) : A(0.5);
-          const A wN = (!PERIODIC && y == ny - 1) ? A(1) : A(0.5);
-          dk[g] += double((wE * Ge + wW * Gw) + (wN * Gn + wS * Gs));
+          A ge = Ge, gw = Gw, gn = Gn, gs = Gs;
+          if (!PERIODIC) {
+            if (bE) ge = Ge + Ge;
+            if (bW) gw = Gw + Gw;
+            if (y == ny - 1) gn = Gn + Gn;
+            if (y == 0) gs = Gs + Gs;
+          }
+          dk[g] += double((ge + gw) + (gn + gs));
         }
       }
-      PnU = FnU;
-      PnV = FnV;
+      dSr = dNr;
+      dSi = dNi;
+      ks = f.y;
       Gs = Gn;
       Lc = Ln;
-      Wc = Wn;
+      Yc = Yn;
     }
   }
 }

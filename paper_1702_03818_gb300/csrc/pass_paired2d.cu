@@ -6,13 +6,15 @@
 //   Y = w + cy f(w),   w' = w + c1 f(w) + c2 f(Y),
 //   cy = T alpha / dx^2,  c1 = T (alpha - beta^2/alpha) / dx^2,  c2 = T (|a|^2/alpha) / dx^2
 // (f here without the 1/dx^2, which the coefficients carry).  The state stays real: 8 bytes
-// per cell in FP64 instead of 16, and 17 floating-point instructions per pair (two
-// flux-shared stencils, 1 + 2 fused multiply-adds) instead of 2 x 18 for two complex stages.
+// per cell in FP64 instead of 16, and 15 floating-point instructions per pair (two stencils
+// f = k_e d_e - k_w d_w + k_n d_n - k_s d_s of 2 differences + 4 multiply-adds each, with
+// every neighbour difference formed once and shared, plus 1 + 2 fused multiply-adds)
+// instead of 2 x 16 for two complex stages.
 //
 // Streaming layout: a warp owns 32 consecutive columns, outputs 29 of them (lanes 2..30), and
 // walks rows upward.  At row y it reads w(y+2), forms f(w) and Y for row y+1 and f(Y) and w'
 // for row y; x-neighbours come by shuffle (lane 31 reads its east neighbour itself), the
-// north fluxes of f(w) and f(Y) are carried to the next row.  Same persistent, balanced work
+// north differences of w and Y are carried to the next row as its south ones.  Same persistent, balanced work
 // split as the complex streaming pass.
 #include <algorithm>
 
@@ -26,6 +28,9 @@ namespace {
 constexpr int PR_THREADS = 256;
 constexpr int PR_WARPS = PR_THREADS / 32;
 constexpr int PR_COLS = 29;  // output columns per warp (lanes 2..30)
+#ifndef FRKC2_PAIRED_MIN_BLOCKS
+#define FRKC2_PAIRED_MIN_BLOCKS 3
+#endif
 
 template <class T> struct P2t;
 template <> struct P2t<double> { using type = double2; };
@@ -35,7 +40,7 @@ __device__ __forceinline__ bool bad_bits(double v) { return (__double2hiint(v) &
 __device__ __forceinline__ bool bad_bits(float v) { return (__float_as_uint(v) & 0x7f800000u) == 0x7f800000u; }
 
 template <class S, class A, bool PERIODIC>
-__global__ void __launch_bounds__(PR_THREADS, 4)
+__global__ void __launch_bounds__(PR_THREADS, FRKC2_PAIRED_MIN_BLOCKS)
     k_paired2d(const PassArgs p, const void* __restrict__ fen_v, long long total, long long nwarps_grid) {
   using A2 = typename P2t<A>::type;
   const int lane = threadIdx.x & 31;
@@ -90,56 +95,56 @@ __global__ void __launch_bounds__(PR_THREADS, 4)
       return __ldg(FEN + size_t(wrapy(yy) + 1) * (nx + 1) + fcol);
     };
     auto cell_in = [&](int yy) { return PERIODIC || (xin && yy >= 0 && yy < ny); };
-    // f along x for one row: east flux by this lane, west flux from lane - 1
-    auto xflux = [&](S wc, S we, A ke) -> A {
-      const A Fe = ke * A(we - wc);
-      const A Fw = __shfl_up_sync(0xffffffffu, Fe, 1);
-      return Fe - Fw;
-    };
     auto east_of = [&](S wc, int yy) -> S {
       S e = __shfl_down_sync(0xffffffffu, wc, 1);
       if (lane == 31) e = ld(yy, xeast, eastin);
       return e;
     };
+    // f at one cell from its neighbour differences: the east one formed here, the west one
+    // (and the west face) from lane - 1, the north one given, the south one carried
+    auto fdiff = [&](S wc, S we, A2 f, A dN, A ks, A dS) -> A {
+      const A dE = A(we - wc);
+      const A dW = __shfl_up_sync(0xffffffffu, dE, 1);
+      const A kw = __shfl_up_sync(0xffffffffu, f.x, 1);
+      return f.y * dN - ks * dS - kw * dW + f.x * dE;
+    };
 
-    // prologue: rows y0-2 .. y0+1 of w; f(w) and Y of rows y0-1, y0; north fluxes
+    // prologue: rows y0-2 .. y0+1 of w; f(w) and Y of rows y0-1, y0
     const S wm2 = ld(y0 - 2, xr, xin), wm1 = ld(y0 - 1, xr, xin), w0 = ld(y0, xr, xin), w1 = ld(y0 + 1, xr, xin);
     const A2 fm2 = faces(y0 - 2), fm1 = faces(y0 - 1), f0 = faces(y0);
-    // north flux of w through the faces below rows y0-1, y0, y0+1
-    const A FnWm2 = fm2.y * A(wm1 - wm2);
-    const A FnWm1 = fm1.y * A(w0 - wm1);
-    const A FnW0 = f0.y * A(w1 - w0);
-    const A fWm1 = xflux(wm1, east_of(wm1, y0 - 1), fm1.x) + (FnWm1 - FnWm2);
-    A fW0 = xflux(w0, east_of(w0, y0), f0.x) + (FnW0 - FnWm1);
+    const A dNm2 = A(wm1 - wm2), dNm1 = A(w0 - wm1), dN0 = A(w1 - w0);
+    const A fWm1 = fdiff(wm1, east_of(wm1, y0 - 1), fm1, dNm1, fm2.y, dNm2);
+    A fWc = fdiff(w0, east_of(w0, y0), f0, dN0, fm1.y, dNm1);
     const S Ym1 = cell_in(y0 - 1) ? wm1 + cy * S(fWm1) : S(0);
-    S Y0 = cell_in(y0) ? w0 + cy * S(fW0) : S(0);
-    A FnYm1 = fm1.y * A(Y0 - Ym1);  // north flux of Y into row y0-1
+    S Yc = cell_in(y0) ? w0 + cy * S(fWc) : S(0);
     // rolling registers for row y (= current output row)
+    A dNYs = A(Yc - Ym1);  // north difference of Y at row y - 1, and that face
+    A kYs = fm1.y;
     S wc = w0, wn = w1;
-    A FnWc = FnW0;  // north flux of w at row y
-    A2 fc = f0;     // faces of row y
-    S Yc = Y0;
+    A dNWc = dN0;  // north difference of w at row y
+    A2 fc = f0;    // faces of row y
 
     for (int y = y0; y < y1; ++y) {
       // row y+1: f(w) and Y
       const S wnn = ld(y + 2, xr, xin);
       const A2 fn = faces(y + 1);
-      const A FnWn = fn.y * A(wnn - wn);
-      const A fWn = xflux(wn, east_of(wn, y + 1), fn.x) + (FnWn - FnWc);
+      const A dNWn = A(wnn - wn);
+      const A fWn = fdiff(wn, east_of(wn, y + 1), fn, dNWn, fc.y, dNWc);
       const S Yn = cell_in(y + 1) ? wn + cy * S(fWn) : S(0);
-      // row y: f(Y) and the new state
-      const A FnYc = fc.y * A(Yn - Yc);
-      // (lane 31 has no east neighbour for Y; its f(Y) is not an output)
-      const A fY = xflux(Yc, __shfl_down_sync(0xffffffffu, Yc, 1), fc.x) + (FnYc - FnYm1);
-      const S wnew = wc + c1 * S(fW0) + c2 * S(fY);
+      // row y: f(Y) and the new state (lane 31 has no east neighbour for Y; its f(Y) is
+      // not an output)
+      const A dNYc = A(Yn - Yc);
+      const A fY = fdiff(Yc, __shfl_down_sync(0xffffffffu, Yc, 1), fc, dNYc, kYs, dNYs);
+      const S wnew = wc + c1 * S(fWc) + c2 * S(fY);
       if (out_ok) {
         Wo[size_t(y) * nx + x] = wnew;
         if (p.check_finite) bad |= bad_bits(wnew);
       }
       // roll
-      FnYm1 = FnYc;
-      fW0 = fWn;
-      FnWc = FnWn;
+      dNYs = dNYc;
+      kYs = fc.y;
+      fWc = fWn;
+      dNWc = dNWn;
       Yc = Yn;
       wc = wn;
       wn = wnn;

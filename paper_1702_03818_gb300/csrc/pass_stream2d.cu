@@ -2,14 +2,18 @@
 // conductivity (FIELD / CONST) flux-form operator.
 //
 // Each warp owns 31 consecutive columns plus one halo lane on the low-x side and walks rows
-// upward.  Every face flux kappa_f (W_nb - W_c) is computed once and used by both cells of
-// the face: the x flux through a lane's east face reaches the next lane through a warp
-// shuffle (the halo lane supplies the chunk's west edge), and the y flux through a cell's
-// north face is carried in registers to the next row.  Per cell and stage this leaves 2
-// differences, 2 products and 3 sums for each of U and V plus 4 fused multiply-adds for the
-// complex update -- 18 floating-point instructions, which is what bounds the FP64 path on
+// upward.  Every neighbour difference W_nb - W_c is formed once and used by both cells of
+// the face: a lane's east difference (and east face conductivity) reaches the next lane
+// through a warp shuffle as its west difference (the halo lane supplies the chunk's west
+// edge), and a cell's north difference and north face conductivity are carried in registers
+// to the next row as its south ones.  Each cell then forms
+//   f = kappa_e d_e - kappa_w d_w + kappa_n d_n - kappa_s d_s
+// with one product and three fused multiply-adds per component: per cell and stage 2
+// differences and 4 multiply-adds for each of U and V plus 4 fused multiply-adds for the
+// complex update -- 16 floating-point instructions, which is what bounds the FP64 path on
 // GB300 (its FP64 pipe issues 2 lanes per clock per SM, far below its memory system).
-// Fluxes are combined by subtraction, never by an explicit negation.
+// Every term is a conductivity times a neighbour difference, as in the flux form; the face
+// sum is rounded per cell, so the two cells of a face see its flux to within rounding.
 //
 // Memory: the stage state between passes is stored interleaved (U, V) so one 16-byte (FP64)
 // load brings a cell's complex value, and each cell's east and north face conductivities
@@ -33,7 +37,7 @@ constexpr int ST_THREADS = 256;
 constexpr int ST_WARPS = ST_THREADS / 32;
 constexpr int ST_COLS = 31;  // output columns per warp
 #ifndef FRKC2_STREAM_MIN_BLOCKS
-#define FRKC2_STREAM_MIN_BLOCKS 6
+#define FRKC2_STREAM_MIN_BLOCKS 4
 #endif
 #ifndef FRKC2_STREAM_PREFETCH
 #define FRKC2_STREAM_PREFETCH 0
@@ -134,14 +138,15 @@ __global__ void __launch_bounds__(ST_THREADS, ST_MIN_BLOCKS)
       return __ldg(FEN + size_t(yy + 1) * (nx + 1) + fcol);
     };
 
-    // prime the stream: row y0 and the flux into row y0 - 1 through its north face
+    // prime the stream: row y0, and the difference across the south face of row y0 (the
+    // north difference of row y0 - 1) with that face's conductivity
     S2 Wc = load(y0, xr, xin);
-    A PnU, PnV;
+    A dSU, dSV, ks;
     {
       const S2 Ws = load(y0 - 1, xr, xin);
-      const A ks = faces(y0 - 1).y;
-      PnU = ks * A(Wc.x - Ws.x);
-      PnV = ks * A(Wc.y - Ws.y);
+      ks = faces(y0 - 1).y;
+      dSU = A(Wc.x - Ws.x);
+      dSV = A(Wc.y - Ws.y);
     }
 #if FRKC2_STREAM_PREFETCH
     // loads for row y+1 are issued one iteration ahead of their use
@@ -172,15 +177,16 @@ __global__ void __launch_bounds__(ST_THREADS, ST_MIN_BLOCKS)
         Ve = We.y;
       }
 #endif
-      // fluxes into this cell through its east and north faces
-      const A FeU = f.x * A(Ue - Wc.x), FeV = f.x * A(Ve - Wc.y);
-      const A FnU = f.y * A(Wn.x - Wc.x), FnV = f.y * A(Wn.y - Wc.y);
-      // through the west face: minus the west neighbour's east flux; through the south
-      // face: minus the north flux of the row below
-      const A wU = __shfl_up_sync(0xffffffffu, FeU, 1);
-      const A wV = __shfl_up_sync(0xffffffffu, FeV, 1);
-      const A fU = (FeU - wU) + (FnU - PnU);
-      const A fV = (FeV - wV) + (FnV - PnV);
+      // differences toward the east and north neighbours
+      const A dEU = A(Ue - Wc.x), dEV = A(Ve - Wc.y);
+      const A dNU = A(Wn.x - Wc.x), dNV = A(Wn.y - Wc.y);
+      // west face: the west neighbour's east difference and conductivity; south face: the
+      // north difference and conductivity of the row below
+      const A dWU = __shfl_up_sync(0xffffffffu, dEU, 1);
+      const A dWV = __shfl_up_sync(0xffffffffu, dEV, 1);
+      const A kw = __shfl_up_sync(0xffffffffu, f.x, 1);
+      const A fU = f.y * dNU - ks * dSU - kw * dWU + f.x * dEU;
+      const A fV = f.y * dNV - ks * dSV - kw * dWV + f.x * dEV;
       const S un = Wc.x + ca * S(fU) - cb * S(fV);
       const S vn = Wc.y + ca * S(fV) + cb * S(fU);
       if (out_ok) {
@@ -196,8 +202,9 @@ __global__ void __launch_bounds__(ST_THREADS, ST_MIN_BLOCKS)
         }
         if (p.check_finite) bad |= nonfinite_bits(un);
       }
-      PnU = FnU;
-      PnV = FnV;
+      dSU = dNU;
+      dSV = dNV;
+      ks = f.y;
       Wc = Wn;
 #if FRKC2_STREAM_PREFETCH
       Wn = Wnn;
