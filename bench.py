@@ -5,8 +5,9 @@ Workload (one bench step = the whole job): 2048^2 periodic grid, kappa = exp(0.5
 unit Gaussian random field of correlation length 32 cells (seed 3818), u0 a smooth random
 field in [0, 1] (correlation length 64, seed 3819), FRKC2 with s = 64 stages, 100 steps of
 dt = 0.9 beta / rho.  A step runs every part of the path: the spectral-radius bound (kernel),
-dt from it, and frkc2_step over 100 x 64 stages.  The primary line is FP64; FP32 and MIXED
-runs of the same job are reported under "variants" with their errors.
+dt from it, and frkc2_step over 100 x 64 stages.  The primary line is FP64; FP32, MIXED and DFLOAT
+(float-pair state on the FP32 pipe) runs of the same job, and FP64 with a PAIRED plan, are
+reported under "variants" with their errors.
 
 Timing: W untimed warm-up steps, then K timed steps, each bracketed by CUDA events on the
 launching stream; L2 is flushed (a 256 MiB write) between timed steps, outside the events.
@@ -44,8 +45,8 @@ FP64_INST_PER_CELL_STAGE = 16  # 2 x (2 differences + 1 product + 3 multiply-add
 # the kernel file at capture time (the value is reported only while the source is unchanged)
 NCU_TRAFFIC = {
     # profiles/stream2d_fp64_varkappa2d_2048.md: two intermediate passes, mean of
-    # (153.2 + 40.5) MB and (152.7 + 37.5) MB
-    ("pass_stream2d.cu", "a7019e6b6e0ef96d"): 191.9e6,
+    # (153.9 + 40.3) MB and (153.7 + 37.6) MB
+    ("pass_stream2d.cu", "1c09ff2fd8d3f460"): 192.8e6,
 }
 
 
@@ -227,7 +228,7 @@ def run_ours(args, rank, world, local_rank):
 
     variants = {}
     if not args.no_variants:
-        for prec in ("fp32", "mixed"):
+        for prec in ("fp32", "mixed", "dfloat"):
             c, vms, _, _ = timed(prec, args.steps, max(3, args.warmup // 2))
             v = cell_stages * args.steps / (np.sum(vms) / 1e3)
             got = c["u"].double().cpu().numpy()
@@ -325,7 +326,7 @@ def cpu_baseline(torch, F, dev, n=1024):
     oplan = O.plan(s)
     errs = {}
     value = None
-    for prec in ("fp64", "fp32", "mixed"):
+    for prec in ("fp64", "fp32", "mixed", "dfloat"):
         kk = k if prec == "fp64" else k.astype(np.float32).astype(np.float64)
         uu = u0 if prec != "fp32" else u0.astype(np.float32).astype(np.float64)
         pr = dict(ndim=2, dx=1.0, bc="periodic", kappa="field", kappa_c=1.0, kappa_p=2.5, kappa_field=kk)

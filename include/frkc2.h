@@ -55,8 +55,13 @@ enum { FRKC2_KAPPA_CONST = 0, FRKC2_KAPPA_FIELD = 1, FRKC2_KAPPA_POWER = 2 };
 
 /* FP64: double state and arithmetic.  FP32: float state and arithmetic.
  * MIXED: double state and double stage update; neighbour differences are formed in double
- * and the flux arithmetic (kappa_f * difference, face sums) runs in float.               */
-enum { FRKC2_FP64 = 0, FRKC2_FP32 = 1, FRKC2_MIXED = 2 };
+ * and the flux arithmetic (kappa_f * difference, face sums) runs in float.
+ * DFLOAT: double state at the interface; between stages the state is a pair of floats
+ * (hi + lo, about 48 significant bits) updated by error-free float sums, neighbour
+ * differences are rounded to float and the flux arithmetic runs in float -- every operation
+ * on the FP32 pipe.  2D FIELD / CONST problems and frkc2_step only (kernel 0 or 2, k = 1);
+ * elsewhere FRKC2_EUNSUPPORTED.  The conductivity field is float.                          */
+enum { FRKC2_FP64 = 0, FRKC2_FP32 = 1, FRKC2_MIXED = 2, FRKC2_DFLOAT = 3 };
 
 /* Plan flags: STRICT makes an unmet Q bound an error; GREEDY / LEBEDEV force one ordering;
  * PAIRED puts each conjugate pair in adjacent stages (pairs in Lebedev-Finogenov order) so
@@ -72,13 +77,13 @@ typedef struct {
   int ndim;          /* 1, 2 or 3                                                            */
   int bc;            /* FRKC2_BC_*; DIRICHLET means w = 0 in the ghost cells outside the grid */
   int kappa_kind;    /* FRKC2_KAPPA_*                                                        */
-  int precision;     /* FRKC2_FP64 / FP32 / MIXED                                            */
+  int precision;     /* FRKC2_FP64 / FP32 / MIXED / DFLOAT                                   */
   int64_t n[3];      /* n[0] = x extent, n[1] = y, n[2] = z; extents past ndim must be 1      */
   double dx;         /* grid spacing, the same along every axis                              */
   double kappa_c;    /* CONST: the value; POWER: the coefficient c                           */
   double kappa_p;    /* POWER: the exponent p (> 0)                                          */
   const void* kappa; /* FIELD: device array of n[0]*n[1]*n[2] cell values, double for FP64,
-                        float for FP32 and MIXED; a Dirichlet boundary face takes the value
+                        float otherwise; a Dirichlet boundary face takes the value
                         of its interior cell.  Ignored for the other kinds.                  */
 } frkc2_problem;
 
@@ -159,7 +164,7 @@ frkc2_status frkc2_workspace_status(const void* ws, void* stream);
 
 /* ---- Forward step (Sec. 3, Eq. 13) ------------------------------------------------------
  * Advances u by nsteps FRKC2 steps of size dt with the plan's stage order.
- *   u     : device array, in/out, real state (double for FP64 and MIXED, float for FP32).
+ *   u     : device array, in/out, real state (float for FP32, double otherwise).
  *   rho   : if > 0, dt*rho <= beta is checked on the host (FRKC2_EUNSTABLE otherwise);
  *           pass a bound from frkc2_rho_bound or 0 to skip the check.
  *   ws    : device workspace of at least frkc2_workspace_size() bytes.

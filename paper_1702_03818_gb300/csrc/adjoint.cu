@@ -301,6 +301,7 @@ frkc2_status adj_setup(AdjCtx& C, frkc2_plan_t plan, const frkc2_problem* prob, 
   if (!plan || !ws || nsteps < 1 || ckpt_every < 1) return FRKC2_EINVAL;
   const frkc2_status v = validate_problem(prob);
   if (v != FRKC2_OK) return v;
+  if (prob->precision == FRKC2_DFLOAT) return FRKC2_EUNSUPPORTED;
   if (!(dt > 0.0) || !std::isfinite(dt)) return FRKC2_EINVAL;
   if (reinterpret_cast<uintptr_t>(ws) & 255) return FRKC2_EINVAL;
   const frkc2_problem& p = *prob;
@@ -498,6 +499,7 @@ frkc2_status frkc2_adjoint_workspace_size(const frkc2_plan_t plan, const frkc2_p
   if (!plan || !bytes || nsteps < 0 || ckpt_every < 1) return FRKC2_EINVAL;
   const frkc2_status v = validate_problem(prob);
   if (v != FRKC2_OK) return v;
+  if (prob->precision == FRKC2_DFLOAT) return FRKC2_EUNSUPPORTED;
   const int n = std::max(nsteps, 1);
   *bytes = adj_layout(*prob, plan->s, n, std::min(ckpt_every, n)).total;
   return FRKC2_OK;

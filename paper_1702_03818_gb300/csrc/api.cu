@@ -91,7 +91,7 @@ frkc2_status validate_problem(const frkc2_problem* p) {
   if (p->ndim < 1 || p->ndim > 3) return FRKC2_EINVAL;
   if (p->bc != FRKC2_BC_PERIODIC && p->bc != FRKC2_BC_DIRICHLET) return FRKC2_EINVAL;
   if (p->kappa_kind < FRKC2_KAPPA_CONST || p->kappa_kind > FRKC2_KAPPA_POWER) return FRKC2_EINVAL;
-  if (p->precision < FRKC2_FP64 || p->precision > FRKC2_MIXED) return FRKC2_EINVAL;
+  if (p->precision < FRKC2_FP64 || p->precision > FRKC2_DFLOAT) return FRKC2_EINVAL;
   for (int d = 0; d < 3; ++d) {
     if (p->n[d] < 1 || p->n[d] > (int64_t(1) << 30)) return FRKC2_EINVAL;
     if (d >= p->ndim && p->n[d] != 1) return FRKC2_EINVAL;
@@ -100,6 +100,8 @@ frkc2_status validate_problem(const frkc2_problem* p) {
   if (!(p->dx > 0.0) || !std::isfinite(p->dx)) return FRKC2_EINVAL;
   if (p->kappa_kind == FRKC2_KAPPA_FIELD && !p->kappa) return FRKC2_EINVAL;
   if (p->kappa_kind == FRKC2_KAPPA_POWER && !(p->kappa_p > 0.0)) return FRKC2_EINVAL;
+  if (p->precision == FRKC2_DFLOAT && (p->ndim != 2 || p->kappa_kind == FRKC2_KAPPA_POWER))
+    return FRKC2_EUNSUPPORTED;  // the float-pair state has a 2D fixed-conductivity pass only
   return FRKC2_OK;
 }
 
@@ -185,7 +187,11 @@ frkc2_status frkc2_step(frkc2_plan_t plan, const frkc2_problem* prob, double dt,
   const bool tb_ok = tb2d_supported(p, k);
   const bool paired_ok = plan->paired && p.ndim == 2 && p.kappa_kind != FRKC2_KAPPA_POWER;
   bool use_stream2d = false, use_tb = false, use_paired = false;
-  if (kern == 4) {
+  const bool dfloat = p.precision == FRKC2_DFLOAT;
+  if (dfloat) {
+    if ((kern != 0 && kern != 2) || k != 1) return FRKC2_EUNSUPPORTED;
+    use_stream2d = true;
+  } else if (kern == 4) {
     if (!paired_ok) return FRKC2_EUNSUPPORTED;
     use_paired = true;
   } else if (kern == 0 && paired_ok && !(tune && tune->k)) {
@@ -291,7 +297,11 @@ frkc2_status frkc2_step(frkc2_plan_t plan, const frkc2_problem* prob, double dt,
         a.check_finite = last ? 1 : 0;
         a.ca[0] = dt * plan->a_re[l] / h2;
         a.cb[0] = dt * plan->a_im[l] / h2;
-        if (launch_pass_stream2d(p, a, base + L.fen, st) != cudaSuccess) return FRKC2_ECUDA;
+        a.caf[0] = float(a.ca[0]);
+        a.cbf[0] = float(a.cb[0]);
+        const cudaError_t e = dfloat ? launch_pass_stream2d_df(p, a, base + L.fen, st)
+                                     : launch_pass_stream2d(p, a, base + L.fen, st);
+        if (e != cudaSuccess) return FRKC2_ECUDA;
         curU = last ? u : outW;
       }
     }
@@ -342,6 +352,7 @@ frkc2_status frkc2_adaptive_workspace_size(const frkc2_problem* prob, const frkc
   if (!bytes) return FRKC2_EINVAL;
   const frkc2_status v = validate_problem(prob);
   if (v != FRKC2_OK) return v;
+  if (prob->precision == FRKC2_DFLOAT) return FRKC2_EUNSUPPORTED;
   const size_t N = cells(*prob), S = state_bytes(prob->precision);
   // step workspace + two embedded-solution buffers + the error sum
   *bytes = step_layout(*prob).total + 2 * align256(N * S) + 256;
@@ -354,6 +365,7 @@ frkc2_status frkc2_step_adaptive(frkc2_plan_t plan, const frkc2_problem* prob, d
   if (!plan || !u || !ws || !(t_end > 0.0) || !(tol > 0.0) || !(dt0 > 0.0)) return FRKC2_EINVAL;
   const frkc2_status v = validate_problem(prob);
   if (v != FRKC2_OK) return v;
+  if (prob->precision == FRKC2_DFLOAT) return FRKC2_EUNSUPPORTED;
   if (reinterpret_cast<uintptr_t>(ws) & 255) return FRKC2_EINVAL;
   size_t need = 0;
   frkc2_adaptive_workspace_size(prob, tune, &need);

@@ -289,6 +289,7 @@ frkc2_status batch_geometry(int nprob, const frkc2_plan_t* plans, const frkc2_pr
     if (v != FRKC2_OK) return v;
     if (!plans[i] || nsteps[i] < 1) return FRKC2_EINVAL;
     if (probs[i].ndim != 2 || probs[i].kappa_kind == FRKC2_KAPPA_POWER) return FRKC2_EUNSUPPORTED;
+    if (probs[i].precision == FRKC2_DFLOAT) return FRKC2_EUNSUPPORTED;
     if (probs[i].precision != p0.precision || probs[i].bc != p0.bc) return FRKC2_EINVAL;
   }
   int k = (tune && tune->k) ? tune->k : (p0.precision == FRKC2_FP32 ? 4 : 2);

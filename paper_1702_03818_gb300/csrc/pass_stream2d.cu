@@ -115,7 +115,10 @@ __global__ void __launch_bounds__(ST_THREADS, ST_MIN_BLOCKS)
       w.y = S(0);
       int yw = yy;
       if (PERIODIC) {
-        yw = yy < 0 ? yy + ny : (yy >= ny ? yy - ny : yy);
+        // rows run from y0 - 1 to y1 (y1 + 1 with the prefetch variant): more than one
+        // period past the grid when ny is 1 or 2
+        if (yw < 0) yw += ny;
+        while (yw >= ny) yw -= ny;
       } else if (!(inx && yy >= 0 && yy < ny)) {
         return w;
       }
@@ -133,7 +136,12 @@ __global__ void __launch_bounds__(ST_THREADS, ST_MIN_BLOCKS)
       A2 f;
       f.x = A(0);
       f.y = A(0);
-      if (PERIODIC) yy = yy < 0 ? yy + ny : (yy >= ny ? yy - ny : yy);
+      if (PERIODIC) {
+        if (yy < 0) yy += ny;
+        while (yy >= ny) yy -= ny;
+      } else if (yy >= ny) {
+        return f;  // face pairs exist for rows -1 .. ny-1
+      }
       if (!has_faces) return f;
       return __ldg(FEN + size_t(yy + 1) * (nx + 1) + fcol);
     };

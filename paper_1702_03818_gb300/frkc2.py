@@ -21,9 +21,9 @@ _lib = C.CDLL(_LIB_PATH)
 OK, EINVAL, EUNSTABLE, EPLAN, ENOMEM, ECUDA, ETIMEOUT, ENONFINITE, EUNSUPPORTED = range(9)
 BC_PERIODIC, BC_DIRICHLET, BC_NEUMANN = 0, 1, 2
 KAPPA_CONST, KAPPA_FIELD, KAPPA_POWER = 0, 1, 2
-FP64, FP32, MIXED = 0, 1, 2
+FP64, FP32, MIXED, DFLOAT = 0, 1, 2, 3
 PLAN_STRICT, PLAN_GREEDY, PLAN_LEBEDEV, PLAN_PAIRED = 1, 2, 4, 8
-PRECISION = {"fp64": FP64, "fp32": FP32, "mixed": MIXED}
+PRECISION = {"fp64": FP64, "fp32": FP32, "mixed": MIXED, "dfloat": DFLOAT}
 BC = {"periodic": BC_PERIODIC, "dirichlet": BC_DIRICHLET, "neumann": BC_NEUMANN}
 KAPPA = {"const": KAPPA_CONST, "field": KAPPA_FIELD, "power": KAPPA_POWER}
 

@@ -16,9 +16,9 @@ pytestmark = pytest.mark.gpu
 
 F = pytest.importorskip("paper_1702_03818_gb300.frkc2")
 
-TOL = {"fp64": 1e-11, "fp32": 1e-4, "mixed": 1e-6}
-DT = {"fp64": torch.float64, "fp32": torch.float32, "mixed": torch.float64}
-KDT = {"fp64": torch.float64, "fp32": torch.float32, "mixed": torch.float32}
+TOL = {"fp64": 1e-11, "fp32": 1e-4, "mixed": 1e-6, "dfloat": 1e-6}
+DT = {"fp64": torch.float64, "fp32": torch.float32, "mixed": torch.float64, "dfloat": torch.float64}
+KDT = {"fp64": torch.float64, "fp32": torch.float32, "mixed": torch.float32, "dfloat": torch.float32}
 
 
 def dev(a, dtype):
@@ -42,7 +42,7 @@ def run_gpu(plan, shape, bc, kappa, prec, u0, field, dt, nsteps, dx=1.0, c=1.0, 
 
 
 def rounded_field(field, prec):
-    """The conductivity the GPU sees: float32-rounded for FP32 and MIXED."""
+    """The conductivity the GPU sees: float32-rounded for every precision but FP64."""
     if field is None or prec == "fp64":
         return field
     return field.astype(np.float32).astype(np.float64)
@@ -264,3 +264,70 @@ def test_paired_plan_on_3d_runs_as_complex_stages():
     ref = O.frkc2_step(u0, oplan["a"], dt, opr, 2)
     got, st = run_gpu(plan, shape, "periodic", "field", "fp64", u0, field, dt, 2)
     assert st == F.OK and rel_l2(got, ref) < 1e-11
+
+
+# ---------------------------------------------------------------------------------------
+# DFLOAT: float-pair state on the FP32 pipe (2D fixed conductivity, k = 1 streaming pass)
+# ---------------------------------------------------------------------------------------
+
+DF_CASES = [
+    # shape, bc, kappa, s, nsteps, kernel
+    ((100, 77), "periodic", "field", 16, 2, 0),
+    ((70, 130), "dirichlet", "field", 32, 2, 2),
+    ((64, 64), "periodic", "const", 64, 1, 0),
+    ((5, 7), "dirichlet", "field", 8, 3, 0),
+    ((1, 9), "periodic", "field", 4, 2, 0),
+    ((33, 1), "dirichlet", "field", 8, 2, 0),
+]
+
+
+@pytest.mark.parametrize("case", DF_CASES, ids=lambda c: f"{'x'.join(map(str, c[0]))}-{c[1]}-{c[2]}-s{c[3]}-kern{c[5]}")
+def test_step_parity_dfloat(case):
+    shape, bc, kappa, s, nsteps, kernel = case
+    u0, field = seeded_case(shape, bc, kappa, 300 + s)
+    oplan = O.plan(s)
+    plan = F.frkc2_plan(s)
+    fo = rounded_field(field, "dfloat")
+    opr = oracle_problem(len(shape), bc, kappa, 1.0, fo)
+    dt = 0.9 * oplan["beta"] / O.rho_bound(opr, u0)
+    ref = O.frkc2_step(u0, oplan["a"], dt, opr, nsteps)
+    got, st = run_gpu(plan, shape, bc, kappa, "dfloat", u0, field, dt, nsteps, tune=F.make_tuning(kernel=kernel))
+    assert st == F.OK
+    err = rel_l2(got, ref)
+    assert err < TOL["dfloat"], err
+
+
+def test_dfloat_keeps_state_precision_fp32_loses():
+    """Many steps on a 2D field problem: the float-pair state stays within MIXED-class error of
+    the FP64 oracle while the float state drifts an order of magnitude further."""
+    shape = (96, 96)
+    u0, field = seeded_case(shape, "periodic", "field", 77)
+    s, nsteps = 64, 12
+    oplan = O.plan(s)
+    plan = F.frkc2_plan(s)
+    fo = rounded_field(field, "fp32")
+    opr = oracle_problem(2, "periodic", "field", 1.0, fo)
+    dt = 0.9 * oplan["beta"] / O.rho_bound(opr)
+    ref = O.frkc2_step(u0, oplan["a"], dt, opr, nsteps)
+    ref32 = O.frkc2_step(u0.astype(np.float32).astype(np.float64), oplan["a"], dt, opr, nsteps)
+    got_df, st = run_gpu(plan, shape, "periodic", "field", "dfloat", u0, field, dt, nsteps)
+    assert st == F.OK
+    got_32, _ = run_gpu(plan, shape, "periodic", "field", "fp32", u0, field, dt, nsteps,
+                        tune=F.make_tuning(k=1, kernel=2))
+    e_df, e_32 = rel_l2(got_df, ref), rel_l2(got_32, ref32)
+    assert e_df < 1e-6 and e_df * 10 < e_32, (e_df, e_32)
+
+
+def test_dfloat_launch_count():
+    shape = (40, 50)
+    u0, field = seeded_case(shape, "periodic", "field", 12)
+    plan = F.frkc2_plan(16)
+    kt = dev(field, torch.float32)
+    pr = lib_problem(shape, "periodic", "field", "dfloat", 1.0, kt)
+    ws = torch.empty(F.frkc2_workspace_size(pr), dtype=torch.uint8, device="cuda")
+    F.frkc2_workspace_reset(ws)
+    dt = 0.5 * plan.info()["beta"] / O.rho_bound(oracle_problem(2, "periodic", "field", 1.0, rounded_field(field, "fp32")))
+    u = dev(u0, torch.float64)
+    F.frkc2_launch_count()
+    F.frkc2_step(plan, pr, dt, 3, 0.0, u, ws)
+    assert F.frkc2_launch_count() == 2 + 3 * 16  # faces, face pairs, one pass per stage

@@ -212,3 +212,37 @@ def test_bruss_step_rejects_before_gpu_work():
         with pytest.raises(F.Frkc2Error) as e:
             F.frkc2_bruss_step(plan, p, kw["dt"], 1, rho, kw["v"], kw["w"], kw["ws"], kw["tune"], stream=0)
         assert e.value.status == st, (over, e.value.status)
+
+
+def test_dfloat_precision_validation_on_host():
+    """DFLOAT (float-pair state) exists for 2D FIELD / CONST problems and frkc2_step only."""
+    p2 = F.make_problem(2, (64, 48), 1.0, "periodic", "const", "dfloat")
+    pm = F.make_problem(2, (64, 48), 1.0, "periodic", "const", "mixed")
+    assert F.frkc2_workspace_size(p2) == F.frkc2_workspace_size(pm)
+    for bad in [F.make_problem(3, (8, 8, 8), 1.0, "periodic", "const", "dfloat"),
+                F.make_problem(2, (8, 8), 1.0, "periodic", "power", "dfloat"),
+                F.make_problem(1, (64,), 1.0, "periodic", "const", "dfloat")]:
+        with pytest.raises(F.Frkc2Error) as e:
+            F.frkc2_workspace_size(bad)
+        assert e.value.status == F.EUNSUPPORTED
+    plan = F.frkc2_plan(8)
+    with pytest.raises(F.Frkc2Error) as e:
+        F.frkc2_adjoint_workspace_size(plan, p2, 4, 2)
+    assert e.value.status == F.EUNSUPPORTED
+    with pytest.raises(F.Frkc2Error) as e:
+        F.frkc2_adaptive_workspace_size(p2)
+    assert e.value.status == F.EUNSUPPORTED
+    with pytest.raises(F.Frkc2Error) as e:
+        F.frkc2_batch_workspace_size([plan], [p2], [1])
+    assert e.value.status == F.EUNSUPPORTED
+    p_bad = F.make_problem(2, (8, 8), 1.0, "periodic", "const", 4)
+    with pytest.raises(F.Frkc2Error) as e:
+        F.frkc2_workspace_size(p_bad)
+    assert e.value.status == F.EINVAL
+    # only the k = 1 streaming pass: other kernels and k > 1 are refused before any GPU work
+    need = F.frkc2_workspace_size(p2)
+    u, ws = _FakeBuf(1 << 20, 64 * 48 * 8), _FakeBuf(1 << 30, need)
+    for t in (F.make_tuning(kernel=1), F.make_tuning(kernel=3), F.make_tuning(k=2)):
+        with pytest.raises(F.Frkc2Error) as e:
+            F.frkc2_step(plan, p2, 0.01, 1, 0.0, u, ws, t, stream=0)
+        assert e.value.status == F.EUNSUPPORTED
