@@ -182,13 +182,17 @@ frkc2_status frkc2_step(frkc2_plan_t plan, const frkc2_problem* prob, double dt,
   if (p.ndim < 3) tz = 1;
   if (tx < 1 || ty < 1 || tz < 1) return FRKC2_EINVAL;
   const int kern = tune ? tune->kernel : 0;
-  if (kern < 0 || kern > 4) return FRKC2_EINVAL;
+  if (kern < 0 || kern > 5) return FRKC2_EINVAL;
   const bool stream_ok = p.ndim == 2 && p.kappa_kind != FRKC2_KAPPA_POWER && k == 1;
   const bool tb_ok = tb2d_supported(p, k);
   const bool paired_ok = plan->paired && p.ndim == 2 && p.kappa_kind != FRKC2_KAPPA_POWER;
-  bool use_stream2d = false, use_tb = false, use_paired = false;
+  bool use_stream2d = false, use_tb = false, use_paired = false, use_stream3d = false;
   const bool dfloat = p.precision == FRKC2_DFLOAT;
-  if (dfloat) {
+  const bool stream3d_ok = p.ndim == 3 && k == 1;
+  if (kern == 5) {
+    if (!stream3d_ok) return FRKC2_EUNSUPPORTED;
+    use_stream3d = true;
+  } else if (dfloat) {
     if ((kern != 0 && kern != 2) || k != 1) return FRKC2_EUNSUPPORTED;
     use_stream2d = true;
   } else if (kern == 4) {
@@ -205,6 +209,8 @@ frkc2_status frkc2_step(frkc2_plan_t plan, const frkc2_problem* prob, double dt,
   } else if (kern == 0) {
     if (tb_ok && k > 1)
       use_tb = true;
+    else if (stream3d_ok)
+      use_stream3d = true;
     else
       use_stream2d = stream_ok;
   }
@@ -217,7 +223,7 @@ frkc2_status frkc2_step(frkc2_plan_t plan, const frkc2_problem* prob, double dt,
     probe.hx = k;
     probe.hy = p.ndim >= 2 ? k : 0;
     probe.hz = p.ndim >= 3 ? k : 0;
-    if (!use_stream2d && !use_tb && !use_paired && generic_smem_bytes(p, probe) > size_t(smem_optin()))
+    if (!use_stream2d && !use_tb && !use_paired && !use_stream3d && generic_smem_bytes(p, probe) > size_t(smem_optin()))
       return FRKC2_EINVAL;
   }
   if (nsteps == 0) return FRKC2_OK;
@@ -333,7 +339,11 @@ frkc2_status frkc2_step(frkc2_plan_t plan, const frkc2_problem* prob, double dt,
         a.caf[j] = float(a.ca[j]);
         a.cbf[j] = float(a.cb[j]);
       }
-      const cudaError_t e = use_tb ? launch_pass_tb2d(p, a, st) : launch_pass_generic(p, a, st);
+      a.in_mode = curV ? PASS_IO_PLANAR : PASS_IO_REAL;
+      a.out_mode = outV ? PASS_IO_PLANAR : PASS_IO_REAL;
+      const cudaError_t e = use_tb ? launch_pass_tb2d(p, a, st)
+                            : use_stream3d ? launch_pass_stream3d(p, a, st)
+                                           : launch_pass_generic(p, a, st);
       if (e != cudaSuccess) return FRKC2_ECUDA;
       curU = outU;
       curV = outV;

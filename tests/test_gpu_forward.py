@@ -331,3 +331,55 @@ def test_dfloat_launch_count():
     F.frkc2_launch_count()
     F.frkc2_step(plan, pr, dt, 3, 0.0, u, ws)
     assert F.frkc2_launch_count() == 2 + 3 * 16  # faces, face pairs, one pass per stage
+
+
+# ---------------------------------------------------------------------------------------
+# 3D pass streaming along z (kernel 5, the 3D default at k = 1)
+# ---------------------------------------------------------------------------------------
+
+S3_CASES = [
+    # shape (nz, ny, nx), bc, kappa, s, nsteps, kernel
+    ((12, 10, 14), "periodic", "field", 16, 1, 0),
+    ((40, 33, 70), "dirichlet", "field", 8, 2, 5),
+    ((35, 70, 7), "periodic", "power", 8, 1, 5),
+    ((10, 11, 9), "dirichlet", "power", 16, 1, 0),
+    ((70, 17, 31), "dirichlet", "power", 8, 1, 5),
+    ((9, 1, 33), "periodic", "field", 8, 2, 5),
+    ((1, 20, 1), "dirichlet", "const", 4, 2, 5),
+    ((2, 2, 2), "periodic", "power", 4, 1, 5),
+]
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "mixed"])
+@pytest.mark.parametrize("case", S3_CASES, ids=lambda c: f"{'x'.join(map(str, c[0]))}-{c[1]}-{c[2]}-s{c[3]}-kern{c[5]}")
+def test_step_parity_stream3d(case, prec):
+    shape, bc, kappa, s, nsteps, kernel = case
+    u0, field = seeded_case(shape, bc, kappa, 400 + s)
+    oplan = O.plan(s)
+    plan = F.frkc2_plan(s)
+    fo = rounded_field(field, prec)
+    opr = oracle_problem(3, bc, kappa, 1.0, fo)
+    dt = 0.9 * oplan["beta"] / O.rho_bound(opr, u0)
+    u0g = u0.astype(np.float32).astype(np.float64) if prec == "fp32" else u0
+    ref = O.frkc2_step(u0g, oplan["a"], dt, opr, nsteps)
+    got, st = run_gpu(plan, shape, bc, kappa, prec, u0, field, dt, nsteps, tune=F.make_tuning(k=1, kernel=kernel))
+    assert st == F.OK
+    err = rel_l2(got, ref)
+    assert err < TOL[prec], err
+
+
+def test_stream3d_equals_tile_pass_and_rejects_k():
+    shape = (24, 20, 40)
+    u0, field = seeded_case(shape, "dirichlet", "power", 9)
+    plan = F.frkc2_plan(8)
+    opr = oracle_problem(3, "dirichlet", "power", 1.0, None)
+    dt = 0.9 * plan.info()["beta"] / O.rho_bound(opr, u0)
+    a, st_a = run_gpu(plan, shape, "dirichlet", "power", "fp64", u0, None, dt, 1, tune=F.make_tuning(k=1, kernel=5))
+    b, st_b = run_gpu(plan, shape, "dirichlet", "power", "fp64", u0, None, dt, 1, tune=F.make_tuning(k=1, kernel=1))
+    assert st_a == F.OK and st_b == F.OK
+    assert rel_l2(a, b) < 1e-13
+    pr = lib_problem(shape, "dirichlet", "power", "fp64")
+    ws = torch.empty(F.frkc2_workspace_size(pr), dtype=torch.uint8, device="cuda")
+    with pytest.raises(F.Frkc2Error) as e:
+        F.frkc2_step(plan, pr, dt, 1, 0.0, dev(u0, torch.float64), ws, F.make_tuning(k=2, kernel=5))
+    assert e.value.status == F.EUNSUPPORTED
