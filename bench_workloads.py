@@ -123,7 +123,7 @@ def nonlinear3d(F, n=None):
     return {"workload": f"nonlinear3d: 3D kappa(u)=1+u^2.5 {n}^3 Dirichlet, s={s}, one FRKC2 step per bench step",
             "metric": "cell-stage/s", "value": out["fp64"]["value"], "unit": UNIT, "dtype": "f64",
             "precisions": out,
-            "kernel": "generic tile pass, k = 1, tile 32x4x4"}
+            "kernel": "3D pass streaming along z (k = 1)"}
 
 
 def adjoint2d(F):
@@ -442,7 +442,7 @@ def profile_case(F, name: str):
         F.frkc2_workspace_reset(ws)
         for _ in range(2):
             F.frkc2_step_batched(plans, probs, dts, [1] * 8, us, ws)
-    elif name == "generic3d":  # FP64 kappa(u) tile pass, 192^3, s = 8
+    elif name in ("generic3d", "stream3d"):  # FP64 kappa(u) pass, 192^3, s = 8 (tile / z-streaming)
         n, s = 192, 8
         u0 = I.hotspot3d_u0(n, sigma=15.0, seed=2017)
         plan = F.frkc2_plan(s)
@@ -452,9 +452,10 @@ def profile_case(F, name: str):
         F.frkc2_rho_bound(pr, u, rho)
         dt = 0.9 * plan.info()["beta"] / rho.item()
         ws = torch.empty(F.frkc2_workspace_size(pr), dtype=torch.uint8, device="cuda")
+        t = F.make_tuning(k=1, tile=(32, 4, 4), kernel=1) if name == "generic3d" else F.make_tuning(k=1, kernel=5)
         for _ in range(2):
             v = u.clone()
-            F.frkc2_step(plan, pr, dt, 1, 0.0, v, ws)
+            F.frkc2_step(plan, pr, dt, 1, 0.0, v, ws, t)
     elif name == "stream2d_df":  # DFLOAT streaming pass, 2048^2 var-kappa, s = 16, 1 step
         n, s = 2048, 16
         u0 = I.smooth_unit((n, n), 64.0, 3819)
