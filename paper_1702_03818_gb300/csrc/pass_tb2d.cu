@@ -238,7 +238,12 @@ bool tb2d_supported(const frkc2_problem& p, int k) {
          2 * k < TB_R;
 }
 
+#ifndef FRKC2_TB_REG
+#define FRKC2_TB_REG 1
+#endif
+
 cudaError_t launch_pass_tb2d(const frkc2_problem& p, const PassArgs& a, cudaStream_t st) {
+  if (FRKC2_TB_REG) return launch_pass_tb2d_reg(p, a, st);  // state in registers
   const size_t smem = tb2d_smem_bytes();
   const int T = TB_R - 2 * a.k;
   dim3 grid((a.nx + T - 1) / T, (a.ny + T - 1) / T, 1);
