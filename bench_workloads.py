@@ -7,7 +7,7 @@ stated against the FP64 GPU result of the same job; parity of every path with th
 is established by the GPU tests (tests/test_gpu_*.py) on reduced instances of these recipes.
 
 Workloads (sizes and seeds from frkc2_inputs.CONFIGS):
-  heat1d       1D heat, N = 256 Dirichlet, s = 16, 87 steps to T = 0.05, FP64.
+  heat1d       1D heat, N = 256 Dirichlet, s = 16, 87 steps to T = 0.05, FP64 (one cluster launch).
   nonlinear3d  3D kappa(u) = 1 + u^2.5, 256^3 Dirichlet hot spot with 1 % noise; one bench
                step = one FRKC2 step at FP64, FP32 and MIXED.  s = 32: with s = 128 the complex
                stages amplify the noise modes until kappa(W) leaves the stability bound and the
@@ -85,7 +85,7 @@ def heat1d(F):
     cs = cfg["n"] * s * nsteps
     return {"workload": "heat1d: 1D heat N=256 Dirichlet, s=16, 87 steps, FP64", "metric": "cell-stage/s",
             "value": cs / (med / 1e3), "unit": UNIT, "ms_per_job": med, "nsteps": nsteps,
-            "kernel": "generic tile pass, k = 16 (one launch per step)"}
+            "kernel": "1D whole-job cluster kernel (one launch for all 87 x 16 stages)"}
 
 
 def nonlinear3d(F, n=None):

@@ -95,7 +95,8 @@ typedef struct {
   int kernel;        /* 0 = library choice, 1 = generic shared-memory tile kernel,
                         2 = 2D streaming kernel (k = 1 only), 3 = 2D FP32 temporally blocked
                         kernel, 4 = 2D real pair kernel (PAIRED plans only), 5 = 3D kernel
-                        streaming along z (k = 1 only)                                       */
+                        streaming along z (k = 1 only), 6 = 1D whole-job cluster kernel
+                        (N <= 16384, s <= 1024, FIELD / CONST; the 1D default there)         */
   long long wait_limit; /* batched launch: polls a device wait makes before it gives up and
                         latches FRKC2_ETIMEOUT (0 = library default, 2^22 polls)           */
   int fault_inject;  /* batched launch, testing only: 1 = the first dependent work item waits

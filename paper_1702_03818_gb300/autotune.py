@@ -17,7 +17,7 @@ import torch
 
 from . import frkc2 as F
 
-PREC_NAMES = {F.FP64: "fp64", F.FP32: "fp32", F.MIXED: "mixed"}
+PREC_NAMES = {F.FP64: "fp64", F.FP32: "fp32", F.MIXED: "mixed", F.DFLOAT: "dfloat"}
 
 
 def _cache_path() -> str:
@@ -53,6 +53,8 @@ def _key(prob, s: int) -> str:
 def candidates(prob) -> list:
     """Candidate (kernel, k, tile) tunings for a problem."""
     c = []
+    if prob.precision == F.DFLOAT:
+        return [F.make_tuning(k=1, kernel=2)]  # the float-pair state has the streaming pass only
     if prob.ndim == 2 and prob.kappa_kind != F.KAPPA_POWER:
         c.append(F.make_tuning(k=1, kernel=2))
         if prob.precision == F.FP32:
@@ -63,6 +65,7 @@ def candidates(prob) -> list:
         for k in (1, 2, 4):
             c += [F.make_tuning(k=k, tile=t, kernel=1) for t in ((64, 16, 1), (32, 32, 1), (32, 16, 1))]
     elif prob.ndim == 3:
+        c.append(F.make_tuning(k=1, kernel=5))
         for k in (1, 2):
             c += [F.make_tuning(k=k, tile=t, kernel=1) for t in ((32, 4, 4), (32, 8, 2), (64, 4, 2), (16, 8, 4))]
     else:

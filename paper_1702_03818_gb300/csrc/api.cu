@@ -182,14 +182,20 @@ frkc2_status frkc2_step(frkc2_plan_t plan, const frkc2_problem* prob, double dt,
   if (p.ndim < 3) tz = 1;
   if (tx < 1 || ty < 1 || tz < 1) return FRKC2_EINVAL;
   const int kern = tune ? tune->kernel : 0;
-  if (kern < 0 || kern > 5) return FRKC2_EINVAL;
+  if (kern < 0 || kern > 6) return FRKC2_EINVAL;
   const bool stream_ok = p.ndim == 2 && p.kappa_kind != FRKC2_KAPPA_POWER && k == 1;
   const bool tb_ok = tb2d_supported(p, k);
   const bool paired_ok = plan->paired && p.ndim == 2 && p.kappa_kind != FRKC2_KAPPA_POWER;
-  bool use_stream2d = false, use_tb = false, use_paired = false, use_stream3d = false;
+  bool use_stream2d = false, use_tb = false, use_paired = false, use_stream3d = false, use_small1d = false;
   const bool dfloat = p.precision == FRKC2_DFLOAT;
   const bool stream3d_ok = p.ndim == 3 && k == 1;
-  if (kern == 5) {
+  const bool small1d_ok = small1d_supported(p, plan->s);
+  if (kern == 6) {
+    if (!small1d_ok) return FRKC2_EUNSUPPORTED;
+    use_small1d = true;
+  } else if (kern == 0 && small1d_ok && !(tune && tune->k)) {
+    use_small1d = true;
+  } else if (kern == 5) {
     if (!stream3d_ok) return FRKC2_EUNSUPPORTED;
     use_stream3d = true;
   } else if (dfloat) {
@@ -223,7 +229,8 @@ frkc2_status frkc2_step(frkc2_plan_t plan, const frkc2_problem* prob, double dt,
     probe.hx = k;
     probe.hy = p.ndim >= 2 ? k : 0;
     probe.hz = p.ndim >= 3 ? k : 0;
-    if (!use_stream2d && !use_tb && !use_paired && !use_stream3d && generic_smem_bytes(p, probe) > size_t(smem_optin()))
+    if (!use_stream2d && !use_tb && !use_paired && !use_stream3d && !use_small1d &&
+        generic_smem_bytes(p, probe) > size_t(smem_optin()))
       return FRKC2_EINVAL;
   }
   if (nsteps == 0) return FRKC2_OK;
@@ -257,6 +264,10 @@ frkc2_status frkc2_step(frkc2_plan_t plan, const frkc2_problem* prob, double dt,
   a.kp = p.kappa_p;
   a.status = reinterpret_cast<unsigned*>(base + L.status);
 
+  if (use_small1d) {  // the whole job in one cluster launch
+    return launch_small1d(p, *plan, dt, nsteps, u, base + L.fx, a.status, st) == cudaSuccess ? FRKC2_OK
+                                                                                              : FRKC2_ECUDA;
+  }
   const void* curU = u;
   const void* curV = nullptr;
   if (use_paired) {

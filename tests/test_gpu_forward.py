@@ -383,3 +383,64 @@ def test_stream3d_equals_tile_pass_and_rejects_k():
     with pytest.raises(F.Frkc2Error) as e:
         F.frkc2_step(plan, pr, dt, 1, 0.0, dev(u0, torch.float64), ws, F.make_tuning(k=2, kernel=5))
     assert e.value.status == F.EUNSUPPORTED
+
+
+# ---------------------------------------------------------------------------------------
+# 1D whole-job cluster kernel (kernel 6, the 1D default for N <= 16384 and s <= 1024)
+# ---------------------------------------------------------------------------------------
+
+S1_CASES = [
+    # shape, bc, kappa, s, nsteps, kernel
+    ((256,), "dirichlet", "const", 16, 5, 0),
+    ((257,), "periodic", "field", 16, 3, 6),
+    ((1000,), "dirichlet", "field", 32, 2, 6),
+    ((31,), "periodic", "field", 8, 4, 6),
+    ((2,), "dirichlet", "const", 4, 2, 6),
+    ((16384,), "periodic", "field", 8, 1, 6),
+    ((5003,), "dirichlet", "field", 64, 1, 0),
+]
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "mixed"])
+@pytest.mark.parametrize("case", S1_CASES, ids=lambda c: f"{c[0][0]}-{c[1]}-{c[2]}-s{c[3]}-kern{c[5]}")
+def test_step_parity_small1d(case, prec):
+    shape, bc, kappa, s, nsteps, kernel = case
+    u0, field = seeded_case(shape, bc, kappa, 500 + s)
+    oplan = O.plan(s)
+    plan = F.frkc2_plan(s)
+    fo = rounded_field(field, prec)
+    opr = oracle_problem(1, bc, kappa, 1.0, fo)
+    dt = 0.9 * oplan["beta"] / O.rho_bound(opr, u0)
+    u0g = u0.astype(np.float32).astype(np.float64) if prec == "fp32" else u0
+    ref = O.frkc2_step(u0g, oplan["a"], dt, opr, nsteps)
+    F.frkc2_launch_count()
+    got, st = run_gpu(plan, shape, bc, kappa, prec, u0, field, dt, nsteps, tune=F.make_tuning(kernel=kernel))
+    assert F.frkc2_launch_count() == 2  # face set-up and the whole job
+    assert st == F.OK
+    err = rel_l2(got, ref)
+    assert err < TOL[prec], err
+
+
+@pytest.mark.parametrize("bc", ["dirichlet", "periodic"])
+def test_small1d_single_cell(bc):
+    """One cell: Dirichlet f = -2 kappa u (both faces to a zero ghost), periodic f = 0."""
+    u0 = np.array([0.7])
+    oplan = O.plan(8)
+    plan = F.frkc2_plan(8)
+    opr = oracle_problem(1, bc, "const", 1.0, None)
+    dt = 0.5 * oplan["beta"] / max(O.rho_bound(opr, u0), 1.0)
+    ref = O.frkc2_step(u0, oplan["a"], dt, opr, 3)
+    got, st = run_gpu(plan, (1,), bc, "const", "fp64", u0, None, dt, 3, tune=F.make_tuning(kernel=6))
+    assert st == F.OK
+    assert abs(got[0] - ref[0]) <= 1e-13 * max(abs(ref[0]), 1e-300) + 1e-300
+
+
+def test_small1d_rejects_out_of_range():
+    plan = F.frkc2_plan(8)
+    for shape, kappa in [((16385,), "const"), ((100,), "power")]:
+        pr = lib_problem(shape, "periodic", kappa, "fp64")
+        ws = torch.empty(F.frkc2_workspace_size(pr), dtype=torch.uint8, device="cuda")
+        with pytest.raises(F.Frkc2Error) as e:
+            F.frkc2_step(plan, pr, 1e-3, 1, 0.0, torch.zeros(shape, dtype=torch.float64, device="cuda"), ws,
+                         F.make_tuning(kernel=6))
+        assert e.value.status == F.EUNSUPPORTED
