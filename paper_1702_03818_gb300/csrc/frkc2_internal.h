@@ -86,7 +86,6 @@ cudaError_t launch_pass_stream2d(const frkc2_problem& p, const PassArgs& a, cons
 size_t face_pair_bytes(const frkc2_problem& p);
 cudaError_t launch_face_pairs(const frkc2_problem& p, const void* fx, const void* fy, void* out, cudaStream_t st);
 cudaError_t launch_pass_tb2d(const frkc2_problem& p, const PassArgs& a, cudaStream_t st);
-cudaError_t launch_pass_tb2d_reg(const frkc2_problem& p, const PassArgs& a, cudaStream_t st);
 bool small1d_supported(const frkc2_problem& p, int s);
 cudaError_t launch_small1d(const frkc2_problem& p, const frkc2_plan_s& plan, double dt, int nsteps, void* u,
                            const void* fx, unsigned* status, cudaStream_t st);
