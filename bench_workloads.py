@@ -14,7 +14,8 @@ Workloads (sizes and seeds from frkc2_inputs.CONFIGS):
                run (and the FP64 oracle on reduced grids) produces non-finite values.
   adjoint2d    2D var-kappa 1024^2, s = 100, 40 steps, checkpoint every 8: forward vs adjoint.
   batched2d    512 2D var-kappa problems (n ~ U{64..1024}, s ~ {16..256}, 10 steps), one
-               persistent launch replayed from a CUDA graph, FP32 and FP64.
+               persistent launch replayed from a CUDA graph, FP32 and FP64; k (and the FP64
+               tile) chosen by the autotuner on a 48-problem slice.
   ssweep       4096^2 var-kappa, s in {32, 128, 512, 1024}, 4 steps, FP32 vs FP64 error growth
                with s (internal amplification).
   bruss2d      the paper's Brusselator (Sec. 3.1): 200^2 periodic, s = 16, dt = 0.9 beta/rho, to
@@ -228,9 +229,15 @@ def batched2d(F):
             us.append(u0s[-1].clone())
             pl.append(plans[p["s"]])
         nst = [nsteps] * len(specs)
-        ws = torch.empty(F.frkc2_batch_workspace_size(pl, probs, nst), dtype=torch.uint8, device="cuda")
+        # stages per pass and tile from the autotuner, timed on a 48-problem slice of the batch
+        from paper_1702_03818_gb300.autotune import autotune_batch
+        m = 48
+        tune, tt = autotune_batch(pl[:m], probs[:m], dts[:m], nst[:m], us[:m], reps=1)
+        for u, u0 in zip(us, u0s):
+            u.copy_(u0)
+        ws = torch.empty(F.frkc2_batch_workspace_size(pl, probs, nst, tune), dtype=torch.uint8, device="cuda")
         F.frkc2_workspace_reset(ws)
-        F.frkc2_batch_prepare(pl, probs, dts, nst, us, ws)
+        F.frkc2_batch_prepare(pl, probs, dts, nst, us, ws, tune)
         g = torch.cuda.CUDAGraph()
         side = torch.cuda.Stream()
         side.wait_stream(torch.cuda.current_stream())
@@ -269,7 +276,8 @@ def batched2d(F):
             errs.append(_rel(us[i].double().cpu().numpy(), v.double().cpu().numpy()))
         res[prec] = {"value": cs / (np.median(ms) / 1e3), "ms_per_launch": float(np.median(ms)),
                      "cell_stages": cs, "max_rel_l2_vs_single_problem_path": max(errs),
-                     "workspace_gb": ws.numel() / 1e9}
+                     "workspace_gb": ws.numel() / 1e9,
+                     "tuning": {"k": tune.k, "tile": [tune.tile_x, tune.tile_y]}, "autotune_ms": tt}
         del ws, g
     return {"workload": "batched2d: 512 var-kappa 2D problems, n~U{64..1024}, s~{16..256}, 10 steps, one persistent launch (CUDA graph)",
             "metric": "cell-stage/s", "value": res["fp32"]["value"], "unit": UNIT, "precisions": res}

@@ -129,8 +129,10 @@ def autotune_batch(plans, probs, dt, nsteps, u, reps: int = 2):
     Returns (frkc2_tuning, {candidate description: milliseconds}).
     """
     prec = probs[0].precision
-    ks = (2, 4, 8) if prec == F.FP32 else (1, 2, 4)
-    tiles = ((64, 32, 1), (64, 16, 1), (32, 32, 1))
+    if prec == F.FP32:  # register-tiled 64 x 64 regions: the tile follows from k
+        ks, tiles = (4, 6, 8, 10), ((0, 0, 0),)
+    else:
+        ks, tiles = (1, 2, 4), ((64, 32, 1), (64, 16, 1), (32, 32, 1))
     scratch = [t.clone() for t in u]
     times = {}
     best, best_ms = None, float("inf")

@@ -15,11 +15,14 @@
 //
 // State buffers are rewritten by other CTAs within the launch, so state loads bypass L1
 // (ld.global.cg); a finished tile is published with a device-scope fence before its counter
-// increment.
+// increment.  FP32 items run the register-tiled 64 x 64 region of the single-problem FP32
+// pass (tb2d_region.cuh: tile 64 - 2k, k-cell recomputed halo); FP64 and MIXED items run a
+// k-stage shared-memory tile pass.
 #include <algorithm>
 #include <cmath>
 #include <mutex>
 #include <numeric>
+#include <type_traits>
 #include <unordered_map>
 #include <vector>
 
@@ -27,6 +30,7 @@
 
 #include "frkc2.h"
 #include "frkc2_internal.h"
+#include "tb2d_region.cuh"
 
 namespace frkc2 {
 
@@ -102,8 +106,14 @@ __device__ __forceinline__ void pass_buffers(const BProb& P, int r, const void*&
   }
 }
 
+// FP32 items hold a 4 x 4 block of cells per thread in registers: two CTAs per SM
 template <class S, class A>
-__global__ void __launch_bounds__(BT_THREADS) k_batched(const BHeader h) {
+constexpr int bt_min_blocks() {
+  return std::is_same<S, float>::value && std::is_same<A, float>::value ? 2 : 1;
+}
+
+template <class S, class A>
+__global__ void __launch_bounds__(BT_THREADS, bt_min_blocks<S, A>()) k_batched(const BHeader h) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ long long s_item;
   __shared__ int s_prob, s_tile, s_round, s_ok;
@@ -160,96 +170,118 @@ __global__ void __launch_bounds__(BT_THREADS) k_batched(const BHeader h) {
     void* Vout_v;
     int l0, kq;
     pass_buffers(P, s_round, Uin_v, Vin_v, Uout_v, Vout_v, l0, kq, h.k);
-    const S* Uin = static_cast<const S*>(Uin_v);
-    const S* Vin = static_cast<const S*>(Vin_v);
-    const A* FX = static_cast<const A*>(P.fx);
-    const A* FY = static_cast<const A*>(P.fy);
-    const int nx = P.nx, ny = P.ny;
     const int tyi = s_tile / P.tiles_x, txi = s_tile - tyi * P.tiles_x;
-    const int RX = h.tx + 2 * kq, RY = h.ty + 2 * kq, R = RX * RY;
-    S* ub0 = reinterpret_cast<S*>(smem);
-    S* vb0 = ub0 + R;
-    S* ub1 = vb0 + R;
-    S* vb1 = ub1 + R;
-    A* fxs = reinterpret_cast<A*>(vb1 + R);
-    A* fys = fxs + R;
-    const int x0 = txi * h.tx - kq, y0 = tyi * h.ty - kq;
-    for (int idx = tid; idx < R; idx += BT_THREADS) {
-      const int y = idx / RX, x = idx - y * RX;
-      const int gx = x0 + x, gy = y0 + y;
-      S uu = S(0), vv = S(0);
-      A a0 = A(0), a1 = A(0);
-      if (periodic) {
-        const int wx = wrap_b(gx, nx), wy = wrap_b(gy, ny);
-        const size_t g = size_t(wy) * nx + wx;
-        uu = load_cg(Uin + g);
-        if (Vin) vv = load_cg(Vin + g);
-        a0 = FX[size_t(wy) * (nx + 1) + wx];
-        a1 = FY[size_t(wy) * nx + wx];
-      } else {
-        const bool inx = gx >= 0 && gx < nx, iny = gy >= 0 && gy < ny;
-        if (inx && iny) {
-          const size_t g = size_t(gy) * nx + gx;
+    if constexpr (std::is_same<S, float>::value && std::is_same<A, float>::value) {
+      __shared__ RegionShared rsh;
+      const double* cf = P.coef + 2 * l0;
+      auto coef = [&](int j, float& ca, float& cb) {
+        ca = float(cf[2 * j]);
+        cb = float(cf[2 * j + 1]);
+      };
+      const int x0 = txi * h.tx - h.k, y0 = tyi * h.ty - h.k;
+      const float* Uin = static_cast<const float*>(Uin_v);
+      const float* Vin = static_cast<const float*>(Vin_v);
+      float* Uout = static_cast<float*>(Uout_v);
+      float* Vout = static_cast<float*>(Vout_v);
+      const bool bad =
+          periodic ? tb2d_region<true, true>(rsh, P.nx, P.ny, h.k, kq, x0, y0, Uin, Vin, Uout, Vout,
+                                             static_cast<const float*>(P.fx), static_cast<const float*>(P.fy), coef,
+                                             Vout == nullptr)
+                   : tb2d_region<false, true>(rsh, P.nx, P.ny, h.k, kq, x0, y0, Uin, Vin, Uout, Vout,
+                                              static_cast<const float*>(P.fx), static_cast<const float*>(P.fy), coef,
+                                              Vout == nullptr);
+      if (bad) atomicOr(h.status, ST_NONFINITE);
+    } else {
+      const S* Uin = static_cast<const S*>(Uin_v);
+      const S* Vin = static_cast<const S*>(Vin_v);
+      const A* FX = static_cast<const A*>(P.fx);
+      const A* FY = static_cast<const A*>(P.fy);
+      const int nx = P.nx, ny = P.ny;
+      const int RX = h.tx + 2 * kq, RY = h.ty + 2 * kq, R = RX * RY;
+      S* ub0 = reinterpret_cast<S*>(smem);
+      S* vb0 = ub0 + R;
+      S* ub1 = vb0 + R;
+      S* vb1 = ub1 + R;
+      A* fxs = reinterpret_cast<A*>(vb1 + R);
+      A* fys = fxs + R;
+      const int x0 = txi * h.tx - kq, y0 = tyi * h.ty - kq;
+      for (int idx = tid; idx < R; idx += BT_THREADS) {
+        const int y = idx / RX, x = idx - y * RX;
+        const int gx = x0 + x, gy = y0 + y;
+        S uu = S(0), vv = S(0);
+        A a0 = A(0), a1 = A(0);
+        if (periodic) {
+          const int wx = wrap_b(gx, nx), wy = wrap_b(gy, ny);
+          const size_t g = size_t(wy) * nx + wx;
           uu = load_cg(Uin + g);
           if (Vin) vv = load_cg(Vin + g);
-        }
-        if (iny && gx >= 0 && gx <= nx) a0 = FX[size_t(gy) * (nx + 1) + gx];
-        if (inx && gy >= 0 && gy <= ny) a1 = FY[size_t(gy) * nx + gx];
-      }
-      ub0[idx] = uu;
-      vb0[idx] = vv;
-      ub1[idx] = S(0);
-      vb1[idx] = S(0);
-      fxs[idx] = a0;
-      fys[idx] = a1;
-    }
-    __syncthreads();
-    for (int j = 1; j <= kq; ++j) {
-      const S* us = (j & 1) ? ub0 : ub1;
-      const S* vs = (j & 1) ? vb0 : vb1;
-      S* ud = (j & 1) ? ub1 : ub0;
-      S* vd = (j & 1) ? vb1 : vb0;
-      const S ca = S(P.coef[2 * (l0 + j - 1)]), cb = S(P.coef[2 * (l0 + j - 1) + 1]);
-      const int w = RX - 2 * j, hgt = RY - 2 * j;
-      for (int idx = tid; idx < w * hgt; idx += BT_THREADS) {
-        const int y = j + idx / w, x = j + idx % w;
-        const int i = y * RX + x;
-        if (!periodic) {
-          const int gx = x0 + x, gy = y0 + y;
-          if (gx < 0 || gx >= nx || gy < 0 || gy >= ny) {
-            ud[i] = S(0);
-            vd[i] = S(0);
-            continue;
+          a0 = FX[size_t(wy) * (nx + 1) + wx];
+          a1 = FY[size_t(wy) * nx + wx];
+        } else {
+          const bool inx = gx >= 0 && gx < nx, iny = gy >= 0 && gy < ny;
+          if (inx && iny) {
+            const size_t g = size_t(gy) * nx + gx;
+            uu = load_cg(Uin + g);
+            if (Vin) vv = load_cg(Vin + g);
           }
+          if (iny && gx >= 0 && gx <= nx) a0 = FX[size_t(gy) * (nx + 1) + gx];
+          if (inx && gy >= 0 && gy <= ny) a1 = FY[size_t(gy) * nx + gx];
         }
-        const S Uc = us[i], Vc = vs[i];
-        const A fe = fxs[i + 1], fw = fxs[i], fn = fys[i + RX], fs = fys[i];
-        const A fR = fe * A(us[i + 1] - Uc) + fw * A(us[i - 1] - Uc) + fn * A(us[i + RX] - Uc) +
-                     fs * A(us[i - RX] - Uc);
-        const A fI = fe * A(vs[i + 1] - Vc) + fw * A(vs[i - 1] - Vc) + fn * A(vs[i + RX] - Vc) +
-                     fs * A(vs[i - RX] - Vc);
-        ud[i] = Uc + ca * S(fR) - cb * S(fI);
-        vd[i] = Vc + ca * S(fI) + cb * S(fR);
+        ub0[idx] = uu;
+        vb0[idx] = vv;
+        ub1[idx] = S(0);
+        vb1[idx] = S(0);
+        fxs[idx] = a0;
+        fys[idx] = a1;
       }
       __syncthreads();
+      for (int j = 1; j <= kq; ++j) {
+        const S* us = (j & 1) ? ub0 : ub1;
+        const S* vs = (j & 1) ? vb0 : vb1;
+        S* ud = (j & 1) ? ub1 : ub0;
+        S* vd = (j & 1) ? vb1 : vb0;
+        const S ca = S(P.coef[2 * (l0 + j - 1)]), cb = S(P.coef[2 * (l0 + j - 1) + 1]);
+        const int w = RX - 2 * j, hgt = RY - 2 * j;
+        for (int idx = tid; idx < w * hgt; idx += BT_THREADS) {
+          const int y = j + idx / w, x = j + idx % w;
+          const int i = y * RX + x;
+          if (!periodic) {
+            const int gx = x0 + x, gy = y0 + y;
+            if (gx < 0 || gx >= nx || gy < 0 || gy >= ny) {
+              ud[i] = S(0);
+              vd[i] = S(0);
+              continue;
+            }
+          }
+          const S Uc = us[i], Vc = vs[i];
+          const A fe = fxs[i + 1], fw = fxs[i], fn = fys[i + RX], fs = fys[i];
+          const A fR = fe * A(us[i + 1] - Uc) + fw * A(us[i - 1] - Uc) + fn * A(us[i + RX] - Uc) +
+                       fs * A(us[i - RX] - Uc);
+          const A fI = fe * A(vs[i + 1] - Vc) + fw * A(vs[i - 1] - Vc) + fn * A(vs[i + RX] - Vc) +
+                       fs * A(vs[i - RX] - Vc);
+          ud[i] = Uc + ca * S(fR) - cb * S(fI);
+          vd[i] = Vc + ca * S(fI) + cb * S(fR);
+        }
+        __syncthreads();
+      }
+      const S* uf = (kq & 1) ? ub1 : ub0;
+      const S* vf = (kq & 1) ? vb1 : vb0;
+      S* Uout = static_cast<S*>(Uout_v);
+      S* Vout = static_cast<S*>(Vout_v);
+      const int ox = txi * h.tx, oy = tyi * h.ty;
+      const int ex = min(h.tx, nx - ox), ey = min(h.ty, ny - oy);
+      bool bad = false;
+      for (int idx = tid; idx < ex * ey; idx += BT_THREADS) {
+        const int y = idx / ex, x = idx - y * ex;
+        const int i = (y + kq) * RX + (x + kq);
+        const size_t g = size_t(oy + y) * nx + (ox + x);
+        const S uu = uf[i];
+        Uout[g] = uu;
+        if (Vout) Vout[g] = vf[i];
+        if (!Vout && !isfinite(double(uu))) bad = true;
+      }
+      if (bad) atomicOr(h.status, ST_NONFINITE);
     }
-    const S* uf = (kq & 1) ? ub1 : ub0;
-    const S* vf = (kq & 1) ? vb1 : vb0;
-    S* Uout = static_cast<S*>(Uout_v);
-    S* Vout = static_cast<S*>(Vout_v);
-    const int ox = txi * h.tx, oy = tyi * h.ty;
-    const int ex = min(h.tx, nx - ox), ey = min(h.ty, ny - oy);
-    bool bad = false;
-    for (int idx = tid; idx < ex * ey; idx += BT_THREADS) {
-      const int y = idx / ex, x = idx - y * ex;
-      const int i = (y + kq) * RX + (x + kq);
-      const size_t g = size_t(oy + y) * nx + (ox + x);
-      const S uu = uf[i];
-      Uout[g] = uu;
-      if (Vout) Vout[g] = vf[i];
-      if (!Vout && !isfinite(double(uu))) bad = true;
-    }
-    if (bad) atomicOr(h.status, ST_NONFINITE);
     __threadfence();
     __syncthreads();
     if (tid == 0) atomicAdd(&h.done[s_prob], 1u);
@@ -280,6 +312,13 @@ struct BatchPlanHost {
   long long total_items;
 };
 
+// dynamic shared memory of an item: none for the FP32 register-tiled regions, the k-halo tile
+// of state ping-pong buffers and face conductivities otherwise
+size_t batch_smem(int precision, int tx, int ty, int k) {
+  if (precision == FRKC2_FP32) return 0;
+  return size_t(tx + 2 * k) * (ty + 2 * k) * (4 * state_bytes(precision) + 2 * arith_bytes(precision));
+}
+
 frkc2_status batch_geometry(int nprob, const frkc2_plan_t* plans, const frkc2_problem* probs, const int* nsteps,
                             const frkc2_tuning* tune, int* k_out, int* tx_out, int* ty_out) {
   if (nprob < 1 || !plans || !probs || !nsteps) return FRKC2_EINVAL;
@@ -292,12 +331,15 @@ frkc2_status batch_geometry(int nprob, const frkc2_plan_t* plans, const frkc2_pr
     if (probs[i].precision == FRKC2_DFLOAT) return FRKC2_EUNSUPPORTED;
     if (probs[i].precision != p0.precision || probs[i].bc != p0.bc) return FRKC2_EINVAL;
   }
-  int k = (tune && tune->k) ? tune->k : (p0.precision == FRKC2_FP32 ? 4 : 2);
+  int k = (tune && tune->k) ? tune->k : (p0.precision == FRKC2_FP32 ? 6 : 2);
   int tx = (tune && tune->tile_x) ? tune->tile_x : 64;
-  int ty = (tune && tune->tile_y) ? tune->tile_y : (p0.precision == FRKC2_FP32 ? 32 : 16);
+  int ty = (tune && tune->tile_y) ? tune->tile_y : 16;
   if (k < 1 || k > KMAX || tx < 1 || ty < 1) return FRKC2_EINVAL;
-  const size_t smem = size_t(tx + 2 * k) * (ty + 2 * k) * (4 * state_bytes(p0.precision) + 2 * arith_bytes(p0.precision));
-  if (smem > 200 * 1024) return FRKC2_EINVAL;
+  if (p0.precision == FRKC2_FP32) {  // register-tiled regions: the tile is the region minus its halo
+    if (2 * k >= RT_R) return FRKC2_EINVAL;
+    tx = ty = RT_R - 2 * k;
+  }
+  if (batch_smem(p0.precision, tx, ty, k) > 200 * 1024) return FRKC2_EINVAL;
   *k_out = k;
   *tx_out = tx;
   *ty_out = ty;
@@ -488,7 +530,7 @@ frkc2_status frkc2_batch_prepare(int nprob, const frkc2_plan_t* plans, const frk
   if (cudaStreamSynchronize(st) != cudaSuccess) return FRKC2_ECUDA;
   LaunchCfg cfg{};
   cfg.precision = prec;
-  cfg.smem = size_t(tx + 2 * k) * (ty + 2 * k) * (4 * SB + 2 * AB);
+  cfg.smem = batch_smem(prec, tx, ty, k);
   cudaError_t e = prec == FRKC2_FP64 ? set_smem<double, double>(cfg.smem)
                                      : (prec == FRKC2_FP32 ? set_smem<float, float>(cfg.smem) : set_smem<double, float>(cfg.smem));
   if (e != cudaSuccess) return FRKC2_ECUDA;

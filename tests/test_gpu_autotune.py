@@ -57,4 +57,5 @@ def test_autotune_batch_runs():
         us.append(torch.as_tensor(u0, dtype=torch.float32, device="cuda"))
         dts.append(0.9 * O.beta(s) / O.rho_bound(oracle_problem(2, "periodic", "field", 1.0, field)))
     best, times = AT.autotune_batch(plans, probs, dts, [2] * 3, us)
-    assert best is not None and len(times) >= 6
+    # FP32 items run register-tiled 64 x 64 regions: one candidate per stages-per-pass k
+    assert best is not None and len(times) >= 4 and best.k in (4, 6, 8, 10)
