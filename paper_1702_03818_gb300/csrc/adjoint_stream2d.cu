@@ -176,19 +176,12 @@ __global__ void __launch_bounds__(AS_THREADS, FRKC2_ADJ_MIN_BLOCKS)
 
 template <class S, class A, bool PERIODIC>
 cudaError_t launch_t(const AdjStreamArgs& a, cudaStream_t st) {
-  static int blocks_per_sm = 0, sms = 0;
-  auto kern = k_adj_stream2d<S, A, PERIODIC>;
-  if (!blocks_per_sm) {
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, kern, AS_THREADS, 0);
-    if (e != cudaSuccess) return e;
-    if (blocks_per_sm < 1) blocks_per_sm = 1;
-  }
+  const auto kern = k_adj_stream2d<S, A, PERIODIC>;
+  static const Residency res = query_residency(kern, AS_THREADS, 0);
+  if (res.err != cudaSuccess) return res.err;
   const int ncolw = (a.nx + AS_COLS - 1) / AS_COLS;
   const long long total = (long long)ncolw * a.ny;
-  long long grid = (long long)sms * blocks_per_sm;
+  long long grid = (long long)res.sms * res.per_sm;
   const long long max_useful = (total + AS_WARPS - 1) / AS_WARPS;
   if (grid > max_useful) grid = max_useful;
   kern<<<unsigned(grid), AS_THREADS, 0, st>>>(a, total, grid * AS_WARPS);

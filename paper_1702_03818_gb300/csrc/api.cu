@@ -76,13 +76,13 @@ static int default_k(const frkc2_problem& p) {
 }
 
 static int smem_optin() {
-  static int v = 0;
-  if (!v) {
-    int dev = 0;
+  static const int v = [] {
+    int dev = 0, r = 0;
     if (cudaGetDevice(&dev) != cudaSuccess ||
-        cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
-      v = 227 * 1024;
-  }
+        cudaDeviceGetAttribute(&r, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
+      r = 227 * 1024;
+    return r;
+  }();
   return v;
 }
 

@@ -274,13 +274,16 @@ template <class S, bool PER>
 cudaError_t run(const frkc2_plan_s& plan, const frkc2_bruss_problem& p, double dt, int nsteps, void* v, void* w,
                 char* ws, int kern, long long wait_limit, int fault_inject, cudaStream_t st) {
   const BrLayout L = br_layout(p);
-  int dev = 0, sms = 0, coop_ok = 0, occ = 0;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&coop_ok, cudaDevAttrCooperativeLaunch, dev);
-  if (e == cudaSuccess)
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_bruss2d<S, PER, BR_MAXS>, BR_THREADS, 0);
-  if (e != cudaSuccess) return e;
+  // device properties, queried once per kernel on the first (eager) call
+  static const Residency res = query_residency(k_bruss2d<S, PER, BR_MAXS>, BR_THREADS, 0);
+  static const int coop_ok = [] {
+    int dev = 0, v = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&v, cudaDevAttrCooperativeLaunch, dev) != cudaSuccess)
+      return 0;
+    return v;
+  }();
+  if (res.err != cudaSuccess) return res.err;
+  const int sms = res.sms, occ = res.per_sm;
   const bool coop = kern != 2 && coop_ok && occ >= 1;
   const long long ncell = (long long)p.nx * p.ny;
   // a multiple of the SM count, about one 256-cell sweep per CTA, at most the resident CTAs

@@ -112,4 +112,23 @@ cudaError_t launch_adj_stream2d(const frkc2_problem& p, const AdjStreamArgs& a, 
 
 void count_launch(int n = 1);
 
+// SM count and resident CTAs per SM of a kernel (at least 1).  Launchers keep the result in a
+// function-local static, initialised once and thread-safely on the first call -- which must
+// not be inside a stream capture; the library assumes one GPU model per process.
+struct Residency {
+  cudaError_t err;
+  int sms;
+  int per_sm;
+};
+template <class K>
+Residency query_residency(K kern, int threads, size_t smem) {
+  Residency r{cudaSuccess, 0, 0};
+  int dev = 0;
+  r.err = cudaGetDevice(&dev);
+  if (r.err == cudaSuccess) r.err = cudaDeviceGetAttribute(&r.sms, cudaDevAttrMultiProcessorCount, dev);
+  if (r.err == cudaSuccess) r.err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&r.per_sm, kern, threads, smem);
+  if (r.per_sm < 1) r.per_sm = 1;
+  return r;
+}
+
 }  // namespace frkc2

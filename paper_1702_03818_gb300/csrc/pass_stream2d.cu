@@ -242,19 +242,12 @@ __global__ void k_face_pairs(const A* __restrict__ fx, const A* __restrict__ fy,
 
 template <class S, class A, bool PERIODIC>
 cudaError_t launch_t(const PassArgs& a, const void* fen, cudaStream_t st) {
-  static int blocks_per_sm = 0, sms = 0;
-  auto kern = k_stream2d<S, A, PERIODIC>;
-  if (!blocks_per_sm) {
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, kern, ST_THREADS, 0);
-    if (e != cudaSuccess) return e;
-    if (blocks_per_sm < 1) blocks_per_sm = 1;
-  }
+  const auto kern = k_stream2d<S, A, PERIODIC>;
+  static const Residency res = query_residency(kern, ST_THREADS, 0);
+  if (res.err != cudaSuccess) return res.err;
   const int ncolw = (a.nx + ST_COLS - 1) / ST_COLS;
   const long long total = (long long)ncolw * a.ny;  // (chunk, row) pairs
-  long long grid = (long long)sms * blocks_per_sm;
+  long long grid = (long long)res.sms * res.per_sm;
   const long long max_useful = (total + ST_WARPS - 1) / ST_WARPS;
   if (grid > max_useful) grid = max_useful;
   kern<<<unsigned(grid), ST_THREADS, 0, st>>>(a, fen, ncolw, total, grid * ST_WARPS);

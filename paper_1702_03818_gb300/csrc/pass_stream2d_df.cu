@@ -218,19 +218,12 @@ __global__ void __launch_bounds__(DF_THREADS, DF_MIN_BLOCKS)
 
 template <bool PERIODIC, bool IN_REAL, bool OUT_REAL>
 cudaError_t launch_t(const PassArgs& a, const void* fen, cudaStream_t st) {
-  static int blocks_per_sm = 0, sms = 0;
-  auto kern = k_stream2d_df<PERIODIC, IN_REAL, OUT_REAL>;
-  if (!blocks_per_sm) {
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, kern, DF_THREADS, 0);
-    if (e != cudaSuccess) return e;
-    if (blocks_per_sm < 1) blocks_per_sm = 1;
-  }
+  const auto kern = k_stream2d_df<PERIODIC, IN_REAL, OUT_REAL>;
+  static const Residency res = query_residency(kern, DF_THREADS, 0);
+  if (res.err != cudaSuccess) return res.err;
   const int ncolw = (a.nx + DF_COLS - 1) / DF_COLS;
   const long long total = (long long)ncolw * a.ny;
-  long long grid = (long long)sms * blocks_per_sm;
+  long long grid = (long long)res.sms * res.per_sm;
   const long long max_useful = (total + DF_WARPS - 1) / DF_WARPS;
   if (grid > max_useful) grid = max_useful;
   kern<<<unsigned(grid), DF_THREADS, 0, st>>>(a, static_cast<const float2*>(fen), total, grid * DF_WARPS);
