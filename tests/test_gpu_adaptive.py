@@ -55,3 +55,45 @@ def test_adaptive_rejects_an_oversized_first_step_and_recovers():
     st = F.frkc2_step_adaptive(plan, pr, 5.0, 1e-8, 5.0, 0.0, u, ws)
     assert st["rejected"] >= 1 and abs(st["t"] - 5.0) < 1e-12
     assert np.all(np.isfinite(u.cpu().numpy()))
+
+
+@pytest.mark.parametrize("ratio", [100.0, 1000.0])
+def test_cmp_two_material(ratio):
+    """Sec. 2.3 on the GPU: uniform 8-stage steps leave spurious extrema in the two-material
+    solution, error-controlled steps do not; both agree with the oracle."""
+    n = 200
+    dx = 1.0 / n
+    x = (np.arange(n) + 0.5) * dx
+    kap = np.where(x < 0.5, 1.0, 1.0 / ratio)
+    u0 = np.where(x < 0.5, 1.0, 0.0)
+    opr = oracle_problem(1, "periodic", "field", dx, kap)
+    oplan = O.plan(8)
+    rho = O.rho_bound(opr)
+    t_end = 0.01
+    nst = int(np.ceil(t_end / (oplan["beta"] / rho)))
+
+    def sign_changes(u, tiny=1e-12):
+        d = np.diff(np.concatenate([u, u[:1]]))
+        d = d[np.abs(d) > tiny]
+        sg = np.sign(d)
+        return int(np.sum(sg != np.roll(sg, 1)))
+
+    plan = F.frkc2_plan(8)
+    kt = torch.as_tensor(kap, device="cuda")
+    pr = F.make_problem(1, (n,), dx, "periodic", "field", "fp64", kappa_field=kt)
+    # uniform stages
+    ws = torch.empty(F.frkc2_workspace_size(pr), dtype=torch.uint8, device="cuda")
+    u = torch.as_tensor(u0, device="cuda")
+    F.frkc2_step(plan, pr, t_end / nst, nst, 0.0, u, ws)
+    fixed = u.cpu().numpy()
+    assert rel_l2(fixed, O.frkc2_step(u0, oplan["a"], t_end / nst, opr, nst)) < 1e-11
+    assert sign_changes(fixed) > 10
+    # error control
+    ref, st_ref = O.frkc2_adaptive(u0, oplan["a"], oplan["beta"], opr, t_end, 1e-3, 1e-6, rho=rho)
+    wsa = torch.empty(F.frkc2_adaptive_workspace_size(pr), dtype=torch.uint8, device="cuda")
+    u = torch.as_tensor(u0, device="cuda")
+    st = F.frkc2_step_adaptive(plan, pr, t_end, 1e-3, 1e-6, rho, u, wsa)
+    ctrl = u.cpu().numpy()
+    assert (st["accepted"], st["rejected"]) == (st_ref["accepted"], st_ref["rejected"])
+    assert rel_l2(ctrl, ref) < 1e-10
+    assert sign_changes(ctrl) == 2 and ctrl.max() <= 1.0 and ctrl.min() >= 0.0

@@ -632,3 +632,45 @@ def test_adaptive_reaches_end_and_tolerance_controls_error():
         steps.append(st["accepted"])
         assert max(st["dts"]) <= O.beta(L) / rho * (1 + 1e-12)
     assert errs[1] < errs[0] and steps[1] > steps[0]
+
+
+# ---------------------------------------------------------------------------------------
+# Convex monotone property (Sec. 2.3, Fig. 4): two materials in contact
+# ---------------------------------------------------------------------------------------
+
+def _two_material(ratio, n=200):
+    """1D periodic bar: kappa = 1 and hot (u = 1) on the left half, kappa = 1/ratio and cold
+    (u = 0) on the right half (the paper's problem, parameters not stated: this reading)."""
+    dx = 1.0 / n
+    x = (np.arange(n) + 0.5) * dx
+    kap = np.where(x < 0.5, 1.0, 1.0 / ratio)
+    u0 = np.where(x < 0.5, 1.0, 0.0)
+    return u0, _prob(1, "periodic", "field", dx, field=kap)
+
+
+def _sign_changes(u, tiny=1e-12):
+    """Sign changes of the periodic differences above ``tiny``: 2 for one maximum region and
+    one minimum region, more when spurious extrema ("noise") appear."""
+    d = np.diff(np.concatenate([u, u[:1]]))
+    d = d[np.abs(d) > tiny]
+    sg = np.sign(d)
+    return int(np.sum(sg != np.roll(sg, 1)))
+
+
+@pytest.mark.parametrize("ratio", [100.0, 1000.0])
+def test_cmp_uniform_stages_noisy_error_control_clean(ratio):
+    """Sec. 2.3: with a uniform 8 stages per step the two-material solution shows noise (here
+    spurious extrema); with the error control of Sec. 3 and about the same number of
+    f-evaluations it does not, and it keeps the maximum principle."""
+    u0, pr = _two_material(ratio)
+    pl = O.plan(8)
+    rho = O.rho_bound(pr)
+    t_end = 0.01
+    n = int(np.ceil(t_end / (pl["beta"] / rho)))
+    fixed = O.frkc2_step(u0, pl["a"], t_end / n, pr, n)
+    ctrl, st = O.frkc2_adaptive(u0, pl["a"], pl["beta"], pr, t_end, 1e-3, dt0=1e-6, rho=rho)
+    assert _sign_changes(fixed) > 10
+    assert _sign_changes(ctrl) == 2
+    assert ctrl.max() <= 1.0 and ctrl.min() >= 0.0
+    evals_fixed, evals_ctrl = n * 8, (st["accepted"] + st["rejected"]) * 8
+    assert evals_ctrl < 1.5 * evals_fixed
