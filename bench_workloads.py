@@ -417,18 +417,20 @@ def profile_case(F, name: str):
         for _ in range(2):
             u = torch.as_tensor(u0, dtype=torch.float32, device="cuda")
             F.frkc2_step(plan, pr, dt, 1, 0.0, u, ws)
-    elif name == "adj_stream2d":  # FP64 streaming adjoint, 2048^2, s = 8, 2 steps
+    elif name in ("adj_stream2d", "adj_stream2d_fp32"):  # streaming adjoint, 2048^2, s = 8, 2 steps
         n, s, nsteps = 2048, 8, 2
+        prec = "fp32" if name.endswith("fp32") else "fp64"
+        sd = torch.float32 if prec == "fp32" else torch.float64
         u0 = I.smooth_unit((n, n), 64.0, 3819)
         k = I.kappa_field((n, n), 3818)
         plan = F.frkc2_plan(s)
-        kt = torch.as_tensor(k, device="cuda")
-        pr = F.make_problem(2, (n, n), 1.0, "periodic", "field", "fp64", kappa_field=kt)
+        kt = torch.as_tensor(k, dtype=sd, device="cuda")
+        pr = F.make_problem(2, (n, n), 1.0, "periodic", "field", prec, kappa_field=kt)
         rho = torch.zeros(1, dtype=torch.float64, device="cuda")
         F.frkc2_rho_bound(pr, None, rho)
         dt = 0.9 * plan.info()["beta"] / rho.item()
         ws = torch.empty(F.frkc2_adjoint_workspace_size(plan, pr, nsteps, 1), dtype=torch.uint8, device="cuda")
-        u = torch.as_tensor(u0, device="cuda")
+        u = torch.as_tensor(u0, dtype=sd, device="cuda")
         g = torch.ones_like(u)
         du, dk = torch.empty_like(u), torch.empty_like(kt)
         for _ in range(2):

@@ -32,13 +32,20 @@ constexpr int AS_COLS = 30;  // output columns per warp: lanes 1..30 (lanes 0 an
 #define FRKC2_ADJ_UNROLL 2
 #endif
 constexpr int AS_UNROLL = FRKC2_ADJ_UNROLL;
+#ifndef FRKC2_ADJ_MIN_BLOCKS_F32
+#define FRKC2_ADJ_MIN_BLOCKS_F32 4
+#endif
+template <class S>
+constexpr int adj_min_blocks() {
+  return sizeof(S) == 4 ? FRKC2_ADJ_MIN_BLOCKS_F32 : FRKC2_ADJ_MIN_BLOCKS;
+}
 
 template <class T> struct V2t;
 template <> struct V2t<double> { using type = double2; };
 template <> struct V2t<float> { using type = float2; };
 
 template <class S, class A, bool PERIODIC>
-__global__ void __launch_bounds__(AS_THREADS, FRKC2_ADJ_MIN_BLOCKS)
+__global__ void __launch_bounds__(AS_THREADS, adj_min_blocks<S>())
     k_adj_stream2d(const AdjStreamArgs p, long long total, long long nwarps_grid) {
   using S2 = typename V2t<S>::type;
   using A2 = typename V2t<A>::type;
@@ -79,7 +86,14 @@ __global__ void __launch_bounds__(AS_THREADS, FRKC2_ADJ_MIN_BLOCKS)
     const bool bW = !PERIODIC && x == 0;
     const bool bE = !PERIODIC && x == nx - 1;
 
-    auto wrapy = [&](int yy) { return PERIODIC ? (yy < 0 ? yy + ny : (yy >= ny ? yy - ny : yy)) : yy; };
+    // rows run from y0 - 1 to y1: more than one period past the grid when ny is 1
+    auto wrapy = [&](int yy) {
+      if (PERIODIC) {
+        if (yy < 0) yy += ny;
+        while (yy >= ny) yy -= ny;
+      }
+      return yy;
+    };
     auto ld = [&](const S2* __restrict__ P2, const S* __restrict__ P1, int cplx, int yy) -> S2 {
       S2 w;
       w.x = S(0);
@@ -101,7 +115,7 @@ __global__ void __launch_bounds__(AS_THREADS, FRKC2_ADJ_MIN_BLOCKS)
       f.x = A(0);
       f.y = A(0);
       yy = wrapy(yy);
-      if (!has_faces) return f;
+      if (!has_faces || (!PERIODIC && yy >= ny)) return f;  // face pairs: rows -1 .. ny-1
       return __ldg(FEN + size_t(yy + 1) * (nx + 1) + fcol);
     };
     // Y = -(c/2) W: a face's sensitivity is then Re(conj(lam_m - lam_i)(Y_m - Y_i))
@@ -128,8 +142,9 @@ __global__ void __launch_bounds__(AS_THREADS, FRKC2_ADJ_MIN_BLOCKS)
 #pragma unroll AS_UNROLL
     for (int y = y0; y < y1; ++y) {
       const S2 Ln = ld(Lin, Lr, p.l_complex, y + 1);
-      const S2 Yn = yof(ld(Wc2, Wr, p.w_complex, y + 1));
+      const S2 Wn = ld(Wc2, Wr, p.w_complex, y + 1);
       const A2 f = faces(y);
+      const S2 Yn = yof(Wn);
       // east face (lane 31 is a halo: its east values are not used)
       const S Le_r = __shfl_down_sync(0xffffffffu, Lc.x, 1);
       const S Le_i = __shfl_down_sync(0xffffffffu, Lc.y, 1);
