@@ -238,7 +238,7 @@ def run_ours(args, rank, world, local_rank):
             kbytes = 8 if prec == "fp64" else 4
             # default passes: k stages each; bytes per cell and pass as for FP64 with the
             # state / kappa sizes of this precision
-            k = 8 if prec == "fp32" else 1
+            k = 8 if prec in ("fp32", "dfloat") else 1
             npv = (s + k - 1) // k
             pass_bytes = cells * (npv * (4 * sbytes + kbytes) - 2 * sbytes)
             g = pass_bytes * nsteps / (smsec / 1e3) / 1e9

@@ -466,8 +466,9 @@ def profile_case(F, name: str):
         for _ in range(2):
             v = u.clone()
             F.frkc2_step(plan, pr, dt, 1, 0.0, v, ws, t)
-    elif name == "stream2d_df":  # DFLOAT streaming pass, 2048^2 var-kappa, s = 16, 1 step
+    elif name in ("stream2d_df", "tb2d_df"):  # DFLOAT pass, 2048^2 var-kappa, s = 16, 1 step
         n, s = 2048, 16
+        t = F.make_tuning(k=1, kernel=2) if name == "stream2d_df" else F.make_tuning(k=8, kernel=3)
         u0 = I.smooth_unit((n, n), 64.0, 3819)
         k = I.kappa_field((n, n), 3818)
         plan = F.frkc2_plan(s)
@@ -479,7 +480,7 @@ def profile_case(F, name: str):
         ws = torch.empty(F.frkc2_workspace_size(pr), dtype=torch.uint8, device="cuda")
         for _ in range(2):
             u = torch.as_tensor(u0, device="cuda")
-            F.frkc2_step(plan, pr, dt, 1, 0.0, u, ws)
+            F.frkc2_step(plan, pr, dt, 1, 0.0, u, ws, t)
     elif name == "bruss":  # FP64 Brusselator persistent launch, 2048^2, s = 16, 1 step
         n, s = 2048, 16
         v0, w0 = I.bruss_u0(n, n, 1.0 / n)

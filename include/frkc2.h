@@ -59,7 +59,8 @@ enum { FRKC2_KAPPA_CONST = 0, FRKC2_KAPPA_FIELD = 1, FRKC2_KAPPA_POWER = 2 };
  * DFLOAT: double state at the interface; between stages the state is a pair of floats
  * (hi + lo, about 48 significant bits) updated by error-free float sums, neighbour
  * differences are rounded to float and the flux arithmetic runs in float -- every operation
- * on the FP32 pipe.  2D FIELD / CONST problems and frkc2_step only (kernel 0 or 2, k = 1);
+ * on the FP32 pipe.  2D FIELD / CONST problems and frkc2_step only: k = 1 streams (kernel 2),
+ * k > 1 runs register-tiled 64 x 64 regions of k stages (kernel 3; the default, k = 8);
  * elsewhere FRKC2_EUNSUPPORTED.  The conductivity field is float.                          */
 enum { FRKC2_FP64 = 0, FRKC2_FP32 = 1, FRKC2_MIXED = 2, FRKC2_DFLOAT = 3 };
 

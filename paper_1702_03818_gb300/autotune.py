@@ -53,8 +53,8 @@ def _key(prob, s: int) -> str:
 def candidates(prob) -> list:
     """Candidate (kernel, k, tile) tunings for a problem."""
     c = []
-    if prob.precision == F.DFLOAT:
-        return [F.make_tuning(k=1, kernel=2)]  # the float-pair state has the streaming pass only
+    if prob.precision == F.DFLOAT:  # the float-pair state: streaming pass or register-tiled regions
+        return [F.make_tuning(k=1, kernel=2)] + [F.make_tuning(k=k, kernel=3) for k in (2, 4, 6, 8, 10)]
     if prob.ndim == 2 and prob.kappa_kind != F.KAPPA_POWER:
         c.append(F.make_tuning(k=1, kernel=2))
         if prob.precision == F.FP32:

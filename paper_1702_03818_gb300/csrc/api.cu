@@ -71,7 +71,10 @@ void default_tiles(const frkc2_problem& p, int k, int* tx, int* ty, int* tz) {
 
 static int default_k(const frkc2_problem& p) {
   if (p.ndim == 1) return 16;
-  if (p.ndim == 2) return (p.precision == FRKC2_FP32 && p.kappa_kind != FRKC2_KAPPA_POWER) ? 8 : 1;
+  if (p.ndim == 2 && p.kappa_kind != FRKC2_KAPPA_POWER) {
+    if (p.precision == FRKC2_FP32) return 8;
+    if (p.precision == FRKC2_DFLOAT) return 8;
+  }
   return 1;
 }
 
@@ -171,6 +174,7 @@ frkc2_status frkc2_step(frkc2_plan_t plan, const frkc2_problem* prob, double dt,
   const frkc2_problem& p = *prob;
 
   int k = (tune && tune->k) ? tune->k : default_k(p);
+  if (tune && !tune->k && (tune->kernel == 2 || tune->kernel == 5)) k = 1;  // single-stage passes
   if (k < 1 || k > KMAX) return FRKC2_EINVAL;
   k = std::min(k, plan->s);
   int tx, ty, tz;
@@ -187,6 +191,7 @@ frkc2_status frkc2_step(frkc2_plan_t plan, const frkc2_problem* prob, double dt,
   const bool tb_ok = tb2d_supported(p, k);
   const bool paired_ok = plan->paired && p.ndim == 2 && p.kappa_kind != FRKC2_KAPPA_POWER;
   bool use_stream2d = false, use_tb = false, use_paired = false, use_stream3d = false, use_small1d = false;
+  bool use_tb_df = false;
   const bool dfloat = p.precision == FRKC2_DFLOAT;
   const bool stream3d_ok = p.ndim == 3 && k == 1;
   const bool small1d_ok = small1d_supported(p, plan->s);
@@ -199,8 +204,12 @@ frkc2_status frkc2_step(frkc2_plan_t plan, const frkc2_problem* prob, double dt,
     if (!stream3d_ok) return FRKC2_EUNSUPPORTED;
     use_stream3d = true;
   } else if (dfloat) {
-    if ((kern != 0 && kern != 2) || k != 1) return FRKC2_EUNSUPPORTED;
-    use_stream2d = true;
+    // k = 1: the streaming pass; k > 1: the register-tiled pass (float-pair regions)
+    if (kern == 1 || kern > 3 || (kern == 2 && k != 1) || 2 * k >= 64) return FRKC2_EUNSUPPORTED;
+    if (kern == 3 || (kern == 0 && k > 1))
+      use_tb_df = true;
+    else
+      use_stream2d = true;
   } else if (kern == 4) {
     if (!paired_ok) return FRKC2_EUNSUPPORTED;
     use_paired = true;
@@ -229,7 +238,7 @@ frkc2_status frkc2_step(frkc2_plan_t plan, const frkc2_problem* prob, double dt,
     probe.hx = k;
     probe.hy = p.ndim >= 2 ? k : 0;
     probe.hz = p.ndim >= 3 ? k : 0;
-    if (!use_stream2d && !use_tb && !use_paired && !use_stream3d && !use_small1d &&
+    if (!use_stream2d && !use_tb && !use_paired && !use_stream3d && !use_small1d && !use_tb_df &&
         generic_smem_bytes(p, probe) > size_t(smem_optin()))
       return FRKC2_EINVAL;
   }
@@ -293,6 +302,33 @@ frkc2_status frkc2_step(frkc2_plan_t plan, const frkc2_problem* prob, double dt,
     if (curU != u &&
         cudaMemcpyAsync(u, curU, cells(p) * state_bytes(p.precision), cudaMemcpyDeviceToDevice, st) != cudaSuccess)
       return FRKC2_ECUDA;
+    return FRKC2_OK;
+  }
+  if (use_tb_df) {
+    // float-pair state (float4 per cell) between passes, in the ua (with va) and ub (with vb) slots
+    for (int n = 0; n < nsteps; ++n) {
+      for (int q = 0; q < npass; ++q) {
+        const int l0 = q * k, kq = std::min(k, s - l0);
+        const bool first = q == 0, last = q == npass - 1;
+        void* outW = (curU == ua) ? ub : ua;
+        a.k = kq;
+        a.U_in = first ? u : curU;
+        a.V_in = nullptr;
+        a.in_mode = first ? PASS_IO_REAL : PASS_IO_COMPLEX;
+        a.U_out = last ? u : outW;
+        a.V_out = nullptr;
+        a.out_mode = last ? PASS_IO_REAL : PASS_IO_COMPLEX;
+        a.check_finite = last ? 1 : 0;
+        for (int j = 0; j < kq; ++j) {
+          a.ca[j] = dt * plan->a_re[l0 + j] / h2;
+          a.cb[j] = dt * plan->a_im[l0 + j] / h2;
+          a.caf[j] = float(a.ca[j]);
+          a.cbf[j] = float(a.cb[j]);
+        }
+        if (launch_pass_tb2d_df(p, a, st) != cudaSuccess) return FRKC2_ECUDA;
+        curU = last ? u : outW;
+      }
+    }
     return FRKC2_OK;
   }
   if (use_stream2d) {

@@ -1,30 +1,192 @@
-// 2D temporally blocked pass for FP32 (fixed conductivity): k stages of Sec. 3, Eq. 13 per
-// HBM round trip, one 64 x 64 register-tiled region per CTA (tb2d_region.cuh).
+// 2D temporally blocked pass for FP32 (fixed conductivity) with the state in registers:
+// k stages of Sec. 3, Eq. 13 per HBM round trip.
+//
+// A CTA of 16 x 16 threads owns a 64 x 64 region: its output tile (64 - 2k)^2 plus a k-cell
+// halo recomputed redundantly (region-edge values go stale one cell per stage, which never
+// reaches the output tile).  Thread (tx, ty) owns the 4 x 4 cells at columns 4tx..4tx+3,
+// rows 4ty..4ty+3 and keeps, for all k stages, their complex state (32 floats) and their 40
+// face conductivities in registers.  Per stage:
+//   - the thread's bottom and top rows go to shared memory (double-buffered by stage parity,
+//     one barrier per stage); its south and north neighbour rows come back from the threads
+//     below and above;
+//   - the columns beyond its own come from the adjacent threads by 16-lane shuffles, one row
+//     at a time, before that row is updated;
+//   - every neighbour difference inside the block is formed once and used by both cells of
+//     the face: f = k_n d_n - k_s d_s + k_e d_e - k_w d_w (one product, three multiply-adds
+//     per component), then the complex update -- about 16.5 FP32 instructions per cell-stage.
+// Shared memory traffic: 8 bytes per cell-stage (the two exchanged rows), against the full
+// state of a shared-memory ping-pong.
+// The batched launch runs the same region computation from tb2d_region.cuh; this kernel keeps
+// its own copy because, written as that shared device function, it compiled to an 11 % slower
+// pass (4.15e11 against 4.61e11 cell-stage/s at 2048^2, k = 8) with the same registers.
 #include <cuda_runtime.h>
 
 #include "frkc2_internal.h"
-#include "tb2d_region.cuh"
 
 namespace frkc2 {
 namespace {
 
+constexpr int RT_R = 64;          // region edge (cells)
+constexpr int RT_THREADS = 256;   // 16 x 16 threads of 4 x 4 cells
 #ifndef FRKC2_TBR_MIN_BLOCKS
 #define FRKC2_TBR_MIN_BLOCKS 2
 #endif
 
+__device__ __forceinline__ int wrap_r(int g, int n) {
+  if (g >= 0 && g < n) return g;
+  if (g < 0 && g >= -n) return g + n;
+  if (g >= n && g < 2 * n) return g - n;
+  const int r = g % n;
+  return r < 0 ? r + n : r;
+}
+
 template <bool PERIODIC>
 __global__ void __launch_bounds__(RT_THREADS, FRKC2_TBR_MIN_BLOCKS) k_tb2d_reg(const PassArgs p) {
-  __shared__ RegionShared sh;
-  const int T = RT_R - 2 * p.k;
-  const int x0 = blockIdx.x * T - p.k, y0 = blockIdx.y * T - p.k;
-  auto coef = [&](int j, float& ca, float& cb) {
-    ca = p.caf[j];
-    cb = p.cbf[j];
-  };
-  const bool bad = tb2d_region<PERIODIC, false>(
-      sh, p.nx, p.ny, p.k, p.k, x0, y0, static_cast<const float*>(p.U_in), static_cast<const float*>(p.V_in),
-      static_cast<float*>(p.U_out), static_cast<float*>(p.V_out), static_cast<const float*>(p.fx),
-      static_cast<const float*>(p.fy), coef, p.check_finite != 0);
+  __shared__ float4 sh_bot[2][2][16][16];  // [stage parity][U, V][ty][tx]: the thread's row 0
+  __shared__ float4 sh_top[2][2][16][16];  // its row 3
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  const int k = p.k;
+  const int T = RT_R - 2 * k;
+  const int x0 = blockIdx.x * T - k, y0 = blockIdx.y * T - k;
+  const int nx = p.nx, ny = p.ny;
+  const float* __restrict__ Uin = static_cast<const float*>(p.U_in);
+  const float* __restrict__ Vin = static_cast<const float*>(p.V_in);
+  const float* __restrict__ FX = static_cast<const float*>(p.fx);
+  const float* __restrict__ FY = static_cast<const float*>(p.fy);
+
+  // wrapped (periodic) or raw (Dirichlet) grid rows / columns of the thread's cells; the fifth
+  // entry is the next row / column (north and east faces)
+  int gyr[5], gxc[5];
+  bool yin[5], xin[5];
+#pragma unroll
+  for (int i = 0; i < 5; ++i) {
+    const int gx = x0 + 4 * tx + i, gy = y0 + 4 * ty + i;
+    gxc[i] = PERIODIC ? wrap_r(gx, nx) : gx;
+    gyr[i] = PERIODIC ? wrap_r(gy, ny) : gy;
+    xin[i] = gx >= 0 && gx < nx;
+    yin[i] = gy >= 0 && gy < ny;
+  }
+  // fx[r][c]: x face c of row r (the west face of cell c; c = 4 is the east face of cell 3);
+  // fy[r][c]: y face r of column c (the south face of row r; r = 4 is the north face of row 3)
+  float fx[4][5], fy[5][4];
+  unsigned inside = 0;  // Dirichlet: bit 4r + c set if cell (r, c) lies in the grid
+#pragma unroll
+  for (int r = 0; r < 5; ++r) {
+#pragma unroll
+    for (int c = 0; c < 5; ++c) {
+      if (r < 4) {
+        float v = 0.f;
+        if (PERIODIC || (yin[r] && gxc[c] >= 0 && gxc[c] <= nx)) v = FX[size_t(gyr[r]) * (nx + 1) + gxc[c]];
+        fx[r][c] = v;
+      }
+      if (c < 4) {
+        float v = 0.f;
+        if (PERIODIC || (xin[c] && gyr[r] >= 0 && gyr[r] <= ny)) v = FY[size_t(gyr[r]) * nx + gxc[c]];
+        fy[r][c] = v;
+        if (r < 4 && xin[c] && yin[r]) inside |= 1u << (4 * r + c);
+      }
+    }
+  }
+  float U[4][4], V[4][4];
+#pragma unroll
+  for (int r = 0; r < 4; ++r)
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      float uu = 0.f, vv = 0.f;
+      if (PERIODIC || (inside & (1u << (4 * r + c)))) {
+        const size_t g = size_t(gyr[r]) * nx + gxc[c];
+        uu = Uin[g];
+        if (Vin) vv = Vin[g];
+      }
+      U[r][c] = uu;
+      V[r][c] = vv;
+    }
+
+  const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+  for (int j = 0; j < k; ++j) {
+    const int b = j & 1;
+    sh_bot[b][0][ty][tx] = make_float4(U[0][0], U[0][1], U[0][2], U[0][3]);
+    sh_bot[b][1][ty][tx] = make_float4(V[0][0], V[0][1], V[0][2], V[0][3]);
+    sh_top[b][0][ty][tx] = make_float4(U[3][0], U[3][1], U[3][2], U[3][3]);
+    sh_top[b][1][ty][tx] = make_float4(V[3][0], V[3][1], V[3][2], V[3][3]);
+    __syncthreads();
+    // the region's outermost thread rows have no neighbour row here: their edge goes stale
+    const float4 su4 = ty > 0 ? sh_top[b][0][ty - 1][tx] : z4, sv4 = ty > 0 ? sh_top[b][1][ty - 1][tx] : z4;
+    const float4 nu4 = ty < 15 ? sh_bot[b][0][ty + 1][tx] : z4, nv4 = ty < 15 ? sh_bot[b][1][ty + 1][tx] : z4;
+    const float ca = p.caf[j], cb = p.cbf[j];
+    const float su[4] = {su4.x, su4.y, su4.z, su4.w}, sv[4] = {sv4.x, sv4.y, sv4.z, sv4.w};
+    const float nu[4] = {nu4.x, nu4.y, nu4.z, nu4.w}, nv[4] = {nv4.x, nv4.y, nv4.z, nv4.w};
+    // differences across the south faces of the current row: W(r) - W(r - 1)
+    float dsU[4], dsV[4];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      dsU[c] = U[0][c] - su[c];
+      dsV[c] = V[0][c] - sv[c];
+    }
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      // columns beyond the thread's own, before this row is updated
+      const float wU = __shfl_up_sync(0xffffffffu, U[r][3], 1, 16);
+      const float wV = __shfl_up_sync(0xffffffffu, V[r][3], 1, 16);
+      const float eU = __shfl_down_sync(0xffffffffu, U[r][0], 1, 16);
+      const float eV = __shfl_down_sync(0xffffffffu, V[r][0], 1, 16);
+      // dx[c]: across x face c, W(c) - W(c - 1)
+      float dxU[5], dxV[5];
+      dxU[0] = U[r][0] - wU;
+      dxV[0] = V[r][0] - wV;
+#pragma unroll
+      for (int c = 1; c < 4; ++c) {
+        dxU[c] = U[r][c] - U[r][c - 1];
+        dxV[c] = V[r][c] - V[r][c - 1];
+      }
+      dxU[4] = eU - U[r][3];
+      dxV[4] = eV - V[r][3];
+      float dnU[4], dnV[4];
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        const float nU = r < 3 ? U[r + 1][c] : nu[c];
+        const float nV = r < 3 ? V[r + 1][c] : nv[c];
+        dnU[c] = nU - U[r][c];
+        dnV[c] = nV - V[r][c];
+      }
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        const float fU = fy[r + 1][c] * dnU[c] - fy[r][c] * dsU[c] + fx[r][c + 1] * dxU[c + 1] - fx[r][c] * dxU[c];
+        const float fV = fy[r + 1][c] * dnV[c] - fy[r][c] * dsV[c] + fx[r][c + 1] * dxV[c + 1] - fx[r][c] * dxV[c];
+        float un = U[r][c] + ca * fU - cb * fV;
+        float vn = V[r][c] + ca * fV + cb * fU;
+        if (!PERIODIC && !(inside & (1u << (4 * r + c)))) {
+          un = 0.f;
+          vn = 0.f;
+        }
+        U[r][c] = un;
+        V[r][c] = vn;
+        dsU[c] = dnU[c];
+        dsV[c] = dnV[c];
+      }
+    }
+  }
+
+  // store the output tile: region cells at distance >= k from the region edge
+  float* __restrict__ Uo = static_cast<float*>(p.U_out);
+  float* __restrict__ Vo = static_cast<float*>(p.V_out);
+  bool bad = false;
+#pragma unroll
+  for (int r = 0; r < 4; ++r) {
+    const int ry = 4 * ty + r;
+    const int gy = y0 + ry;
+    if (ry < k || ry >= RT_R - k || gy >= ny) continue;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      const int rx = 4 * tx + c;
+      const int gx = x0 + rx;
+      if (rx < k || rx >= RT_R - k || gx >= nx) continue;
+      const size_t g = size_t(gy) * nx + gx;
+      Uo[g] = U[r][c];
+      if (Vo) Vo[g] = V[r][c];
+      if (p.check_finite) bad |= (__float_as_uint(U[r][c]) & 0x7f800000u) == 0x7f800000u;
+    }
+  }
   if (bad) atomicOr(p.status, ST_NONFINITE);
 }
 

@@ -271,19 +271,23 @@ def test_paired_plan_on_3d_runs_as_complex_stages():
 # ---------------------------------------------------------------------------------------
 
 DF_CASES = [
-    # shape, bc, kappa, s, nsteps, kernel
-    ((100, 77), "periodic", "field", 16, 2, 0),
-    ((70, 130), "dirichlet", "field", 32, 2, 2),
-    ((64, 64), "periodic", "const", 64, 1, 0),
-    ((5, 7), "dirichlet", "field", 8, 3, 0),
-    ((1, 9), "periodic", "field", 4, 2, 0),
-    ((33, 1), "dirichlet", "field", 8, 2, 0),
+    # shape, bc, kappa, s, nsteps, kernel, k (0: default)
+    ((100, 77), "periodic", "field", 16, 2, 0, 0),
+    ((70, 130), "dirichlet", "field", 32, 2, 2, 0),
+    ((64, 64), "periodic", "const", 64, 1, 0, 0),
+    ((5, 7), "dirichlet", "field", 8, 3, 0, 0),
+    ((1, 9), "periodic", "field", 4, 2, 0, 0),
+    ((33, 1), "dirichlet", "field", 8, 2, 0, 0),
+    ((200, 130), "periodic", "field", 32, 2, 3, 8),
+    ((130, 300), "dirichlet", "field", 16, 1, 3, 5),
+    ((57, 200), "dirichlet", "const", 32, 2, 3, 16),
+    ((9, 13), "periodic", "field", 8, 3, 3, 1),
 ]
 
 
-@pytest.mark.parametrize("case", DF_CASES, ids=lambda c: f"{'x'.join(map(str, c[0]))}-{c[1]}-{c[2]}-s{c[3]}-kern{c[5]}")
+@pytest.mark.parametrize("case", DF_CASES, ids=lambda c: f"{'x'.join(map(str, c[0]))}-{c[1]}-{c[2]}-s{c[3]}-kern{c[5]}-k{c[6]}")
 def test_step_parity_dfloat(case):
-    shape, bc, kappa, s, nsteps, kernel = case
+    shape, bc, kappa, s, nsteps, kernel, kk = case
     u0, field = seeded_case(shape, bc, kappa, 300 + s)
     oplan = O.plan(s)
     plan = F.frkc2_plan(s)
@@ -291,7 +295,7 @@ def test_step_parity_dfloat(case):
     opr = oracle_problem(len(shape), bc, kappa, 1.0, fo)
     dt = 0.9 * oplan["beta"] / O.rho_bound(opr, u0)
     ref = O.frkc2_step(u0, oplan["a"], dt, opr, nsteps)
-    got, st = run_gpu(plan, shape, bc, kappa, "dfloat", u0, field, dt, nsteps, tune=F.make_tuning(kernel=kernel))
+    got, st = run_gpu(plan, shape, bc, kappa, "dfloat", u0, field, dt, nsteps, tune=F.make_tuning(k=kk, kernel=kernel))
     assert st == F.OK
     err = rel_l2(got, ref)
     assert err < TOL["dfloat"], err
@@ -329,8 +333,12 @@ def test_dfloat_launch_count():
     dt = 0.5 * plan.info()["beta"] / O.rho_bound(oracle_problem(2, "periodic", "field", 1.0, rounded_field(field, "fp32")))
     u = dev(u0, torch.float64)
     F.frkc2_launch_count()
-    F.frkc2_step(plan, pr, dt, 3, 0.0, u, ws)
+    F.frkc2_step(plan, pr, dt, 3, 0.0, u, ws, F.make_tuning(kernel=2))
     assert F.frkc2_launch_count() == 2 + 3 * 16  # faces, face pairs, one pass per stage
+    v = dev(u0, torch.float64)
+    F.frkc2_step(plan, pr, dt, 3, 0.0, v, ws)
+    assert F.frkc2_launch_count() == 1 + 3 * 2  # faces, then passes of 8 and 8 stages
+    assert rel_l2(v.cpu().numpy(), u.cpu().numpy()) < 1e-6
 
 
 # ---------------------------------------------------------------------------------------

@@ -239,10 +239,12 @@ def test_dfloat_precision_validation_on_host():
     with pytest.raises(F.Frkc2Error) as e:
         F.frkc2_workspace_size(p_bad)
     assert e.value.status == F.EINVAL
-    # only the k = 1 streaming pass: other kernels and k > 1 are refused before any GPU work
+    # the streaming pass (kernel 2, k = 1) and the register-tiled pass (kernel 3): other
+    # kernels, and k > 1 on the streaming pass, are refused before any GPU work
     need = F.frkc2_workspace_size(p2)
     u, ws = _FakeBuf(1 << 20, 64 * 48 * 8), _FakeBuf(1 << 30, need)
-    for t in (F.make_tuning(kernel=1), F.make_tuning(kernel=3), F.make_tuning(k=2)):
+    for t in (F.make_tuning(kernel=1), F.make_tuning(kernel=4), F.make_tuning(kernel=5),
+              F.make_tuning(k=2, kernel=2)):
         with pytest.raises(F.Frkc2Error) as e:
             F.frkc2_step(plan, p2, 0.01, 1, 0.0, u, ws, t, stream=0)
         assert e.value.status == F.EUNSUPPORTED
