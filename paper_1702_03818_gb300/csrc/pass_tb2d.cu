@@ -12,8 +12,12 @@
 //   - the columns beyond its own come from the adjacent threads by 16-lane shuffles, one row
 //     at a time, before that row is updated;
 //   - every neighbour difference inside the block is formed once and used by both cells of
-//     the face: f = k_n d_n - k_s d_s + k_e d_e - k_w d_w (one product, three multiply-adds
-//     per component), then the complex update -- about 16.5 FP32 instructions per cell-stage.
+//     the face: f = k_n d_n - k_s d_s + k_e d_e - k_w d_w, then the complex update;
+//   - the cells are held as horizontal pairs (float2), so the y differences, the y terms of f
+//     and the complex update run as packed two-lane FP32 instructions (add / fma .f32x2, new
+//     with the sm_100 family), two cells per instruction; the x differences and x terms, whose
+//     pairs would straddle the register pairs, stay scalar: 11.5 FP32 instructions per
+//     cell-stage for 16.5 floating-point operations.
 // Shared memory traffic: 8 bytes per cell-stage (the two exchanged rows), against the full
 // state of a shared-memory ping-pong.
 // The batched launch runs the same region computation from tb2d_region.cuh; this kernel keeps
@@ -39,6 +43,9 @@ __device__ __forceinline__ int wrap_r(int g, int n) {
   const int r = g % n;
   return r < 0 ? r + n : r;
 }
+
+// a - b on both halves in one packed instruction (sm_100 family)
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __fadd2_rn(a, make_float2(-b.x, -b.y)); }
 
 template <bool PERIODIC>
 __global__ void __launch_bounds__(RT_THREADS, FRKC2_TBR_MIN_BLOCKS) k_tb2d_reg(const PassArgs p) {
@@ -87,7 +94,12 @@ __global__ void __launch_bounds__(RT_THREADS, FRKC2_TBR_MIN_BLOCKS) k_tb2d_reg(c
       }
     }
   }
-  float U[4][4], V[4][4];
+  // the state as horizontal cell pairs: U2[r][h] = (U[r][2h], U[r][2h + 1]); the y faces too
+  float2 U2[4][2], V2[4][2], FY2[5][2];
+#pragma unroll
+  for (int r = 0; r < 5; ++r)
+#pragma unroll
+    for (int h = 0; h < 2; ++h) FY2[r][h] = make_float2(fy[r][2 * h], fy[r][2 * h + 1]);
 #pragma unroll
   for (int r = 0; r < 4; ++r)
 #pragma unroll
@@ -98,71 +110,85 @@ __global__ void __launch_bounds__(RT_THREADS, FRKC2_TBR_MIN_BLOCKS) k_tb2d_reg(c
         uu = Uin[g];
         if (Vin) vv = Vin[g];
       }
-      U[r][c] = uu;
-      V[r][c] = vv;
+      if (c & 1) {
+        U2[r][c >> 1].y = uu;
+        V2[r][c >> 1].y = vv;
+      } else {
+        U2[r][c >> 1].x = uu;
+        V2[r][c >> 1].x = vv;
+      }
     }
 
   const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
   for (int j = 0; j < k; ++j) {
     const int b = j & 1;
-    sh_bot[b][0][ty][tx] = make_float4(U[0][0], U[0][1], U[0][2], U[0][3]);
-    sh_bot[b][1][ty][tx] = make_float4(V[0][0], V[0][1], V[0][2], V[0][3]);
-    sh_top[b][0][ty][tx] = make_float4(U[3][0], U[3][1], U[3][2], U[3][3]);
-    sh_top[b][1][ty][tx] = make_float4(V[3][0], V[3][1], V[3][2], V[3][3]);
+    sh_bot[b][0][ty][tx] = make_float4(U2[0][0].x, U2[0][0].y, U2[0][1].x, U2[0][1].y);
+    sh_bot[b][1][ty][tx] = make_float4(V2[0][0].x, V2[0][0].y, V2[0][1].x, V2[0][1].y);
+    sh_top[b][0][ty][tx] = make_float4(U2[3][0].x, U2[3][0].y, U2[3][1].x, U2[3][1].y);
+    sh_top[b][1][ty][tx] = make_float4(V2[3][0].x, V2[3][0].y, V2[3][1].x, V2[3][1].y);
     __syncthreads();
     // the region's outermost thread rows have no neighbour row here: their edge goes stale
     const float4 su4 = ty > 0 ? sh_top[b][0][ty - 1][tx] : z4, sv4 = ty > 0 ? sh_top[b][1][ty - 1][tx] : z4;
     const float4 nu4 = ty < 15 ? sh_bot[b][0][ty + 1][tx] : z4, nv4 = ty < 15 ? sh_bot[b][1][ty + 1][tx] : z4;
     const float ca = p.caf[j], cb = p.cbf[j];
-    const float su[4] = {su4.x, su4.y, su4.z, su4.w}, sv[4] = {sv4.x, sv4.y, sv4.z, sv4.w};
-    const float nu[4] = {nu4.x, nu4.y, nu4.z, nu4.w}, nv[4] = {nv4.x, nv4.y, nv4.z, nv4.w};
+    const float2 ca2 = make_float2(ca, ca), cb2 = make_float2(cb, cb), ncb2 = make_float2(-cb, -cb);
+    const float2 su2[2] = {make_float2(su4.x, su4.y), make_float2(su4.z, su4.w)};
+    const float2 sv2[2] = {make_float2(sv4.x, sv4.y), make_float2(sv4.z, sv4.w)};
+    const float2 nu2[2] = {make_float2(nu4.x, nu4.y), make_float2(nu4.z, nu4.w)};
+    const float2 nv2[2] = {make_float2(nv4.x, nv4.y), make_float2(nv4.z, nv4.w)};
     // differences across the south faces of the current row: W(r) - W(r - 1)
-    float dsU[4], dsV[4];
+    float2 dsU[2], dsV[2];
 #pragma unroll
-    for (int c = 0; c < 4; ++c) {
-      dsU[c] = U[0][c] - su[c];
-      dsV[c] = V[0][c] - sv[c];
+    for (int h = 0; h < 2; ++h) {
+      dsU[h] = sub2(U2[0][h], su2[h]);
+      dsV[h] = sub2(V2[0][h], sv2[h]);
     }
 #pragma unroll
     for (int r = 0; r < 4; ++r) {
       // columns beyond the thread's own, before this row is updated
-      const float wU = __shfl_up_sync(0xffffffffu, U[r][3], 1, 16);
-      const float wV = __shfl_up_sync(0xffffffffu, V[r][3], 1, 16);
-      const float eU = __shfl_down_sync(0xffffffffu, U[r][0], 1, 16);
-      const float eV = __shfl_down_sync(0xffffffffu, V[r][0], 1, 16);
-      // dx[c]: across x face c, W(c) - W(c - 1)
+      const float wU = __shfl_up_sync(0xffffffffu, U2[r][1].y, 1, 16);
+      const float wV = __shfl_up_sync(0xffffffffu, V2[r][1].y, 1, 16);
+      const float eU = __shfl_down_sync(0xffffffffu, U2[r][0].x, 1, 16);
+      const float eV = __shfl_down_sync(0xffffffffu, V2[r][0].x, 1, 16);
+      const float u[6] = {wU, U2[r][0].x, U2[r][0].y, U2[r][1].x, U2[r][1].y, eU};
+      const float v[6] = {wV, V2[r][0].x, V2[r][0].y, V2[r][1].x, V2[r][1].y, eV};
+      // dx[c]: across x face c, W(c) - W(c - 1), each formed once for the two cells of the face
       float dxU[5], dxV[5];
-      dxU[0] = U[r][0] - wU;
-      dxV[0] = V[r][0] - wV;
 #pragma unroll
-      for (int c = 1; c < 4; ++c) {
-        dxU[c] = U[r][c] - U[r][c - 1];
-        dxV[c] = V[r][c] - V[r][c - 1];
+      for (int c = 0; c < 5; ++c) {
+        dxU[c] = u[c + 1] - u[c];
+        dxV[c] = v[c + 1] - v[c];
       }
-      dxU[4] = eU - U[r][3];
-      dxV[4] = eV - V[r][3];
-      float dnU[4], dnV[4];
+      // x part of f per cell, written straight into the halves of the pairs
+      float2 fU[2], fV[2];
 #pragma unroll
-      for (int c = 0; c < 4; ++c) {
-        const float nU = r < 3 ? U[r + 1][c] : nu[c];
-        const float nV = r < 3 ? V[r + 1][c] : nv[c];
-        dnU[c] = nU - U[r][c];
-        dnV[c] = nV - V[r][c];
+      for (int h = 0; h < 2; ++h) {
+        const int c = 2 * h;
+        fU[h].x = fx[r][c + 1] * dxU[c + 1] - fx[r][c] * dxU[c];
+        fU[h].y = fx[r][c + 2] * dxU[c + 2] - fx[r][c + 1] * dxU[c + 1];
+        fV[h].x = fx[r][c + 1] * dxV[c + 1] - fx[r][c] * dxV[c];
+        fV[h].y = fx[r][c + 2] * dxV[c + 2] - fx[r][c + 1] * dxV[c + 1];
       }
 #pragma unroll
-      for (int c = 0; c < 4; ++c) {
-        const float fU = fy[r + 1][c] * dnU[c] - fy[r][c] * dsU[c] + fx[r][c + 1] * dxU[c + 1] - fx[r][c] * dxU[c];
-        const float fV = fy[r + 1][c] * dnV[c] - fy[r][c] * dsV[c] + fx[r][c + 1] * dxV[c + 1] - fx[r][c] * dxV[c];
-        float un = U[r][c] + ca * fU - cb * fV;
-        float vn = V[r][c] + ca * fV + cb * fU;
-        if (!PERIODIC && !(inside & (1u << (4 * r + c)))) {
-          un = 0.f;
-          vn = 0.f;
+      for (int h = 0; h < 2; ++h) {
+        const float2 nU = r < 3 ? U2[r + 1][h] : nu2[h];
+        const float2 nV = r < 3 ? V2[r + 1][h] : nv2[h];
+        const float2 dnU = sub2(nU, U2[r][h]), dnV = sub2(nV, V2[r][h]);
+        // y part, two cells per instruction: f += k_n d_n - k_s d_s
+        const float2 nks = make_float2(-FY2[r][h].x, -FY2[r][h].y);
+        fU[h] = __ffma2_rn(nks, dsU[h], __ffma2_rn(FY2[r + 1][h], dnU, fU[h]));
+        fV[h] = __ffma2_rn(nks, dsV[h], __ffma2_rn(FY2[r + 1][h], dnV, fV[h]));
+        // W += (ca + i cb) f
+        float2 un = __ffma2_rn(ncb2, fV[h], __ffma2_rn(ca2, fU[h], U2[r][h]));
+        float2 vn = __ffma2_rn(cb2, fU[h], __ffma2_rn(ca2, fV[h], V2[r][h]));
+        if (!PERIODIC) {
+          if (!(inside & (1u << (4 * r + 2 * h)))) un.x = vn.x = 0.f;
+          if (!(inside & (1u << (4 * r + 2 * h + 1)))) un.y = vn.y = 0.f;
         }
-        U[r][c] = un;
-        V[r][c] = vn;
-        dsU[c] = dnU[c];
-        dsV[c] = dnV[c];
+        U2[r][h] = un;
+        V2[r][h] = vn;
+        dsU[h] = dnU;
+        dsV[h] = dnV;
       }
     }
   }
@@ -182,9 +208,10 @@ __global__ void __launch_bounds__(RT_THREADS, FRKC2_TBR_MIN_BLOCKS) k_tb2d_reg(c
       const int gx = x0 + rx;
       if (rx < k || rx >= RT_R - k || gx >= nx) continue;
       const size_t g = size_t(gy) * nx + gx;
-      Uo[g] = U[r][c];
-      if (Vo) Vo[g] = V[r][c];
-      if (p.check_finite) bad |= (__float_as_uint(U[r][c]) & 0x7f800000u) == 0x7f800000u;
+      const float uu = (c & 1) ? U2[r][c >> 1].y : U2[r][c >> 1].x;
+      Uo[g] = uu;
+      if (Vo) Vo[g] = (c & 1) ? V2[r][c >> 1].y : V2[r][c >> 1].x;
+      if (p.check_finite) bad |= (__float_as_uint(uu) & 0x7f800000u) == 0x7f800000u;
     }
   }
   if (bad) atomicOr(p.status, ST_NONFINITE);
