@@ -4,13 +4,16 @@
 // Same region scheme as the FP32 register-tiled pass: a CTA of 16 x 16 threads owns a 64 x 64
 // region (output (64 - 2k)^2, k-cell recomputed halo), thread (tx, ty) the 4 x 4 cells at
 // columns 4tx.., rows 4ty..  Each cell's state is two float pairs (U = Uh + Ul, V = Vh + Vl:
-// 64 registers per thread); the thread's 40 face conductivities sit in its own slots of shared
-// memory (written and read by that thread only, element-major so a warp hits 32 banks).  Per
+// 64 registers per thread, held as horizontal cell pairs); the thread's 40 face conductivities
+// sit in its own slots of shared memory (written and read by that thread only, element-major
+// so a warp's accesses are conflict-free; the y faces as pairs of adjacent columns).  Per
 // stage the thread's bottom and top rows go through shared memory (double-buffered, one barrier
 // per stage), its edge columns come by 16-lane shuffles, neighbour differences are rounded to
 // float from the pairs ((h_nb - h_c) + (l_nb - l_c)), f is formed in float with each difference
 // shared inside the block, and the float increment is added to each pair by TwoSum and a fast
-// renormalisation -- every operation on the FP32 pipe.  A step's first pass splits the caller's
+// renormalisation -- every operation on the FP32 pipe, and all of it but the x differences
+// and x flux terms as packed two-lane instructions (add / fma .f32x2 of the sm_100 family) on
+// two cells at once.  A step's first pass splits the caller's
 // double state, its last pass writes hi + lo back as a double; in between the state is one
 // float4 (Uh, Ul, Vh, Vl) per cell, as in the DFLOAT streaming pass.
 #include <cuda_runtime.h>
@@ -21,25 +24,32 @@
 namespace frkc2 {
 namespace {
 
-constexpr int DT_FACES = 40;  // per thread: 4 rows x 5 x faces, 5 rows x 4 y faces
-
 struct DfShared {
   float4 bot[2][4][16][16];  // [stage parity][Uh, Ul, Vh, Vl][ty][tx]: the thread's row 0
   float4 top[2][4][16][16];  // its row 3
-  float faces[DT_FACES][RT_THREADS];
+  float4 fx4[4][RT_THREADS];  // x faces 1..4 of row r (face c: west of cell c; 4 = east of 3)
+  float4 fy4[5][RT_THREADS];  // y face r of columns 0..3 (face r: south of row r; 4 = north of 3)
 };
 
-__device__ __forceinline__ void df_add2(float& h, float& l, float d) {
-  const float s = h + d;
-  const float bb = s - h;
-  const float e = (h - (s - bb)) + (d - bb);
-  const float t = l + e;
-  const float hi = s + t;
-  l = t - (hi - s);
+// (h, l) += d on both halves: TwoSum of h and d, then the fast renormalisation with l
+__device__ __forceinline__ void df_add2(float2& h, float2& l, float2 d) {
+  const float2 s = __fadd2_rn(h, d);
+  const float2 bb = sub2(s, h);
+  const float2 e = __fadd2_rn(sub2(h, sub2(s, bb)), sub2(d, bb));
+  const float2 t = __fadd2_rn(l, e);
+  const float2 hi = __fadd2_rn(s, t);
+  l = sub2(t, sub2(hi, s));
   h = hi;
 }
 
+// (ah + al) - (bh + bl) rounded to float
 __device__ __forceinline__ float dfd(float ah, float al, float bh, float bl) { return (ah - bh) + (al - bl); }
+__device__ __forceinline__ float2 dfd2(float2 ah, float2 al, float2 bh, float2 bl) {
+  return __fadd2_rn(sub2(ah, bh), sub2(al, bl));
+}
+
+__device__ __forceinline__ float2 pair_of(float4 a, int h) { return h == 0 ? make_float2(a.x, a.y) : make_float2(a.z, a.w); }
+__device__ __forceinline__ float half_of(float2 a, int i) { return i ? a.y : a.x; }
 
 template <bool PERIODIC, bool IN_REAL, bool OUT_REAL>
 __global__ void __launch_bounds__(RT_THREADS, 2) k_tb2d_df(const PassArgs p) {
@@ -52,7 +62,8 @@ __global__ void __launch_bounds__(RT_THREADS, 2) k_tb2d_df(const PassArgs p) {
   const int nx = p.nx, ny = p.ny;
   const float* __restrict__ FX = static_cast<const float*>(p.fx);
   const float* __restrict__ FY = static_cast<const float*>(p.fy);
-  float* myf = &sh.faces[0][tid];  // face e at myf[e * RT_THREADS]
+  float4* myfx = &sh.fx4[0][tid];  // row r at myfx[r * RT_THREADS]
+  float4* myfy = &sh.fy4[0][tid];
 
   int gyr[5], gxc[5];
   bool yin[5], xin[5];
@@ -67,121 +78,147 @@ __global__ void __launch_bounds__(RT_THREADS, 2) k_tb2d_df(const PassArgs p) {
   unsigned inside = 0;
 #pragma unroll
   for (int r = 0; r < 5; ++r) {
+    float fxr[5], fyr[4];
 #pragma unroll
     for (int c = 0; c < 5; ++c) {
       if (r < 4) {  // x face c of row r
         float v = 0.f;
         if (PERIODIC || (yin[r] && gxc[c] >= 0 && gxc[c] <= nx)) v = FX[size_t(gyr[r]) * (nx + 1) + gxc[c]];
-        myf[(5 * r + c) * RT_THREADS] = v;
+        fxr[c] = v;
       }
       if (c < 4) {  // y face r of column c
         float v = 0.f;
         if (PERIODIC || (xin[c] && gyr[r] >= 0 && gyr[r] <= ny)) v = FY[size_t(gyr[r]) * nx + gxc[c]];
-        myf[(20 + 4 * r + c) * RT_THREADS] = v;
+        fyr[c] = v;
         if (r < 4 && xin[c] && yin[r]) inside |= 1u << (4 * r + c);
       }
     }
+    // face 0 of a row is the west neighbour's face 4: its flux term comes from there
+    if (r < 4) myfx[r * RT_THREADS] = make_float4(fxr[1], fxr[2], fxr[3], fxr[4]);
+    myfy[r * RT_THREADS] = make_float4(fyr[0], fyr[1], fyr[2], fyr[3]);
   }
-  float Uh[4][4], Ul[4][4], Vh[4][4], Vl[4][4];
+  // the state as horizontal cell pairs: Uh[r][h] = (Uh of cell (r, 2h), of cell (r, 2h + 1))
+  float2 Uh[4][2], Ul[4][2], Vh[4][2], Vl[4][2];
 #pragma unroll
   for (int r = 0; r < 4; ++r)
 #pragma unroll
-    for (int c = 0; c < 4; ++c) {
-      float4 w = make_float4(0.f, 0.f, 0.f, 0.f);
-      if (PERIODIC || (inside & (1u << (4 * r + c)))) {
-        const size_t g = size_t(gyr[r]) * nx + gxc[c];
-        if (IN_REAL) {
-          const double u = static_cast<const double*>(p.U_in)[g];
-          w.x = __double2float_rn(u);
-          w.y = __double2float_rn(u - double(w.x));
-        } else {
-          w = static_cast<const float4*>(p.U_in)[g];
+    for (int h = 0; h < 2; ++h) {
+      float4 w[2];
+#pragma unroll
+      for (int i = 0; i < 2; ++i) {
+        const int c = 2 * h + i;
+        w[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (PERIODIC || (inside & (1u << (4 * r + c)))) {
+          const size_t g = size_t(gyr[r]) * nx + gxc[c];
+          if (IN_REAL) {
+            const double u = static_cast<const double*>(p.U_in)[g];
+            w[i].x = __double2float_rn(u);
+            w[i].y = __double2float_rn(u - double(w[i].x));
+          } else {
+            w[i] = static_cast<const float4*>(p.U_in)[g];
+          }
         }
       }
-      Uh[r][c] = w.x;
-      Ul[r][c] = w.y;
-      Vh[r][c] = w.z;
-      Vl[r][c] = w.w;
+      Uh[r][h] = make_float2(w[0].x, w[1].x);
+      Ul[r][h] = make_float2(w[0].y, w[1].y);
+      Vh[r][h] = make_float2(w[0].z, w[1].z);
+      Vl[r][h] = make_float2(w[0].w, w[1].w);
     }
 
   const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
   for (int j = 0; j < k; ++j) {
     const int b = j & 1;
-    sh.bot[b][0][ty][tx] = make_float4(Uh[0][0], Uh[0][1], Uh[0][2], Uh[0][3]);
-    sh.bot[b][1][ty][tx] = make_float4(Ul[0][0], Ul[0][1], Ul[0][2], Ul[0][3]);
-    sh.bot[b][2][ty][tx] = make_float4(Vh[0][0], Vh[0][1], Vh[0][2], Vh[0][3]);
-    sh.bot[b][3][ty][tx] = make_float4(Vl[0][0], Vl[0][1], Vl[0][2], Vl[0][3]);
-    sh.top[b][0][ty][tx] = make_float4(Uh[3][0], Uh[3][1], Uh[3][2], Uh[3][3]);
-    sh.top[b][1][ty][tx] = make_float4(Ul[3][0], Ul[3][1], Ul[3][2], Ul[3][3]);
-    sh.top[b][2][ty][tx] = make_float4(Vh[3][0], Vh[3][1], Vh[3][2], Vh[3][3]);
-    sh.top[b][3][ty][tx] = make_float4(Vl[3][0], Vl[3][1], Vl[3][2], Vl[3][3]);
+    sh.bot[b][0][ty][tx] = make_float4(Uh[0][0].x, Uh[0][0].y, Uh[0][1].x, Uh[0][1].y);
+    sh.bot[b][1][ty][tx] = make_float4(Ul[0][0].x, Ul[0][0].y, Ul[0][1].x, Ul[0][1].y);
+    sh.bot[b][2][ty][tx] = make_float4(Vh[0][0].x, Vh[0][0].y, Vh[0][1].x, Vh[0][1].y);
+    sh.bot[b][3][ty][tx] = make_float4(Vl[0][0].x, Vl[0][0].y, Vl[0][1].x, Vl[0][1].y);
+    sh.top[b][0][ty][tx] = make_float4(Uh[3][0].x, Uh[3][0].y, Uh[3][1].x, Uh[3][1].y);
+    sh.top[b][1][ty][tx] = make_float4(Ul[3][0].x, Ul[3][0].y, Ul[3][1].x, Ul[3][1].y);
+    sh.top[b][2][ty][tx] = make_float4(Vh[3][0].x, Vh[3][0].y, Vh[3][1].x, Vh[3][1].y);
+    sh.top[b][3][ty][tx] = make_float4(Vl[3][0].x, Vl[3][0].y, Vl[3][1].x, Vl[3][1].y);
     __syncthreads();
     const float ca = p.caf[j], cb = p.cbf[j];
+    const float2 ca2 = make_float2(ca, ca), cb2 = make_float2(cb, cb), ncb2 = make_float2(-cb, -cb);
     // differences across the south faces of row 0 (the region's bottom thread row has none)
-    float dsU[4], dsV[4];
+    float2 dsU[2], dsV[2];
     {
       const float4 a = ty > 0 ? sh.top[b][0][ty - 1][tx] : z4, bl = ty > 0 ? sh.top[b][1][ty - 1][tx] : z4;
       const float4 cvh = ty > 0 ? sh.top[b][2][ty - 1][tx] : z4, cvl = ty > 0 ? sh.top[b][3][ty - 1][tx] : z4;
-      const float sUh[4] = {a.x, a.y, a.z, a.w}, sUl[4] = {bl.x, bl.y, bl.z, bl.w};
-      const float sVh[4] = {cvh.x, cvh.y, cvh.z, cvh.w}, sVl[4] = {cvl.x, cvl.y, cvl.z, cvl.w};
 #pragma unroll
-      for (int c = 0; c < 4; ++c) {
-        dsU[c] = dfd(Uh[0][c], Ul[0][c], sUh[c], sUl[c]);
-        dsV[c] = dfd(Vh[0][c], Vl[0][c], sVh[c], sVl[c]);
+      for (int h = 0; h < 2; ++h) {
+        dsU[h] = dfd2(Uh[0][h], Ul[0][h], pair_of(a, h), pair_of(bl, h));
+        dsV[h] = dfd2(Vh[0][h], Vl[0][h], pair_of(cvh, h), pair_of(cvl, h));
       }
     }
 #pragma unroll
     for (int r = 0; r < 4; ++r) {
-      // columns beyond the thread's own, before this row is updated
-      const float wUh = __shfl_up_sync(0xffffffffu, Uh[r][3], 1, 16);
-      const float wUl = __shfl_up_sync(0xffffffffu, Ul[r][3], 1, 16);
-      const float wVh = __shfl_up_sync(0xffffffffu, Vh[r][3], 1, 16);
-      const float wVl = __shfl_up_sync(0xffffffffu, Vl[r][3], 1, 16);
-      const float eUh = __shfl_down_sync(0xffffffffu, Uh[r][0], 1, 16);
-      const float eUl = __shfl_down_sync(0xffffffffu, Ul[r][0], 1, 16);
-      const float eVh = __shfl_down_sync(0xffffffffu, Vh[r][0], 1, 16);
-      const float eVl = __shfl_down_sync(0xffffffffu, Vl[r][0], 1, 16);
-      float dxU[5], dxV[5];
-      dxU[0] = dfd(Uh[r][0], Ul[r][0], wUh, wUl);
-      dxV[0] = dfd(Vh[r][0], Vl[r][0], wVh, wVl);
+      // the column east of the thread's own, before this row is updated
+      const float eUh = __shfl_down_sync(0xffffffffu, Uh[r][0].x, 1, 16);
+      const float eUl = __shfl_down_sync(0xffffffffu, Ul[r][0].x, 1, 16);
+      const float eVh = __shfl_down_sync(0xffffffffu, Vh[r][0].x, 1, 16);
+      const float eVl = __shfl_down_sync(0xffffffffu, Vl[r][0].x, 1, 16);
+      const float uh[5] = {Uh[r][0].x, Uh[r][0].y, Uh[r][1].x, Uh[r][1].y, eUh};
+      const float ul[5] = {Ul[r][0].x, Ul[r][0].y, Ul[r][1].x, Ul[r][1].y, eUl};
+      const float vh[5] = {Vh[r][0].x, Vh[r][0].y, Vh[r][1].x, Vh[r][1].y, eVh};
+      const float vl[5] = {Vl[r][0].x, Vl[r][0].y, Vl[r][1].x, Vl[r][1].y, eVl};
+      // x flux terms k_c d_c of faces 1..4 (face c between cells c - 1 and c), each formed once;
+      // face 0's is the west neighbour's face 4 (the region's west column goes stale)
+      const float4 kx = myfx[r * RT_THREADS];
+      const float kxa[4] = {kx.x, kx.y, kx.z, kx.w};
+      float pU[5], pV[5];
 #pragma unroll
-      for (int c = 1; c < 4; ++c) {
-        dxU[c] = dfd(Uh[r][c], Ul[r][c], Uh[r][c - 1], Ul[r][c - 1]);
-        dxV[c] = dfd(Vh[r][c], Vl[r][c], Vh[r][c - 1], Vl[r][c - 1]);
+      for (int c = 1; c < 5; ++c) {
+        pU[c] = kxa[c - 1] * dfd(uh[c], ul[c], uh[c - 1], ul[c - 1]);
+        pV[c] = kxa[c - 1] * dfd(vh[c], vl[c], vh[c - 1], vl[c - 1]);
       }
-      dxU[4] = dfd(eUh, eUl, Uh[r][3], Ul[r][3]);
-      dxV[4] = dfd(eVh, eVl, Vh[r][3], Vl[r][3]);
-      float dnU[4], dnV[4];
+      pU[0] = __shfl_up_sync(0xffffffffu, pU[4], 1, 16);
+      pV[0] = __shfl_up_sync(0xffffffffu, pV[4], 1, 16);
+      // x part of f per cell, into the halves of the pairs
+      float2 fU[2], fV[2];
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int c = 2 * h;
+        fU[h] = make_float2(pU[c + 1] - pU[c], pU[c + 2] - pU[c + 1]);
+        fV[h] = make_float2(pV[c + 1] - pV[c], pV[c + 2] - pV[c + 1]);
+      }
+      float2 dnU[2], dnV[2];
       if (r < 3) {
 #pragma unroll
-        for (int c = 0; c < 4; ++c) {
-          dnU[c] = dfd(Uh[r + 1 < 4 ? r + 1 : 3][c], Ul[r + 1 < 4 ? r + 1 : 3][c], Uh[r][c], Ul[r][c]);
-          dnV[c] = dfd(Vh[r + 1 < 4 ? r + 1 : 3][c], Vl[r + 1 < 4 ? r + 1 : 3][c], Vh[r][c], Vl[r][c]);
+        for (int h = 0; h < 2; ++h) {
+          const int rn = r + 1 < 4 ? r + 1 : 3;
+          dnU[h] = dfd2(Uh[rn][h], Ul[rn][h], Uh[r][h], Ul[r][h]);
+          dnV[h] = dfd2(Vh[rn][h], Vl[rn][h], Vh[r][h], Vl[r][h]);
         }
       } else {  // the north neighbour row (the region's top thread row has none)
         const float4 a = ty < 15 ? sh.bot[b][0][ty + 1][tx] : z4, bl = ty < 15 ? sh.bot[b][1][ty + 1][tx] : z4;
         const float4 cvh = ty < 15 ? sh.bot[b][2][ty + 1][tx] : z4, cvl = ty < 15 ? sh.bot[b][3][ty + 1][tx] : z4;
-        const float nUh[4] = {a.x, a.y, a.z, a.w}, nUl[4] = {bl.x, bl.y, bl.z, bl.w};
-        const float nVh[4] = {cvh.x, cvh.y, cvh.z, cvh.w}, nVl[4] = {cvl.x, cvl.y, cvl.z, cvl.w};
 #pragma unroll
-        for (int c = 0; c < 4; ++c) {
-          dnU[c] = dfd(nUh[c], nUl[c], Uh[3][c], Ul[3][c]);
-          dnV[c] = dfd(nVh[c], nVl[c], Vh[3][c], Vl[3][c]);
+        for (int h = 0; h < 2; ++h) {
+          dnU[h] = dfd2(pair_of(a, h), pair_of(bl, h), Uh[3][h], Ul[3][h]);
+          dnV[h] = dfd2(pair_of(cvh, h), pair_of(cvl, h), Vh[3][h], Vl[3][h]);
         }
       }
 #pragma unroll
-      for (int c = 0; c < 4; ++c) {
-        const float kw = myf[(5 * r + c) * RT_THREADS], ke = myf[(5 * r + c + 1) * RT_THREADS];
-        const float ks = myf[(20 + 4 * r + c) * RT_THREADS], kn = myf[(20 + 4 * (r + 1) + c) * RT_THREADS];
-        const float fU = kn * dnU[c] - ks * dsU[c] + ke * dxU[c + 1] - kw * dxU[c];
-        const float fV = kn * dnV[c] - ks * dsV[c] + ke * dxV[c + 1] - kw * dxV[c];
-        df_add2(Uh[r][c], Ul[r][c], ca * fU - cb * fV);
-        df_add2(Vh[r][c], Vl[r][c], ca * fV + cb * fU);
-        if (!PERIODIC && !(inside & (1u << (4 * r + c)))) {
-          Uh[r][c] = Ul[r][c] = Vh[r][c] = Vl[r][c] = 0.f;
+      for (int h = 0; h < 2; ++h) {
+        const float4 ks4 = myfy[r * RT_THREADS], kn4 = myfy[(r + 1) * RT_THREADS];
+        const float2 ks = pair_of(ks4, h), kn = pair_of(kn4, h);
+        const float2 nks = make_float2(-ks.x, -ks.y);
+        // y part, two cells per instruction: f += k_n d_n - k_s d_s
+        fU[h] = __ffma2_rn(nks, dsU[h], __ffma2_rn(kn, dnU[h], fU[h]));
+        fV[h] = __ffma2_rn(nks, dsV[h], __ffma2_rn(kn, dnV[h], fV[h]));
+        // the float increments Re, Im of (ca + i cb) f, added to the pairs error-free
+        df_add2(Uh[r][h], Ul[r][h], __ffma2_rn(ncb2, fV[h], __fmul2_rn(ca2, fU[h])));
+        df_add2(Vh[r][h], Vl[r][h], __ffma2_rn(cb2, fU[h], __fmul2_rn(ca2, fV[h])));
+        if (!PERIODIC) {
+#pragma unroll
+          for (int i = 0; i < 2; ++i)
+            if (!(inside & (1u << (4 * r + 2 * h + i)))) {
+              if (i) Uh[r][h].y = Ul[r][h].y = Vh[r][h].y = Vl[r][h].y = 0.f;
+              else Uh[r][h].x = Ul[r][h].x = Vh[r][h].x = Vl[r][h].x = 0.f;
+            }
         }
-        dsU[c] = dnU[c];
-        dsV[c] = dnV[c];
+        dsU[h] = dnU[h];
+        dsV[h] = dnV[h];
       }
     }
   }
@@ -198,12 +235,14 @@ __global__ void __launch_bounds__(RT_THREADS, 2) k_tb2d_df(const PassArgs p) {
       const int gx = x0 + rx;
       if (rx < k || rx >= RT_R - k || gx >= nx) continue;
       const size_t g = size_t(gy) * nx + gx;
+      const int h = c >> 1, i = c & 1;
       if (OUT_REAL) {
-        const double u = double(Uh[r][c]) + double(Ul[r][c]);
+        const double u = double(half_of(Uh[r][h], i)) + double(half_of(Ul[r][h], i));
         static_cast<double*>(p.U_out)[g] = u;
         if (p.check_finite) bad |= (__double2hiint(u) & 0x7ff00000) == 0x7ff00000;
       } else {
-        static_cast<float4*>(p.U_out)[g] = make_float4(Uh[r][c], Ul[r][c], Vh[r][c], Vl[r][c]);
+        static_cast<float4*>(p.U_out)[g] =
+            make_float4(half_of(Uh[r][h], i), half_of(Ul[r][h], i), half_of(Vh[r][h], i), half_of(Vl[r][h], i));
       }
     }
   }
