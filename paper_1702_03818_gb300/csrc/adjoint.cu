@@ -14,7 +14,8 @@
 // then the segment's stages are reversed (last step first, last stage first).  The last
 // segment's tape is still in place after the forward run and is not recomputed.  2D problems
 // with a fixed conductivity use the streaming kernels with the tape and lambda stored
-// interleaved (U, V); the others use the tile kernels with planar U, V.
+// interleaved (U, V) -- in FP32 the temporally blocked tape and reverse passes of
+// adjoint_tb2d.cu, 8 stages each; the others use the tile kernels with planar U, V.
 #include <algorithm>
 #include <cmath>
 
@@ -289,6 +290,8 @@ struct AdjCtx {
   cudaStream_t st;
   size_t N, SB, slot;
   bool stream2d;  // 2D fixed conductivity: streaming kernels, interleaved tape and lambda
+  bool tb;        // ... in FP32: temporally blocked tape and reverse passes of tbk stages
+  int tbk;
   int tx, ty, tz;
   char* ckpt(int j) const { return base + L.ckpt + size_t(j) * slot; }
   char* tape(int q, int l) const { return base + L.tape + (size_t(q) * s + l) * 2 * slot; }
@@ -320,6 +323,8 @@ frkc2_status adj_setup(AdjCtx& C, frkc2_plan_t plan, const frkc2_problem* prob, 
   C.SB = state_bytes(p.precision);
   C.slot = align256(C.N * C.SB);
   C.stream2d = p.ndim == 2 && p.kappa_kind != FRKC2_KAPPA_POWER;
+  C.tbk = 8;
+  C.tb = C.stream2d && adj_tb2d_supported(p, C.tbk);
   default_tiles(p, 1, &C.tx, &C.ty, &C.tz);
   if (p.ndim < 2) C.ty = 1;
   if (p.ndim < 3) C.tz = 1;
@@ -351,6 +356,26 @@ bool run_segment(const AdjCtx& C, int j) {
   a.kp = p.kappa_p;
   a.status = reinterpret_cast<unsigned*>(C.base + C.L.status);
   const int n0 = j * C.c, m = std::min(C.c, C.nsteps - n0);
+  if (C.tb) {
+    for (int q = 0; q < m; ++q)
+      for (int l0 = 0; l0 < C.s;) {
+        AdjTbPass t{};
+        t.nst = std::min(C.tbk, C.s - l0);
+        t.in = l0 == 0 ? C.w0(j, q) : C.tape(q, l0);
+        t.in_complex = l0 != 0;
+        for (int jj = 0; jj < t.nst; ++jj) {
+          const int l = l0 + jj;
+          t.out[jj] = l + 1 < C.s ? C.tape(q, l + 1) : (q + 1 < m ? C.tape(q + 1, 0) : C.ckpt(j + 1));
+          t.ca[jj] = C.dt * C.plan->a_re[l] / C.h2;
+          t.cb[jj] = C.dt * C.plan->a_im[l] / C.h2;
+        }
+        t.last_real = l0 + t.nst == C.s;
+        if (launch_tape_tb2d(p, C.tbk, t, C.base + C.L.fx, C.base + C.L.fy, a.status, C.st) != cudaSuccess)
+          return false;
+        l0 += t.nst;
+      }
+    return true;
+  }
   for (int q = 0; q < m; ++q) {
     for (int l = 0; l < C.s; ++l) {
       const bool last = l + 1 == C.s;
@@ -424,6 +449,36 @@ frkc2_status adj_backward(const AdjCtx& C, const void* g, void* dJdu0, void* dJd
     if (j != C.L.nseg - 1 && !run_segment(C, j)) return FRKC2_ECUDA;
     const int m = std::min(C.c, C.nsteps - j * C.c);
     for (int q = m - 1; q >= 0; --q) {
+      if (C.tb) {  // passes of up to tbk stages, last stage first
+        for (int lhi = C.s; lhi > 0;) {
+          AdjTbPass t{};
+          t.nst = std::min(C.tbk, lhi);
+          for (int jj = 0; jj < t.nst; ++jj) {
+            const int l = lhi - 1 - jj;
+            t.W[jj] = l == 0 ? C.w0(j, q) : C.tape(q, l);
+            t.w_complex[jj] = l != 0;
+            t.ca[jj] = C.dt * C.plan->a_re[l] / C.h2;
+            t.cb[jj] = C.dt * C.plan->a_im[l] / C.h2;
+          }
+          if (lhi == C.s) {  // the step output is Re W^L: a real lambda
+            t.L_in = lam_src;
+            t.l_mode = lam_real_input ? 0 : 2;
+          } else {
+            t.L_in = lam[cur];
+            t.l_mode = 1;
+          }
+          t.L_out = lam[cur ^ 1];
+          t.dk = dk;
+          if (launch_adjrev_tb2d(p, C.tbk, t, C.base + C.L.fx, C.base + C.L.fy,
+                                 reinterpret_cast<unsigned*>(C.base + C.L.status), C.st) != cudaSuccess)
+            return FRKC2_ECUDA;
+          cur ^= 1;
+          lhi -= t.nst;
+        }
+        lam_src = lam[cur];
+        lam_real_input = false;
+        continue;
+      }
       // the step output is Re W^L: the adjoint of a step starts from a real lambda
       for (int l = C.s - 1; l >= 0; --l) {
         const bool first = l == C.s - 1;

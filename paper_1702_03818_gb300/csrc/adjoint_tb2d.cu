@@ -1,0 +1,541 @@
+// 2D adjoint for FP32 with a fixed conductivity, temporally blocked: both halves of the
+// backward sweep run k stages per HBM round trip on the register-tiled 64 x 64 regions of
+// the FP32 forward pass (16 x 16 threads, 4 x 4 cells each, k-cell recomputed halo, rows
+// exchanged through shared memory, columns by 16-lane shuffles, cells held as horizontal
+// pairs for the packed f32x2 instructions).
+//
+// Tape pass (k_tape_tb2d): the forward stages of Sec. 3, Eq. 13 from the tape entry W^{l0},
+// writing every stage state W^{l0+1} .. W^{l0+k} of the output tile to the tape (the last as
+// the real step output when the pass ends the step) -- 8 bytes written per cell-stage.
+//
+// Reverse pass (k_adjrev_tb2d): k adjoint stages, last stage first.  The operator is
+// symmetric (J^H = A for a fixed conductivity), so stage l maps
+//   lam <- lam + conj(c_l) A lam,                        c_l = dt a_l / dx^2,
+// and contributes to dJ/dkappa through every face f between cells m and i
+//   G_f = Re(conj(lam_m - lam_i)(Y_m - Y_i)),            Y = -(c_l / 2) W^l,
+// half of the face's sensitivity to each of its cells (the 1/2 folded into Y; a Dirichlet
+// boundary face gives all of it to its interior cell), both with lam^{l+1}, before the update.
+// lam stays in registers for the k stages; each cell sums the sensitivities of its east and
+// north faces in registers and the cell's dJ/dkappa is formed once per pass from its own two
+// sums and those of its west and south neighbours, then added to the FP64 accumulator.  Per
+// cell-stage the pass reads the tape entry W^l (8 bytes; the halo recomputes (64/48)^2 of it
+// at k = 8) and, once per pass, lam in and out, the faces and the accumulator.
+#include <cuda_runtime.h>
+
+#include "frkc2_internal.h"
+#include "tb2d_region.cuh"
+
+namespace frkc2 {
+namespace {
+
+constexpr int AT_KMAX = 16;
+
+struct AdjTbArgs {
+  int nx, ny;
+  int k;    // halo width of the launch (the output tile is 64 - 2k)
+  int nst;  // stages in this pass, 1 .. k
+  const float* fx;  // x faces [ny][nx + 1], y faces [ny + 1][nx] (face i between cells i-1, i)
+  const float* fy;
+  // tape pass
+  const void* in;           // W^{l0}: interleaved (U, V) or real
+  int in_complex;
+  void* out[AT_KMAX];       // W^{l0+1+j}, interleaved; the last real when last_real
+  int last_real;
+  // reverse pass, stage j = the j-th stage from the end of the pass
+  const void* W[AT_KMAX];   // W^l: interleaved, or real (imaginary part 0) when !w_complex[j]
+  int w_complex[AT_KMAX];
+  const void* L_in;         // lam^{l_hi}
+  int l_mode;               // 0: real array, 1: interleaved, 2: real part of an interleaved array
+  float2* L_out;            // lam^{l_hi - nst}, interleaved
+  double* dk;               // dJ/dkappa per cell (FP64 accumulator) or nullptr
+  float ca[AT_KMAX];        // dt Re(a_l) / dx^2 of stage j, rounded to float once on the host
+  float cb[AT_KMAX];
+  unsigned* status;
+  int check_finite;
+};
+
+struct RevShared {
+  float4 bot[2][4][16][16];  // [parity][lam x, lam y, Y x, Y y][ty][tx]: the thread's row 0
+  float4 top[2][2][16][16];  // [parity][lam x, lam y]: its row 3
+  float4 fx4[4][RT_THREADS];  // x faces 0..3 of row r (thread-private slots)
+  float fxe[4][RT_THREADS];   // x face 4 of row r
+  float4 fy4[5][RT_THREADS];  // y face r of columns 0..3 (r = 4: north of row 3)
+  float4 se[4][RT_THREADS];   // east-face sensitivity sums of row r (thread-private slots)
+};
+
+// Grid rows / columns of a thread's cells (fifth entry: the next row / column), their
+// in-grid flags, the Dirichlet inside mask and the output-tile mask (bit 4r + c).
+struct RegionIdx {
+  int gyr[5], gxc[5];
+  bool yin[5], xin[5];
+  unsigned inside, outm;
+};
+
+template <bool PERIODIC>
+__device__ __forceinline__ RegionIdx region_idx(int nx, int ny, int k, int x0, int y0, int tx, int ty) {
+  RegionIdx R;
+#pragma unroll
+  for (int i = 0; i < 5; ++i) {
+    const int gx = x0 + 4 * tx + i, gy = y0 + 4 * ty + i;
+    R.gxc[i] = PERIODIC ? wrap_r(gx, nx) : gx;
+    R.gyr[i] = PERIODIC ? wrap_r(gy, ny) : gy;
+    R.xin[i] = gx >= 0 && gx < nx;
+    R.yin[i] = gy >= 0 && gy < ny;
+  }
+  R.inside = 0;
+  R.outm = 0;
+#pragma unroll
+  for (int r = 0; r < 4; ++r)
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      const int ry = 4 * ty + r, rx = 4 * tx + c;
+      if (R.xin[c] && R.yin[r]) {
+        R.inside |= 1u << (4 * r + c);
+        if (ry >= k && ry < RT_R - k && rx >= k && rx < RT_R - k) R.outm |= 1u << (4 * r + c);
+      }
+    }
+  return R;
+}
+
+// x face c of row r and y face r of column c, 0 outside a Dirichlet grid
+template <bool PERIODIC>
+__device__ __forceinline__ float face_x(const RegionIdx& R, const float* __restrict__ FX, int nx, int r, int c) {
+  if (PERIODIC || (R.yin[r] && R.gxc[c] >= 0 && R.gxc[c] <= nx)) return FX[size_t(R.gyr[r]) * (nx + 1) + R.gxc[c]];
+  return 0.f;
+}
+template <bool PERIODIC>
+__device__ __forceinline__ float face_y(const RegionIdx& R, const float* __restrict__ FY, int nx, int ny, int r, int c) {
+  if (PERIODIC || (R.xin[c] && R.gyr[r] >= 0 && R.gyr[r] <= ny)) return FY[size_t(R.gyr[r]) * nx + R.gxc[c]];
+  return 0.f;
+}
+
+__device__ __forceinline__ float2 pairh(float4 a, int h) { return h ? make_float2(a.z, a.w) : make_float2(a.x, a.y); }
+__device__ __forceinline__ float halfv(float2 a, int i) { return i ? a.y : a.x; }
+__device__ __forceinline__ void set_half(float2& a, int i, float v) {
+  if (i)
+    a.y = v;
+  else
+    a.x = v;
+}
+
+// ------------------------------------------------------------------------------------------
+// Tape pass: forward stages, every stage state of the output tile written.
+
+template <bool PERIODIC>
+__global__ void __launch_bounds__(RT_THREADS, 2) k_tape_tb2d(const AdjTbArgs a) {
+  __shared__ float4 sh_bot[2][2][16][16];  // [parity][U, V][ty][tx]: the thread's row 0
+  __shared__ float4 sh_top[2][2][16][16];  // its row 3
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  const int k = a.k, T = RT_R - 2 * k;
+  const int x0 = blockIdx.x * T - k, y0 = blockIdx.y * T - k;
+  const int nx = a.nx, ny = a.ny;
+  const RegionIdx R = region_idx<PERIODIC>(nx, ny, k, x0, y0, tx, ty);
+  float fx[4][5];
+  float2 FY2[5][2];
+#pragma unroll
+  for (int r = 0; r < 5; ++r) {
+    if (r < 4)
+#pragma unroll
+      for (int c = 0; c < 5; ++c) fx[r][c] = face_x<PERIODIC>(R, a.fx, nx, r, c);
+#pragma unroll
+    for (int h = 0; h < 2; ++h)
+      FY2[r][h] = make_float2(face_y<PERIODIC>(R, a.fy, nx, ny, r, 2 * h), face_y<PERIODIC>(R, a.fy, nx, ny, r, 2 * h + 1));
+  }
+  float2 U2[4][2], V2[4][2];
+#pragma unroll
+  for (int r = 0; r < 4; ++r)
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      float uu = 0.f, vv = 0.f;
+      if (PERIODIC || (R.inside & (1u << (4 * r + c)))) {
+        const size_t g = size_t(R.gyr[r]) * nx + R.gxc[c];
+        if (a.in_complex) {
+          const float2 w = static_cast<const float2*>(a.in)[g];
+          uu = w.x;
+          vv = w.y;
+        } else {
+          uu = static_cast<const float*>(a.in)[g];
+        }
+      }
+      set_half(U2[r][c >> 1], c & 1, uu);
+      set_half(V2[r][c >> 1], c & 1, vv);
+    }
+
+  bool bad = false;
+  const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+  for (int j = 0; j < a.nst; ++j) {
+    const int b = j & 1;
+    sh_bot[b][0][ty][tx] = make_float4(U2[0][0].x, U2[0][0].y, U2[0][1].x, U2[0][1].y);
+    sh_bot[b][1][ty][tx] = make_float4(V2[0][0].x, V2[0][0].y, V2[0][1].x, V2[0][1].y);
+    sh_top[b][0][ty][tx] = make_float4(U2[3][0].x, U2[3][0].y, U2[3][1].x, U2[3][1].y);
+    sh_top[b][1][ty][tx] = make_float4(V2[3][0].x, V2[3][0].y, V2[3][1].x, V2[3][1].y);
+    __syncthreads();
+    const float4 su4 = ty > 0 ? sh_top[b][0][ty - 1][tx] : z4, sv4 = ty > 0 ? sh_top[b][1][ty - 1][tx] : z4;
+    const float4 nu4 = ty < 15 ? sh_bot[b][0][ty + 1][tx] : z4, nv4 = ty < 15 ? sh_bot[b][1][ty + 1][tx] : z4;
+    const float ca = a.ca[j], cb = a.cb[j];
+    const float2 ca2 = make_float2(ca, ca), cb2 = make_float2(cb, cb), ncb2 = make_float2(-cb, -cb);
+    float2 dsU[2], dsV[2];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      dsU[h] = sub2(U2[0][h], pairh(su4, h));
+      dsV[h] = sub2(V2[0][h], pairh(sv4, h));
+    }
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      const float wU = __shfl_up_sync(0xffffffffu, U2[r][1].y, 1, 16);
+      const float wV = __shfl_up_sync(0xffffffffu, V2[r][1].y, 1, 16);
+      const float eU = __shfl_down_sync(0xffffffffu, U2[r][0].x, 1, 16);
+      const float eV = __shfl_down_sync(0xffffffffu, V2[r][0].x, 1, 16);
+      const float u[6] = {wU, U2[r][0].x, U2[r][0].y, U2[r][1].x, U2[r][1].y, eU};
+      const float v[6] = {wV, V2[r][0].x, V2[r][0].y, V2[r][1].x, V2[r][1].y, eV};
+      float dxU[5], dxV[5];
+#pragma unroll
+      for (int c = 0; c < 5; ++c) {
+        dxU[c] = u[c + 1] - u[c];
+        dxV[c] = v[c + 1] - v[c];
+      }
+      float2 fU[2], fV[2];
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int c = 2 * h;
+        fU[h].x = fx[r][c + 1] * dxU[c + 1] - fx[r][c] * dxU[c];
+        fU[h].y = fx[r][c + 2] * dxU[c + 2] - fx[r][c + 1] * dxU[c + 1];
+        fV[h].x = fx[r][c + 1] * dxV[c + 1] - fx[r][c] * dxV[c];
+        fV[h].y = fx[r][c + 2] * dxV[c + 2] - fx[r][c + 1] * dxV[c + 1];
+      }
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const float2 nU = r < 3 ? U2[r + 1][h] : pairh(nu4, h);
+        const float2 nV = r < 3 ? V2[r + 1][h] : pairh(nv4, h);
+        const float2 dnU = sub2(nU, U2[r][h]), dnV = sub2(nV, V2[r][h]);
+        const float2 nks = make_float2(-FY2[r][h].x, -FY2[r][h].y);
+        fU[h] = __ffma2_rn(nks, dsU[h], __ffma2_rn(FY2[r + 1][h], dnU, fU[h]));
+        fV[h] = __ffma2_rn(nks, dsV[h], __ffma2_rn(FY2[r + 1][h], dnV, fV[h]));
+        float2 un = __ffma2_rn(ncb2, fV[h], __ffma2_rn(ca2, fU[h], U2[r][h]));
+        float2 vn = __ffma2_rn(cb2, fU[h], __ffma2_rn(ca2, fV[h], V2[r][h]));
+        if (!PERIODIC) {
+          if (!(R.inside & (1u << (4 * r + 2 * h)))) un.x = vn.x = 0.f;
+          if (!(R.inside & (1u << (4 * r + 2 * h + 1)))) un.y = vn.y = 0.f;
+        }
+        U2[r][h] = un;
+        V2[r][h] = vn;
+        dsU[h] = dnU;
+        dsV[h] = dnV;
+      }
+    }
+    // this stage's state of the output tile to the tape
+    const bool real_out = a.last_real && j == a.nst - 1;
+    void* out = a.out[j];
+#pragma unroll
+    for (int r = 0; r < 4; ++r)
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        if (!(R.outm & (1u << (4 * r + c)))) continue;
+        const size_t g = size_t(y0 + 4 * ty + r) * nx + (x0 + 4 * tx + c);
+        const float uu = halfv(U2[r][c >> 1], c & 1);
+        if (real_out) {
+          static_cast<float*>(out)[g] = uu;
+          if (a.check_finite) bad |= (__float_as_uint(uu) & 0x7f800000u) == 0x7f800000u;
+        } else {
+          static_cast<float2*>(out)[g] = make_float2(uu, halfv(V2[r][c >> 1], c & 1));
+        }
+      }
+  }
+  if (bad) atomicOr(a.status, ST_NONFINITE);
+}
+
+// ------------------------------------------------------------------------------------------
+// Reverse pass.
+
+template <bool PERIODIC>
+__global__ void __launch_bounds__(RT_THREADS, 2) k_adjrev_tb2d(const AdjTbArgs a) {
+  extern __shared__ __align__(16) unsigned char at_smem[];
+  RevShared& sh = *reinterpret_cast<RevShared*>(at_smem);
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  const int k = a.k, T = RT_R - 2 * k;
+  const int x0 = blockIdx.x * T - k, y0 = blockIdx.y * T - k;
+  const int nx = a.nx, ny = a.ny;
+  const RegionIdx R = region_idx<PERIODIC>(nx, ny, k, x0, y0, tx, ty);
+#pragma unroll
+  for (int r = 0; r < 5; ++r) {
+    if (r < 4) {
+      sh.fx4[r][tid] = make_float4(face_x<PERIODIC>(R, a.fx, nx, r, 0), face_x<PERIODIC>(R, a.fx, nx, r, 1),
+                                   face_x<PERIODIC>(R, a.fx, nx, r, 2), face_x<PERIODIC>(R, a.fx, nx, r, 3));
+      sh.fxe[r][tid] = face_x<PERIODIC>(R, a.fx, nx, r, 4);
+    }
+    sh.fy4[r][tid] = make_float4(face_y<PERIODIC>(R, a.fy, nx, ny, r, 0), face_y<PERIODIC>(R, a.fy, nx, ny, r, 1),
+                                 face_y<PERIODIC>(R, a.fy, nx, ny, r, 2), face_y<PERIODIC>(R, a.fy, nx, ny, r, 3));
+  }
+  // lam as horizontal cell pairs: LX[r][h] = (Re lam of cell (r, 2h), of cell (r, 2h + 1))
+  float2 LX[4][2], LY[4][2];
+#pragma unroll
+  for (int r = 0; r < 4; ++r)
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      float lx = 0.f, ly = 0.f;
+      if (PERIODIC || (R.inside & (1u << (4 * r + c)))) {
+        const size_t g = size_t(R.gyr[r]) * nx + R.gxc[c];
+        if (a.l_mode == 1) {
+          const float2 w = static_cast<const float2*>(a.L_in)[g];
+          lx = w.x;
+          ly = w.y;
+        } else if (a.l_mode == 2) {
+          lx = static_cast<const float2*>(a.L_in)[g].x;
+        } else {
+          lx = static_cast<const float*>(a.L_in)[g];
+        }
+      }
+      set_half(LX[r][c >> 1], c & 1, lx);
+      set_half(LY[r][c >> 1], c & 1, ly);
+    }
+  // sensitivity sums of each cell's north faces (registers) and east faces (shared slots)
+  float2 SN[4][2];
+#pragma unroll
+  for (int r = 0; r < 4; ++r) {
+#pragma unroll
+    for (int h = 0; h < 2; ++h) SN[r][h] = make_float2(0.f, 0.f);
+    sh.se[r][tid] = make_float4(0.f, 0.f, 0.f, 0.f);
+  }
+
+  const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+  for (int j = 0; j < a.nst; ++j) {
+    const int b = j & 1;
+    const float ca = a.ca[j], cb = a.cb[j];
+    const float hr = 0.5f * ca, hi = 0.5f * cb;
+    const void* Wp = a.W[j];
+    const bool wc = a.w_complex[j] != 0;
+    // Y = -(c/2) W^l of row r of the thread's cells (0 outside a Dirichlet grid), two rows
+    // live at a time
+    auto yrow = [&](int r, float2 (&yx2)[2], float2 (&yy2)[2]) {
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        float wx = 0.f, wy = 0.f;
+        if (PERIODIC || (R.inside & (1u << (4 * r + c)))) {
+          const int g = R.gyr[r] * nx + R.gxc[c];  // cells < 2^31 (checked on the host)
+          if (wc) {
+            const float2 w = static_cast<const float2*>(Wp)[g];
+            wx = w.x;
+            wy = w.y;
+          } else {
+            wx = static_cast<const float*>(Wp)[g];
+          }
+        }
+        set_half(yx2[c >> 1], c & 1, hi * wy - hr * wx);
+        set_half(yy2[c >> 1], c & 1, -(hi * wx) - hr * wy);
+      }
+    };
+    float2 YXc[2], YYc[2];
+    yrow(0, YXc, YYc);
+    sh.bot[b][0][ty][tx] = make_float4(LX[0][0].x, LX[0][0].y, LX[0][1].x, LX[0][1].y);
+    sh.bot[b][1][ty][tx] = make_float4(LY[0][0].x, LY[0][0].y, LY[0][1].x, LY[0][1].y);
+    sh.bot[b][2][ty][tx] = make_float4(YXc[0].x, YXc[0].y, YXc[1].x, YXc[1].y);
+    sh.bot[b][3][ty][tx] = make_float4(YYc[0].x, YYc[0].y, YYc[1].x, YYc[1].y);
+    sh.top[b][0][ty][tx] = make_float4(LX[3][0].x, LX[3][0].y, LX[3][1].x, LX[3][1].y);
+    sh.top[b][1][ty][tx] = make_float4(LY[3][0].x, LY[3][0].y, LY[3][1].x, LY[3][1].y);
+    __syncthreads();
+    // the region's outermost thread rows have no neighbour row here: their edge goes stale
+    const float4 slx = ty > 0 ? sh.top[b][0][ty - 1][tx] : z4, sly = ty > 0 ? sh.top[b][1][ty - 1][tx] : z4;
+    const float4 nlx = ty < 15 ? sh.bot[b][0][ty + 1][tx] : z4, nly = ty < 15 ? sh.bot[b][1][ty + 1][tx] : z4;
+    const float4 nyx = ty < 15 ? sh.bot[b][2][ty + 1][tx] : z4, nyy = ty < 15 ? sh.bot[b][3][ty + 1][tx] : z4;
+    const float2 ca2 = make_float2(ca, ca), cb2 = make_float2(cb, cb), ncb2 = make_float2(-cb, -cb);
+    float2 dsX[2], dsY[2];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      dsX[h] = sub2(LX[0][h], pairh(slx, h));
+      dsY[h] = sub2(LY[0][h], pairh(sly, h));
+    }
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      const float wX = __shfl_up_sync(0xffffffffu, LX[r][1].y, 1, 16);
+      const float wY = __shfl_up_sync(0xffffffffu, LY[r][1].y, 1, 16);
+      const float eX = __shfl_down_sync(0xffffffffu, LX[r][0].x, 1, 16);
+      const float eY = __shfl_down_sync(0xffffffffu, LY[r][0].x, 1, 16);
+      // Y of the next row (the row above comes from the thread above)
+      float2 YXn[2], YYn[2];
+      if (r < 3) {
+        yrow(r + 1 < 4 ? r + 1 : 3, YXn, YYn);
+      } else {
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          YXn[h] = pairh(nyx, h);
+          YYn[h] = pairh(nyy, h);
+        }
+      }
+      const float yeX = __shfl_down_sync(0xffffffffu, YXc[0].x, 1, 16);
+      const float yeY = __shfl_down_sync(0xffffffffu, YYc[0].x, 1, 16);
+      const float lx[6] = {wX, LX[r][0].x, LX[r][0].y, LX[r][1].x, LX[r][1].y, eX};
+      const float ly[6] = {wY, LY[r][0].x, LY[r][0].y, LY[r][1].x, LY[r][1].y, eY};
+      const float yx[5] = {YXc[0].x, YXc[0].y, YXc[1].x, YXc[1].y, yeX};
+      const float yy[5] = {YYc[0].x, YYc[0].y, YYc[1].x, YYc[1].y, yeY};
+      // lam differences across x faces 0..4 (face c between cells c - 1 and c)
+      float dX[5], dY[5];
+#pragma unroll
+      for (int c = 0; c < 5; ++c) {
+        dX[c] = lx[c + 1] - lx[c];
+        dY[c] = ly[c + 1] - ly[c];
+      }
+      const float4 k4 = sh.fx4[r][tid];
+      const float kx[5] = {k4.x, k4.y, k4.z, k4.w, sh.fxe[r][tid]};
+      float2 fX[2], fY[2];
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int c = 2 * h;
+        fX[h].x = kx[c + 1] * dX[c + 1] - kx[c] * dX[c];
+        fX[h].y = kx[c + 2] * dX[c + 2] - kx[c + 1] * dX[c + 1];
+        fY[h].x = kx[c + 1] * dY[c + 1] - kx[c] * dY[c];
+        fY[h].y = kx[c + 2] * dY[c + 2] - kx[c + 1] * dY[c + 1];
+      }
+      {  // east faces of cells 0..3
+        float4 se = sh.se[r][tid];
+        se.x += dX[1] * (yx[1] - yx[0]) + dY[1] * (yy[1] - yy[0]);
+        se.y += dX[2] * (yx[2] - yx[1]) + dY[2] * (yy[2] - yy[1]);
+        se.z += dX[3] * (yx[3] - yx[2]) + dY[3] * (yy[3] - yy[2]);
+        se.w += dX[4] * (yx[4] - yx[3]) + dY[4] * (yy[4] - yy[3]);
+        sh.se[r][tid] = se;
+      }
+      const float4 ks4 = sh.fy4[r][tid], kn4 = sh.fy4[r + 1][tid];
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const float2 nX = r < 3 ? LX[r + 1][h] : pairh(nlx, h);
+        const float2 nY = r < 3 ? LY[r + 1][h] : pairh(nly, h);
+        const float2 dnX = sub2(nX, LX[r][h]), dnY = sub2(nY, LY[r][h]);
+        // north faces, two cells per instruction
+        SN[r][h] = __ffma2_rn(dnY, sub2(YYn[h], YYc[h]), __ffma2_rn(dnX, sub2(YXn[h], YXc[h]), SN[r][h]));
+        const float2 ks = pairh(ks4, h), kn = pairh(kn4, h);
+        const float2 nks = make_float2(-ks.x, -ks.y);
+        fX[h] = __ffma2_rn(nks, dsX[h], __ffma2_rn(kn, dnX, fX[h]));
+        fY[h] = __ffma2_rn(nks, dsY[h], __ffma2_rn(kn, dnY, fY[h]));
+        // lam += conj(c) A lam
+        float2 ox = __ffma2_rn(cb2, fY[h], __ffma2_rn(ca2, fX[h], LX[r][h]));
+        float2 oy = __ffma2_rn(ncb2, fX[h], __ffma2_rn(ca2, fY[h], LY[r][h]));
+        if (!PERIODIC) {
+          if (!(R.inside & (1u << (4 * r + 2 * h)))) ox.x = oy.x = 0.f;
+          if (!(R.inside & (1u << (4 * r + 2 * h + 1)))) ox.y = oy.y = 0.f;
+        }
+        LX[r][h] = ox;
+        LY[r][h] = oy;
+        dsX[h] = dnX;
+        dsY[h] = dnY;
+      }
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        YXc[h] = YXn[h];
+        YYc[h] = YYn[h];
+      }
+    }
+  }
+
+  // dJ/dkappa of each cell: its east and north sums plus its west neighbour's east sum and its
+  // south neighbour's north sum.  The south neighbours' sums of row 0 come through the parity
+  // buffer the last stage did not read (its last readers finished before that stage's barrier).
+  const int b = a.nst & 1;
+  sh.top[b][0][ty][tx] = make_float4(SN[3][0].x, SN[3][0].y, SN[3][1].x, SN[3][1].y);
+  __syncthreads();
+  const float4 ss4 = ty > 0 ? sh.top[b][0][ty - 1][tx] : z4;
+  const float ssr[4] = {ss4.x, ss4.y, ss4.z, ss4.w};
+  bool bad = false;
+#pragma unroll
+  for (int r = 0; r < 4; ++r) {
+    const float4 se4 = sh.se[r][tid];
+    const float ser[4] = {se4.x, se4.y, se4.z, se4.w};
+    const float sw0 = __shfl_up_sync(0xffffffffu, se4.w, 1, 16);
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      if (!(R.outm & (1u << (4 * r + c)))) continue;
+      const int gx = x0 + 4 * tx + c, gy = y0 + 4 * ty + r;
+      const size_t g = size_t(gy) * nx + gx;
+      const float lxo = halfv(LX[r][c >> 1], c & 1);
+      a.L_out[g] = make_float2(lxo, halfv(LY[r][c >> 1], c & 1));
+      if (a.check_finite) bad |= (__float_as_uint(lxo) & 0x7f800000u) == 0x7f800000u;
+      if (a.dk) {
+        float se = ser[c], sn = halfv(SN[r][c >> 1], c & 1);
+        float sw = c == 0 ? sw0 : ser[c > 0 ? c - 1 : 0];
+        float ss = r == 0 ? ssr[c] : halfv(SN[r - 1][c >> 1], c & 1);
+        if (!PERIODIC) {  // a boundary face gives all of its sensitivity to its interior cell
+          if (gx == nx - 1) se += se;
+          if (gx == 0) sw += sw;
+          if (gy == ny - 1) sn += sn;
+          if (gy == 0) ss += ss;
+        }
+        a.dk[g] += double((se + sw) + (sn + ss));
+      }
+    }
+  }
+  if (bad) atomicOr(a.status, ST_NONFINITE);
+}
+
+template <bool PERIODIC>
+cudaError_t launch_rev(const AdjTbArgs& a, dim3 grid, cudaStream_t st) {
+  const auto kern = k_adjrev_tb2d<PERIODIC>;
+  static const cudaError_t attr =
+      cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sizeof(RevShared)));
+  if (attr != cudaSuccess) return attr;
+  kern<<<grid, RT_THREADS, sizeof(RevShared), st>>>(a);
+  count_launch();
+  return cudaGetLastError();
+}
+
+AdjTbArgs base_args(const frkc2_problem& p, int k, int nst, const void* fx, const void* fy, unsigned* status) {
+  AdjTbArgs a{};
+  a.nx = int(p.n[0]);
+  a.ny = int(p.n[1]);
+  a.k = k;
+  a.nst = nst;
+  a.fx = static_cast<const float*>(fx);
+  a.fy = static_cast<const float*>(fy);
+  a.status = status;
+  return a;
+}
+
+dim3 region_grid(const frkc2_problem& p, int k) {
+  const int T = RT_R - 2 * k;
+  return dim3(unsigned((p.n[0] + T - 1) / T), unsigned((p.n[1] + T - 1) / T), 1);
+}
+
+}  // namespace
+
+bool adj_tb2d_supported(const frkc2_problem& p, int k) {
+  return p.ndim == 2 && p.precision == FRKC2_FP32 && p.kappa_kind != FRKC2_KAPPA_POWER && k >= 1 &&
+         k <= AT_KMAX && 2 * k < RT_R && p.n[0] * p.n[1] < (int64_t(1) << 31);
+}
+
+cudaError_t launch_tape_tb2d(const frkc2_problem& p, int k, const AdjTbPass& t, const void* fx, const void* fy,
+                             unsigned* status, cudaStream_t st) {
+  AdjTbArgs a = base_args(p, k, t.nst, fx, fy, status);
+  a.in = t.in;
+  a.in_complex = t.in_complex;
+  a.last_real = t.last_real;
+  a.check_finite = t.last_real;
+  for (int j = 0; j < t.nst; ++j) {
+    a.out[j] = t.out[j];
+    a.ca[j] = float(t.ca[j]);
+    a.cb[j] = float(t.cb[j]);
+  }
+  const dim3 grid = region_grid(p, k);
+  if (p.bc == FRKC2_BC_PERIODIC)
+    k_tape_tb2d<true><<<grid, RT_THREADS, 0, st>>>(a);
+  else
+    k_tape_tb2d<false><<<grid, RT_THREADS, 0, st>>>(a);
+  count_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_adjrev_tb2d(const frkc2_problem& p, int k, const AdjTbPass& t, const void* fx, const void* fy,
+                               unsigned* status, cudaStream_t st) {
+  AdjTbArgs a = base_args(p, k, t.nst, fx, fy, status);
+  a.L_in = t.L_in;
+  a.l_mode = t.l_mode;
+  a.L_out = static_cast<float2*>(t.L_out);
+  a.dk = t.dk;
+  a.check_finite = 0;
+  for (int j = 0; j < t.nst; ++j) {
+    a.W[j] = t.W[j];
+    a.w_complex[j] = t.w_complex[j];
+    a.ca[j] = float(t.ca[j]);
+    a.cb[j] = float(t.cb[j]);
+  }
+  const dim3 grid = region_grid(p, k);
+  return p.bc == FRKC2_BC_PERIODIC ? launch_rev<true>(a, grid, st) : launch_rev<false>(a, grid, st);
+}
+
+}  // namespace frkc2

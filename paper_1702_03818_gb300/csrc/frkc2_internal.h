@@ -111,6 +111,30 @@ struct AdjStreamArgs {
 };
 cudaError_t launch_adj_stream2d(const frkc2_problem& p, const AdjStreamArgs& a, cudaStream_t st);
 
+// Temporally blocked FP32 adjoint (2D fixed conductivity): one pass of nst <= k stages.
+struct AdjTbPass {
+  int nst;
+  // tape pass: forward stages from W^{l0}; out[j] receives W^{l0+1+j} (interleaved), the last
+  // as a real array when last_real (the step output)
+  const void* in;
+  int in_complex;
+  void* out[16];
+  int last_real;
+  // reverse pass: stage j is the j-th from the end; W[j] its tape entry (real when !w_complex)
+  const void* W[16];
+  int w_complex[16];
+  const void* L_in;
+  int l_mode;  // 0: real array, 1: interleaved, 2: real part of an interleaved array
+  void* L_out;
+  double* dk;
+  double ca[16], cb[16];  // dt a_l / dx^2 of stage j
+};
+bool adj_tb2d_supported(const frkc2_problem& p, int k);
+cudaError_t launch_tape_tb2d(const frkc2_problem& p, int k, const AdjTbPass& t, const void* fx, const void* fy,
+                             unsigned* status, cudaStream_t st);
+cudaError_t launch_adjrev_tb2d(const frkc2_problem& p, int k, const AdjTbPass& t, const void* fx, const void* fy,
+                               unsigned* status, cudaStream_t st);
+
 void count_launch(int n = 1);
 
 // SM count and resident CTAs per SM of a kernel (at least 1).  Launchers keep the result in a

@@ -160,3 +160,50 @@ def test_split_forward_backward_equals_combined(shape, bc):
     assert np.array_equal(du.cpu().numpy(), du2) and np.array_equal(dk.cpu().numpy(), dk2)
     ref_u, ref_k = O.frkc2_adjoint(u0, O.plan(s)["a"], dt, oracle_problem(2, bc, "field", 1.0, field), nsteps, g)
     assert rel_l2(du2, ref_u) < 1e-10 and rel_l2(dk2, ref_k) < 1e-10
+
+
+TB_CASES = [
+    # shape (ny, nx), bc, s, nsteps, ckpt: FP32 fixed-conductivity 2D problems run the
+    # temporally blocked tape and reverse passes (8 stages each): several 64 x 64 regions,
+    # a ragged last pass, grids smaller than a region, segments recomputed from checkpoints
+    ((70, 100), "periodic", 20, 3, 2),
+    ((61, 97), "dirichlet", 12, 2, 1),
+    ((3, 5), "periodic", 8, 2, 2),
+    ((50, 130), "dirichlet", 64, 1, 1),
+    ((49, 49), "periodic", 10, 4, 3),
+]
+
+
+@pytest.mark.parametrize("case", TB_CASES, ids=lambda c: f"{c[0][0]}x{c[0][1]}-{c[1]}-s{c[2]}")
+def test_adjoint_fp32_temporal_blocking_matches_oracle(case):
+    shape, bc, s, nsteps, ckpt = case
+    u0, field = seeded_case(shape, bc, "field", 900 + s)
+    fo = field.astype(np.float32).astype(np.float64)
+    u0o = u0.astype(np.float32).astype(np.float64)
+    opr = oracle_problem(2, bc, "field", 1.0, fo)
+    oplan = O.plan(s)
+    plan = F.frkc2_plan(s)
+    dt = 0.8 * oplan["beta"] / O.rho_bound(opr, u0o)
+    g = np.random.default_rng(8).standard_normal(shape).astype(np.float32).astype(np.float64)
+    ref_u, ref_k = O.frkc2_adjoint(u0o, oplan["a"], dt, opr, nsteps, g)
+    du, dk = gpu_adjoint(plan, shape, bc, "field", "fp32", u0, field, dt, nsteps, ckpt, g)
+    assert rel_l2(du, ref_u) < 2e-3, rel_l2(du, ref_u)
+    assert rel_l2(dk, ref_k) < 2e-3, rel_l2(dk, ref_k)
+
+
+def test_adjoint_fp32_dot_product_with_fp32_forward():
+    """<J v, w> = <v, J^T w> between the FP32 forward (register-tiled passes) and the FP32
+    temporally blocked adjoint, to FP32 rounding."""
+    shape = (96, 80)
+    _, field = seeded_case(shape, "periodic", "field", 47)
+    rng = np.random.default_rng(48)
+    v = rng.standard_normal(shape).astype(np.float32).astype(np.float64)
+    w = rng.standard_normal(shape).astype(np.float32).astype(np.float64)
+    s, nsteps = 24, 3
+    plan = F.frkc2_plan(s)
+    opr = oracle_problem(2, "periodic", "field", 1.0, field.astype(np.float32).astype(np.float64))
+    dt = 0.9 * O.beta(s) / O.rho_bound(opr)
+    Jv = gpu_forward(plan, shape, "periodic", "field", "fp32", v, field, dt, nsteps)
+    JTw, _ = gpu_adjoint(plan, shape, "periodic", "field", "fp32", v, field, dt, nsteps, 2, w, want_dk=False)
+    lhs, rhs = float(np.vdot(Jv, w)), float(np.vdot(v, JTw))
+    assert abs(lhs - rhs) < 1e-4 * np.linalg.norm(Jv) * np.linalg.norm(w), (lhs, rhs)
