@@ -15,11 +15,15 @@
 //   G_f = Re(conj(lam_m - lam_i)(Y_m - Y_i)),            Y = -(c_l / 2) W^l,
 // half of the face's sensitivity to each of its cells (the 1/2 folded into Y; a Dirichlet
 // boundary face gives all of it to its interior cell), both with lam^{l+1}, before the update.
-// lam stays in registers for the k stages; each cell sums the sensitivities of its east and
-// north faces in registers and the cell's dJ/dkappa is formed once per pass from its own two
-// sums and those of its west and south neighbours, then added to the FP64 accumulator.  Per
-// cell-stage the pass reads the tape entry W^l (8 bytes; the halo recomputes (64/48)^2 of it
-// at k = 8) and, once per pass, lam in and out, the faces and the accumulator.
+// lam stays in registers for the k stages and each cell sums its dJ/dkappa over them in a
+// register (its east and north faces' sensitivities formed by itself, the west one by shuffle,
+// the south one from the row below -- for a thread's bottom row from the thread below, one
+// stage later), added to the FP64 accumulator once per pass.  The tape entries arrive by
+// cp.async in a per-thread ring in shared memory (the thread's four rows and the row above),
+// each row's entry for the next stage issued as soon as the current one is read, so the loads
+// run a whole stage ahead of their use without holding registers.  Per cell-stage the pass
+// reads the tape entry W^l (8 bytes; the halo recomputes (64/48)^2 of it at k = 8) and, once
+// per pass, lam in and out, the faces and the accumulator.
 #include <cuda_runtime.h>
 
 #include "frkc2_internal.h"
@@ -55,13 +59,31 @@ struct AdjTbArgs {
 };
 
 struct RevShared {
-  float4 bot[2][4][16][16];  // [parity][lam x, lam y, Y x, Y y][ty][tx]: the thread's row 0
-  float4 top[2][2][16][16];  // [parity][lam x, lam y]: its row 3
-  float4 fx4[4][RT_THREADS];  // x faces 0..3 of row r (thread-private slots)
-  float fxe[4][RT_THREADS];   // x face 4 of row r
-  float4 fy4[5][RT_THREADS];  // y face r of columns 0..3 (r = 4: north of row 3)
-  float4 se[4][RT_THREADS];   // east-face sensitivity sums of row r (thread-private slots)
+  float4 bot[2][2][16][16];  // [parity][lam x, lam y][ty][tx]: the thread's row 0
+  float4 top[2][3][16][16];  // [parity][lam x, lam y, north-face sensitivity][ty][tx]: its row 3
+  float4 fx4[4][RT_THREADS];  // x faces 0..3 of row r (face 4 is the east thread's face 0)
+  float4 fy4[4][RT_THREADS];  // y faces of row r (row 4 is the north thread's row 0)
+  float4 ring[5][2][RT_THREADS];  // tape entries of the thread's rows 0..3 and the row above,
+                                  // two cells per float4, filled by cp.async a stage ahead
 };
+
+__device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(unsigned(__cvta_generic_to_shared(smem))), "l"(gmem)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async4(void* smem, const void* gmem) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(unsigned(__cvta_generic_to_shared(smem))), "l"(gmem)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(unsigned(__cvta_generic_to_shared(smem))), "l"(gmem)
+               : "memory");
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+// at most 4 groups still in flight: with one group committed per ring row and stage, the
+// group of the row about to be read (issued a stage earlier) has landed
+__device__ __forceinline__ void cp_wait4() { asm volatile("cp.async.wait_group 4;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_wait0() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
 
 // Grid rows / columns of a thread's cells (fifth entry: the next row / column), their
 // in-grid flags, the Dirichlet inside mask and the output-tile mask (bit 4r + c).
@@ -256,16 +278,70 @@ __global__ void __launch_bounds__(RT_THREADS, 2) k_adjrev_tb2d(const AdjTbArgs a
   const int x0 = blockIdx.x * T - k, y0 = blockIdx.y * T - k;
   const int nx = a.nx, ny = a.ny;
   const RegionIdx R = region_idx<PERIODIC>(nx, ny, k, x0, y0, tx, ty);
+
+  // tape entries of stage jj for ring row i (i = 4: the grid row above the thread's rows):
+  // complex entries as (x, y) per cell, two cells per float4; real entries as the four values
+  // of ring[i][0].  Four consecutive aligned cells go as 16-byte copies.
+  auto issue = [&](int jj, int i) {
+    if (jj < a.nst) {
+      const bool wc = a.w_complex[jj] != 0;
+      const char* Wp = static_cast<const char*>(a.W[jj]);
+      const int g0 = R.gyr[i] * nx + R.gxc[0];  // cells < 2^31 (checked on the host)
+      const bool run = PERIODIC ? R.gxc[3] == R.gxc[0] + 3 : (R.yin[i] && R.xin[0] && R.xin[3]);
+      if (run && (g0 & (wc ? 1 : 3)) == 0) {
+        if (wc) {
+          cp_async16(&sh.ring[i][0][tid], Wp + size_t(g0) * 8);
+          cp_async16(&sh.ring[i][1][tid], Wp + size_t(g0) * 8 + 16);
+        } else {
+          cp_async16(&sh.ring[i][0][tid], Wp + size_t(g0) * 4);
+        }
+      } else {
 #pragma unroll
-  for (int r = 0; r < 5; ++r) {
-    if (r < 4) {
-      sh.fx4[r][tid] = make_float4(face_x<PERIODIC>(R, a.fx, nx, r, 0), face_x<PERIODIC>(R, a.fx, nx, r, 1),
-                                   face_x<PERIODIC>(R, a.fx, nx, r, 2), face_x<PERIODIC>(R, a.fx, nx, r, 3));
-      sh.fxe[r][tid] = face_x<PERIODIC>(R, a.fx, nx, r, 4);
+        for (int c = 0; c < 4; ++c) {
+          if (!(PERIODIC || (R.yin[i] && R.xin[c]))) continue;
+          const int g = R.gyr[i] * nx + R.gxc[c];
+          if (wc)
+            cp_async8(reinterpret_cast<float*>(&sh.ring[i][c >> 1][tid]) + 2 * (c & 1), Wp + size_t(g) * 8);
+          else
+            cp_async4(reinterpret_cast<float*>(&sh.ring[i][0][tid]) + c, Wp + size_t(g) * 4);
+        }
+      }
     }
+    cp_commit();
+  };
+#pragma unroll
+  for (int i = 0; i < 5; ++i) issue(0, i);
+
+#pragma unroll
+  for (int r = 0; r < 4; ++r) {
+    sh.fx4[r][tid] = make_float4(face_x<PERIODIC>(R, a.fx, nx, r, 0), face_x<PERIODIC>(R, a.fx, nx, r, 1),
+                                 face_x<PERIODIC>(R, a.fx, nx, r, 2), face_x<PERIODIC>(R, a.fx, nx, r, 3));
     sh.fy4[r][tid] = make_float4(face_y<PERIODIC>(R, a.fy, nx, ny, r, 0), face_y<PERIODIC>(R, a.fy, nx, ny, r, 1),
                                  face_y<PERIODIC>(R, a.fy, nx, ny, r, 2), face_y<PERIODIC>(R, a.fy, nx, ny, r, 3));
   }
+  // the faces beyond the thread's own cells, kept in registers: x face 4 of each row and the
+  // y faces of row 4
+  float kxe[4];
+#pragma unroll
+  for (int r = 0; r < 4; ++r) kxe[r] = face_x<PERIODIC>(R, a.fx, nx, r, 4);
+  const float4 kyn = make_float4(face_y<PERIODIC>(R, a.fy, nx, ny, 4, 0), face_y<PERIODIC>(R, a.fy, nx, ny, 4, 1),
+                                 face_y<PERIODIC>(R, a.fy, nx, ny, 4, 2), face_y<PERIODIC>(R, a.fy, nx, ny, 4, 3));
+  // Dirichlet: a boundary face gives all of its sensitivity to its interior cell
+  unsigned bE = 0, bW = 0, bN = 0, bS = 0;
+  if (!PERIODIC) {
+#pragma unroll
+    for (int r = 0; r < 4; ++r)
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        const int gx = x0 + 4 * tx + c, gy = y0 + 4 * ty + r, bit = 1 << (4 * r + c);
+        if (gx == nx - 1) bE |= bit;
+        if (gx == 0) bW |= bit;
+        if (gy == ny - 1) bN |= bit;
+        if (gy == 0) bS |= bit;
+      }
+  }
+  auto wgt = [&](unsigned m, int bit, float g) { return (!PERIODIC && (m & (1u << bit))) ? g + g : g; };
+
   // lam as horizontal cell pairs: LX[r][h] = (Re lam of cell (r, 2h), of cell (r, 2h + 1))
   float2 LX[4][2], LY[4][2];
 #pragma unroll
@@ -288,55 +364,54 @@ __global__ void __launch_bounds__(RT_THREADS, 2) k_adjrev_tb2d(const AdjTbArgs a
       set_half(LX[r][c >> 1], c & 1, lx);
       set_half(LY[r][c >> 1], c & 1, ly);
     }
-  // sensitivity sums of each cell's north faces (registers) and east faces (shared slots)
-  float2 SN[4][2];
+  float dk[4][4];  // dJ/dkappa of each cell over the pass's stages
 #pragma unroll
-  for (int r = 0; r < 4; ++r) {
+  for (int r = 0; r < 4; ++r)
 #pragma unroll
-    for (int h = 0; h < 2; ++h) SN[r][h] = make_float2(0.f, 0.f);
-    sh.se[r][tid] = make_float4(0.f, 0.f, 0.f, 0.f);
-  }
+    for (int c = 0; c < 4; ++c) dk[r][c] = 0.f;
+  float gn3[4] = {0.f, 0.f, 0.f, 0.f};  // north-face sensitivities of row 3, passed up a stage later
+  __syncthreads();  // faces in shared memory
 
   const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
   for (int j = 0; j < a.nst; ++j) {
     const int b = j & 1;
     const float ca = a.ca[j], cb = a.cb[j];
     const float hr = 0.5f * ca, hi = 0.5f * cb;
-    const void* Wp = a.W[j];
     const bool wc = a.w_complex[j] != 0;
-    // Y = -(c/2) W^l of row r of the thread's cells (0 outside a Dirichlet grid), two rows
-    // live at a time
-    auto yrow = [&](int r, float2 (&yx2)[2], float2 (&yy2)[2]) {
+    // Y = -(c/2) W^l of ring row i (0 outside a Dirichlet grid); ring rows hold stage j now
+    auto yrow = [&](int i, float2 (&yx2)[2], float2 (&yy2)[2]) {
+      const float4 p0 = sh.ring[i][0][tid], p1 = sh.ring[i][1][tid];
+      const float w[8] = {p0.x, p0.y, p0.z, p0.w, p1.x, p1.y, p1.z, p1.w};
+      const float wr[4] = {p0.x, p0.y, p0.z, p0.w};
 #pragma unroll
       for (int c = 0; c < 4; ++c) {
-        float wx = 0.f, wy = 0.f;
-        if (PERIODIC || (R.inside & (1u << (4 * r + c)))) {
-          const int g = R.gyr[r] * nx + R.gxc[c];  // cells < 2^31 (checked on the host)
-          if (wc) {
-            const float2 w = static_cast<const float2*>(Wp)[g];
-            wx = w.x;
-            wy = w.y;
-          } else {
-            wx = static_cast<const float*>(Wp)[g];
-          }
-        }
+        const bool in = PERIODIC || (R.yin[i] && R.xin[c]);
+        const float wx = in ? (wc ? w[2 * c] : wr[c]) : 0.f;
+        const float wy = in && wc ? w[2 * c + 1] : 0.f;
         set_half(yx2[c >> 1], c & 1, hi * wy - hr * wx);
         set_half(yy2[c >> 1], c & 1, -(hi * wx) - hr * wy);
       }
     };
+    cp_wait4();
     float2 YXc[2], YYc[2];
     yrow(0, YXc, YYc);
+    issue(j + 1, 0);
     sh.bot[b][0][ty][tx] = make_float4(LX[0][0].x, LX[0][0].y, LX[0][1].x, LX[0][1].y);
     sh.bot[b][1][ty][tx] = make_float4(LY[0][0].x, LY[0][0].y, LY[0][1].x, LY[0][1].y);
-    sh.bot[b][2][ty][tx] = make_float4(YXc[0].x, YXc[0].y, YXc[1].x, YXc[1].y);
-    sh.bot[b][3][ty][tx] = make_float4(YYc[0].x, YYc[0].y, YYc[1].x, YYc[1].y);
     sh.top[b][0][ty][tx] = make_float4(LX[3][0].x, LX[3][0].y, LX[3][1].x, LX[3][1].y);
     sh.top[b][1][ty][tx] = make_float4(LY[3][0].x, LY[3][0].y, LY[3][1].x, LY[3][1].y);
+    sh.top[b][2][ty][tx] = make_float4(gn3[0], gn3[1], gn3[2], gn3[3]);  // previous stage's
     __syncthreads();
     // the region's outermost thread rows have no neighbour row here: their edge goes stale
     const float4 slx = ty > 0 ? sh.top[b][0][ty - 1][tx] : z4, sly = ty > 0 ? sh.top[b][1][ty - 1][tx] : z4;
     const float4 nlx = ty < 15 ? sh.bot[b][0][ty + 1][tx] : z4, nly = ty < 15 ? sh.bot[b][1][ty + 1][tx] : z4;
-    const float4 nyx = ty < 15 ? sh.bot[b][2][ty + 1][tx] : z4, nyy = ty < 15 ? sh.bot[b][3][ty + 1][tx] : z4;
+    {  // the south faces of row 0, from the thread below, one stage late
+      const float4 gs = ty > 0 ? sh.top[b][2][ty - 1][tx] : z4;
+      dk[0][0] += wgt(bS, 0, gs.x);
+      dk[0][1] += wgt(bS, 1, gs.y);
+      dk[0][2] += wgt(bS, 2, gs.z);
+      dk[0][3] += wgt(bS, 3, gs.w);
+    }
     const float2 ca2 = make_float2(ca, ca), cb2 = make_float2(cb, cb), ncb2 = make_float2(-cb, -cb);
     float2 dsX[2], dsY[2];
 #pragma unroll
@@ -344,23 +419,18 @@ __global__ void __launch_bounds__(RT_THREADS, 2) k_adjrev_tb2d(const AdjTbArgs a
       dsX[h] = sub2(LX[0][h], pairh(slx, h));
       dsY[h] = sub2(LY[0][h], pairh(sly, h));
     }
+    float gs[4] = {0.f, 0.f, 0.f, 0.f};  // north-face sensitivities of the row below (this stage)
 #pragma unroll
     for (int r = 0; r < 4; ++r) {
+      // Y of the row above (ring row r + 1; row 4 is the grid row above the thread's)
+      cp_wait4();
+      float2 YXn[2], YYn[2];
+      yrow(r + 1, YXn, YYn);
+      issue(j + 1, r + 1);
       const float wX = __shfl_up_sync(0xffffffffu, LX[r][1].y, 1, 16);
       const float wY = __shfl_up_sync(0xffffffffu, LY[r][1].y, 1, 16);
       const float eX = __shfl_down_sync(0xffffffffu, LX[r][0].x, 1, 16);
       const float eY = __shfl_down_sync(0xffffffffu, LY[r][0].x, 1, 16);
-      // Y of the next row (the row above comes from the thread above)
-      float2 YXn[2], YYn[2];
-      if (r < 3) {
-        yrow(r + 1 < 4 ? r + 1 : 3, YXn, YYn);
-      } else {
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-          YXn[h] = pairh(nyx, h);
-          YYn[h] = pairh(nyy, h);
-        }
-      }
       const float yeX = __shfl_down_sync(0xffffffffu, YXc[0].x, 1, 16);
       const float yeY = __shfl_down_sync(0xffffffffu, YYc[0].x, 1, 16);
       const float lx[6] = {wX, LX[r][0].x, LX[r][0].y, LX[r][1].x, LX[r][1].y, eX};
@@ -375,7 +445,7 @@ __global__ void __launch_bounds__(RT_THREADS, 2) k_adjrev_tb2d(const AdjTbArgs a
         dY[c] = ly[c + 1] - ly[c];
       }
       const float4 k4 = sh.fx4[r][tid];
-      const float kx[5] = {k4.x, k4.y, k4.z, k4.w, sh.fxe[r][tid]};
+      const float kx[5] = {k4.x, k4.y, k4.z, k4.w, kxe[r]};
       float2 fX[2], fY[2];
 #pragma unroll
       for (int h = 0; h < 2; ++h) {
@@ -385,22 +455,21 @@ __global__ void __launch_bounds__(RT_THREADS, 2) k_adjrev_tb2d(const AdjTbArgs a
         fY[h].x = kx[c + 1] * dY[c + 1] - kx[c] * dY[c];
         fY[h].y = kx[c + 2] * dY[c + 2] - kx[c + 1] * dY[c + 1];
       }
-      {  // east faces of cells 0..3
-        float4 se = sh.se[r][tid];
-        se.x += dX[1] * (yx[1] - yx[0]) + dY[1] * (yy[1] - yy[0]);
-        se.y += dX[2] * (yx[2] - yx[1]) + dY[2] * (yy[2] - yy[1]);
-        se.z += dX[3] * (yx[3] - yx[2]) + dY[3] * (yy[3] - yy[2]);
-        se.w += dX[4] * (yx[4] - yx[3]) + dY[4] * (yy[4] - yy[3]);
-        sh.se[r][tid] = se;
-      }
-      const float4 ks4 = sh.fy4[r][tid], kn4 = sh.fy4[r + 1][tid];
+      // east-face sensitivities; the west face of cell 0 is the west thread's cell 3 east face
+      float ge[4];
+#pragma unroll
+      for (int c = 0; c < 4; ++c) ge[c] = dX[c + 1] * (yx[c + 1] - yx[c]) + dY[c + 1] * (yy[c + 1] - yy[c]);
+      const float gw0 = __shfl_up_sync(0xffffffffu, ge[3], 1, 16);
+      const float4 ks4 = sh.fy4[r][tid];
+      const float4 kn4 = r < 3 ? sh.fy4[r + 1 < 4 ? r + 1 : 3][tid] : kyn;
+      float2 gn2[2];
 #pragma unroll
       for (int h = 0; h < 2; ++h) {
-        const float2 nX = r < 3 ? LX[r + 1][h] : pairh(nlx, h);
-        const float2 nY = r < 3 ? LY[r + 1][h] : pairh(nly, h);
+        const float2 nX = r < 3 ? LX[r + 1 < 4 ? r + 1 : 3][h] : pairh(nlx, h);
+        const float2 nY = r < 3 ? LY[r + 1 < 4 ? r + 1 : 3][h] : pairh(nly, h);
         const float2 dnX = sub2(nX, LX[r][h]), dnY = sub2(nY, LY[r][h]);
-        // north faces, two cells per instruction
-        SN[r][h] = __ffma2_rn(dnY, sub2(YYn[h], YYc[h]), __ffma2_rn(dnX, sub2(YXn[h], YXc[h]), SN[r][h]));
+        // north-face sensitivities, two cells per instruction
+        gn2[h] = __ffma2_rn(dnY, sub2(YYn[h], YYc[h]), __fmul2_rn(dnX, sub2(YXn[h], YXc[h])));
         const float2 ks = pairh(ks4, h), kn = pairh(kn4, h);
         const float2 nks = make_float2(-ks.x, -ks.y);
         fX[h] = __ffma2_rn(nks, dsX[h], __ffma2_rn(kn, dnX, fX[h]));
@@ -417,51 +486,48 @@ __global__ void __launch_bounds__(RT_THREADS, 2) k_adjrev_tb2d(const AdjTbArgs a
         dsX[h] = dnX;
         dsY[h] = dnY;
       }
+      const float gn[4] = {gn2[0].x, gn2[0].y, gn2[1].x, gn2[1].y};
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        const int bit = 4 * r + c;
+        const float gwc = c == 0 ? gw0 : ge[c > 0 ? c - 1 : 0];
+        float acc = wgt(bE, bit, ge[c]) + wgt(bW, bit, gwc) + wgt(bN, bit, gn[c]);
+        if (r > 0) acc += wgt(bS, bit, gs[c]);  // row 0's comes from the thread below, later
+        dk[r][c] += acc;
+        gs[c] = gn[c];
+      }
 #pragma unroll
       for (int h = 0; h < 2; ++h) {
         YXc[h] = YXn[h];
         YYc[h] = YYn[h];
       }
     }
-  }
-
-  // dJ/dkappa of each cell: its east and north sums plus its west neighbour's east sum and its
-  // south neighbour's north sum.  The south neighbours' sums of row 0 come through the parity
-  // buffer the last stage did not read (its last readers finished before that stage's barrier).
-  const int b = a.nst & 1;
-  sh.top[b][0][ty][tx] = make_float4(SN[3][0].x, SN[3][0].y, SN[3][1].x, SN[3][1].y);
-  __syncthreads();
-  const float4 ss4 = ty > 0 ? sh.top[b][0][ty - 1][tx] : z4;
-  const float ssr[4] = {ss4.x, ss4.y, ss4.z, ss4.w};
-  bool bad = false;
 #pragma unroll
-  for (int r = 0; r < 4; ++r) {
-    const float4 se4 = sh.se[r][tid];
-    const float ser[4] = {se4.x, se4.y, se4.z, se4.w};
-    const float sw0 = __shfl_up_sync(0xffffffffu, se4.w, 1, 16);
+    for (int c = 0; c < 4; ++c) gn3[c] = gs[c];
+  }
+  cp_wait0();
+
+  // the last stage's south faces of row 0, through the parity buffer the last stage did not
+  // read (its last readers finished before that stage's barrier)
+  const int b = a.nst & 1;
+  sh.top[b][2][ty][tx] = make_float4(gn3[0], gn3[1], gn3[2], gn3[3]);
+  __syncthreads();
+  {
+    const float4 gs = ty > 0 ? sh.top[b][2][ty - 1][tx] : z4;
+    dk[0][0] += wgt(bS, 0, gs.x);
+    dk[0][1] += wgt(bS, 1, gs.y);
+    dk[0][2] += wgt(bS, 2, gs.z);
+    dk[0][3] += wgt(bS, 3, gs.w);
+  }
+#pragma unroll
+  for (int r = 0; r < 4; ++r)
 #pragma unroll
     for (int c = 0; c < 4; ++c) {
       if (!(R.outm & (1u << (4 * r + c)))) continue;
-      const int gx = x0 + 4 * tx + c, gy = y0 + 4 * ty + r;
-      const size_t g = size_t(gy) * nx + gx;
-      const float lxo = halfv(LX[r][c >> 1], c & 1);
-      a.L_out[g] = make_float2(lxo, halfv(LY[r][c >> 1], c & 1));
-      if (a.check_finite) bad |= (__float_as_uint(lxo) & 0x7f800000u) == 0x7f800000u;
-      if (a.dk) {
-        float se = ser[c], sn = halfv(SN[r][c >> 1], c & 1);
-        float sw = c == 0 ? sw0 : ser[c > 0 ? c - 1 : 0];
-        float ss = r == 0 ? ssr[c] : halfv(SN[r - 1][c >> 1], c & 1);
-        if (!PERIODIC) {  // a boundary face gives all of its sensitivity to its interior cell
-          if (gx == nx - 1) se += se;
-          if (gx == 0) sw += sw;
-          if (gy == ny - 1) sn += sn;
-          if (gy == 0) ss += ss;
-        }
-        a.dk[g] += double((se + sw) + (sn + ss));
-      }
+      const size_t g = size_t(y0 + 4 * ty + r) * nx + (x0 + 4 * tx + c);
+      a.L_out[g] = make_float2(halfv(LX[r][c >> 1], c & 1), halfv(LY[r][c >> 1], c & 1));
+      if (a.dk) a.dk[g] += double(dk[r][c]);
     }
-  }
-  if (bad) atomicOr(a.status, ST_NONFINITE);
 }
 
 template <bool PERIODIC>
