@@ -1,6 +1,8 @@
 // 2D temporally blocked stage pass for FP32 (fixed conductivity) with the state in registers:
-// the computation of one 64 x 64 region, shared by the single-problem pass (pass_tb2d.cu)
-// and the batched persistent launch (batched.cu).
+// the computation of one 64 x 64 region for the batched persistent launch (batched.cu), and
+// the region constants and helpers (RT_R, RT_THREADS, wrap_r, sub2) of the other register-
+// tiled kernels.  The single-problem FP32 pass (pass_tb2d.cu) keeps its own copy of the same
+// computation, which compiles to a faster kernel than this function inlined into one.
 //
 // A CTA of 16 x 16 threads owns a 64 x 64 region: its output tile (64 - 2k)^2 plus a k-cell
 // halo recomputed redundantly (region-edge values go stale one cell per stage, which never
