@@ -466,6 +466,22 @@ def profile_case(F, name: str):
         for _ in range(2):
             v = u.clone()
             F.frkc2_step(plan, pr, dt, 1, 0.0, v, ws, t)
+    elif name in ("stream2d_mixed", "stream2d_fp32"):  # k = 1 streaming pass, 2048^2, s = 16, 1 step
+        n, s = 2048, 16
+        prec = name.split("_")[1]
+        sd = torch.float32 if prec == "fp32" else torch.float64
+        u0 = I.smooth_unit((n, n), 64.0, 3819)
+        k = I.kappa_field((n, n), 3818)
+        plan = F.frkc2_plan(s)
+        kt = torch.as_tensor(k, dtype=torch.float32, device="cuda")
+        pr = F.make_problem(2, (n, n), 1.0, "periodic", "field", prec, kappa_field=kt)
+        rho = torch.zeros(1, dtype=torch.float64, device="cuda")
+        F.frkc2_rho_bound(pr, None, rho)
+        dt = 0.9 * plan.info()["beta"] / rho.item()
+        ws = torch.empty(F.frkc2_workspace_size(pr), dtype=torch.uint8, device="cuda")
+        for _ in range(2):
+            u = torch.as_tensor(u0, dtype=sd, device="cuda")
+            F.frkc2_step(plan, pr, dt, 1, 0.0, u, ws, F.make_tuning(k=1, kernel=2))
     elif name in ("stream2d_df", "tb2d_df"):  # DFLOAT pass, 2048^2 var-kappa, s = 16, 1 step
         n, s = 2048, 16
         t = F.make_tuning(k=1, kernel=2) if name == "stream2d_df" else F.make_tuning(k=8, kernel=3)
