@@ -452,13 +452,14 @@ def profile_case(F, name: str):
         F.frkc2_workspace_reset(ws)
         for _ in range(2):
             F.frkc2_step_batched(plans, probs, dts, [1] * 8, us, ws)
-    elif name in ("generic3d", "stream3d"):  # FP64 kappa(u) pass, 192^3, s = 8 (tile / z-streaming)
+    elif name in ("generic3d", "stream3d", "stream3d_fp32"):  # kappa(u) pass, 192^3, s = 8 (tile / z-streaming)
         n, s = 192, 8
         u0 = I.hotspot3d_u0(n, sigma=15.0, seed=2017)
         plan = F.frkc2_plan(s)
-        pr = F.make_problem(3, (n, n, n), 1.0, "dirichlet", "power", "fp64", kappa_c=1.0, kappa_p=2.5)
+        prec = "fp32" if name.endswith("fp32") else "fp64"
+        pr = F.make_problem(3, (n, n, n), 1.0, "dirichlet", "power", prec, kappa_c=1.0, kappa_p=2.5)
         rho = torch.zeros(1, dtype=torch.float64, device="cuda")
-        u = torch.as_tensor(u0, device="cuda")
+        u = torch.as_tensor(u0, dtype=torch.float32 if prec == "fp32" else torch.float64, device="cuda")
         F.frkc2_rho_bound(pr, u, rho)
         dt = 0.9 * plan.info()["beta"] / rho.item()
         ws = torch.empty(F.frkc2_workspace_size(pr), dtype=torch.uint8, device="cuda")

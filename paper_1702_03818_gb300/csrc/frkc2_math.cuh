@@ -35,6 +35,16 @@ __device__ __forceinline__ void csqrt_principal(T x, T y, T& rr, T& ri) {
   }
 }
 
+// kappa(w) = 1 + c w^2.5 = 1 + c w^2 sqrt(w) for complex w = u + i v (principal branch).
+template <class T>
+__device__ __forceinline__ void kappa_power25(T u, T v, T c, T& kr, T& ki) {
+  T sr, si;
+  csqrt_principal<T>(u, v, sr, si);  // sqrt(0) = 0, so 0^2.5 = 0 needs no test
+  const T qr = u * u - v * v, qi = T(2) * u * v;
+  kr = T(1) + c * (qr * sr - qi * si);
+  ki = c * (qr * si + qi * sr);
+}
+
 // kappa(w) = 1 + c w^p for complex w = u + i v on the principal branch, 0^p = 0 (p > 0).
 // p = 2.5 uses w^2 * sqrt(w); other exponents use the polar form |w|^p e^{i p arg w}.
 template <class T>
