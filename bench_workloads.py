@@ -321,6 +321,53 @@ def ssweep(F):
             "by_s": out}
 
 
+def precision(F):
+    """Error of each reduced precision against the FP64 GPU run of the same 2048^2 var-kappa
+    job (the bench recipe) by stage count and ordering, after 1 and 10 steps: the stage count
+    up to which FP32 state and arithmetic stay within 1e-4 relative L2, and what the
+    float-pair state (DFLOAT) and MIXED give beyond it."""
+    torch = _torch()
+    cfg = I.CONFIGS["varkappa2d"]
+    n = cfg["n"]
+    u0 = I.smooth_unit((n, n), 64.0, cfg["u0_seed"])
+    kap = I.kappa_field((n, n), cfg["kappa_seed"])
+    precs = ("fp64", "fp32", "dfloat", "mixed")
+    probs, wss = {}, {}
+    for prec in precs:
+        kd = torch.float64 if prec == "fp64" else torch.float32
+        kt = torch.as_tensor(kap, dtype=kd, device="cuda")
+        probs[prec] = (F.make_problem(2, (n, n), 1.0, "periodic", "field", prec, kappa_field=kt), kt)
+        wss[prec] = torch.empty(F.frkc2_workspace_size(probs[prec][0]), dtype=torch.uint8, device="cuda")
+    rho = torch.zeros(1, dtype=torch.float64, device="cuda")
+    F.frkc2_rho_bound(probs["fp64"][0], None, rho)
+    rows = {}
+    threshold = {}
+    for order, flag in (("greedy", F.PLAN_GREEDY), ("lebedev", F.PLAN_LEBEDEV)):
+        best = 0
+        for s in (16, 32, 48, 64, 96, 128, 192, 256):
+            plan = F.frkc2_plan(s, flags=flag)
+            info = plan.info()
+            dt = cfg["cfl"] * info["beta"] / rho.item()
+            row = {"Q_over_L2": info["Q"] / s ** 2}
+            for nsteps in (1, 10):
+                outs = {}
+                for prec in precs:
+                    sd = torch.float32 if prec == "fp32" else torch.float64
+                    u = torch.as_tensor(u0, dtype=sd, device="cuda")
+                    F.frkc2_workspace_reset(wss[prec])
+                    F.frkc2_step(plan, probs[prec][0], dt, nsteps, 0.0, u, wss[prec])
+                    outs[prec] = u.double().cpu().numpy()
+                row[f"steps{nsteps}"] = {p: _rel(outs[p], outs["fp64"]) for p in precs if p != "fp64"}
+            rows[f"{order}_s{s}"] = row
+            if row["steps1"]["fp32"] <= 1e-4 and row["steps10"]["fp32"] <= 1e-4 and s > best:
+                best = s
+        threshold[order] = best
+    return {"workload": "precision: 2048^2 var-kappa periodic (bench recipe), error vs the FP64 GPU run by s and "
+                        "ordering, 1 and 10 steps",
+            "metric": "largest s with FP32 rel L2 <= 1e-4 after 1 and 10 steps", "value": threshold,
+            "unit": "stages", "by_s": rows}
+
+
 BRUSS_INST_PER_CELL_STAGE = 41  # 4 Laplacians (4 each), v^2 and v^2 w (8), 4 rhs (9), 4 updates (8)
 BRUSS_BYTES_PER_CELL_STAGE = {"fp64": 64, "fp32": 32}  # 4 state values read and written
 FP64_PEAK_TINST = 152 * 2 * 2.07e9 / 1e12
@@ -396,7 +443,7 @@ def bruss2d(F, hbm_peak_gbs: float = 6787.2):
 
 
 WORKLOADS = {"heat1d": heat1d, "nonlinear3d": nonlinear3d, "adjoint2d": adjoint2d,
-             "batched2d": batched2d, "ssweep": ssweep, "bruss2d": bruss2d}
+             "batched2d": batched2d, "ssweep": ssweep, "bruss2d": bruss2d, "precision": precision}
 
 
 def profile_case(F, name: str):
