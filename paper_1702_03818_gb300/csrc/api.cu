@@ -306,16 +306,19 @@ frkc2_status frkc2_step(frkc2_plan_t plan, const frkc2_problem* prob, double dt,
   }
   if (use_tb_df) {
     // float-pair state (float4 per cell) between passes, in the ua (with va) and ub (with vb) slots
+    // a pass never writes the array it reads (its regions' halos overlap other CTAs' output
+    // tiles): with one pass per step the real state alternates between u and ua
     for (int n = 0; n < nsteps; ++n) {
       for (int q = 0; q < npass; ++q) {
         const int l0 = q * k, kq = std::min(k, s - l0);
         const bool first = q == 0, last = q == npass - 1;
         void* outW = (curU == ua) ? ub : ua;
+        void* outU = last && curU != u ? u : outW;
         a.k = kq;
-        a.U_in = first ? u : curU;
+        a.U_in = curU;
         a.V_in = nullptr;
         a.in_mode = first ? PASS_IO_REAL : PASS_IO_COMPLEX;
-        a.U_out = last ? u : outW;
+        a.U_out = outU;
         a.V_out = nullptr;
         a.out_mode = last ? PASS_IO_REAL : PASS_IO_COMPLEX;
         a.check_finite = last ? 1 : 0;
@@ -325,10 +328,13 @@ frkc2_status frkc2_step(frkc2_plan_t plan, const frkc2_problem* prob, double dt,
           a.caf[j] = float(a.ca[j]);
           a.cbf[j] = float(a.cb[j]);
         }
-        if (launch_pass_tb2d_df(p, a, st) != cudaSuccess) return FRKC2_ECUDA;
-        curU = last ? u : outW;
+        if (launch_pass_tb2d_df(p, a, st, n > 0 || q > 0) != cudaSuccess) return FRKC2_ECUDA;
+        curU = outU;
       }
     }
+    if (curU != u &&
+        cudaMemcpyAsync(u, curU, cells(p) * sizeof(double), cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+      return FRKC2_ECUDA;
     return FRKC2_OK;
   }
   if (use_stream2d) {
@@ -388,7 +394,9 @@ frkc2_status frkc2_step(frkc2_plan_t plan, const frkc2_problem* prob, double dt,
       }
       a.in_mode = curV ? PASS_IO_PLANAR : PASS_IO_REAL;
       a.out_mode = outV ? PASS_IO_PLANAR : PASS_IO_REAL;
-      const cudaError_t e = use_tb ? launch_pass_tb2d(p, a, st)
+      // passes after the first may start while the previous one drains (face conductivities,
+      // written before the first pass, are read before the wait for the previous pass)
+      const cudaError_t e = use_tb ? launch_pass_tb2d(p, a, st, n > 0 || q > 0)
                             : use_stream3d ? launch_pass_stream3d(p, a, st)
                                            : launch_pass_generic(p, a, st);
       if (e != cudaSuccess) return FRKC2_ECUDA;

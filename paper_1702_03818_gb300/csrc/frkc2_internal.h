@@ -85,12 +85,14 @@ cudaError_t launch_err_sum(const frkc2_problem& p, const void* u, const void* h,
 cudaError_t launch_pass_stream2d(const frkc2_problem& p, const PassArgs& a, const void* fen, cudaStream_t st);
 size_t face_pair_bytes(const frkc2_problem& p);
 cudaError_t launch_face_pairs(const frkc2_problem& p, const void* fx, const void* fy, void* out, cudaStream_t st);
-cudaError_t launch_pass_tb2d(const frkc2_problem& p, const PassArgs& a, cudaStream_t st);
+// overlap_previous: the launch may start while the previous launch on the stream (a pass of
+// the same kind) finishes; its CTAs read the pass input only after that launch completes.
+cudaError_t launch_pass_tb2d(const frkc2_problem& p, const PassArgs& a, cudaStream_t st, bool overlap_previous);
 bool small1d_supported(const frkc2_problem& p, int s);
 cudaError_t launch_small1d(const frkc2_problem& p, const frkc2_plan_s& plan, double dt, int nsteps, void* u,
                            const void* fx, unsigned* status, cudaStream_t st);
 cudaError_t launch_pass_stream3d(const frkc2_problem& p, const PassArgs& a, cudaStream_t st);
-cudaError_t launch_pass_tb2d_df(const frkc2_problem& p, const PassArgs& a, cudaStream_t st);
+cudaError_t launch_pass_tb2d_df(const frkc2_problem& p, const PassArgs& a, cudaStream_t st, bool overlap_previous);
 cudaError_t launch_pass_stream2d_df(const frkc2_problem& p, const PassArgs& a, const void* fen, cudaStream_t st);
 cudaError_t launch_pass_paired2d(const frkc2_problem& p, const PassArgs& a, const void* fen, cudaStream_t st);
 bool tb2d_supported(const frkc2_problem& p, int k);

@@ -56,6 +56,9 @@ __global__ void __launch_bounds__(RT_THREADS, FRKC2_TBR_MIN_BLOCKS) k_tb2d_reg(c
   const int T = RT_R - 2 * k;
   const int x0 = blockIdx.x * T - k, y0 = blockIdx.y * T - k;
   const int nx = p.nx, ny = p.ny;
+  // the next pass may be launched as soon as every CTA of this one is running (it then loads
+  // its face conductivities, which no pass writes, and waits below for this pass's state)
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
   const float* __restrict__ Uin = static_cast<const float*>(p.U_in);
   const float* __restrict__ Vin = static_cast<const float*>(p.V_in);
   const float* __restrict__ FX = static_cast<const float*>(p.fx);
@@ -95,6 +98,9 @@ __global__ void __launch_bounds__(RT_THREADS, FRKC2_TBR_MIN_BLOCKS) k_tb2d_reg(c
     }
   }
   // the state as horizontal cell pairs: U2[r][h] = (U[r][2h], U[r][2h + 1]); the y faces too
+  // the previous pass's state is complete and visible after this (a no-op for a launch
+  // without the programmatic-serialization attribute)
+  asm volatile("griddepcontrol.wait;" ::: "memory");
   float2 U2[4][2], V2[4][2], FY2[5][2];
 #pragma unroll
   for (int r = 0; r < 5; ++r)
@@ -224,16 +230,23 @@ bool tb2d_supported(const frkc2_problem& p, int k) {
          2 * k < RT_R;
 }
 
-cudaError_t launch_pass_tb2d(const frkc2_problem& p, const PassArgs& a, cudaStream_t st) {
+cudaError_t launch_pass_tb2d(const frkc2_problem& p, const PassArgs& a, cudaStream_t st, bool overlap_previous) {
   (void)p;
   const int T = RT_R - 2 * a.k;
-  dim3 grid((a.nx + T - 1) / T, (a.ny + T - 1) / T, 1);
-  if (a.bc == FRKC2_BC_PERIODIC)
-    k_tb2d_reg<true><<<grid, RT_THREADS, 0, st>>>(a);
-  else
-    k_tb2d_reg<false><<<grid, RT_THREADS, 0, st>>>(a);
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((a.nx + T - 1) / T, (a.ny + T - 1) / T, 1);
+  cfg.blockDim = dim3(RT_THREADS, 1, 1);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = overlap_previous ? 1 : 0;
+  const cudaError_t e = a.bc == FRKC2_BC_PERIODIC ? cudaLaunchKernelEx(&cfg, k_tb2d_reg<true>, a)
+                                                  : cudaLaunchKernelEx(&cfg, k_tb2d_reg<false>, a);
   count_launch();
-  return cudaGetLastError();
+  return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 }  // namespace frkc2

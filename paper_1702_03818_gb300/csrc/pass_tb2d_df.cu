@@ -60,6 +60,9 @@ __global__ void __launch_bounds__(RT_THREADS, 2) k_tb2d_df(const PassArgs p) {
   const int T = RT_R - 2 * k;
   const int x0 = blockIdx.x * T - k, y0 = blockIdx.y * T - k;
   const int nx = p.nx, ny = p.ny;
+  // the next pass may be launched as soon as every CTA of this one is running (it then stores
+  // its face conductivities, which no pass writes, and waits below for this pass's state)
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
   const float* __restrict__ FX = static_cast<const float*>(p.fx);
   const float* __restrict__ FY = static_cast<const float*>(p.fy);
   float4* myfx = &sh.fx4[0][tid];  // row r at myfx[r * RT_THREADS]
@@ -97,6 +100,9 @@ __global__ void __launch_bounds__(RT_THREADS, 2) k_tb2d_df(const PassArgs p) {
     if (r < 4) myfx[r * RT_THREADS] = make_float4(fxr[1], fxr[2], fxr[3], fxr[4]);
     myfy[r * RT_THREADS] = make_float4(fyr[0], fyr[1], fyr[2], fyr[3]);
   }
+  // the previous pass's state is complete and visible after this (a no-op for a launch
+  // without the programmatic-serialization attribute)
+  asm volatile("griddepcontrol.wait;" ::: "memory");
   // the state as horizontal cell pairs: Uh[r][h] = (Uh of cell (r, 2h), of cell (r, 2h + 1))
   float2 Uh[4][2], Ul[4][2], Vh[4][2], Vl[4][2];
 #pragma unroll
@@ -250,28 +256,40 @@ __global__ void __launch_bounds__(RT_THREADS, 2) k_tb2d_df(const PassArgs p) {
 }
 
 template <bool PERIODIC, bool IN_REAL, bool OUT_REAL>
-cudaError_t launch_t(const PassArgs& a, cudaStream_t st) {
+cudaError_t launch_t(const PassArgs& a, cudaStream_t st, bool overlap_previous) {
   const auto kern = k_tb2d_df<PERIODIC, IN_REAL, OUT_REAL>;
   static const cudaError_t attr =
       cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sizeof(DfShared)));
   if (attr != cudaSuccess) return attr;
   const int T = RT_R - 2 * a.k;
-  kern<<<dim3((a.nx + T - 1) / T, (a.ny + T - 1) / T, 1), RT_THREADS, sizeof(DfShared), st>>>(a);
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((a.nx + T - 1) / T, (a.ny + T - 1) / T, 1);
+  cfg.blockDim = dim3(RT_THREADS, 1, 1);
+  cfg.dynamicSmemBytes = sizeof(DfShared);
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = overlap_previous ? 1 : 0;
+  const cudaError_t e = cudaLaunchKernelEx(&cfg, kern, a);
   count_launch();
-  return cudaGetLastError();
+  return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 template <bool PERIODIC>
-cudaError_t launch_bc(const PassArgs& a, cudaStream_t st) {
+cudaError_t launch_bc(const PassArgs& a, cudaStream_t st, bool ov) {
   const bool in_real = a.in_mode == PASS_IO_REAL, out_real = a.out_mode == PASS_IO_REAL;
-  if (in_real) return out_real ? launch_t<PERIODIC, true, true>(a, st) : launch_t<PERIODIC, true, false>(a, st);
-  return out_real ? launch_t<PERIODIC, false, true>(a, st) : launch_t<PERIODIC, false, false>(a, st);
+  if (in_real)
+    return out_real ? launch_t<PERIODIC, true, true>(a, st, ov) : launch_t<PERIODIC, true, false>(a, st, ov);
+  return out_real ? launch_t<PERIODIC, false, true>(a, st, ov) : launch_t<PERIODIC, false, false>(a, st, ov);
 }
 
 }  // namespace
 
-cudaError_t launch_pass_tb2d_df(const frkc2_problem& p, const PassArgs& a, cudaStream_t st) {
-  return p.bc == FRKC2_BC_PERIODIC ? launch_bc<true>(a, st) : launch_bc<false>(a, st);
+cudaError_t launch_pass_tb2d_df(const frkc2_problem& p, const PassArgs& a, cudaStream_t st, bool overlap_previous) {
+  return p.bc == FRKC2_BC_PERIODIC ? launch_bc<true>(a, st, overlap_previous)
+                                   : launch_bc<false>(a, st, overlap_previous);
 }
 
 }  // namespace frkc2

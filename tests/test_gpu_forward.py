@@ -186,6 +186,7 @@ def test_launch_count_matches_passes():
 TB_CASES = [
     # shape, bc, kappa, s, nsteps, k
     ((100, 77), "periodic", "field", 16, 2, 4),
+    ((200, 130), "periodic", "field", 8, 3, 8),  # one pass per step over many regions
     ((100, 77), "periodic", "field", 16, 2, 1),
     ((200, 130), "dirichlet", "field", 32, 2, 3),
     ((64, 64), "periodic", "const", 64, 1, 8),
@@ -282,6 +283,10 @@ DF_CASES = [
     ((130, 300), "dirichlet", "field", 16, 1, 3, 5),
     ((57, 200), "dirichlet", "const", 32, 2, 3, 16),
     ((9, 13), "periodic", "field", 8, 3, 3, 1),
+    # one pass per step on a grid of many regions (s <= k): a pass must not write the array
+    # it reads, since its regions' halos overlap other CTAs' output tiles
+    ((200, 130), "periodic", "field", 8, 3, 0, 0),
+    ((150, 170), "dirichlet", "field", 4, 2, 3, 8),
 ]
 
 
