@@ -64,6 +64,10 @@ __global__ void __launch_bounds__(AS_THREADS, adj_min_blocks<S>())
   const S ca = S(p.ca), cb = S(p.cb);
   const S hr = S(0.5 * p.ca), hi = S(0.5 * p.cb);  // c/2: each face gives half to each cell
 
+  // launched with programmatic stream serialization: the next launch may start its CTAs as this
+  // one's exit, and every global load below comes after the previous launch has completed
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+  asm volatile("griddepcontrol.wait;" ::: "memory");
   while (idx < end) {
     const int wcol = int(idx / ny);
     const int y0 = int(idx - (long long)wcol * ny);
@@ -199,7 +203,20 @@ cudaError_t launch_t(const AdjStreamArgs& a, cudaStream_t st) {
   long long grid = (long long)res.sms * res.per_sm;
   const long long max_useful = (total + AS_WARPS - 1) / AS_WARPS;
   if (grid > max_useful) grid = max_useful;
-  kern<<<unsigned(grid), AS_THREADS, 0, st>>>(a, total, grid * AS_WARPS);
+  {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(unsigned(grid), 1, 1);
+    cfg.blockDim = dim3(AS_THREADS, 1, 1);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    const cudaError_t le = cudaLaunchKernelEx(&cfg, kern, a, total, grid * AS_WARPS);
+    if (le != cudaSuccess) return le;
+  }
   count_launch();
   return cudaGetLastError();
 }

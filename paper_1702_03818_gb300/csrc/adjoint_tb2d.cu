@@ -151,6 +151,10 @@ __global__ void __launch_bounds__(RT_THREADS, 2) k_tape_tb2d(const AdjTbArgs a) 
   const int k = a.k, T = RT_R - 2 * k;
   const int x0 = blockIdx.x * T - k, y0 = blockIdx.y * T - k;
   const int nx = a.nx, ny = a.ny;
+  // launched with programmatic stream serialization: the next launch may start its CTAs as this
+  // one's exit, and every global load below comes after the previous launch has completed
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+  asm volatile("griddepcontrol.wait;" ::: "memory");
   const RegionIdx R = region_idx<PERIODIC>(nx, ny, k, x0, y0, tx, ty);
   float fx[4][5];
   float2 FY2[5][2];
@@ -277,6 +281,10 @@ __global__ void __launch_bounds__(RT_THREADS, 2) k_adjrev_tb2d(const AdjTbArgs a
   const int k = a.k, T = RT_R - 2 * k;
   const int x0 = blockIdx.x * T - k, y0 = blockIdx.y * T - k;
   const int nx = a.nx, ny = a.ny;
+  // launched with programmatic stream serialization: the next launch may start its CTAs as this
+  // one's exit, and every global load below comes after the previous launch has completed
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+  asm volatile("griddepcontrol.wait;" ::: "memory");
   const RegionIdx R = region_idx<PERIODIC>(nx, ny, k, x0, y0, tx, ty);
 
   // tape entries of stage jj for ring row i (i = 4: the grid row above the thread's rows):
@@ -536,7 +544,20 @@ cudaError_t launch_rev(const AdjTbArgs& a, dim3 grid, cudaStream_t st) {
   static const cudaError_t attr =
       cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sizeof(RevShared)));
   if (attr != cudaSuccess) return attr;
-  kern<<<grid, RT_THREADS, sizeof(RevShared), st>>>(a);
+  {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = dim3(RT_THREADS, 1, 1);
+    cfg.dynamicSmemBytes = sizeof(RevShared);
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    const cudaError_t le = cudaLaunchKernelEx(&cfg, kern, a);
+    if (le != cudaSuccess) return le;
+  }
   count_launch();
   return cudaGetLastError();
 }
@@ -578,10 +599,21 @@ cudaError_t launch_tape_tb2d(const frkc2_problem& p, int k, const AdjTbPass& t, 
     a.cb[j] = float(t.cb[j]);
   }
   const dim3 grid = region_grid(p, k);
-  if (p.bc == FRKC2_BC_PERIODIC)
-    k_tape_tb2d<true><<<grid, RT_THREADS, 0, st>>>(a);
-  else
-    k_tape_tb2d<false><<<grid, RT_THREADS, 0, st>>>(a);
+  const auto tk = p.bc == FRKC2_BC_PERIODIC ? k_tape_tb2d<true> : k_tape_tb2d<false>;
+  {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = dim3(RT_THREADS, 1, 1);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    const cudaError_t le = cudaLaunchKernelEx(&cfg, tk, a);
+    if (le != cudaSuccess) return le;
+  }
   count_launch();
   return cudaGetLastError();
 }

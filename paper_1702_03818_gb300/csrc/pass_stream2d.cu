@@ -76,6 +76,10 @@ __global__ void __launch_bounds__(ST_THREADS, ST_MIN_BLOCKS)
   S2* __restrict__ Wo = static_cast<S2*>(p.U_out);
   const S ca = S(p.ca[0]), cb = S(p.cb[0]);
   bool bad = false;
+  // launched with programmatic stream serialization: the next pass may start its CTAs as this
+  // one's exit, and every global load below comes after the previous launch has completed
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+  asm volatile("griddepcontrol.wait;" ::: "memory");
 
   while (idx < end) {  // warp-uniform
     const int wcol = int(idx / ny);
@@ -250,9 +254,19 @@ cudaError_t launch_t(const PassArgs& a, const void* fen, cudaStream_t st) {
   long long grid = (long long)res.sms * res.per_sm;
   const long long max_useful = (total + ST_WARPS - 1) / ST_WARPS;
   if (grid > max_useful) grid = max_useful;
-  kern<<<unsigned(grid), ST_THREADS, 0, st>>>(a, fen, ncolw, total, grid * ST_WARPS);
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(unsigned(grid), 1, 1);
+  cfg.blockDim = dim3(ST_THREADS, 1, 1);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  const cudaError_t e = cudaLaunchKernelEx(&cfg, kern, a, fen, ncolw, total, grid * ST_WARPS);
   count_launch();
-  return cudaGetLastError();
+  return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 template <class S, class A>
