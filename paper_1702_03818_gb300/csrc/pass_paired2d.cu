@@ -42,6 +42,10 @@ __device__ __forceinline__ bool bad_bits(float v) { return (__float_as_uint(v) &
 template <class S, class A, bool PERIODIC>
 __global__ void __launch_bounds__(PR_THREADS, FRKC2_PAIRED_MIN_BLOCKS)
     k_paired2d(const PassArgs p, const void* __restrict__ fen_v, long long total, long long nwarps_grid) {
+  // launched with programmatic stream serialization: the next launch may start its CTAs as this
+  // one's exit, and every global load below comes after the previous launch has completed
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+  asm volatile("griddepcontrol.wait;" ::: "memory");
   using A2 = typename P2t<A>::type;
   const int lane = threadIdx.x & 31;
   const long long gw = (long long)blockIdx.x * PR_WARPS + (threadIdx.x >> 5);
@@ -164,7 +168,20 @@ cudaError_t launch_t(const PassArgs& a, const void* fen, cudaStream_t st) {
   long long grid = (long long)res.sms * res.per_sm;
   const long long max_useful = (total + PR_WARPS - 1) / PR_WARPS;
   if (grid > max_useful) grid = max_useful;
-  kern<<<unsigned(grid), PR_THREADS, 0, st>>>(a, fen, total, grid * PR_WARPS);
+  {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(unsigned(grid), 1, 1);
+    cfg.blockDim = dim3(PR_THREADS, 1, 1);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    const cudaError_t le = cudaLaunchKernelEx(&cfg, kern, a, fen, total, grid * PR_WARPS);
+    if (le != cudaSuccess) return le;
+  }
   count_launch();
   return cudaGetLastError();
 }

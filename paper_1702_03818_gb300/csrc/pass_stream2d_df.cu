@@ -72,6 +72,10 @@ __device__ __forceinline__ bool nonfinite_d(double v) { return (__double2hiint(v
 template <bool PERIODIC, bool IN_REAL, bool OUT_REAL>
 __global__ void __launch_bounds__(DF_THREADS, DF_MIN_BLOCKS)
     k_stream2d_df(const PassArgs p, const float2* __restrict__ FEN, long long total, long long nwarps_grid) {
+  // launched with programmatic stream serialization: the next launch may start its CTAs as this
+  // one's exit, and every global load below comes after the previous launch has completed
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+  asm volatile("griddepcontrol.wait;" ::: "memory");
   const int lane = threadIdx.x & 31;
   const long long gw = (long long)blockIdx.x * DF_WARPS + (threadIdx.x >> 5);
   const int nx = p.nx, ny = p.ny;
@@ -226,7 +230,20 @@ cudaError_t launch_t(const PassArgs& a, const void* fen, cudaStream_t st) {
   long long grid = (long long)res.sms * res.per_sm;
   const long long max_useful = (total + DF_WARPS - 1) / DF_WARPS;
   if (grid > max_useful) grid = max_useful;
-  kern<<<unsigned(grid), DF_THREADS, 0, st>>>(a, static_cast<const float2*>(fen), total, grid * DF_WARPS);
+  {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(unsigned(grid), 1, 1);
+    cfg.blockDim = dim3(DF_THREADS, 1, 1);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    const cudaError_t le = cudaLaunchKernelEx(&cfg, kern, a, static_cast<const float2*>(fen), total, grid * DF_WARPS);
+    if (le != cudaSuccess) return le;
+  }
   count_launch();
   return cudaGetLastError();
 }

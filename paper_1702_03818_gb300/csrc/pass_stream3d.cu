@@ -51,6 +51,10 @@ __device__ __forceinline__ int wrap3(int g, int n) {
 // P25: kappa(u) with the exponent 2.5, evaluated as w^2 sqrt(w) without the general path
 template <class S, class A, bool PERIODIC, bool POWER, bool P25>
 __global__ void __launch_bounds__(S3_THREADS) k_stream3d(const PassArgs p, int zchunk) {
+  // launched with programmatic stream serialization: the next launch may start its CTAs as this
+  // one's exit, and every global load below comes after the previous launch has completed
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+  asm volatile("griddepcontrol.wait;" ::: "memory");
   using S2 = typename V2s<S>::type;
   using A2 = typename V2s<A>::type;
   __shared__ S2 shW[2][S3_TY][32];
@@ -224,10 +228,22 @@ cudaError_t launch_t(const PassArgs& a, cudaStream_t st) {
   const int zchunk = 32;
   dim3 grid((a.nx + S3_OX - 1) / S3_OX, (a.ny + S3_OY - 1) / S3_OY, (a.nz + zchunk - 1) / zchunk);
   // (MIXED measured 8 % slower with the specialisation, so it keeps the general evaluation)
-  if (POWER && a.kp == 2.5 && std::is_same<S, A>::value)
-    k_stream3d<S, A, PERIODIC, POWER, true><<<grid, S3_THREADS, 0, st>>>(a, zchunk);
-  else
-    k_stream3d<S, A, PERIODIC, POWER, false><<<grid, S3_THREADS, 0, st>>>(a, zchunk);
+  const auto kern = POWER && a.kp == 2.5 && std::is_same<S, A>::value ? k_stream3d<S, A, PERIODIC, POWER, true>
+                                                                        : k_stream3d<S, A, PERIODIC, POWER, false>;
+  {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = dim3(S3_THREADS, 1, 1);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    const cudaError_t le = cudaLaunchKernelEx(&cfg, kern, a, zchunk);
+    if (le != cudaSuccess) return le;
+  }
   count_launch();
   return cudaGetLastError();
 }
