@@ -55,7 +55,7 @@ __global__ void __launch_bounds__(S1_TMAX) k_small1d(const Small1dArgs a) {
   cg::cluster_group cluster = cg::this_cluster();
   const int CL = int(cluster.num_blocks());
   const int c = int(cluster.block_rank());
-  const int t = threadIdx.x, nt = blockDim.x;
+  const int t = threadIdx.x;
   const int n = a.n, R = a.R;
   // chunk of this CTA and of the previous one (for the index of its last occupied thread)
   const int c0 = int((long long)c * n / CL), c1 = int((long long)(c + 1) * n / CL);
