@@ -37,10 +37,10 @@ constexpr int ST_THREADS = 256;
 constexpr int ST_WARPS = ST_THREADS / 32;
 constexpr int ST_COLS = 31;  // output columns per warp
 #ifndef FRKC2_STREAM_MIN_BLOCKS
-#define FRKC2_STREAM_MIN_BLOCKS 4
+#define FRKC2_STREAM_MIN_BLOCKS 3
 #endif
 #ifndef FRKC2_STREAM_PREFETCH
-#define FRKC2_STREAM_PREFETCH 0
+#define FRKC2_STREAM_PREFETCH 1  // loads for row y + 1 issued one row ahead
 #endif
 constexpr int ST_MIN_BLOCKS = FRKC2_STREAM_MIN_BLOCKS;  // CTAs per SM the register budget allows
 
