@@ -26,7 +26,10 @@ constexpr int AS_THREADS = 256;
 constexpr int AS_WARPS = AS_THREADS / 32;
 constexpr int AS_COLS = 30;  // output columns per warp: lanes 1..30 (lanes 0 and 31 are halos)
 #ifndef FRKC2_ADJ_MIN_BLOCKS
-#define FRKC2_ADJ_MIN_BLOCKS 3
+#define FRKC2_ADJ_MIN_BLOCKS 2
+#endif
+#ifndef FRKC2_ADJ_PREFETCH
+#define FRKC2_ADJ_PREFETCH 1
 #endif
 #ifndef FRKC2_ADJ_UNROLL
 #define FRKC2_ADJ_UNROLL 2
@@ -143,11 +146,23 @@ __global__ void __launch_bounds__(AS_THREADS, adj_min_blocks<S>())
       dSi = A(Lc.y - Ls.y);
       Gs = dSr * A(Yc.x - Ys.x) + dSi * A(Yc.y - Ys.y);
     }
+#if FRKC2_ADJ_PREFETCH
+    // the next row's lam, tape entry and faces are loaded one iteration ahead of their use
+    S2 Ln = ld(Lin, Lr, p.l_complex, y0 + 1);
+    S2 Wn = ld(Wc2, Wr, p.w_complex, y0 + 1);
+    A2 f = faces(y0);
+#endif
 #pragma unroll AS_UNROLL
     for (int y = y0; y < y1; ++y) {
+#if FRKC2_ADJ_PREFETCH
+      const S2 Lnn = ld(Lin, Lr, p.l_complex, y + 2);
+      const S2 Wnn = ld(Wc2, Wr, p.w_complex, y + 2);
+      const A2 fnext = faces(y + 1);
+#else
       const S2 Ln = ld(Lin, Lr, p.l_complex, y + 1);
       const S2 Wn = ld(Wc2, Wr, p.w_complex, y + 1);
       const A2 f = faces(y);
+#endif
       const S2 Yn = yof(Wn);
       // east face (lane 31 is a halo: its east values are not used)
       const S Le_r = __shfl_down_sync(0xffffffffu, Lc.x, 1);
@@ -189,6 +204,11 @@ __global__ void __launch_bounds__(AS_THREADS, adj_min_blocks<S>())
       Gs = Gn;
       Lc = Ln;
       Yc = Yn;
+#if FRKC2_ADJ_PREFETCH
+      Ln = Lnn;
+      Wn = Wnn;
+      f = fnext;
+#endif
     }
   }
 }
