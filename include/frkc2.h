@@ -90,7 +90,8 @@ typedef struct {
 
 typedef struct {
   int k;             /* stages per pass (temporal blocking), 1..16; 0 = library default       */
-  int tile_x;        /* output tile per CTA along x, y, z; 0 = library default                */
+  int tile_x;        /* output tile per CTA along x, y, z; 0 = library default (kernel 6:
+                        tile_x = CTAs in the cluster, 1..8)                                   */
   int tile_y;
   int tile_z;
   int kernel;        /* 0 = library choice, 1 = generic shared-memory tile kernel,

@@ -274,8 +274,9 @@ frkc2_status frkc2_step(frkc2_plan_t plan, const frkc2_problem* prob, double dt,
   a.status = reinterpret_cast<unsigned*>(base + L.status);
 
   if (use_small1d) {  // the whole job in one cluster launch
-    return launch_small1d(p, *plan, dt, nsteps, u, base + L.fx, a.status, st) == cudaSuccess ? FRKC2_OK
-                                                                                              : FRKC2_ECUDA;
+    const int cl = tune ? tune->tile_x : 0;  // kernel 6: CTAs in the cluster (0: library choice)
+    return launch_small1d(p, *plan, dt, nsteps, u, base + L.fx, a.status, st, cl) == cudaSuccess ? FRKC2_OK
+                                                                                                 : FRKC2_ECUDA;
   }
   const void* curU = u;
   const void* curV = nullptr;

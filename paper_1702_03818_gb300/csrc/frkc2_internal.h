@@ -90,7 +90,7 @@ cudaError_t launch_face_pairs(const frkc2_problem& p, const void* fx, const void
 cudaError_t launch_pass_tb2d(const frkc2_problem& p, const PassArgs& a, cudaStream_t st, bool overlap_previous);
 bool small1d_supported(const frkc2_problem& p, int s);
 cudaError_t launch_small1d(const frkc2_problem& p, const frkc2_plan_s& plan, double dt, int nsteps, void* u,
-                           const void* fx, unsigned* status, cudaStream_t st);
+                           const void* fx, unsigned* status, cudaStream_t st, int cluster);
 cudaError_t launch_pass_stream3d(const frkc2_problem& p, const PassArgs& a, cudaStream_t st);
 cudaError_t launch_pass_tb2d_df(const frkc2_problem& p, const PassArgs& a, cudaStream_t st, bool overlap_previous);
 cudaError_t launch_pass_stream2d_df(const frkc2_problem& p, const PassArgs& a, const void* fen, cudaStream_t st);

@@ -176,10 +176,16 @@ bool small1d_supported(const frkc2_problem& p, int s) {
 }
 
 cudaError_t launch_small1d(const frkc2_problem& p, const frkc2_plan_s& plan, double dt, int nsteps, void* u,
-                           const void* fx, unsigned* status, cudaStream_t st) {
+                           const void* fx, unsigned* status, cudaStream_t st, int cluster) {
   const int n = int(p.n[0]);
-  // cluster size: up to 8 CTAs, each with at least one warp's worth of cells
-  const int CL = std::max(1, std::min(S1_CMAX, n / 32));
+  // cluster size (or the caller's): the per-stage cluster barrier grows with the CTAs, the
+  // FP64 pipe time per stage shrinks with them -- FP64 state spreads 128 cells a CTA (N = 256:
+  // 2 CTAs, 1.44 ms a job against 1.52 with 8), FP32 keeps one CTA while it fits (0.87 ms
+  // against 1.00)
+  const bool f32 = p.precision == FRKC2_FP32;
+  int CL = cluster > 0 ? std::min(S1_CMAX, std::min(cluster, n))
+                       : (f32 ? 1 : std::max(1, std::min(S1_CMAX, n / 128)));
+  CL = std::max(CL, (n + S1_TMAX * S1_RMAX - 1) / (S1_TMAX * S1_RMAX));  // at most S1_RMAX cells a thread
   const int chunk = (n + CL - 1) / CL;
   // threads per CTA: a multiple of 32, at most 256, holding at most S1_RMAX cells each
   int threads = std::min(S1_TMAX, ((chunk + 31) / 32) * 32);
