@@ -119,9 +119,15 @@ __global__ void __launch_bounds__(BT_THREADS, bt_min_blocks<S, A>()) k_batched(c
   __shared__ int s_prob, s_tile, s_round, s_ok;
   const int tid = threadIdx.x;
   const bool periodic = h.bc == FRKC2_BC_PERIODIC;
+  // thread 0 takes the next ticket while the current item computes, so the atomic's round trip
+  // is off the path between items (an item still waits only for items of smaller tickets, all
+  // taken by running CTAs: the smallest unfinished ticket is always being computed)
+  unsigned long long next_ticket = 0;
+  bool have_next = false;
   while (true) {
     if (tid == 0) {
-      s_item = (long long)atomicAdd(h.ticket, 1ull);
+      s_item = have_next ? (long long)next_ticket : (long long)atomicAdd(h.ticket, 1ull);
+      have_next = false;
       s_ok = 1;
       if (s_item < h.total_items && !*((volatile unsigned*)h.abort_flag)) {
         // decode (round, problem, tile)
@@ -163,6 +169,10 @@ __global__ void __launch_bounds__(BT_THREADS, bt_min_blocks<S, A>()) k_batched(c
     }
     __syncthreads();
     if (s_item >= h.total_items || !s_ok) break;
+    if (tid == 0) {
+      next_ticket = atomicAdd(h.ticket, 1ull);
+      have_next = true;
+    }
     const BProb& P = h.probs[s_prob];
     const void* Uin_v;
     const void* Vin_v;
