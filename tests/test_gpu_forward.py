@@ -448,6 +448,32 @@ def test_small1d_single_cell(bc):
     assert abs(got[0] - ref[0]) <= 1e-13 * max(abs(ref[0]), 1e-300) + 1e-300
 
 
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-11), ("fp32", 1e-4)])
+@pytest.mark.parametrize("n", [256, 3001])
+def test_small1d_cluster_size_choice(n, prec, tol):
+    """The 1D whole-job kernel with 1, 2, 4 and 8 CTAs in its cluster (tile_x) and the
+    library's choice: each against the oracle, and all within rounding of each other (the
+    split changes how many cells a thread holds, and the multiply-adds of different cell
+    positions in a thread may be contracted differently)."""
+    u0, field = seeded_case((n,), "dirichlet", "field", 60 + n)
+    plan = F.frkc2_plan(16)
+    oplan = O.plan(16)
+    fo = rounded_field(field, prec)
+    opr = oracle_problem(1, "dirichlet", "field", 1.0, fo)
+    dt = 0.9 * oplan["beta"] / O.rho_bound(opr, u0)
+    u0o = u0.astype(np.float32).astype(np.float64) if prec == "fp32" else u0
+    ref = O.frkc2_step(u0o, oplan["a"], dt, opr, 5)
+    outs = []
+    for cl in (0, 1, 2, 4, 8):
+        got, st = run_gpu(plan, (n,), "dirichlet", "field", prec, u0, field, dt, 5,
+                          tune=F.make_tuning(kernel=6, tile=(cl, 0, 0)))
+        assert st == F.OK
+        assert rel_l2(got, ref) < tol, (cl, rel_l2(got, ref))
+        outs.append(got)
+    for o in outs[1:]:
+        assert rel_l2(o, outs[0]) < (1e-14 if prec == "fp64" else 1e-6), rel_l2(o, outs[0])
+
+
 def test_small1d_rejects_out_of_range():
     plan = F.frkc2_plan(8)
     for shape, kappa in [((16385,), "const"), ((100,), "power")]:
