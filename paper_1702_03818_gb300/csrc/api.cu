@@ -484,6 +484,12 @@ frkc2_status frkc2_step_adaptive(frkc2_plan_t plan, const frkc2_problem* prob, d
   void* VA = base + L.va;
   void* UB = base + L.ub;
   void* VB = base + L.vb;
+  // 2D fixed conductivity: the streaming pass (one stage a launch, interleaved complex state
+  // in the ua / ub slots, the embedded solution advanced alongside); otherwise the tile pass
+  const bool streamed = p.ndim == 2 && p.kappa_kind != FRKC2_KAPPA_POWER && p.precision != FRKC2_DFLOAT &&
+                        !(tune && (tune->kernel != 0 || tune->k > 1 || tune->tile_x || tune->tile_y));
+  if (streamed && launch_face_pairs(p, base + L.fx, base + L.fy, base + L.fen, st) != cudaSuccess)
+    return FRKC2_ECUDA;
   const int s = plan->s, npass = (s + k - 1) / k;
   const double h2 = p.dx * p.dx, safe = 0.8, tmax = rho > 0.0 ? plan->beta / rho : 0.0;
   double t = 0.0, T = dt0, T_prev = 0.0, e_prev = 0.0;
@@ -496,7 +502,26 @@ frkc2_status frkc2_step_adaptive(frkc2_plan_t plan, const frkc2_problem* prob, d
     const void* cU = u;
     const void* cV = nullptr;
     const void* cH = u;
-    for (int q = 0; q < npass; ++q) {
+    for (int l = 0; streamed && l < s; ++l) {
+      const bool first = l == 0, last = l == s - 1;
+      void* oW = (cU == UA) ? UB : UA;  // the step's result stays off u until it is accepted
+      void* oH = (cH == hA) ? hB : hA;
+      a.U_in = cU;
+      a.V_in = nullptr;
+      a.in_mode = first ? PASS_IO_REAL : PASS_IO_COMPLEX;
+      a.U_out = oW;
+      a.V_out = nullptr;
+      a.out_mode = last ? PASS_IO_REAL : PASS_IO_COMPLEX;
+      a.H_in = cH;
+      a.H_out = oH;
+      a.check_finite = 0;
+      a.ca[0] = T * plan->a_re[l] / h2;
+      a.cb[0] = T * plan->a_im[l] / h2;
+      if (launch_pass_stream2d(p, a, base + L.fen, st) != cudaSuccess) return FRKC2_ECUDA;
+      cU = oW;
+      cH = oH;
+    }
+    for (int q = 0; !streamed && q < npass; ++q) {
       const int l0 = q * k, kq = std::min(k, s - l0);
       const bool last = q == npass - 1;
       void* oU = (cU == UA) ? UB : UA;

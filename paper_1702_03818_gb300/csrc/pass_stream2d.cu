@@ -55,7 +55,9 @@ __device__ __forceinline__ bool nonfinite_bits(float v) {
   return (__float_as_uint(v) & 0x7f800000u) == 0x7f800000u;
 }
 
-template <class S, class A, bool PERIODIC>
+// HAT: the pass also advances the embedded first-order solution of Eq. 14 (real, one value a
+// cell): What <- What + ca f_R, read from H_in and written to H_out (the adaptive step).
+template <class S, class A, bool PERIODIC, bool HAT>
 __global__ void __launch_bounds__(ST_THREADS, ST_MIN_BLOCKS)
     k_stream2d(const PassArgs p, const void* __restrict__ fen_v, int ncolw, long long total,
                long long nwarps_grid) {
@@ -213,6 +215,7 @@ __global__ void __launch_bounds__(ST_THREADS, ST_MIN_BLOCKS)
           if (out_mode == PASS_IO_PLANAR) Vo[g] = vn;
         }
         if (p.check_finite) bad |= nonfinite_bits(un);
+        if (HAT) static_cast<S*>(p.H_out)[g] = __ldg(static_cast<const S*>(p.H_in) + g) + ca * S(fU);
       }
       dSU = dNU;
       dSV = dNV;
@@ -244,9 +247,9 @@ __global__ void k_face_pairs(const A* __restrict__ fx, const A* __restrict__ fy,
   }
 }
 
-template <class S, class A, bool PERIODIC>
+template <class S, class A, bool PERIODIC, bool HAT>
 cudaError_t launch_t(const PassArgs& a, const void* fen, cudaStream_t st) {
-  const auto kern = k_stream2d<S, A, PERIODIC>;
+  const auto kern = k_stream2d<S, A, PERIODIC, HAT>;
   static const Residency res = query_residency(kern, ST_THREADS, 0);
   if (res.err != cudaSuccess) return res.err;
   const int ncolw = (a.nx + ST_COLS - 1) / ST_COLS;
@@ -271,7 +274,8 @@ cudaError_t launch_t(const PassArgs& a, const void* fen, cudaStream_t st) {
 
 template <class S, class A>
 cudaError_t launch_s(const PassArgs& a, const void* fen, cudaStream_t st) {
-  return a.bc == FRKC2_BC_PERIODIC ? launch_t<S, A, true>(a, fen, st) : launch_t<S, A, false>(a, fen, st);
+  if (a.H_out) return a.bc == FRKC2_BC_PERIODIC ? launch_t<S, A, true, true>(a, fen, st) : launch_t<S, A, false, true>(a, fen, st);
+  return a.bc == FRKC2_BC_PERIODIC ? launch_t<S, A, true, false>(a, fen, st) : launch_t<S, A, false, false>(a, fen, st);
 }
 
 }  // namespace
