@@ -190,6 +190,9 @@ frkc2_status frkc2_step(frkc2_plan_t plan, const frkc2_problem* prob, double dt,
  * stability limit beta/rho.  The plan's stage count is used for every step.
  * The call is synchronous: each step reads the error norm back to the host.  u is updated
  * only by accepted steps.  Returns FRKC2_ETIMEOUT if 10^6 attempts did not reach t_end.
+ * Kernels: 2D FIELD / CONST problems with the default tuning run the single-stage streaming
+ * pass with the embedded solution fused into it; other problems, or a tuning that sets
+ * kernel, k > 1 or a tile, run the shared-memory tile pass of tune->k stages.
  *   dt0   : first step size to try (> 0).
  *   stats : may be NULL; receives the accepted and rejected step counts, the time reached,
  *           the last accepted step size and its scaled error.
