@@ -97,3 +97,38 @@ def test_cmp_two_material(ratio):
     assert (st["accepted"], st["rejected"]) == (st_ref["accepted"], st_ref["rejected"])
     assert rel_l2(ctrl, ref) < 1e-10
     assert sign_changes(ctrl) == 2 and ctrl.max() <= 1.0 and ctrl.min() >= 0.0
+
+
+@pytest.mark.parametrize("prec,tol_u", [("fp64", 1e-10), ("mixed", 1e-6), ("fp32", 1e-3)])
+def test_adaptive_streaming_and_tile_paths_agree(prec, tol_u):
+    """2D fixed-conductivity adaptive steps take the streaming pass with the embedded solution
+    fused in; kernel 1 forces the shared-memory tile pass.  Both against the oracle's
+    controller: the same state to the precision, and (FP64, MIXED: the error estimate in a
+    double state) the same accepted / rejected steps.  In FP32 the estimate's rounding may move
+    a step size slightly, so only the time reached and the state are compared."""
+    shape = (56, 72)
+    u0, field = seeded_case(shape, "periodic", "field", 95)
+    s, t_end, tol = 16, 30.0, 1e-4
+    fo = field if prec == "fp64" else field.astype(np.float32).astype(np.float64)
+    u0o = u0.astype(np.float32).astype(np.float64) if prec == "fp32" else u0
+    opr = oracle_problem(2, "periodic", "field", 1.0, fo)
+    rho = O.rho_bound(opr, u0o)
+    oplan = O.plan(s)
+    dt0 = O.beta(s) / rho
+    ref, st_ref = O.frkc2_adaptive(u0o, oplan["a"], O.beta(s), opr, t_end, tol, dt0, rho=rho)
+    plan = F.frkc2_plan(s)
+    sd = torch.float32 if prec == "fp32" else torch.float64
+    kt = torch.as_tensor(field, dtype=torch.float64 if prec == "fp64" else torch.float32, device="cuda")
+    pr = F.make_problem(2, tuple(reversed(shape)), 1.0, "periodic", "field", prec, kappa_field=kt)
+    outs = []
+    for tune in (None, F.make_tuning(kernel=1)):
+        ws = torch.empty(F.frkc2_adaptive_workspace_size(pr), dtype=torch.uint8, device="cuda")
+        u = torch.as_tensor(u0, dtype=sd, device="cuda")
+        st = F.frkc2_step_adaptive(plan, pr, t_end, tol, dt0, rho, u, ws, tune)
+        assert abs(st["t"] - t_end) < 1e-9 * t_end
+        if prec != "fp32":
+            assert (st["accepted"], st["rejected"]) == (st_ref["accepted"], st_ref["rejected"]), (tune, st, st_ref)
+        got = u.double().cpu().numpy()
+        assert rel_l2(got, ref) < tol_u, (tune, rel_l2(got, ref))
+        outs.append(got)
+    assert rel_l2(outs[0], outs[1]) < tol_u
