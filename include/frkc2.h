@@ -222,8 +222,9 @@ frkc2_status frkc2_step_adaptive(frkc2_plan_t plan, const frkc2_problem* prob, d
  *   - Problems whose workspace (frkc2_workspace_size) exceeds the array are rejected with
  *     FRKC2_ENOMEM before any work is queued (e.g. FP64 2D grids up to about 590^2 cells,
  *     FP32 2D grids up to about 830^2 cells).
- *   - The first call on a device looks up the array's device address (cudaGetSymbolAddress)
- *     with that device current; make that first call before any stream capture.
+ *   - Every call looks up the array's device address on the current device
+ *     (cudaGetSymbolAddress, which allocates nothing).  The first call on a device may load
+ *     the library's device code: make that first call before any stream capture.
  *   - Every call shares the one array and it keeps the last call's contents; the call
  *     clears the status word itself.  Calls whose work overlaps on the GPU (different
  *     streams, or different host threads on the same device) race on the array: serialise

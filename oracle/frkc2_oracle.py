@@ -589,13 +589,15 @@ def frkc2_adaptive(u0, a, beta_, prob, t_end: float, tol: float, dt0: float, rho
     lacks the leading T^n), and from T^n SAFE / sqrt(e_n) for the first step.  Readings: T is
     also capped by the stability limit beta/rho (when rho > 0), by the time left, and may grow
     by at most 5x per step; e is floored at 1e-10.
-    Returns (u, dict(accepted, rejected, t, dts)).
+    Returns (u, dict(accepted, rejected, t, dts, trace)); ``trace`` lists every attempt as
+    (T, ||err||, accepted).
     """
     u = np.array(u0, dtype=np.float64)
     t, T = 0.0, float(dt0)
     T_prev, e_prev = None, None
     acc = rej = 0
     dts = []
+    trace = []
     while t < t_end * (1.0 - 1e-14) and acc + rej < max_steps:
         T = min(T, t_end - t)
         if rho > 0:
@@ -604,9 +606,11 @@ def frkc2_adaptive(u0, a, beta_, prob, t_end: float, tol: float, dt0: float, rho
         e = error_norm(w, h, tol)
         if not np.isfinite(e) or e > 1.0:
             rej += 1
+            trace.append((T, e, False))
             T = T * safe / np.sqrt(e if np.isfinite(e) else 1e10)
             continue
         acc += 1
+        trace.append((T, e, True))
         u = w
         t += T
         dts.append(T)
@@ -616,4 +620,4 @@ def frkc2_adaptive(u0, a, beta_, prob, t_end: float, tol: float, dt0: float, rho
             fac *= (T / T_prev) * np.sqrt(e_prev / e)
         T_prev, e_prev = T, e
         T = T * min(fac, 5.0)
-    return u, dict(accepted=acc, rejected=rej, t=t, dts=dts)
+    return u, dict(accepted=acc, rejected=rej, t=t, dts=dts, trace=trace)

@@ -472,7 +472,11 @@ frkc2_status frkc2_step_adaptive(frkc2_plan_t plan, const frkc2_problem* prob, d
   a.kc = p.kappa_c;
   a.kp = p.kappa_p;
   a.status = reinterpret_cast<unsigned*>(base + L.status);
-  {
+  // 2D fixed conductivity: the streaming pass (one stage a launch, interleaved complex state
+  // in the ua / ub slots, the embedded solution advanced alongside); otherwise the tile pass
+  const bool streamed = p.ndim == 2 && p.kappa_kind != FRKC2_KAPPA_POWER && p.precision != FRKC2_DFLOAT &&
+                        !(tune && (tune->kernel != 0 || tune->k > 1 || tune->tile_x || tune->tile_y));
+  if (!streamed) {  // only the tile pass needs shared memory for a tile of k stages
     PassArgs probe = a;
     probe.hx = k;
     probe.hy = p.ndim >= 2 ? k : 0;
@@ -484,10 +488,6 @@ frkc2_status frkc2_step_adaptive(frkc2_plan_t plan, const frkc2_problem* prob, d
   void* VA = base + L.va;
   void* UB = base + L.ub;
   void* VB = base + L.vb;
-  // 2D fixed conductivity: the streaming pass (one stage a launch, interleaved complex state
-  // in the ua / ub slots, the embedded solution advanced alongside); otherwise the tile pass
-  const bool streamed = p.ndim == 2 && p.kappa_kind != FRKC2_KAPPA_POWER && p.precision != FRKC2_DFLOAT &&
-                        !(tune && (tune->kernel != 0 || tune->k > 1 || tune->tile_x || tune->tile_y));
   if (streamed && launch_face_pairs(p, base + L.fx, base + L.fy, base + L.fen, st) != cudaSuccess)
     return FRKC2_ECUDA;
   const int s = plan->s, npass = (s + k - 1) / k;

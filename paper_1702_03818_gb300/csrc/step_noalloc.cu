@@ -11,10 +11,10 @@
 // The array is a file-scope __device__ variable, so every GPU that loads the library holds
 // FRKC2_NOALLOC_SCRATCH_BYTES of device memory for it until the process exits.  Host code
 // cannot use the array's name as a device address (on the host it names a host-side
-// stand-in); the device address is obtained once per device with cudaGetSymbolAddress,
-// with that device current, on the first call made on the device.
-#include <mutex>
-
+// stand-in); every call obtains the device address with cudaGetSymbolAddress on the current
+// device.  The address is not cached: after cudaDeviceReset, or when the primary context is
+// destroyed and created again, the library's device code is loaded anew and the array may
+// move, and a cached address would then point at freed memory.
 #include <cuda_runtime.h>
 
 #include "frkc2.h"
@@ -24,21 +24,12 @@ namespace {
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[FRKC2_NOALLOC_SCRATCH_BYTES];
 
-constexpr int kMaxDevices = 64;
-std::mutex g_mu;
-void* g_addr[kMaxDevices] = {};
-
-// Device address of the scratch array on the current device (looked up once per device).
+// Device address of the scratch array in the current device's context.  The lookup allocates
+// nothing; the first one in a context may load the library's device code.
 frkc2_status scratch_address(void** out) {
-  int dev = -1;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return FRKC2_ECUDA;
-  std::lock_guard<std::mutex> lk(g_mu);
-  if (!g_addr[dev]) {
-    void* p = nullptr;
-    if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return FRKC2_ECUDA;
-    g_addr[dev] = p;
-  }
-  *out = g_addr[dev];
+  void* p = nullptr;
+  if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return FRKC2_ECUDA;
+  *out = p;
   return FRKC2_OK;
 }
 

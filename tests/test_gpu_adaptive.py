@@ -99,13 +99,14 @@ def test_cmp_two_material(ratio):
     assert sign_changes(ctrl) == 2 and ctrl.max() <= 1.0 and ctrl.min() >= 0.0
 
 
-@pytest.mark.parametrize("prec,tol_u", [("fp64", 1e-10), ("mixed", 1e-6), ("fp32", 1e-3)])
+@pytest.mark.parametrize("prec,tol_u", [("fp64", 1e-10), ("mixed", 1e-6), ("fp32", 1e-4)])
 def test_adaptive_streaming_and_tile_paths_agree(prec, tol_u):
     """2D fixed-conductivity adaptive steps take the streaming pass with the embedded solution
     fused in; kernel 1 forces the shared-memory tile pass.  Both against the oracle's
-    controller: the same state to the precision, and (FP64, MIXED: the error estimate in a
-    double state) the same accepted / rejected steps.  In FP32 the estimate's rounding may move
-    a step size slightly, so only the time reached and the state are compared."""
+    controller: the same state to the precision (FP32: the 1e-4 of s <= 64), and (FP64, MIXED:
+    the error estimate in a double state) the same accepted / rejected steps.  In FP32 the
+    estimate's rounding moves each step size by about 1e-4 relative (a state change of order
+    1e-8), so the step counts may differ by one at most."""
     shape = (56, 72)
     u0, field = seeded_case(shape, "periodic", "field", 95)
     s, t_end, tol = 16, 30.0, 1e-4
@@ -128,6 +129,8 @@ def test_adaptive_streaming_and_tile_paths_agree(prec, tol_u):
         assert abs(st["t"] - t_end) < 1e-9 * t_end
         if prec != "fp32":
             assert (st["accepted"], st["rejected"]) == (st_ref["accepted"], st_ref["rejected"]), (tune, st, st_ref)
+        else:
+            assert abs(st["accepted"] - st_ref["accepted"]) <= 1, (tune, st, st_ref)
         got = u.double().cpu().numpy()
         assert rel_l2(got, ref) < tol_u, (tune, rel_l2(got, ref))
         outs.append(got)

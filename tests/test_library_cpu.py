@@ -62,8 +62,23 @@ def test_plan_from_steps_and_errors():
     with pytest.raises(F.Frkc2Error) as e:
         F.frkc2_plan(16, nu=0.95)
     assert e.value.status == F.EINVAL
-    # strict plan with an unreachable bound is not possible to request; a normal plan is OK
+    # a strict plan that meets the 10 L^2 bound is returned
     assert F.frkc2_plan(16, flags=F.PLAN_STRICT).info()["Q"] <= 10 * 16 ** 2
+    with pytest.raises(F.Frkc2Error) as e:
+        F.frkc2_plan(16, flags=F.PLAN_GREEDY | F.PLAN_LEBEDEV)
+    assert e.value.status == F.EINVAL
+
+
+def test_strict_plan_above_bound_is_eplan():
+    """Sec. 2.2: a strict plan whose realised Q stays above 10 L^2 is refused with EPLAN.  A
+    pair-adjacent order has Q >= the largest quadratic factor (about 0.12 L^4), above the
+    bound from L = 10 on; without STRICT the same plan is returned with that Q."""
+    for s in (16, 64):
+        with pytest.raises(F.Frkc2Error) as e:
+            F.frkc2_plan(s, flags=F.PLAN_PAIRED | F.PLAN_STRICT)
+        assert e.value.status == F.EPLAN
+        q = F.frkc2_plan(s, flags=F.PLAN_PAIRED).info()["Q"]
+        assert q > 10 * s * s and abs(q / O.realised_Q(O.plan(s, method="paired")["a"], O.beta(s), 16 * s) - 1) < 1e-9
 
 
 def test_workspace_size_and_validation_on_host():

@@ -674,3 +674,140 @@ def test_cmp_uniform_stages_noisy_error_control_clean(ratio):
     assert ctrl.max() <= 1.0 and ctrl.min() >= 0.0
     evals_fixed, evals_ctrl = n * 8, (st["accepted"] + st["rejected"]) * 8
     assert evals_ctrl < 1.5 * evals_fixed
+
+
+# ---------------------------------------------------------------------------------------
+# Step-size controller (Sec. 3, Eqs. 14-16) on a problem with closed-form step errors
+# ---------------------------------------------------------------------------------------
+
+def _one_cell_polys(a, L):
+    """One Dirichlet cell (1D, n = 1, dx = 1, kappa = 1): f(w) = -2 w, so z = -2 T.  The step's
+    factor R(z) comes from the Chebyshev closed form and the embedded factor
+    Ehat(z) = 1 + z sum_l Re(a_l) Re(P_l(z)), P_l = prod_{j<l} (1 + a_j z), from polynomial
+    algebra on the coefficients -- neither from the oracle's grid stepping."""
+    Poly = np.polynomial.Polynomial
+    Pl, E = Poly([1.0 + 0j]), Poly([1.0])
+    for al in a:
+        E = E + Poly([0.0, 1.0]) * al.real * Poly(Pl.coef.real)
+        Pl = Pl * Poly([1.0, al])
+    return (lambda z: R_closed(z, L)), E
+
+
+def _controller_by_hand(a, L, u0, tol, dt0, attempts, safe=0.8, mutate=None):
+    """Eq. 16 written out from the paper for the one-cell problem: rejection scales T by
+    SAFE/sqrt(e); after an accepted step T <- T (SAFE/sqrt(e_n)) (T_n/T_{n-1}) sqrt(e_{n-1}/e_n)
+    (SAFE/sqrt(e_n) alone after the first).  ``mutate`` plants a plausible mistake."""
+    R, E = _one_cell_polys(a, L)
+    lam = -2.0
+    u, T, Tp, ep, seq = u0, dt0, None, None, []
+    for _ in range(attempts):
+        w, h = R(T * lam) * u, E(T * lam) * u
+        e = abs(w - h) / (tol * (1.0 + max(abs(w), abs(h))))
+        if e > 1.0:
+            seq.append((T, e, False))
+            T *= safe / np.sqrt(e)
+            continue
+        seq.append((T, e, True))
+        u = w
+        expo = 1.0 / 3.0 if mutate == "exponent" else 0.5
+        fac = safe / e ** expo
+        if Tp is not None:
+            if mutate != "no_ratio":
+                fac *= T / Tp
+            if mutate != "no_err_ratio":
+                fac *= np.sqrt(ep / e)
+        if mutate == "no_leading_T":
+            Tp, ep, T = T, e, min(fac, 5.0)
+        else:
+            Tp, ep, T = T, e, T * min(fac, 5.0)
+    return seq
+
+
+def test_controller_sequence_closed_form_one_cell():
+    """The oracle's attempt sequence (T, ||err||, accepted) equals Eq. 16 evaluated on closed-
+    form step errors: one rejection, then accepted steps with changing T.  The same scenario
+    tells the reading apart from a dropped leading T^n, a dropped T^n/T^{n-1}, a dropped
+    sqrt(e_{n-1}/e_n) and a wrong exponent."""
+    L = 16
+    a = O.plan(L)["a"]
+    pr = _prob(1, "dirichlet", "const", 1.0, c=1.0)
+    tol, dt0, attempts = 0.01, 0.5, 7
+    _, st = O.frkc2_adaptive(np.array([1.0]), a, O.beta(L), pr, t_end=100.0, tol=tol, dt0=dt0,
+                             max_steps=attempts)
+    got = st["trace"]
+    ref = _controller_by_hand(a, L, 1.0, tol, dt0, attempts)
+    assert [g[2] for g in got] == [r[2] for r in ref]
+    assert not ref[0][2] and sum(r[2] for r in ref) >= 5
+    Ts = [r[0] for r in ref if r[2]]
+    assert max(Ts) / min(Ts) > 1.5  # the step size really changes
+    for g, r in zip(got, ref):
+        assert abs(g[0] / r[0] - 1.0) < 1e-10 and abs(g[1] / r[1] - 1.0) < 1e-8
+    for m in ("no_leading_T", "no_ratio", "no_err_ratio", "exponent"):
+        bad = _controller_by_hand(a, L, 1.0, tol, dt0, attempts, mutate=m)
+        assert max(abs(b[0] / r[0] - 1.0) for b, r in zip(bad, ref)) > 1e-3, m
+
+
+def test_controller_deadbeat_when_error_scales_as_T_squared():
+    """Eq. 16 is built for a local error estimate ||err|| = C T^2 (Eq. 14 is first order): then
+    one rejection, or one controlled step, sets ||err|| = SAFE^2 and the predictive factor
+    keeps it there.  Small z = T lambda on one cell makes ||err|| proportional to T^2 to
+    about 0.1 %."""
+    L = 16
+    a = O.plan(L)["a"]
+    pr = _prob(1, "dirichlet", "const", 1.0, c=1.0)
+    _, st = O.frkc2_adaptive(np.array([1.0]), a, O.beta(L), pr, t_end=100.0, tol=1e-9, dt0=1e-3,
+                             max_steps=8)
+    tr = st["trace"]
+    assert not tr[0][2]  # e(dt0) > 1: rejected
+    for T, e, ok in tr[1:]:
+        assert ok and abs(e - 0.64) < 5e-3, (T, e)
+
+
+def test_real_pair_form_equals_complex_stages():
+    """Two adjacent conjugate stages on a real state, w + 2 T Re(a) f(w) + T^2 |a|^2 f(f(w)) in
+    the evaluated real form, equal the two literal complex Euler stages for a linear f
+    (a pin of the paired variant, Sec. 2.2 order with pairs adjacent)."""
+    rng = np.random.default_rng(31)
+    shape = (12, 10)
+    pr = _prob(2, "periodic", "field", 1.0, np.exp(0.5 * rng.standard_normal(shape)))
+    u0 = rng.random(shape)
+    for L in (8, 32):
+        a = O.plan(L, method="paired")["a"]
+        dt = 0.9 * O.beta(L) / O.rho_bound(pr)
+        ref = O.frkc2_step(u0, a, dt, pr, 2)
+        got = O.frkc2_step_paired(u0, a, dt, pr, 2)
+        assert np.linalg.norm(got - ref) / np.linalg.norm(ref) < 1e-13
+    # a non-adjacent order is not a pair form: the real form then differs
+    a = O.plan(8)["a"]
+    dt = 0.9 * O.beta(8) / O.rho_bound(pr)
+    assert np.linalg.norm(O.frkc2_step_paired(u0, a, dt, pr, 1) - O.frkc2_step(u0, a, dt, pr, 1)) > 1e-3
+
+
+# ---------------------------------------------------------------------------------------
+# The 3D kappa(u) workload at s = 128 (finding: complex stages of a strongly nonlinear f)
+# ---------------------------------------------------------------------------------------
+
+def test_nonlinear3d_recipe_overflows_at_s128_not_s32():
+    """The 3D recipe (kappa(u) = 1 + u^2.5, hot spot of peak 2 with 1 % noise, Dirichlet,
+    T = 0.9 beta / rho) on a 32^3 instance: at s = 128 the complex stage states of one FP64
+    oracle step overflow; at s = 32 the step is finite and stays near [0, 2]; with kappa
+    frozen at kappa(u0) -- a linear f with the same rho -- the s = 128 step is finite and
+    bounded by max u0.  The failure is the nonlinear kappa evaluated on strongly complex stage
+    states (Sec. 2.2: partial products amplify stage states by up to Q), not the stage count
+    or the step size."""
+    u0 = I.hotspot3d_u0(32, sigma=20.0)
+    pr = _prob(3, "dirichlet", "power", 1.0, c=1.0, p=2.5)
+    rho = O.rho_bound(pr, u0)
+    frozen = _prob(3, "dirichlet", "field", 1.0, field=1.0 + u0 ** 2.5)
+    assert abs(O.rho_bound(frozen) / rho - 1.0) < 1e-12
+    with np.errstate(all="ignore"):
+        for s in (32, 128):
+            pl = O.plan(s)
+            dt = 0.9 * pl["beta"] / rho
+            out = O.frkc2_step(u0, pl["a"], dt, pr, 1)
+            lin = O.frkc2_step(u0, pl["a"], dt, frozen, 1)
+            assert np.all(np.isfinite(lin)) and np.abs(lin).max() <= u0.max()
+            if s == 32:
+                assert np.all(np.isfinite(out)) and -0.05 < out.min() and out.max() < 2.1
+            else:
+                assert not np.all(np.isfinite(out))
