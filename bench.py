@@ -5,9 +5,11 @@ Workload (one bench step = the whole job): 2048^2 periodic grid, kappa = exp(0.5
 unit Gaussian random field of correlation length 32 cells (seed 3818), u0 a smooth random
 field in [0, 1] (correlation length 64, seed 3819), FRKC2 with s = 64 stages, 100 steps of
 dt = 0.9 beta / rho.  A step runs every part of the path: the spectral-radius bound (kernel),
-dt from it, and frkc2_step over 100 x 64 stages.  The primary line is FP64; FP32, MIXED and DFLOAT
-(float-pair state on the FP32 pipe) runs of the same job, and FP64 with a PAIRED plan, are
-reported under "variants" with their errors.
+dt from it, and frkc2_step over 100 x 64 stages.  The primary line is FP64 with the paper's
+stage order; FP32 (with the plan and precision frkc2_plan_auto chooses for this job at a 1e-4
+tolerance: the Lebedev-Finogenov order), MIXED and DFLOAT (float-pair state on the FP32 pipe)
+runs of the same job, and FP64 with a PAIRED plan, are reported under "variants", each with its
+error against the FP64 GPU run and against the FP64 oracle over the whole job length.
 
 Timing: W untimed warm-up steps, then K timed steps, each bracketed by CUDA events on the
 launching stream; L2 is flushed (a 256 MiB write) between timed steps, outside the events.
@@ -37,6 +39,8 @@ import frkc2_inputs as I  # noqa: E402
 CFG = I.CONFIGS["varkappa2d"]
 METRIC = "FRKC2 cell-stage updates/s (2D var-kappa 2048^2, s=64, 100 steps)"
 UNIT = "cell-stage/s"
+# spec tolerance of the FP32 state (relative L2 against the FP64 result, s <= 64)
+POLICY_TOL = 1e-4
 MEASURED_PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
 # FP64 pipe: 152 SMs x 2 FP64 instructions per clock x 2.07 GHz (1.259 TFLOP/s with FMA = 2)
 FP64_PEAK_TINST = 152 * 2 * 2.07e9 / 1e12
@@ -281,14 +285,24 @@ def run_ours(args, rank, world, local_rank):
         "hbm_frac": hbm_gbs / peak_hbm, "avg_launch_us": launch_s * 1e6,
     }
 
+    # precision policy for this job at the FP32 tolerance: plan (stage order) and precision
+    # together; FP32 runs with the plan it returns
+    pol_probe = F.make_problem(2, (n, n), 1.0, "periodic", "field", "fp64")
+    pol_plan, pol_prec, pol_pred = F.frkc2_plan_auto(s, pol_probe, nsteps, POLICY_TOL)
+    policy = {"tol": POLICY_TOL, "precision": pol_prec, "predicted_rel_l2": pol_pred,
+              "order": "Lebedev-Finogenov (FRKC2_PLAN_LEBEDEV)", "rounding_gain": F.frkc2_plan_rounding_gain(pol_plan),
+              "paper_order": {"rounding_gain": F.frkc2_plan_rounding_gain(plan),
+                              "precision": F.frkc2_precision_policy(plan, pol_probe, nsteps, POLICY_TOL)[0]}}
+    variant_plan = {"fp32": pol_plan if pol_prec == "fp32" else plan}
+
     variants = {}
     if not args.no_variants:
         for prec in ("fp32", "mixed", "dfloat"):
-            c, vms, _, _ = timed(prec, args.steps, max(3, args.warmup // 2))
+            c, vms, _, _ = timed(prec, args.steps, max(3, args.warmup // 2), pl=variant_plan.get(prec))
             v = cell_stages * args.steps / (np.sum(vms) / 1e3)
             got = c["u"].double().cpu().numpy()
             err = float(np.linalg.norm(got - u64) / np.linalg.norm(u64))
-            smsec = step_only_ms(c)
+            smsec = step_only_ms(c, pl=variant_plan.get(prec))
             sbytes = 4 if prec == "fp32" else 8
             kbytes = 8 if prec == "fp64" else 4
             # default passes: k stages each; bytes per cell and pass as for FP64 with the
@@ -312,6 +326,8 @@ def run_ours(args, rank, world, local_rank):
                         "hbm_achieved_gbs": g, "hbm_frac": g / peak_hbm, "traffic": None}
             variants[prec] = {
                 "value": v, "ms_per_step": float(np.mean(vms)), "k": k,
+                "plan": ("Lebedev-Finogenov order (frkc2_plan_auto, tol 1e-4)" if variant_plan.get(prec) is pol_plan
+                         else "the paper's greedy order"),
                 "speedup_vs_fp64": v / (cell_stages * args.steps / (float(np.sum(ms)) / 1e3)),
                 "rel_l2_vs_fp64_gpu_after_100_steps": err,
                 "roofline": roof,
@@ -363,6 +379,7 @@ def run_ours(args, rank, world, local_rank):
 
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "precision_policy": policy,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic (seeded GRF conductivity and initial state)",
@@ -377,29 +394,53 @@ def run_ours(args, rank, world, local_rank):
         "gpu_launches": launches,
     }
     if rank == 0 and not args.no_cpu_baseline and world == 1:
-        out["cpu_baseline"], out["error_vs_oracle"] = cpu_baseline(torch, F, dev)
+        out["cpu_baseline"], out["error_vs_oracle"] = cpu_baseline(torch, F, dev, pol_plan)
     return out
 
 
-def cpu_baseline(torch, F, dev, n=1024, stages=16):
-    """The CPU baseline leg: the FP64 oracle timed on every host core at once (one process per
-    core, each on the first ``stages`` stages of one step of the 2048^2 job), and the GPU
-    path's error at each precision against the oracle's output for one full step (64 stages)
-    of a 1024^2 instance of the recipe."""
+def _oracle_job(order, kappa_f32, u0_f32, n, nsteps):
+    """The FP64 oracle over the whole job (nsteps steps of s stages) on an n^2 instance of the
+    recipe, with the stage order of the variant it checks; inputs rounded to float where the
+    variant stores them in float."""
     from oracle import frkc2_oracle as O
 
     u0, k = inputs(n)
+    if kappa_f32:
+        k = k.astype(np.float32).astype(np.float64)
+    if u0_f32:
+        u0 = u0.astype(np.float32).astype(np.float64)
     s = CFG["s"]
+    a = {"greedy": lambda: O.plan(s)["a"], "lebedev": lambda: O.step_sizes(s)[O.order_lebedev(s)],
+         "paired": lambda: O.plan(s, method="paired")["a"]}[order]()
+    pr = dict(ndim=2, dx=1.0, bc="periodic", kappa="field", kappa_c=1.0, kappa_p=2.5, kappa_field=k)
+    dt = CFG["cfl"] * O.beta(s) / O.rho_bound(pr)
+    return O.frkc2_step(u0, a, dt, pr, nsteps), dt
+
+
+def cpu_baseline(torch, F, dev, pol_plan, n=128, stages=16):
+    """The CPU baseline leg: the FP64 oracle timed on every host core at once (one process per
+    core, each on the first ``stages`` stages of one step of the 2048^2 job), and each
+    variant's error against the oracle over the whole job length (100 steps of 64 stages) on an
+    n^2 instance of the recipe, the oracle taking the variant's stage order."""
+    import multiprocessing as mp
+
+    nsteps = CFG["steps"]
+    s = CFG["s"]
+    u0, k = inputs(n)
     plan = F.frkc2_plan(s)
-    oplan = O.plan(s)
+    pplan = F.frkc2_plan(s, flags=F.PLAN_PAIRED)
+    # variant: (precision, library plan, oracle order, kappa in float, u0 in float)
+    cases = {"fp64": ("fp64", plan, "greedy", False, False),
+             "fp32": ("fp32", pol_plan, "lebedev", True, True),
+             "mixed": ("mixed", plan, "greedy", True, False),
+             "dfloat": ("dfloat", plan, "greedy", True, False),
+             "fp64_paired": ("fp64", pplan, "paired", False, False)}
+    jobs = sorted({(c[2], c[3], c[4]) for c in cases.values()})
+    with mp.get_context("spawn").Pool(len(jobs)) as pool:
+        refs = dict(zip(jobs, pool.starmap(_oracle_job, [(o, kf, uf, n, nsteps) for o, kf, uf in jobs])))
     errs = {}
-    value = None
-    for prec in ("fp64", "fp32", "mixed", "dfloat"):
-        kk = k if prec == "fp64" else k.astype(np.float32).astype(np.float64)
-        uu = u0 if prec != "fp32" else u0.astype(np.float32).astype(np.float64)
-        pr = dict(ndim=2, dx=1.0, bc="periodic", kappa="field", kappa_c=1.0, kappa_p=2.5, kappa_field=kk)
-        dt = CFG["cfl"] * O.beta(s) / O.rho_bound(pr)
-        ref = O.frkc2_step(uu, oplan["a"], dt, pr, 1)
+    for name, (prec, pl, order, kf, uf) in cases.items():
+        ref, dt = refs[(order, kf, uf)]
         sd = torch.float32 if prec == "fp32" else torch.float64
         kd = torch.float64 if prec == "fp64" else torch.float32
         u = torch.as_tensor(u0, dtype=sd, device=dev)
@@ -407,21 +448,12 @@ def cpu_baseline(torch, F, dev, n=1024, stages=16):
         lp = F.make_problem(2, (n, n), 1.0, "periodic", "field", prec, kappa_field=kt)
         ws = torch.empty(F.frkc2_workspace_size(lp), dtype=torch.uint8, device=dev)
         F.frkc2_workspace_reset(ws)
-        F.frkc2_step(plan, lp, dt, 1, 0.0, u, ws)
+        F.frkc2_step(pl, lp, dt, nsteps, 0.0, u, ws)
         got = u.double().cpu().numpy()
-        errs[prec] = float(np.linalg.norm(got - ref) / np.linalg.norm(ref))
-    # the paired variant against the oracle's complex stages in the same (paired) order
-    pplan = F.frkc2_plan(s, flags=F.PLAN_PAIRED)
-    opl = O.plan(s, method="paired")
-    pr = dict(ndim=2, dx=1.0, bc="periodic", kappa="field", kappa_c=1.0, kappa_p=2.5, kappa_field=k)
-    dt = CFG["cfl"] * O.beta(s) / O.rho_bound(pr)
-    ref = O.frkc2_step(u0, opl["a"], dt, pr, 1)
-    u = torch.as_tensor(u0, dtype=torch.float64, device=dev)
-    lp = F.make_problem(2, (n, n), 1.0, "periodic", "field", "fp64", kappa_field=torch.as_tensor(k, device=dev))
-    ws = torch.empty(F.frkc2_workspace_size(lp), dtype=torch.uint8, device=dev)
-    F.frkc2_step(pplan, lp, dt, 1, 0.0, u, ws)
-    errs["fp64_paired"] = float(np.linalg.norm(u.cpu().numpy() - ref) / np.linalg.norm(ref))
-    errs["sample"] = f"one step (64 stages) on a {n}^2 instance of the recipe"
+        errs[name] = {"rel_l2": float(np.linalg.norm(got - ref) / np.linalg.norm(ref)),
+                      "max_abs_over_max_ref": float(np.abs(got - ref).max() / np.abs(ref).max())}
+    errs["sample"] = (f"the whole job length ({nsteps} steps of {s} stages) on a {n}^2 instance of the recipe "
+                      f"(correlation lengths scaled by {n}/2048), the oracle with each variant's stage order")
     times, cores = oracle_on_host_cores(stages, 1)
     N = CFG["n"]
     value = cores * N * N * stages / times[0]

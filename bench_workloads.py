@@ -323,9 +323,10 @@ def ssweep(F):
 
 def precision(F):
     """Error of each reduced precision against the FP64 GPU run of the same 2048^2 var-kappa
-    job (the bench recipe) by stage count and ordering, after 1 and 10 steps: the stage count
-    up to which FP32 state and arithmetic stay within 1e-4 relative L2, and what the
-    float-pair state (DFLOAT) and MIXED give beyond it."""
+    job (the bench recipe) by stage count and ordering, after 1, 10 and 100 steps (the job's
+    length): the stage count up to which FP32 state and arithmetic stay within 1e-4 relative
+    L2, what the float-pair state (DFLOAT) and MIXED give beyond it, and beside each the
+    precision policy's predicted FP32 error and its choice (frkc2_precision_policy)."""
     torch = _torch()
     cfg = I.CONFIGS["varkappa2d"]
     n = cfg["n"]
@@ -348,8 +349,8 @@ def precision(F):
             plan = F.frkc2_plan(s, flags=flag)
             info = plan.info()
             dt = cfg["cfl"] * info["beta"] / rho.item()
-            row = {"Q_over_L2": info["Q"] / s ** 2}
-            for nsteps in (1, 10):
+            row = {"Q_over_L2": info["Q"] / s ** 2, "rounding_gain": F.frkc2_plan_rounding_gain(plan)}
+            for nsteps in (1, 10, 100):
                 outs = {}
                 for prec in precs:
                     sd = torch.float32 if prec == "fp32" else torch.float64
@@ -358,13 +359,17 @@ def precision(F):
                     F.frkc2_step(plan, probs[prec][0], dt, nsteps, 0.0, u, wss[prec])
                     outs[prec] = u.double().cpu().numpy()
                 row[f"steps{nsteps}"] = {p: _rel(outs[p], outs["fp64"]) for p in precs if p != "fp64"}
+                choice, pred = F.frkc2_precision_policy(plan, probs["fp64"][0], nsteps, 1e-4)
+                row[f"steps{nsteps}"]["fp32_predicted"] = pred if choice == "fp32" else pred / 5e-2 if choice in (
+                    "dfloat", "mixed") else pred * 2.0 ** 29
+                row[f"steps{nsteps}"]["policy_at_1e-4"] = choice
             rows[f"{order}_s{s}"] = row
-            if row["steps1"]["fp32"] <= 1e-4 and row["steps10"]["fp32"] <= 1e-4 and s > best:
+            if all(row[f"steps{m}"]["fp32"] <= 1e-4 for m in (1, 10, 100)) and s > best:
                 best = s
         threshold[order] = best
     return {"workload": "precision: 2048^2 var-kappa periodic (bench recipe), error vs the FP64 GPU run by s and "
-                        "ordering, 1 and 10 steps",
-            "metric": "largest s with FP32 rel L2 <= 1e-4 after 1 and 10 steps", "value": threshold,
+                        "ordering, 1, 10 and 100 steps",
+            "metric": "largest s with FP32 rel L2 <= 1e-4 after 1, 10 and 100 steps", "value": threshold,
             "unit": "stages", "by_s": rows}
 
 

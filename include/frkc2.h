@@ -143,6 +143,44 @@ frkc2_status frkc2_plan_info(frkc2_plan_t plan, int* s, double* beta, double* Q,
 
 void frkc2_plan_destroy(frkc2_plan_t plan);
 
+/* ---- Precision policy (Sec. 2.2 applied to rounding) -------------------------------------
+ * Rounding gain of the plan's stage order, g = sqrt(sum_l mean_x |prod_{j>l}(1 + a_j x)|^2),
+ * the mean over max(2048, 4 s) evenly spaced midpoints x of [-beta, 0].  A rounding error
+ * made in stage l reaches the step's output through the factors of the later stages (the
+ * partial products of Sec. 2.2, Eq. 10), so with rounding spread evenly over the spectrum
+ * one step's relative error is about (unit roundoff) * g.  The paper's greedy order has g of
+ * about 30 (s = 16) to 6300 (s = 256); the Lebedev-Finogenov order about 1.8 to 3.4.      */
+frkc2_status frkc2_plan_rounding_gain(frkc2_plan_t plan, double* gain);
+
+/* The cheapest state precision whose predicted relative L2 error after nsteps steps (against
+ * FP64 arithmetic with the same plan) is at most tol.  With n = nsteps, s the plan's stage
+ * count and A = g sqrt(n) + 4e-3 s n (the stage roundings amplified by the later stages and
+ * adding like a random walk over steps, plus the s n roundings of a slowly changing state,
+ * which do not cancel):
+ *   FP32                          if e32 = 1.5 * 2^-24 * A <= tol,
+ *   DFLOAT (2D FIELD / CONST) or
+ *   MIXED (other problems)        if 5e-2 * e32 <= tol (double-class state, float flux
+ *                                 arithmetic),
+ *   FP64                          otherwise (predicted 1.5 * 2^-53 * A).
+ * The constants are measured on GB300 (2048^2 diffusion recipe, greedy and Lebedev-Finogenov
+ * orders, s = 16..256, 1 to 100 steps): every FP32 error measured is at most 0.9 of e32;
+ * DFLOAT and MIXED measured 1.1e-3..2.3e-2 of the FP32 error.  The prediction assumes
+ * rounding spread over the spectrum, as for smooth data; it is a forecast, not a bound.
+ *   prob      : only ndim and kappa_kind are read (precision and pointers are ignored).
+ *   nsteps    : >= 1.   tol : > 0.
+ *   precision : receives FRKC2_FP32, FRKC2_DFLOAT, FRKC2_MIXED or FRKC2_FP64.
+ *   predicted : receives the predicted error (may be NULL).                                */
+frkc2_status frkc2_precision_policy(frkc2_plan_t plan, const frkc2_problem* prob, int nsteps,
+                                    double tol, int* precision, double* predicted);
+
+/* A plan and a precision together.  FIELD / CONST problems get the stage order of least
+ * rounding gain (the Lebedev-Finogenov order, FRKC2_PLAN_LEBEDEV); POWER problems get the
+ * default plan of frkc2_plan, because with kappa(u) the strongly complex stage states of that
+ * order leave the range where kappa(W) is tame.  Then frkc2_precision_policy chooses the
+ * precision.  *plan receives a new plan (release with frkc2_plan_destroy).               */
+frkc2_status frkc2_plan_auto(int s, const frkc2_problem* prob, int nsteps, double tol,
+                             frkc2_plan_t* plan, int* precision, double* predicted);
+
 /* ---- Spectral-radius bound --------------------------------------------------------------
  * rho = max_c (2/dx^2) sum_faces kappa_f (Gershgorin), the |lambda|_max of Sec. 3 that sets
  * T <= beta / rho.  For POWER the conductivity is evaluated at the real state u (device

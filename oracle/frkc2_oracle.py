@@ -13,7 +13,8 @@ Contents
 * stability polynomial and step sizes (Sec. 2, Eqs. 5-8): ``alpha``, ``beta``, ``roots``,
   ``step_sizes``;
 * internal stability (Sec. 2.2, Eqs. 10-12): ``realised_Q`` (brute force over all
-  sub-sequences), ``order_greedy``, ``order_lebedev`` and ``plan`` (the n-loop);
+  sub-sequences), ``rounding_gain`` (the partial products applied to rounding errors),
+  ``order_greedy``, ``order_lebedev`` and ``plan`` (the n-loop);
 * the diffusion operator f(w) = div(kappa grad w) in flux form (the semi-discrete system of
   Eq. 1): ``cell_kappa``, ``apply_f``, ``rho_bound``;
 * the FRKC2 step (Sec. 3, Eq. 13), stages applied literally as complex forward-Euler steps:
@@ -171,6 +172,29 @@ def realised_Q(a: np.ndarray, beta_: float, points: int) -> float:
         sub = np.cumsum(logv[j:], axis=0)  # row k-j holds log prod_{l=j}^{k}
         best = max(best, float(sub.max()))
     return float(np.exp(best))
+
+
+def rounding_gain(a: np.ndarray, beta_: float, points: int | None = None) -> float:
+    """Rounding gain of a stage order: g = sqrt(sum_l mean_x |prod_{j>l} (1 + a_j x)|^2).
+
+    A rounding error made in stage l (while forming W^{l+1}) reaches the step's output through
+    the factors of the later stages l+1..L-1 (the partial products of Sec. 2.2, Eq. 10), so if
+    the rounding is spread evenly over the spectrum x = T lambda in [-beta, 0] one step's
+    relative error is about (unit roundoff) * g.  The mean is over ``points`` midpoints
+    x_i = -beta (i + 1/2) / points (default max(2048, 4 L)).  Plain definition: each suffix
+    product is formed afresh.
+    """
+    a = np.asarray(a)
+    L = len(a)
+    P = points or max(2048, 4 * L)
+    x = -beta_ * (np.arange(P) + 0.5) / P
+    total = 0.0
+    for l in range(L):
+        prod = np.ones(P, dtype=np.complex128)
+        for j in range(l + 1, L):
+            prod = prod * (1.0 + a[j] * x)
+        total += float(np.mean(np.abs(prod) ** 2))
+    return float(np.sqrt(total))
 
 
 def order_greedy(a: np.ndarray, beta_: float, n: int, samples: int, C: float = 1e-4) -> np.ndarray:

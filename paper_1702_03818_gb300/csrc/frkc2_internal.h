@@ -18,6 +18,7 @@ struct frkc2_plan_s {
   std::vector<double> a_re;   // step sizes in stage order
   std::vector<double> a_im;
   bool paired = false;        // conjugates adjacent: stages 2p, 2p+1 form one real pair
+  double gain = 0.0;          // rounding gain of the stage order (frkc2_plan_rounding_gain)
 };
 
 namespace frkc2 {

@@ -209,6 +209,31 @@ double realised_Q(const std::vector<cplx>& a, double beta, int P) {
   return std::exp(*std::max_element(best.begin(), best.end()));
 }
 
+// Rounding gain g = sqrt(sum_l mean_x |prod_{j>l} (1 + a_j x)|^2) over P = max(2048, 4L)
+// midpoints x_i = -beta (i + 1/2)/P.  A rounding error of stage l reaches the step's output
+// through the factors of the later stages (the partial products of Sec. 2.2), so with the
+// rounding spread evenly over the spectrum one step's relative error is about
+// (unit roundoff) x g.  Per x the suffix products are built from the last stage backwards.
+double rounding_gain(const std::vector<cplx>& a, double beta) {
+  const int L = int(a.size()), P = std::max(2048, 4 * L);
+  std::vector<double> part(P, 0.0);
+  parallel_ranges(P, [&](int lo, int hi) {
+    for (int i = lo; i < hi; ++i) {
+      const double x = -beta * (double(i) + 0.5) / double(P);
+      cplx suf = 1.0;
+      double acc = 0.0;
+      for (int l = L - 1; l >= 0; --l) {
+        acc += std::norm(suf);  // |prod_{j>l} (1 + a_j x)|^2
+        suf *= 1.0 + a[l] * x;
+      }
+      part[i] = acc;
+    }
+  });
+  double total = 0.0;
+  for (double v : part) total += v;
+  return std::sqrt(total / double(P));
+}
+
 // Lebedev-Finogenov recursive permutation of 0..m-1: P(1) = (0); P(2q) interleaves each v of
 // P(q) with 2q-1-v; P(2q+1) = P(2q) followed by 2q.
 std::vector<int> lebedev_permutation(int m) {
@@ -296,10 +321,13 @@ frkc2_status frkc2_plan(int s, double nu, unsigned flags, frkc2_plan_t* out) {
   p->paired = paired;
   p->a_re.resize(L);
   p->a_im.resize(L);
+  std::vector<cplx> ao(L);
   for (int l = 0; l < L; ++l) {
     p->a_re[l] = a[best_order[l]].real();
     p->a_im[l] = a[best_order[l]].imag();
+    ao[l] = a[best_order[l]];
   }
+  p->gain = rounding_gain(ao, beta);
   *out = p;
   return FRKC2_OK;
 }
@@ -319,6 +347,7 @@ frkc2_status frkc2_plan_from_steps(int s, const double* a_re, const double* a_im
   std::vector<cplx> ao(s);
   for (int l = 0; l < s; ++l) ao[l] = cplx(a_re[l], a_im[l]);
   p->Q = realised_Q(ao, p->beta, 16 * s);
+  p->gain = rounding_gain(ao, p->beta);
   *out = p;
   return FRKC2_OK;
 }
@@ -333,6 +362,12 @@ frkc2_status frkc2_plan_info(frkc2_plan_t plan, int* s, double* beta, double* Q,
   if (a_re) std::memcpy(a_re, plan->a_re.data(), sizeof(double) * plan->s);
   if (a_im) std::memcpy(a_im, plan->a_im.data(), sizeof(double) * plan->s);
   if (order) std::memcpy(order, plan->order.data(), sizeof(int) * plan->s);
+  return FRKC2_OK;
+}
+
+frkc2_status frkc2_plan_rounding_gain(frkc2_plan_t plan, double* gain) {
+  if (!plan || !gain) return FRKC2_EINVAL;
+  *gain = plan->gain;
   return FRKC2_OK;
 }
 

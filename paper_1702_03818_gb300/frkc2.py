@@ -55,6 +55,11 @@ _sig = {
     "frkc2_plan_from_steps": (C.c_int, [C.c_int, _P, _P, C.POINTER(_P)]),
     "frkc2_plan_info": (C.c_int, [_P, _P, _P, _P, _P, _P, _P, _P]),
     "frkc2_plan_destroy": (None, [_P]),
+    "frkc2_plan_rounding_gain": (C.c_int, [_P, C.POINTER(C.c_double)]),
+    "frkc2_precision_policy": (C.c_int, [_P, C.POINTER(frkc2_problem), C.c_int, C.c_double,
+                                         C.POINTER(C.c_int), C.POINTER(C.c_double)]),
+    "frkc2_plan_auto": (C.c_int, [C.c_int, C.POINTER(frkc2_problem), C.c_int, C.c_double, C.POINTER(_P),
+                                  C.POINTER(C.c_int), C.POINTER(C.c_double)]),
     "frkc2_rho_bound": (C.c_int, [C.POINTER(frkc2_problem), _P, _P, _P]),
     "frkc2_workspace_size": (C.c_int, [C.POINTER(frkc2_problem), C.POINTER(frkc2_tuning), C.POINTER(C.c_size_t)]),
     "frkc2_workspace_reset": (C.c_int, [_P, _P]),
@@ -180,6 +185,31 @@ def frkc2_plan_info(plan: Plan) -> dict:
     _check(_lib.frkc2_plan_info(plan.handle, None, None, None, None, re.ctypes.data, im.ctypes.data,
                                 order.ctypes.data), "frkc2_plan_info")
     return dict(s=L, beta=beta.value, Q=Q.value, n_iter=n_iter.value, a=re + 1j * im, order=order)
+
+
+def frkc2_plan_rounding_gain(plan: Plan) -> float:
+    g = C.c_double()
+    _check(_lib.frkc2_plan_rounding_gain(plan.handle, C.byref(g)), "frkc2_plan_rounding_gain")
+    return g.value
+
+
+PRECISION_NAME = {v: k for k, v in PRECISION.items()}
+
+
+def frkc2_precision_policy(plan: Plan, prob: frkc2_problem, nsteps: int, tol: float):
+    """Returns (precision name, predicted relative error)."""
+    pr, e = C.c_int(), C.c_double()
+    _check(_lib.frkc2_precision_policy(plan.handle, C.byref(prob), int(nsteps), float(tol), C.byref(pr),
+                                       C.byref(e)), "frkc2_precision_policy")
+    return PRECISION_NAME[pr.value], e.value
+
+
+def frkc2_plan_auto(s: int, prob: frkc2_problem, nsteps: int, tol: float):
+    """Returns (Plan, precision name, predicted relative error)."""
+    h, pr, e = _P(), C.c_int(), C.c_double()
+    _check(_lib.frkc2_plan_auto(int(s), C.byref(prob), int(nsteps), float(tol), C.byref(h), C.byref(pr),
+                                C.byref(e)), "frkc2_plan_auto")
+    return Plan(h), PRECISION_NAME[pr.value], e.value
 
 
 def make_problem(ndim: int, n, dx: float, bc="periodic", kappa="field", precision="fp64",

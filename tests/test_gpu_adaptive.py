@@ -4,7 +4,7 @@ import numpy as np
 import pytest
 
 from oracle import frkc2_oracle as O
-from helpers import oracle_problem, rel_l2, seeded_case
+from helpers import oracle_problem, rel_err, seeded_case
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -38,7 +38,7 @@ def test_adaptive_matches_oracle_controller(case):
     assert abs(st["t"] - t_end) < 1e-9 * t_end
     assert (st["accepted"], st["rejected"]) == (st_ref["accepted"], st_ref["rejected"])
     assert st_ref["rejected"] >= 0 and st_ref["accepted"] >= 2
-    assert rel_l2(u.cpu().numpy(), ref) < 1e-10
+    assert rel_err(u.cpu().numpy(), ref) < 1e-10
 
 
 def test_adaptive_rejects_an_oversized_first_step_and_recovers():
@@ -86,7 +86,7 @@ def test_cmp_two_material(ratio):
     u = torch.as_tensor(u0, device="cuda")
     F.frkc2_step(plan, pr, t_end / nst, nst, 0.0, u, ws)
     fixed = u.cpu().numpy()
-    assert rel_l2(fixed, O.frkc2_step(u0, oplan["a"], t_end / nst, opr, nst)) < 1e-11
+    assert rel_err(fixed, O.frkc2_step(u0, oplan["a"], t_end / nst, opr, nst)) < 1e-11
     assert sign_changes(fixed) > 10
     # error control
     ref, st_ref = O.frkc2_adaptive(u0, oplan["a"], oplan["beta"], opr, t_end, 1e-3, 1e-6, rho=rho)
@@ -95,7 +95,7 @@ def test_cmp_two_material(ratio):
     st = F.frkc2_step_adaptive(plan, pr, t_end, 1e-3, 1e-6, rho, u, wsa)
     ctrl = u.cpu().numpy()
     assert (st["accepted"], st["rejected"]) == (st_ref["accepted"], st_ref["rejected"])
-    assert rel_l2(ctrl, ref) < 1e-10
+    assert rel_err(ctrl, ref) < 1e-10
     assert sign_changes(ctrl) == 2 and ctrl.max() <= 1.0 and ctrl.min() >= 0.0
 
 
@@ -132,6 +132,6 @@ def test_adaptive_streaming_and_tile_paths_agree(prec, tol_u):
         else:
             assert abs(st["accepted"] - st_ref["accepted"]) <= 1, (tune, st, st_ref)
         got = u.double().cpu().numpy()
-        assert rel_l2(got, ref) < tol_u, (tune, rel_l2(got, ref))
+        assert rel_err(got, ref) < tol_u, (tune, rel_err(got, ref))
         outs.append(got)
-    assert rel_l2(outs[0], outs[1]) < tol_u
+    assert rel_err(outs[0], outs[1]) < tol_u

@@ -4,7 +4,7 @@ import numpy as np
 import pytest
 
 from oracle import frkc2_oracle as O
-from helpers import oracle_problem, rel_l2, seeded_case
+from helpers import oracle_problem, rel_err, seeded_case
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -66,9 +66,9 @@ def test_adjoint_matches_oracle(case, prec, tol):
         g = g.astype(np.float32).astype(np.float64)
     ref_u, ref_k = O.frkc2_adjoint(u0o, oplan["a"], dt, opr, nsteps, g)
     du, dk = gpu_adjoint(plan, shape, bc, kappa, prec, u0, field, dt, nsteps, ckpt, g)
-    assert rel_l2(du, ref_u) < tol, rel_l2(du, ref_u)
+    assert rel_err(du, ref_u) < tol, rel_err(du, ref_u)
     if kappa == "field":
-        assert rel_l2(dk, ref_k) < tol, rel_l2(dk, ref_k)
+        assert rel_err(dk, ref_k) < tol, rel_err(dk, ref_k)
 
 
 def test_dot_product_gpu_forward_vs_gpu_adjoint():
@@ -134,8 +134,8 @@ def test_autograd_wrapper():
     opr = oracle_problem(2, "periodic", "field", 1.0, field)
     uT = O.frkc2_step(u0, oplan["a"], dt, opr, nsteps)
     ref_u, ref_k = O.frkc2_adjoint(u0, oplan["a"], dt, opr, nsteps, 2 * uT)
-    assert rel_l2(u.grad.cpu().numpy(), ref_u) < 1e-10
-    assert rel_l2(k.grad.cpu().numpy(), ref_k) < 1e-10
+    assert rel_err(u.grad.cpu().numpy(), ref_u) < 1e-10
+    assert rel_err(k.grad.cpu().numpy(), ref_k) < 1e-10
 
 
 @pytest.mark.parametrize("shape,bc", [((50, 44), "periodic"), ((33, 41), "dirichlet")])
@@ -151,7 +151,7 @@ def test_split_forward_backward_equals_combined(shape, bc):
     uT = torch.empty_like(u0d)
     F.frkc2_adjoint_forward(plan, pr, dt, nsteps, ck, u0d, uT, ws)
     ref_uT = gpu_forward(plan, shape, bc, "field", "fp64", u0, field, dt, nsteps)
-    assert rel_l2(uT.cpu().numpy(), ref_uT) < 1e-13
+    assert rel_err(uT.cpu().numpy(), ref_uT) < 1e-13
     g = np.random.default_rng(62).standard_normal(shape)
     du = torch.empty_like(u0d)
     dk = torch.empty_like(kt)
@@ -159,7 +159,7 @@ def test_split_forward_backward_equals_combined(shape, bc):
     du2, dk2 = gpu_adjoint(plan, shape, bc, "field", "fp64", u0, field, dt, nsteps, ck, g)
     assert np.array_equal(du.cpu().numpy(), du2) and np.array_equal(dk.cpu().numpy(), dk2)
     ref_u, ref_k = O.frkc2_adjoint(u0, O.plan(s)["a"], dt, oracle_problem(2, bc, "field", 1.0, field), nsteps, g)
-    assert rel_l2(du2, ref_u) < 1e-10 and rel_l2(dk2, ref_k) < 1e-10
+    assert rel_err(du2, ref_u) < 1e-10 and rel_err(dk2, ref_k) < 1e-10
 
 
 TB_CASES = [
@@ -187,8 +187,8 @@ def test_adjoint_fp32_temporal_blocking_matches_oracle(case):
     g = np.random.default_rng(8).standard_normal(shape).astype(np.float32).astype(np.float64)
     ref_u, ref_k = O.frkc2_adjoint(u0o, oplan["a"], dt, opr, nsteps, g)
     du, dk = gpu_adjoint(plan, shape, bc, "field", "fp32", u0, field, dt, nsteps, ckpt, g)
-    assert rel_l2(du, ref_u) < 2e-3, rel_l2(du, ref_u)
-    assert rel_l2(dk, ref_k) < 2e-3, rel_l2(dk, ref_k)
+    assert rel_err(du, ref_u) < 2e-3, rel_err(du, ref_u)
+    assert rel_err(dk, ref_k) < 2e-3, rel_err(dk, ref_k)
 
 
 def test_adjoint_fp32_dot_product_with_fp32_forward():

@@ -7,7 +7,7 @@ import numpy as np
 import pytest
 
 from oracle import frkc2_oracle as O
-from helpers import oracle_problem, rel_l2, seeded_case
+from helpers import oracle_problem, rel_err, seeded_case
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -41,7 +41,7 @@ def test_autotune_step_fp32_and_cache(tmp_path, monkeypatch):
     b = u.clone()
     ws2 = torch.empty(F.frkc2_workspace_size(pr), dtype=torch.uint8, device="cuda")
     F.frkc2_step(plan, pr, dt, 2, 0.0, b, ws2)
-    assert rel_l2(a.double().cpu().numpy(), b.double().cpu().numpy()) < 1e-4
+    assert rel_err(a.double().cpu().numpy(), b.double().cpu().numpy()) < 1e-4
 
 
 def test_autotune_batch_runs():

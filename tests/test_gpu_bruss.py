@@ -6,7 +6,7 @@ import pytest
 import frkc2_inputs as I
 from oracle import brusselator as BR
 from oracle import frkc2_oracle as O
-from helpers import rel_l2
+from helpers import rel_err
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -73,7 +73,7 @@ def test_bruss_matches_oracle(case, prec, kernel):
     F.frkc2_bruss_step(plan, p, dt, nsteps, 0.0, v, w, ws, F.make_tuning(kernel=kernel))
     assert F.frkc2_workspace_status(ws) == F.OK
     gv, gw = v.double().cpu().numpy(), w.double().cpu().numpy()
-    ev, ew = rel_l2(gv, rv), rel_l2(gw, rw)
+    ev, ew = rel_err(gv, rv), rel_err(gw, rw)
     assert ev < TOL[prec] and ew < TOL[prec], (ev, ew)
 
 
@@ -106,7 +106,7 @@ def test_more_than_1024_stages_chunked_launches():
     g2 = run_gpu(plan, shape, "neumann", "fp64", v0, w0, dt, 2, kernel=2)
     assert g1[2] == F.OK and g2[2] == F.OK
     assert np.array_equal(g1[0], g2[0]) and np.array_equal(g1[1], g2[1])
-    assert rel_l2(g1[0], rv) < 1e-11 and rel_l2(g1[1], rw) < 1e-11
+    assert rel_err(g1[0], rv) < 1e-11 and rel_err(g1[1], rw) < 1e-11
 
 
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
@@ -161,7 +161,7 @@ def test_barrier_wait_runs_out_and_context_survives():
     v, w, st = run_gpu(plan, shape, "periodic", "fp64", v0, w0, dt, 2, kernel=1)
     assert st == F.OK
     rv, rw = BR.frkc2_step(v0, w0, O.plan(8)["a"], dt, BR.problem(shape), 2)
-    assert rel_l2(v, rv) < 1e-11 and rel_l2(w, rw) < 1e-11
+    assert rel_err(v, rv) < 1e-11 and rel_err(w, rw) < 1e-11
 
 
 def test_launch_counts():

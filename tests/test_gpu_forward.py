@@ -9,7 +9,7 @@ import pytest
 
 from oracle import frkc2_oracle as O
 import frkc2_inputs as I
-from helpers import oracle_problem, rel_l2, seeded_case
+from helpers import oracle_problem, rel_err, seeded_case
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -124,7 +124,7 @@ def test_step_parity(case, prec):
     tune = F.make_tuning(k=k, kernel=kernel)
     got, st = run_gpu(plan, shape, bc, kappa, prec, u0, field, dt, nsteps, tune=tune)
     assert st == F.OK
-    err = rel_l2(got, ref)
+    err = rel_err(got, ref)
     assert err < TOL[prec], err
 
 
@@ -140,7 +140,7 @@ def test_heat1d_workload_matches_closed_form_and_oracle():
     ref = O.frkc2_step(u0, O.plan(L)["a"], dt, opr, nsteps)
     got, st = run_gpu(plan, (cfg["n"],), "dirichlet", "const", "fp64", u0, None, dt, nsteps, dx=dx)
     assert st == F.OK and nsteps == 87
-    assert rel_l2(got, ref) < 1e-12
+    assert rel_err(got, ref) < 1e-12
 
 
 def test_varkappa2d_reduced_many_steps_fp64_fp32():
@@ -158,7 +158,7 @@ def test_varkappa2d_reduced_many_steps_fp64_fp32():
         ref = O.frkc2_step(u0g, oplan["a"], dt, opr, 4)
         got, st = run_gpu(plan, shape, "periodic", "field", prec, u0, field, dt, 4)
         assert st == F.OK
-        assert rel_l2(got, ref) < tol, (prec, rel_l2(got, ref))
+        assert rel_err(got, ref) < tol, (prec, rel_err(got, ref))
 
 
 def test_nsteps_zero_and_nonfinite_flag():
@@ -210,7 +210,7 @@ def test_step_parity_fp32_temporal_blocking(case):
     ref = O.frkc2_step(u0.astype(np.float32).astype(np.float64), oplan["a"], dt, opr, nsteps)
     got, st = run_gpu(plan, shape, bc, kappa, "fp32", u0, field, dt, nsteps, tune=F.make_tuning(k=k, kernel=3))
     assert st == F.OK
-    assert rel_l2(got, ref) < TOL["fp32"], rel_l2(got, ref)
+    assert rel_err(got, ref) < TOL["fp32"], rel_err(got, ref)
 
 
 def test_tb_kernel_rejects_unsupported():
@@ -250,9 +250,9 @@ def test_step_parity_paired_real_pairs(case, prec, tol):
     ref = O.frkc2_step(u0g, oplan["a"], dt, opr, nsteps)
     got, st = run_gpu(plan, shape, bc, kappa, prec, u0, field, dt, nsteps, tune=F.make_tuning(kernel=4))
     assert st == F.OK
-    assert rel_l2(got, ref) < tol, rel_l2(got, ref)
+    assert rel_err(got, ref) < tol, rel_err(got, ref)
     # the oracle's own real pair form agrees with its complex stages
-    assert rel_l2(O.frkc2_step_paired(u0g, oplan["a"], dt, opr, nsteps), ref) < 1e-12
+    assert rel_err(O.frkc2_step_paired(u0g, oplan["a"], dt, opr, nsteps), ref) < 1e-12
 
 
 def test_paired_plan_on_3d_runs_as_complex_stages():
@@ -264,7 +264,7 @@ def test_paired_plan_on_3d_runs_as_complex_stages():
     dt = 0.9 * oplan["beta"] / O.rho_bound(opr)
     ref = O.frkc2_step(u0, oplan["a"], dt, opr, 2)
     got, st = run_gpu(plan, shape, "periodic", "field", "fp64", u0, field, dt, 2)
-    assert st == F.OK and rel_l2(got, ref) < 1e-11
+    assert st == F.OK and rel_err(got, ref) < 1e-11
 
 
 # ---------------------------------------------------------------------------------------
@@ -302,7 +302,7 @@ def test_step_parity_dfloat(case):
     ref = O.frkc2_step(u0, oplan["a"], dt, opr, nsteps)
     got, st = run_gpu(plan, shape, bc, kappa, "dfloat", u0, field, dt, nsteps, tune=F.make_tuning(k=kk, kernel=kernel))
     assert st == F.OK
-    err = rel_l2(got, ref)
+    err = rel_err(got, ref)
     assert err < TOL["dfloat"], err
 
 
@@ -323,7 +323,7 @@ def test_dfloat_keeps_state_precision_fp32_loses():
     assert st == F.OK
     got_32, _ = run_gpu(plan, shape, "periodic", "field", "fp32", u0, field, dt, nsteps,
                         tune=F.make_tuning(k=1, kernel=2))
-    e_df, e_32 = rel_l2(got_df, ref), rel_l2(got_32, ref32)
+    e_df, e_32 = rel_err(got_df, ref), rel_err(got_32, ref32)
     assert e_df < 1e-6 and e_df * 10 < e_32, (e_df, e_32)
 
 
@@ -343,7 +343,7 @@ def test_dfloat_launch_count():
     v = dev(u0, torch.float64)
     F.frkc2_step(plan, pr, dt, 3, 0.0, v, ws)
     assert F.frkc2_launch_count() == 1 + 3 * 2  # faces, then passes of 8 and 8 stages
-    assert rel_l2(v.cpu().numpy(), u.cpu().numpy()) < 1e-6
+    assert rel_err(v.cpu().numpy(), u.cpu().numpy()) < 1e-6
 
 
 # ---------------------------------------------------------------------------------------
@@ -377,7 +377,7 @@ def test_step_parity_stream3d(case, prec):
     ref = O.frkc2_step(u0g, oplan["a"], dt, opr, nsteps)
     got, st = run_gpu(plan, shape, bc, kappa, prec, u0, field, dt, nsteps, tune=F.make_tuning(k=1, kernel=kernel))
     assert st == F.OK
-    err = rel_l2(got, ref)
+    err = rel_err(got, ref)
     assert err < TOL[prec], err
 
 
@@ -390,7 +390,7 @@ def test_stream3d_equals_tile_pass_and_rejects_k():
     a, st_a = run_gpu(plan, shape, "dirichlet", "power", "fp64", u0, None, dt, 1, tune=F.make_tuning(k=1, kernel=5))
     b, st_b = run_gpu(plan, shape, "dirichlet", "power", "fp64", u0, None, dt, 1, tune=F.make_tuning(k=1, kernel=1))
     assert st_a == F.OK and st_b == F.OK
-    assert rel_l2(a, b) < 1e-13
+    assert rel_err(a, b) < 1e-13
     pr = lib_problem(shape, "dirichlet", "power", "fp64")
     ws = torch.empty(F.frkc2_workspace_size(pr), dtype=torch.uint8, device="cuda")
     with pytest.raises(F.Frkc2Error) as e:
@@ -430,7 +430,7 @@ def test_step_parity_small1d(case, prec):
     got, st = run_gpu(plan, shape, bc, kappa, prec, u0, field, dt, nsteps, tune=F.make_tuning(kernel=kernel))
     assert F.frkc2_launch_count() == 2  # face set-up and the whole job
     assert st == F.OK
-    err = rel_l2(got, ref)
+    err = rel_err(got, ref)
     assert err < TOL[prec], err
 
 
@@ -468,10 +468,10 @@ def test_small1d_cluster_size_choice(n, prec, tol):
         got, st = run_gpu(plan, (n,), "dirichlet", "field", prec, u0, field, dt, 5,
                           tune=F.make_tuning(kernel=6, tile=(cl, 0, 0)))
         assert st == F.OK
-        assert rel_l2(got, ref) < tol, (cl, rel_l2(got, ref))
+        assert rel_err(got, ref) < tol, (cl, rel_err(got, ref))
         outs.append(got)
     for o in outs[1:]:
-        assert rel_l2(o, outs[0]) < (1e-14 if prec == "fp64" else 1e-6), rel_l2(o, outs[0])
+        assert rel_err(o, outs[0]) < (1e-14 if prec == "fp64" else 1e-6), rel_err(o, outs[0])
 
 
 def test_small1d_rejects_out_of_range():

@@ -30,6 +30,16 @@ def sampled_cells(shape, count, seed):
     return [tuple(int(rng.integers(0, n)) for n in shape) for _ in range(count)]
 
 
+def seam_cells_2d(n):
+    """Corners, edges and the seams of the launch layouts on an n x n grid: 48-cell output
+    tiles of the 64 x 64 register-tiled regions (k = 8), 31- and 30-column warp chunks of the
+    streaming passes, the wrap of the periodic grid and the middle of the grid."""
+    xs = sorted({0, 1, 30, 31, 47, 48, 61, 62, 95, 96, n // 2 - 1, n // 2, n - 49, n - 48, n - 2, n - 1})
+    ys = [0, 47, 48, n // 2, n - 48, n - 1]
+    cells = [(y, x) for y in ys for x in xs[::2]] + [(y, x) for y in ys[::3] for x in xs[1::2]]
+    return sorted(set(cells))
+
+
 @pytest.fixture(scope="module")
 def varkappa2048():
     cfg = I.CONFIGS["varkappa2d"]
@@ -39,17 +49,25 @@ def varkappa2048():
     return u0, kap
 
 
-@pytest.mark.parametrize("prec,tol", [("fp64", 1e-11), ("fp32", 3e-4), ("dfloat", 2e-6), ("mixed", 2e-6)])
-def test_varkappa2d_2048_one_step_sampled(varkappa2048, prec, tol):
+@pytest.mark.parametrize("prec,order,tol", [("fp64", "greedy", 1e-11), ("fp32", "greedy", 3e-4),
+                                            ("fp32", "lebedev", 5e-6), ("dfloat", "greedy", 2e-6),
+                                            ("mixed", "greedy", 2e-6)])
+def test_varkappa2d_2048_one_step_sampled(varkappa2048, prec, order, tol):
     """The 2D variable-conductivity workload at 2048^2, s = 64, one step of the benchmark's dt
-    and default launch configuration; 6 sampled cells against the oracle on 131^2 windows."""
+    and default launch configuration (FP32 also with the plan the precision policy chooses for
+    the job, the Lebedev-Finogenov order); 80 cells -- corners, edges, tile and warp seams and
+    random cells -- against the oracle on 131^2 windows."""
     u0, kap = varkappa2048
     n, s = u0.shape[0], I.CONFIGS["varkappa2d"]["s"]
     kd = torch.float64 if prec == "fp64" else torch.float32
     sd = torch.float32 if prec == "fp32" else torch.float64
     kt = torch.as_tensor(kap, dtype=kd, device="cuda")
     pr = F.make_problem(2, (n, n), 1.0, "periodic", "field", prec, kappa_field=kt)
-    plan = F.frkc2_plan(s)
+    if order == "lebedev":
+        plan, chosen, _ = F.frkc2_plan_auto(s, pr, I.CONFIGS["varkappa2d"]["steps"], 1e-4)
+        assert chosen == prec
+    else:
+        plan = F.frkc2_plan(s)
     rho = torch.zeros(1, dtype=torch.float64, device="cuda")
     F.frkc2_rho_bound(pr, None, rho)
     dt = I.CONFIGS["varkappa2d"]["cfl"] * plan.info()["beta"] / rho.item()
@@ -61,9 +79,12 @@ def test_varkappa2d_2048_one_step_sampled(varkappa2048, prec, tol):
     got = u.double().cpu().numpy()
     kap_o = kap if prec == "fp64" else kap.astype(np.float32).astype(np.float64)
     u0_o = u0.astype(np.float32).astype(np.float64) if prec == "fp32" else u0
-    a = O.plan(s)["a"]
+    a = O.plan(s)["a"] if order == "greedy" else O.step_sizes(s)[O.order_lebedev(s)]
     r = s + 1
-    for c in sampled_cells(u0.shape, 6, 2048):
+    cells = seam_cells_2d(n)
+    cells += sampled_cells(u0.shape, 80 - len(cells), 2048)
+    assert len(cells) >= 64
+    for c in cells:
         opr = oracle_problem(2, "dirichlet", "field", 1.0, window(kap_o, c, r))
         ref = O.frkc2_step(window(u0_o, c, r), a, dt, opr, 1)[r, r]
         assert abs(got[c] - ref) <= tol, (c, got[c], ref)  # the state lies in [0, 1]

@@ -811,3 +811,58 @@ def test_nonlinear3d_recipe_overflows_at_s128_not_s32():
                 assert np.all(np.isfinite(out)) and -0.05 < out.min() and out.max() < 2.1
             else:
                 assert not np.all(np.isfinite(out))
+
+
+# ---------------------------------------------------------------------------------------
+# Rounding gain of a stage order (Sec. 2.2 applied to rounding errors)
+# ---------------------------------------------------------------------------------------
+
+def _lap5(W, k):
+    """Periodic 5-point flux-form operator written out here (not the oracle's), any dtype."""
+    kx = 0.5 * (k + np.roll(k, 1, 1))
+    ky = 0.5 * (k + np.roll(k, 1, 0))
+    fx = kx * (W - np.roll(W, 1, 1))
+    fy = ky * (W - np.roll(W, 1, 0))
+    return (np.roll(fx, -1, 1) - fx) + (np.roll(fy, -1, 0) - fy)
+
+
+@pytest.mark.parametrize("method", ["greedy", "lebedev"])
+def test_rounding_gain_predicts_float32_step_error(method):
+    """One FRKC2 step run in numpy complex64 against the same step in complex128: the
+    relative error is (unit roundoff 2^-24) x rounding_gain within a factor of three, for the
+    paper's greedy order (g from 30 to 1300) and the Lebedev-Finogenov order (g about 2-3),
+    a span of three decades of error."""
+    n = 96
+    u0 = I.smooth_unit((n, n), 12.0, 3819)
+    k = I.kappa_field((n, n), 3818, ell=3.0).astype(np.float32)
+    kx = 0.5 * (k + np.roll(k, 1, 1))
+    ky = 0.5 * (k + np.roll(k, 1, 0))
+    rho = float(np.max(2 * (kx + np.roll(kx, -1, 1) + ky + np.roll(ky, -1, 0))))
+    k64 = k.astype(np.float64)
+    for s in (16, 64, 128):
+        a = O.plan(s, method=method)["a"] if method == "greedy" else O.step_sizes(s)[O.order_lebedev(s)]
+        dt = 0.9 * O.beta(s) / rho
+        W64 = u0.astype(np.complex128)
+        W32 = u0.astype(np.complex64)
+        for al in a:
+            W64 = W64 + (dt * al) * _lap5(W64, k64)
+            W32 = W32 + np.complex64(dt * al) * _lap5(W32, k)
+        err = np.linalg.norm(W32.real - W64.real) / np.linalg.norm(W64.real)
+        g = O.rounding_gain(a, O.beta(s))
+        ratio = err / (2.0 ** -24 * g)
+        assert 0.33 < ratio < 3.0, (s, g, err, ratio)
+
+
+def test_rounding_gain_closed_forms():
+    """Two stages a, conj(a) (L = 2): g^2 = 1 + mean_x |1 + conj(a) x|^2, the mean of a
+    quadratic in x over midpoints, in closed form; and a reversed order changes g."""
+    a = O.step_sizes(2)
+    b = O.beta(2)
+    P = 4096
+    x = -b * (np.arange(P) + 0.5) / P
+    m1, m2 = x.mean(), (x * x).mean()
+    ab = a[1]
+    want = 1.0 + (1.0 + 2.0 * ab.real * m1 + abs(ab) ** 2 * m2)
+    assert abs(O.rounding_gain(a, b, P) ** 2 / want - 1.0) < 1e-12
+    a16 = O.plan(16)["a"]
+    assert abs(O.rounding_gain(a16[::-1], O.beta(16)) / O.rounding_gain(a16, O.beta(16)) - 1.0) > 1e-3
