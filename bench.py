@@ -65,6 +65,17 @@ NCU_TRAFFIC = {
 }
 
 
+def wf2d_recompute(nx, ny, k=8, sms=152, ctas_per_sm=3):
+    """Computed / output cell-stages of the FP32 wavefront pass at its default launch: strips of
+    256 columns with 2h = 16 halo columns (h = k rounded up to 4), one wave of 3 CTAs per SM
+    (ncu occupancy), chunks of H rows in which every level runs H + 2k rows."""
+    h = (k + 3) // 4 * 4
+    strips = -(-nx // (256 - 2 * h))
+    chunks = max(1, min(ny, sms * ctas_per_sm // strips))
+    H = -(-ny // chunks)
+    return strips * 256 / nx * (H + 2 * k) / H
+
+
 def kernel_source_hash(name: str) -> str:
     path = os.path.join(ROOT, "paper_1702_03818_gb300", "csrc", name)
     return hashlib.sha256(open(path, "rb").read()).hexdigest()[:16]
@@ -312,12 +323,15 @@ def run_ours(args, rank, world, local_rank):
             pass_bytes = cells * (npv * (4 * sbytes + kbytes) - 2 * sbytes)
             g = pass_bytes * nsteps / (smsec / 1e3) / 1e9
             if prec in FP32_OPS_PER_CELL_STAGE:
-                # k = 8 register-tiled passes: compute bound (the FP32 pipe and issue), with
-                # the 64 x 64 region recomputing (64 / 48)^2 = 1.78x the output cells
+                # k = 8 passes: compute bound (the FP32 pipe and issue).  FP32 runs the wavefront
+                # pass (strips of 256 columns, 16 halo columns; chunks of H rows, every level
+                # running H + 16 rows); DFLOAT the 64 x 64 register-tiled regions ((64/48)^2)
                 ops = FP32_OPS_PER_CELL_STAGE[prec]
                 ach = ops * cells * s * nsteps / (smsec / 1e3) / 1e12
                 roof = {"bound": "alu", "achieved": ach, "peak": FP32_PEAK_TOPS, "unit": "Tops/s (FP32 pipe)",
-                        "frac": ach / FP32_PEAK_TOPS, "ops_per_cell_stage": ops, "halo_recompute": (64 / 48) ** 2,
+                        "frac": ach / FP32_PEAK_TOPS, "ops_per_cell_stage": ops,
+                        "halo_recompute": wf2d_recompute(n, n) if prec == "fp32" else (64 / 48) ** 2,
+                        "kernel": "k_wf2d<8> (wavefront, TMA row ring)" if prec == "fp32" else "k_tb2d_df (regions)",
                         "hbm_achieved_gbs": g, "hbm_frac": g / peak_hbm, "traffic": None}
             else:  # MIXED, k = 1 streaming: bound by the FP64 pipe
                 ach = MIXED_FP64_INST_PER_CELL_STAGE * cells * s * nsteps / (smsec / 1e3) / 1e12

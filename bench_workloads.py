@@ -373,6 +373,56 @@ def precision(F):
             "unit": "stages", "by_s": rows}
 
 
+def fp32passes(F):
+    """The FP32 k-stage passes on the 2D var-kappa recipe (2048^2 and 4096^2, s = 64, 10 steps,
+    the policy's Lebedev-Finogenov plan): the wavefront pass (kernel 7) by k and rows per chunk
+    against the register-tiled 64 x 64 regions (kernel 3), cell-stage/s of the whole frkc2_step
+    call and the error of each against the FP64 GPU run of the same plan."""
+    torch = _torch()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    out = {}
+    for n in (2048, 4096):
+        u0 = I.smooth_unit((n, n), 64.0 * n / 2048, 3819)
+        kap = I.kappa_field((n, n), 3818, ell=32.0 * n / 2048)
+        s, nsteps = 64, 10
+        plan = F.frkc2_plan(s, flags=F.PLAN_LEBEDEV)
+        k64 = torch.as_tensor(kap, dtype=torch.float64, device="cuda")
+        p64 = F.make_problem(2, (n, n), 1.0, "periodic", "field", "fp64", kappa_field=k64)
+        rho = torch.zeros(1, dtype=torch.float64, device="cuda")
+        F.frkc2_rho_bound(p64, None, rho)
+        dt = 0.9 * plan.info()["beta"] / rho.item()
+        ws64 = torch.empty(F.frkc2_workspace_size(p64), dtype=torch.uint8, device="cuda")
+        ref = torch.as_tensor(u0, dtype=torch.float64, device="cuda")
+        F.frkc2_step(plan, p64, dt, nsteps, 0.0, ref, ws64)
+        ref = ref.cpu().numpy()
+        del ws64
+        k32 = torch.as_tensor(kap, dtype=torch.float32, device="cuda")
+        p32 = F.make_problem(2, (n, n), 1.0, "periodic", "field", "fp32", kappa_field=k32)
+        ws = torch.empty(F.frkc2_workspace_size(p32), dtype=torch.uint8, device="cuda")
+        u0d = torch.as_tensor(u0, dtype=torch.float32, device="cuda")
+        u = u0d.clone()
+        rows = {}
+        cases = [("regions_k8", F.make_tuning(k=8, kernel=3))]
+        for k in (4, 6, 8, 10, 12):
+            cases.append((f"wavefront_k{k}", F.make_tuning(k=k, kernel=7)))
+        for H in (24, 32, 48, 64, 96):
+            cases.append((f"wavefront_k8_H{H}", F.make_tuning(k=8, tile=(0, H, 0), kernel=7)))
+        for name, tune in cases:
+            def job():
+                u.copy_(u0d)
+                F.frkc2_step(plan, p32, dt, nsteps, 0.0, u, ws, tune)
+
+            med, _ = _timed(job, 2, 3, flush)
+            rows[name] = {"value": n * n * s * nsteps / (med / 1e3), "ms": med,
+                          "rel_l2_vs_fp64_gpu": _rel(u.double().cpu().numpy(), ref)}
+        out[str(n)] = rows
+        del ws
+    best = max(out["2048"].items(), key=lambda kv: kv[1]["value"])
+    return {"workload": "fp32passes: 2D var-kappa periodic, 2048^2 and 4096^2, s = 64 (Lebedev order), 10 steps, "
+                        "FP32 wavefront pass by k and chunk rows vs register-tiled regions",
+            "metric": "cell-stage/s", "value": best[1]["value"], "best": best[0], "unit": UNIT, "cases": out}
+
+
 BRUSS_INST_PER_CELL_STAGE = 41  # 4 Laplacians (4 each), v^2 and v^2 w (8), 4 rhs (9), 4 updates (8)
 BRUSS_BYTES_PER_CELL_STAGE = {"fp64": 64, "fp32": 32}  # 4 state values read and written
 FP64_PEAK_TINST = 152 * 2 * 2.07e9 / 1e12
@@ -447,7 +497,7 @@ def bruss2d(F, hbm_peak_gbs: float = 6787.2):
             "kernel": "k_bruss2d: persistent cooperative launch, grid barrier between stages"}
 
 
-WORKLOADS = {"heat1d": heat1d, "nonlinear3d": nonlinear3d, "adjoint2d": adjoint2d,
+WORKLOADS = {"fp32passes": fp32passes, "heat1d": heat1d, "nonlinear3d": nonlinear3d, "adjoint2d": adjoint2d,
              "batched2d": batched2d, "ssweep": ssweep, "bruss2d": bruss2d, "precision": precision}
 
 
@@ -455,7 +505,21 @@ def profile_case(F, name: str):
     """One small instance per kernel family for ncu captures (inputs above the 129 MB L2,
     a few GB on the device at most): runs each case twice so a capture can skip the first."""
     torch = _torch()
-    if name == "tb2d":  # FP32 temporally blocked pass, 4096^2, k = 8
+    if name == "wf2d":  # FP32 wavefront pass, 4096^2, k = 8, the policy's plan
+        n, s = 4096, 16
+        u0 = I.smooth_unit((n, n), 128.0, 3819)
+        k = I.kappa_field((n, n), 3818, ell=64.0)
+        plan = F.frkc2_plan(s, flags=F.PLAN_LEBEDEV)
+        kt = torch.as_tensor(k, dtype=torch.float32, device="cuda")
+        pr = F.make_problem(2, (n, n), 1.0, "periodic", "field", "fp32", kappa_field=kt)
+        rho = torch.zeros(1, dtype=torch.float64, device="cuda")
+        F.frkc2_rho_bound(pr, None, rho)
+        dt = 0.9 * plan.info()["beta"] / rho.item()
+        ws = torch.empty(F.frkc2_workspace_size(pr), dtype=torch.uint8, device="cuda")
+        for _ in range(2):
+            u = torch.as_tensor(u0, dtype=torch.float32, device="cuda")
+            F.frkc2_step(plan, pr, dt, 1, 0.0, u, ws, F.make_tuning(kernel=7))
+    elif name == "tb2d":  # FP32 temporally blocked pass, 4096^2, k = 8
         n, s = 4096, 16
         u0 = I.smooth_unit((n, n), 128.0, 3819)
         k = I.kappa_field((n, n), 3818, ell=64.0)

@@ -91,14 +91,19 @@ typedef struct {
 typedef struct {
   int k;             /* stages per pass (temporal blocking), 1..16; 0 = library default       */
   int tile_x;        /* output tile per CTA along x, y, z; 0 = library default (kernel 6:
-                        tile_x = CTAs in the cluster, 1..8)                                   */
+                        tile_x = CTAs in the cluster, 1..8; kernel 7: tile_y = rows per CTA,
+                        0 = one wave of CTAs)                                                */
   int tile_y;
   int tile_z;
   int kernel;        /* 0 = library choice, 1 = generic shared-memory tile kernel,
                         2 = 2D streaming kernel (k = 1 only), 3 = 2D FP32 temporally blocked
                         kernel, 4 = 2D real pair kernel (PAIRED plans only), 5 = 3D kernel
                         streaming along z (k = 1 only), 6 = 1D whole-job cluster kernel
-                        (N <= 16384, s <= 1024, FIELD / CONST; the 1D default there)         */
+                        (N <= 16384, s <= 1024, FIELD / CONST; the 1D default there), 7 = 2D
+                        FP32 wavefront pass: strips of 256 columns walked up the grid with k
+                        stage levels in flight, rows staged in shared memory by TMA bulk
+                        copies (n[0] a multiple of 4 and >= 256, u 16-byte aligned, every
+                        pass of 1, 2, 4, 6, 8, 10 or 12 stages; the FP32 2D default there)  */
   long long wait_limit; /* batched launch: polls a device wait makes before it gives up and
                         latches FRKC2_ETIMEOUT (0 = library default, 2^22 polls)           */
   int fault_inject;  /* batched launch, testing only: 1 = the first dependent work item waits

@@ -186,13 +186,14 @@ frkc2_status frkc2_step(frkc2_plan_t plan, const frkc2_problem* prob, double dt,
   if (p.ndim < 3) tz = 1;
   if (tx < 1 || ty < 1 || tz < 1) return FRKC2_EINVAL;
   const int kern = tune ? tune->kernel : 0;
-  if (kern < 0 || kern > 6) return FRKC2_EINVAL;
+  if (kern < 0 || kern > 7) return FRKC2_EINVAL;
   const bool stream_ok = p.ndim == 2 && p.kappa_kind != FRKC2_KAPPA_POWER && k == 1;
   const bool tb_ok = tb2d_supported(p, k);
   const bool paired_ok = plan->paired && p.ndim == 2 && p.kappa_kind != FRKC2_KAPPA_POWER;
   bool use_stream2d = false, use_tb = false, use_paired = false, use_stream3d = false, use_small1d = false;
-  bool use_tb_df = false;
+  bool use_tb_df = false, use_wf = false;
   const bool dfloat = p.precision == FRKC2_DFLOAT;
+  const bool wf_ok = wf2d_supported(p, k, plan->s, u);
   const bool stream3d_ok = p.ndim == 3 && k == 1;
   const bool small1d_ok = small1d_supported(p, plan->s);
   if (kern == 6) {
@@ -221,8 +222,13 @@ frkc2_status frkc2_step(frkc2_plan_t plan, const frkc2_problem* prob, double dt,
   } else if (kern == 3) {
     if (!tb_ok) return FRKC2_EUNSUPPORTED;
     use_tb = true;
+  } else if (kern == 7) {
+    if (!wf_ok) return FRKC2_EUNSUPPORTED;
+    use_wf = true;
   } else if (kern == 0) {
-    if (tb_ok && k > 1)
+    if (wf_ok && k > 1)
+      use_wf = true;
+    else if (tb_ok && k > 1)
       use_tb = true;
     else if (stream3d_ok)
       use_stream3d = true;
@@ -238,7 +244,7 @@ frkc2_status frkc2_step(frkc2_plan_t plan, const frkc2_problem* prob, double dt,
     probe.hx = k;
     probe.hy = p.ndim >= 2 ? k : 0;
     probe.hz = p.ndim >= 3 ? k : 0;
-    if (!use_stream2d && !use_tb && !use_paired && !use_stream3d && !use_small1d && !use_tb_df &&
+    if (!use_stream2d && !use_tb && !use_paired && !use_stream3d && !use_small1d && !use_tb_df && !use_wf &&
         generic_smem_bytes(p, probe) > size_t(smem_optin()))
       return FRKC2_EINVAL;
   }
@@ -335,6 +341,39 @@ frkc2_status frkc2_step(frkc2_plan_t plan, const frkc2_problem* prob, double dt,
     }
     if (curU != u &&
         cudaMemcpyAsync(u, curU, cells(p) * sizeof(double), cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+      return FRKC2_ECUDA;
+    return FRKC2_OK;
+  }
+  if (use_wf) {
+    // interleaved (U, V) float2 state between passes in the ua (with va) and ub (with vb) slots;
+    // a step's first pass reads the real state, its last writes it.  A pass never writes the
+    // array it reads (a strip's halo columns and a chunk's first rows are other CTAs' output):
+    // with one pass per step the real state alternates between u and ua.
+    if (launch_faces_wf(p, base + L.fx, base + L.fy, base + L.fen, st) != cudaSuccess) return FRKC2_ECUDA;
+    const int chunk_rows = tune ? tune->tile_y : 0;
+    for (int n = 0; n < nsteps; ++n) {
+      for (int q = 0; q < npass; ++q) {
+        const int l0 = q * k, kq = std::min(k, s - l0);
+        const bool first = q == 0, last = q == npass - 1;
+        void* outW = (curU == ua) ? ub : ua;
+        void* outU = last && curU != u ? u : outW;
+        a.k = kq;
+        a.U_in = curU;
+        a.V_in = nullptr;
+        a.U_out = outU;
+        a.V_out = nullptr;
+        a.check_finite = last ? 1 : 0;
+        for (int j = 0; j < kq; ++j) {
+          a.caf[j] = float(dt * plan->a_re[l0 + j] / h2);
+          a.cbf[j] = float(dt * plan->a_im[l0 + j] / h2);
+        }
+        if (launch_pass_wf2d(p, a, base + L.fen, chunk_rows, first, last, st, n > 0 || q > 0) != cudaSuccess)
+          return FRKC2_ECUDA;
+        curU = outU;
+      }
+    }
+    if (curU != u &&
+        cudaMemcpyAsync(u, curU, cells(p) * sizeof(float), cudaMemcpyDeviceToDevice, st) != cudaSuccess)
       return FRKC2_ECUDA;
     return FRKC2_OK;
   }

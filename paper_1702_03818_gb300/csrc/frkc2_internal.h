@@ -90,6 +90,18 @@ cudaError_t launch_face_pairs(const frkc2_problem& p, const void* fx, const void
 // the same kind) finishes; its CTAs read the pass input only after that launch completes.
 cudaError_t launch_pass_tb2d(const frkc2_problem& p, const PassArgs& a, cudaStream_t st, bool overlap_previous);
 bool small1d_supported(const frkc2_problem& p, int s);
+// 2D FP32 wavefront pass (pass_wf2d.cu): CTAs of WF_NW warps stream column strips of
+// 64 WF_NW cells up the grid with up to WF_KMAX stage levels in flight; rows arrive by TMA.
+constexpr int WF_NW = 4;
+int wf2d_face_pitch(int nx);
+// k stages per pass and s stages per step: every pass (the last may be shorter) needs an
+// instantiated stage count (1, 2, 4, 6, 8, 10 or 12)
+bool wf2d_supported(const frkc2_problem& p, int k, int s, const void* u);
+cudaError_t launch_faces_wf(const frkc2_problem& p, const void* fx, const void* fy, void* out, cudaStream_t st);
+// chunk_rows: rows per CTA (0 = one wave of two CTAs per SM); in_real / out_real: the pass reads
+// / writes the real state (float [ny][nx]) instead of interleaved (U, V) float2 [ny][nx]
+cudaError_t launch_pass_wf2d(const frkc2_problem& p, const PassArgs& a, const void* faces_wf, int chunk_rows,
+                             bool in_real, bool out_real, cudaStream_t st, bool overlap_previous);
 cudaError_t launch_small1d(const frkc2_problem& p, const frkc2_plan_s& plan, double dt, int nsteps, void* u,
                            const void* fx, unsigned* status, cudaStream_t st, int cluster);
 cudaError_t launch_pass_stream3d(const frkc2_problem& p, const PassArgs& a, cudaStream_t st);

@@ -281,7 +281,9 @@ cudaError_t launch_s(const PassArgs& a, const void* fen, cudaStream_t st) {
 }  // namespace
 
 size_t face_pair_bytes(const frkc2_problem& p) {
-  return size_t(p.n[1] + 1) * size_t(p.n[0] + 1) * 2 * arith_bytes(p.precision);
+  // the streaming passes' [ny + 1][nx + 1] pairs, or the FP32 wavefront pass's padded
+  // [ny + 1][nx + 4] pairs (wf2d_face_pitch), whichever the call builds
+  return size_t(p.n[1] + 1) * size_t(p.n[0] + 4) * 2 * arith_bytes(p.precision);
 }
 
 cudaError_t launch_face_pairs(const frkc2_problem& p, const void* fx, const void* fy, void* out, cudaStream_t st) {

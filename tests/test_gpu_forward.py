@@ -213,6 +213,79 @@ def test_step_parity_fp32_temporal_blocking(case):
     assert rel_err(got, ref) < TOL["fp32"], rel_err(got, ref)
 
 
+WF_CASES = [
+    # shape (ny, nx), bc, kappa, s, nsteps, k, rows per chunk (0 = library default)
+    ((96, 256), "periodic", "field", 16, 2, 8, 0),
+    ((77, 260), "dirichlet", "field", 32, 2, 8, 0),
+    ((130, 516), "periodic", "const", 24, 1, 6, 0),
+    ((64, 300), "dirichlet", "field", 20, 2, 12, 0),
+    ((41, 256), "periodic", "field", 8, 3, 8, 0),
+    ((50, 264), "dirichlet", "field", 4, 3, 4, 0),
+    ((200, 512), "periodic", "field", 64, 1, 8, 7),
+    ((33, 260), "periodic", "field", 10, 2, 2, 5),
+    ((40, 256), "dirichlet", "field", 6, 1, 1, 0),
+    ((9, 1024), "dirichlet", "field", 16, 2, 8, 2),
+]
+
+
+@pytest.mark.parametrize("case", WF_CASES, ids=lambda c: f"{'x'.join(map(str, c[0]))}-{c[1]}-{c[2]}-s{c[3]}-k{c[5]}-H{c[6]}")
+def test_step_parity_fp32_wavefront(case):
+    """The FP32 wavefront pass (kernel 7): strips of 256 columns walked up in chunks of rows,
+    k stage levels in flight, rows staged by TMA bulk copies.  Periodic strips that wrap,
+    Dirichlet strips that leave the grid, ragged rows and strips, one pass per step (the real
+    state alternating between the caller's array and the workspace), a short last pass (s not a
+    multiple of k), k from 1 to 12, and chunks of a few rows.  Against the oracle (grid norm and
+    every element) and against the register-tiled FP32 pass."""
+    shape, bc, kappa, s, nsteps, k, H = case
+    u0, field = seeded_case(shape, bc, kappa, 700 + s)
+    oplan = O.plan(s)
+    plan = F.frkc2_plan(s)
+    fo = rounded_field(field, "fp32")
+    opr = oracle_problem(2, bc, kappa, 1.0, fo)
+    dt = 0.9 * oplan["beta"] / O.rho_bound(opr, u0)
+    ref = O.frkc2_step(u0.astype(np.float32).astype(np.float64), oplan["a"], dt, opr, nsteps)
+    got, st = run_gpu(plan, shape, bc, kappa, "fp32", u0, field, dt, nsteps,
+                      tune=F.make_tuning(k=k, tile=(0, H, 0), kernel=7))
+    assert st == F.OK
+    assert rel_err(got, ref) < TOL["fp32"], rel_err(got, ref)
+    if 2 * k < 64:
+        reg, st = run_gpu(plan, shape, bc, kappa, "fp32", u0, field, dt, nsteps, tune=F.make_tuning(k=k, kernel=3))
+        assert rel_err(got, reg) < TOL["fp32"], rel_err(got, reg)  # two roundings of the same stages
+
+
+def test_wavefront_launches_and_rejects_unsupported():
+    """Kernel 7 on an FP32 2D problem with nx a multiple of 4 and at least 256: one face set-up
+    kernel for the call, one for the wavefront layout, then one launch per pass; other widths,
+    or a state array off a 16-byte boundary, are refused."""
+    shape = (48, 256)
+    u0, field = seeded_case(shape, "periodic", "field", 5)
+    plan = F.frkc2_plan(16)
+    u = dev(u0, torch.float32)
+    kt = dev(field, torch.float32)
+    pr = lib_problem(shape, "periodic", "field", "fp32", 1.0, kt, 1.0)
+    ws = torch.empty(F.frkc2_workspace_size(pr), dtype=torch.uint8, device="cuda")
+    F.frkc2_launch_count()
+    F.frkc2_step(plan, pr, 0.1, 3, 0.0, u, ws, F.make_tuning(kernel=7))
+    assert F.frkc2_launch_count() == 1 + 1 + 3 * 2  # faces, wavefront faces, 2 passes of 8 stages x 3 steps
+    a = u.double().cpu().numpy()
+    u2 = dev(u0, torch.float32)
+    F.frkc2_step(plan, pr, 0.1, 3, 0.0, u2, ws, F.make_tuning(kernel=7))
+    assert np.array_equal(a, u2.double().cpu().numpy())  # deterministic
+    for bad_shape in [(48, 252), (48, 254), (48, 128)]:
+        ub = dev(seeded_case(bad_shape, "periodic", "field", 6)[0], torch.float32)
+        kb = dev(seeded_case(bad_shape, "periodic", "field", 6)[1], torch.float32)
+        pb = lib_problem(bad_shape, "periodic", "field", "fp32", 1.0, kb, 1.0)
+        wsb = torch.empty(F.frkc2_workspace_size(pb), dtype=torch.uint8, device="cuda")
+        with pytest.raises(F.Frkc2Error) as e:
+            F.frkc2_step(plan, pb, 0.1, 1, 0.0, ub, wsb, F.make_tuning(kernel=7))
+        assert e.value.status == F.EUNSUPPORTED
+        F.frkc2_step(plan, pb, 0.1, 1, 0.0, ub, wsb)  # the default falls back to another pass
+    big = torch.zeros(48 * 256 + 2, dtype=torch.float32, device="cuda")
+    with pytest.raises(F.Frkc2Error) as e:  # state array 8 bytes off a 16-byte boundary
+        F.frkc2_step(plan, pr, 0.1, 1, 0.0, big[2:].view(48, 256), ws, F.make_tuning(kernel=7))
+    assert e.value.status == F.EUNSUPPORTED
+
+
 def test_tb_kernel_rejects_unsupported():
     shape = (32, 32)
     u0, field = seeded_case(shape, "periodic", "field", 5)

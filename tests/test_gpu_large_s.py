@@ -55,7 +55,8 @@ def test_large_s_one_step_matches_oracle(refs, prec, s, order):
     flags = {"greedy": F.PLAN_GREEDY, "lebedev": F.PLAN_LEBEDEV, "default": 0}[order]
     plan = F.frkc2_plan(s, flags=flags)
     a_o = _oracle_order(s, order)
-    assert np.max(np.abs(plan.info()["a"] - a_o) / np.abs(a_o)) < 1e-12  # the same stage order
+    # the same stage order; the step sizes agree to the conditioning of 1 - zeta_j (about eps L^2)
+    assert np.max(np.abs(plan.info()["a"] - a_o) / np.abs(a_o)) < 1e-9
     kd = torch.float64 if prec == "fp64" else torch.float32
     sd = torch.float32 if prec == "fp32" else torch.float64
     kt = torch.as_tensor(kap, dtype=kd, device="cuda")
@@ -74,7 +75,7 @@ def test_large_s_one_step_matches_oracle(refs, prec, s, order):
         m = ref.mean()
         assert rel_l2(got - m, ref - m) < 1e-9
     else:
-        pred = F.frkc2_precision_policy(plan, pr, 1, 1e-4)[1]
+        pred = F.frkc2_precision_policy(plan, pr, 1, 1.0)[1]  # the FP32 forecast (FP32 is chosen at tol 1)
         tol = 3e-4 if order == "greedy" else 1e-4  # the paper's order at s = 128 is above 1e-4 in FP32
         err = rel_err(got, ref)
         assert err < tol, (err, pred)
