@@ -13,8 +13,9 @@ error against the FP64 GPU run and against the FP64 oracle over the whole job le
 
 Timing: W untimed warm-up steps, then K timed steps, each bracketed by CUDA events on the
 launching stream; L2 is flushed (a 256 MiB write) between timed steps, outside the events.
-Under torchrun every rank runs its own replica (the job does not shard without a halo
-exchange), so scaling is weak and value = all ranks' cell-stages / the slowest rank's time.
+Under torchrun the one job is split into row slabs (paper_1702_03818_gb300/slab.py: halo rows
+exchanged between groups of stages), so scaling is strong and value = the job's cell-stages /
+the slowest rank's time.
 
 ``--impl reference`` times the FP64 oracle (the CPU statement of the method) on the host on a
 bounded sample of the same workload, rank 0 only.
@@ -431,6 +432,120 @@ def _oracle_job(order, kappa_f32, u0_f32, n, nsteps):
     return O.frkc2_step(u0, a, dt, pr, nsteps), dt
 
 
+SLAB_HALO = 16  # halo rows of each slab, and stages per exchange, under torchrun
+
+
+def run_slabs(args, rank, world, local_rank):
+    """N > 1: the one 2048^2 job split into row slabs (paper_1702_03818_gb300/slab.py), each rank
+    running frkc2_stages on its slab extended by 16 halo rows each side and exchanging the halo
+    rows (NCCL point-to-point, into the receiver's memory) before every 16 stages: strong
+    scaling, value = the whole job's cell-stages / the slowest rank's time."""
+    import torch
+    from paper_1702_03818_gb300 import dist as D
+    from paper_1702_03818_gb300 import frkc2 as F
+    from paper_1702_03818_gb300 import slab as SL
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    s, nsteps, n = CFG["s"], CFG["steps"], CFG["n"]
+    u0_np, k_np = inputs()
+    plan = F.frkc2_plan(s)
+    # dt from the whole grid's Gershgorin bound (every rank holds the seeded inputs)
+    kg = torch.as_tensor(k_np, device=dev)
+    pg = F.make_problem(2, (n, n), 1.0, "periodic", "field", "fp64", kappa_field=kg)
+    rho_t = torch.zeros(1, dtype=torch.float64, device=dev)
+    F.frkc2_rho_bound(pg, None, rho_t)
+    dt = CFG["cfl"] * plan.info()["beta"] / rho_t.item()
+    del kg
+    sl = SL.Slab(n, world, rank, SLAB_HALO)
+    k_ext = torch.zeros((sl.rows_ext, n), dtype=torch.float64, device=dev)
+    k_ext[sl.interior()] = torch.as_tensor(k_np[sl.y0:sl.y1], device=dev)
+    SL.exchange_halos(k_ext, sl)  # the conductivity's halo rows, once
+    pr = F.make_problem(2, (n, sl.rows_ext), 1.0, "periodic", "field", "fp64", kappa_field=k_ext)
+    ws = torch.empty(F.frkc2_workspace_size(pr), dtype=torch.uint8, device=dev)
+    F.frkc2_workspace_reset(ws)
+    w_ext = torch.zeros((sl.rows_ext, n, 2), dtype=torch.float64, device=dev)
+    u_slab = torch.as_tensor(u0_np[sl.y0:sl.y1], device=dev)
+    stages = SL.device_stages(F, plan, pr, dt, w_ext, ws)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def job():
+        w_ext[sl.interior(), :, 0] = u_slab
+        return SL.slab_steps(plan, s, nsteps, w_ext, sl, stages)
+
+    for _ in range(args.warmup):
+        job()
+    torch.cuda.synchronize()
+    D.barrier(dev)
+    clocks = Clocks(local_rank)
+    clocks.start()
+    ms, launches, exchanges = [], 0, 0
+    for _ in range(args.steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        F.frkc2_launch_count()
+        e0.record(stream)
+        exchanges += job()
+        e1.record(stream)
+        launches += F.frkc2_launch_count()
+        e1.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    torch.cuda.synchronize()
+    D.barrier(dev)
+    clk = clocks.stop()
+    assert F.frkc2_workspace_status(ws) == F.OK
+    total_ms = D.max_over_ranks(float(np.sum(ms)), dev)
+    # e2e: this rank's slab of the inputs from pinned host memory, the conductivity's halo
+    # exchange, the job, and the slab's result back to the host, all inside the events
+    hu = torch.as_tensor(u0_np[sl.y0:sl.y1]).pin_memory()
+    hk = torch.as_tensor(k_np[sl.y0:sl.y1]).pin_memory()
+    hout = torch.empty_like(hu).pin_memory()
+    tms = []
+    for it in range(args.warmup + args.steps):
+        flush.zero_()
+        D.barrier(dev)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        u_slab.copy_(hu, non_blocking=True)
+        k_ext[sl.interior()].copy_(hk, non_blocking=True)
+        SL.exchange_halos(k_ext, sl)
+        job()
+        hout.copy_(w_ext[sl.interior(), :, 0], non_blocking=True)
+        e1.record(stream)
+        e1.synchronize()
+        if it >= args.warmup:
+            tms.append(e0.elapsed_time(e1))
+    e2e_ms = D.max_over_ranks(float(np.sum(tms)), dev)
+    e2e = {"value": n * n * s * nsteps * len(tms) / (e2e_ms / 1e3), "unit": UNIT,
+           "h2d_bytes_per_step": D.sum_over_ranks(hu.numel() * 8 + hk.numel() * 8, dev),
+           "d2h_bytes_per_step": D.sum_over_ranks(hout.numel() * 8, dev)}
+    cell_stages = n * n * s * nsteps
+    value = cell_stages * args.steps / (total_ms / 1e3)
+    # per-rank FP64-pipe rate on the cells each rank computes (its slab and halo rows)
+    mine = sl.rows_ext * n * s * nsteps * args.steps / (float(np.sum(ms)) / 1e3)
+    ach = FP64_INST_PER_CELL_STAGE * mine / 1e12
+    return {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "strong", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic (seeded GRF conductivity and initial state)",
+        "config": {"workload": "varkappa2d: 2D var-kappa diffusion 2048^2 periodic, FRKC2 s=64, 100 steps, FP64",
+                   "grid": [n, n], "s": s, "nsteps": nsteps, "cell_stages_per_step": cell_stages,
+                   "kernel": "k = 1 streaming pass on row slabs (frkc2_stages)",
+                   "l2": "flushed between timed steps (256 MiB write)",
+                   "parallelism": f"row slabs x{world}, {SLAB_HALO} halo rows exchanged before every "
+                                  f"{SLAB_HALO} stages ({args.dist_backend} point-to-point)",
+                   "exchanges_per_job": exchanges // max(1, args.steps)},
+        "roofline": {"bound": "alu", "achieved": ach, "peak": FP64_PEAK_TINST, "unit": "Tinst/s (FP64 pipe), rank 0",
+                     "frac": ach / FP64_PEAK_TINST, "traffic": None,
+                     "computed_over_owned_cells": sl.rows_ext / sl.n},
+        "clocks": clk, "gpu_launches": launches, "e2e": e2e,
+    }
+
+
 def cpu_baseline(torch, F, dev, pol_plan, n=128, stages=16):
     """The CPU baseline leg: the FP64 oracle timed on every host core at once (one process per
     core, each on the first ``stages`` stages of one step of the 2048^2 job), and each
@@ -507,6 +622,8 @@ def main():
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--dist-backend", default="nccl", choices=["nccl", "gloo"],
+                    help="torchrun transport of the slab halos (gloo stages them through host memory)")
     ap.add_argument("--workload", default="varkappa2d",
                     help="varkappa2d (the default line) or one of bench_workloads.WORKLOADS")
     args = ap.parse_args()
@@ -532,9 +649,10 @@ def main():
         return
     if world > 1:
         import torch
+        local_rank %= torch.cuda.device_count()  # ranks sharing a device (gloo, host-staged halos)
         torch.cuda.set_device(local_rank)
-        torch.distributed.init_process_group("nccl")
-    out = run_ours(args, rank, world, local_rank)
+        torch.distributed.init_process_group(args.dist_backend)
+    out = run_slabs(args, rank, world, local_rank) if world > 1 else run_ours(args, rank, world, local_rank)
     if rank == 0:
         print(json.dumps(out), flush=True)
     if world > 1:

@@ -222,6 +222,23 @@ frkc2_status frkc2_step(frkc2_plan_t plan, const frkc2_problem* prob, double dt,
                         double rho, void* u, void* ws, size_t ws_bytes,
                         const frkc2_tuning* tune, void* stream);
 
+/* ---- A range of stages (Sec. 3, Eq. 13) on a complex state ---------------------------------
+ * Applies the plan's stages l0 .. l1-1 of one step of size dt to the complex stage state
+ * W^{l0} and leaves W^{l1}: W^{l+1} = W^l + dt a_l f(W^l).  For callers that split the stage
+ * loop, such as a grid decomposed into slabs whose halo rows are exchanged between groups of
+ * stages (paper_1702_03818_gb300/slab.py).  2D FIELD / CONST problems in FP64, FP32 or MIXED
+ * (FRKC2_EUNSUPPORTED otherwise).
+ *   w      : device array of 2 n[0] n[1] values (state precision), interleaved (re, im) per cell,
+ *            in and out.  With l0 == 0 (a step's first stages) the imaginary parts are first set
+ *            to zero: a step starts from the real state w^n.  After l1 == s the real parts are
+ *            w^{n+1}.
+ *   l0, l1 : 0 <= l0 < l1 <= s.
+ *   ws     : workspace of frkc2_workspace_size(prob) bytes (face conductivities are rebuilt by
+ *            every call).
+ * Each stage is one launch of the single-stage streaming pass; the last one writes w.        */
+frkc2_status frkc2_stages(frkc2_plan_t plan, const frkc2_problem* prob, double dt, int l0, int l1,
+                          void* w, void* ws, size_t ws_bytes, void* stream);
+
 /* ---- Error-controlled integration (Sec. 3, Eqs. 14-16) --------------------------------
  * Integrates u from t = 0 to t_end with the embedded first-order solution
  * What^{l+1} = What^l + T Re(a_l) Re(f(W^l)) (Eq. 14) carried through every step and the

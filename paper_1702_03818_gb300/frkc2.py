@@ -67,6 +67,8 @@ _sig = {
     "frkc2_step": (C.c_int, [_P, C.POINTER(frkc2_problem), C.c_double, C.c_int, C.c_double, _P, _P,
                              C.c_size_t, C.POINTER(frkc2_tuning), _P]),
     "frkc2_step_noalloc": (C.c_int, [_P, C.POINTER(frkc2_problem), C.c_double, C.c_int, C.c_double, _P, _P]),
+    "frkc2_stages": (C.c_int, [_P, C.POINTER(frkc2_problem), C.c_double, C.c_int, C.c_int, _P, _P, C.c_size_t,
+                               _P]),
     "frkc2_adaptive_workspace_size": (C.c_int, [C.POINTER(frkc2_problem), C.POINTER(frkc2_tuning),
                                                 C.POINTER(C.c_size_t)]),
     "frkc2_step_adaptive": (C.c_int, [_P, C.POINTER(frkc2_problem), C.c_double, C.c_double, C.c_double,
@@ -268,6 +270,12 @@ def frkc2_step(plan: Plan, prob: frkc2_problem, dt: float, nsteps: int, rho: flo
                            _ptr(ws), ws.numel() * ws.element_size(),
                            C.byref(tune) if tune is not None else None, _stream_ptr(stream)),
            "frkc2_step")
+
+
+def frkc2_stages(plan: Plan, prob: frkc2_problem, dt: float, l0: int, l1: int, w, ws, stream=None):
+    """Stages l0 .. l1-1 of one step on the interleaved complex state w (in place)."""
+    _check(_lib.frkc2_stages(plan.handle, C.byref(prob), float(dt), int(l0), int(l1), _ptr(w), _ptr(ws),
+                             ws.numel() * ws.element_size(), _stream_ptr(stream)), "frkc2_stages")
 
 
 def frkc2_adaptive_workspace_size(prob: frkc2_problem, tune: frkc2_tuning | None = None) -> int:
