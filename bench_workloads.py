@@ -373,6 +373,28 @@ def precision(F):
             "unit": "stages", "by_s": rows}
 
 
+def peaks(F):
+    """FMA throughput of the FP64 and FP32 pipes (frkc2_fma_probe: 8 independent FMA chains per
+    thread, 152 x 8 CTAs of 256 threads), against the unit-count figures the rooflines use:
+    152 SMs x 2 FP64 FMA per clock and x 128 FP32 FMA per clock at 2.07 GHz."""
+    torch = _torch()
+    blocks = 152 * 8
+    out = {}
+    for prec, iters, units in (("fp64", 4096, 2), ("fp32", 65536, 128)):
+        buf = torch.empty(blocks * 256, dtype=torch.float64 if prec == "fp64" else torch.float32, device="cuda")
+
+        def job():
+            F.frkc2_fma_probe(prec, blocks, iters, buf)
+
+        med, ms = _timed(job, 2, 5)
+        fmas = blocks * 256 * iters * 8
+        nominal = 152 * units * 2.07e9
+        out[prec] = {"tfma_per_s": fmas / (med / 1e3) / 1e12, "ms": med,
+                     "nominal_tfma_per_s": nominal / 1e12, "frac_of_nominal": fmas / (med / 1e3) / nominal}
+    return {"workload": "peaks: FP64 / FP32 FMA throughput probe", "metric": "TFMA/s", "unit": "TFMA/s",
+            "value": out["fp64"]["tfma_per_s"], "pipes": out}
+
+
 def fp32passes(F):
     """The FP32 k-stage passes on the 2D var-kappa recipe (2048^2 and 4096^2, s = 64, 10 steps,
     the policy's Lebedev-Finogenov plan): the wavefront pass (kernel 7) by k and rows per chunk
@@ -497,7 +519,7 @@ def bruss2d(F, hbm_peak_gbs: float = 6787.2):
             "kernel": "k_bruss2d: persistent cooperative launch, grid barrier between stages"}
 
 
-WORKLOADS = {"fp32passes": fp32passes, "heat1d": heat1d, "nonlinear3d": nonlinear3d, "adjoint2d": adjoint2d,
+WORKLOADS = {"peaks": peaks, "fp32passes": fp32passes, "heat1d": heat1d, "nonlinear3d": nonlinear3d, "adjoint2d": adjoint2d,
              "batched2d": batched2d, "ssweep": ssweep, "bruss2d": bruss2d, "precision": precision}
 
 

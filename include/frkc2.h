@@ -390,6 +390,14 @@ frkc2_status frkc2_bruss_step(frkc2_plan_t plan, const frkc2_bruss_problem* prob
                               int nsteps, double rho, void* v, void* w, void* ws,
                               size_t ws_bytes, const frkc2_tuning* tune, void* stream);
 
+/* ---- FMA throughput probe ------------------------------------------------------------------
+ * Not part of the method: measures the FP64 or FP32 fused multiply-add rate that the kernels'
+ * rooflines are stated against.  Launches `blocks` CTAs of 256 threads, each thread running
+ * `iters` rounds of 8 independent FMA chains (FMAs = blocks * 256 * iters * 8) and writing one
+ * value to out (device array of blocks * 256 elements of the precision).  The caller times it.
+ *   precision : FRKC2_FP64 or FRKC2_FP32.                                                    */
+frkc2_status frkc2_fma_probe(int precision, int blocks, int iters, void* out, void* stream);
+
 /* Short text for a status code (static storage).                                          */
 const char* frkc2_status_string(frkc2_status st);
 

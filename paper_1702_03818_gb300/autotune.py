@@ -59,6 +59,8 @@ def candidates(prob) -> list:
         c.append(F.make_tuning(k=1, kernel=2))
         if prob.precision == F.FP32:
             c += [F.make_tuning(k=k, kernel=3) for k in (2, 3, 4, 5, 6, 8, 10, 12)]
+            if int(prob.n[0]) % 4 == 0 and int(prob.n[0]) >= 256:  # the wavefront pass
+                c += [F.make_tuning(k=k, kernel=7) for k in (4, 6, 8, 10, 12)]
         for k in (1, 2, 4):
             c += [F.make_tuning(k=k, tile=t, kernel=1) for t in ((64, 16, 1), (32, 32, 1), (64, 32, 1))]
     elif prob.ndim == 2:

@@ -4,6 +4,7 @@
 #include <cstring>
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include "frkc2.h"
 #include "frkc2_internal.h"
@@ -11,6 +12,14 @@
 namespace frkc2 {
 
 static thread_local long long g_launches = 0;
+
+// NVTX range for the enclosing scope (host timeline: a call, a step; no cost without a tool)
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
 void count_launch(int n) { g_launches += n; }
 
 size_t state_bytes(int precision) { return precision == FRKC2_FP32 ? 4 : 8; }
@@ -226,7 +235,15 @@ frkc2_status frkc2_step(frkc2_plan_t plan, const frkc2_problem* prob, double dt,
     if (!wf_ok) return FRKC2_EUNSUPPORTED;
     use_wf = true;
   } else if (kern == 0) {
-    if (wf_ok && k > 1)
+    // FP32 k-stage passes: the wavefront where it recomputes fewer cells than the 64 x 64 regions,
+    // allowing for its 8 % higher cost per computed cell-stage (measured at 2048^2, k = 8)
+    bool wf_wins = false;
+    if (wf_ok && tb_ok && k > 1) {
+      const int T = 64 - 2 * k, nx = int(p.n[0]), ny = int(p.n[1]);
+      const double regions = double((nx + T - 1) / T) * ((ny + T - 1) / T) * 64.0 * 64.0 / (double(nx) * ny);
+      wf_wins = 1.08 * wf2d_recompute(nx, ny, k) < regions;
+    }
+    if (wf_wins || (wf_ok && !tb_ok && k > 1))
       use_wf = true;
     else if (tb_ok && k > 1)
       use_tb = true;
@@ -249,6 +266,7 @@ frkc2_status frkc2_step(frkc2_plan_t plan, const frkc2_problem* prob, double dt,
       return FRKC2_EINVAL;
   }
   if (nsteps == 0) return FRKC2_OK;
+  const NvtxRange call_range("frkc2_step");
 
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   char* base = static_cast<char*>(ws);
@@ -291,6 +309,7 @@ frkc2_status frkc2_step(frkc2_plan_t plan, const frkc2_problem* prob, double dt,
     if (launch_face_pairs(p, base + L.fx, base + L.fy, base + L.fen, st) != cudaSuccess) return FRKC2_ECUDA;
     const int npair = s / 2;
     for (int n = 0; n < nsteps; ++n) {
+      const NvtxRange step_range("frkc2 step");
       for (int q = 0; q < npair; ++q) {
         const bool last = n == nsteps - 1 && q == npair - 1;
         void* out = (last && curU != u) ? u : (curU == ua ? ub : ua);
@@ -316,6 +335,7 @@ frkc2_status frkc2_step(frkc2_plan_t plan, const frkc2_problem* prob, double dt,
     // a pass never writes the array it reads (its regions' halos overlap other CTAs' output
     // tiles): with one pass per step the real state alternates between u and ua
     for (int n = 0; n < nsteps; ++n) {
+      const NvtxRange step_range("frkc2 step");
       for (int q = 0; q < npass; ++q) {
         const int l0 = q * k, kq = std::min(k, s - l0);
         const bool first = q == 0, last = q == npass - 1;
@@ -352,6 +372,7 @@ frkc2_status frkc2_step(frkc2_plan_t plan, const frkc2_problem* prob, double dt,
     if (launch_faces_wf(p, base + L.fx, base + L.fy, base + L.fen, st) != cudaSuccess) return FRKC2_ECUDA;
     const int chunk_rows = tune ? tune->tile_y : 0;
     for (int n = 0; n < nsteps; ++n) {
+      const NvtxRange step_range("frkc2 step");
       for (int q = 0; q < npass; ++q) {
         const int l0 = q * k, kq = std::min(k, s - l0);
         const bool first = q == 0, last = q == npass - 1;
@@ -384,6 +405,7 @@ frkc2_status frkc2_step(frkc2_plan_t plan, const frkc2_problem* prob, double dt,
     a.hx = a.hy = 1;
     a.hz = 0;
     for (int n = 0; n < nsteps; ++n) {
+      const NvtxRange step_range("frkc2 step");
       for (int l = 0; l < s; ++l) {
         const bool first = l == 0, last = l == s - 1;
         a.U_in = first ? u : curU;
@@ -407,6 +429,7 @@ frkc2_status frkc2_step(frkc2_plan_t plan, const frkc2_problem* prob, double dt,
     return FRKC2_OK;
   }
   for (int n = 0; n < nsteps; ++n) {
+      const NvtxRange step_range("frkc2 step");
     for (int q = 0; q < npass; ++q) {
       const int l0 = q * k;
       const int kq = std::min(k, s - l0);

@@ -94,6 +94,8 @@ bool small1d_supported(const frkc2_problem& p, int s);
 // 64 WF_NW cells up the grid with up to WF_KMAX stage levels in flight; rows arrive by TMA.
 constexpr int WF_NW = 4;
 int wf2d_face_pitch(int nx);
+// computed / output cell-stages of the wavefront pass at its default launch
+double wf2d_recompute(int nx, int ny, int k);
 // k stages per pass and s stages per step: every pass (the last may be shorter) needs an
 // instantiated stage count (1, 2, 4, 6, 8, 10 or 12)
 bool wf2d_supported(const frkc2_problem& p, int k, int s, const void* u);

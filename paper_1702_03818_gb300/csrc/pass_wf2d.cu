@@ -459,6 +459,22 @@ bool wf2d_k_supported(int k) { return k == 1 || k == 2 || k == 4 || k == 6 || k 
 
 int wf2d_face_pitch(int nx) { return nx + 4; }
 
+double wf2d_recompute(int nx, int ny, int k) {
+  // strips of 256 columns with 2h halo columns; one wave of 3 CTAs per SM (the occupancy of the
+  // k <= 8 instantiations); chunks of H rows in which every level runs H + 2k rows
+  static const int sms = [] {
+    int dev = 0, n = 152;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+      n = 152;
+    return n;
+  }();
+  const int h = (k + 3) / 4 * 4, ow = 64 * WF_NW - 2 * h;
+  const int strips = (nx + ow - 1) / ow;
+  const int chunks = std::max(1, std::min(ny, 3 * sms / strips));
+  const int H = (ny + chunks - 1) / chunks;
+  return double(strips) * (64 * WF_NW) / nx * double(H + 2 * k) / H;
+}
+
 bool wf2d_supported(const frkc2_problem& p, int k, int s, const void* u) {
   const int nx = int(p.n[0]);
   const int last = s % k == 0 ? k : s % k;  // stages of a step's last pass

@@ -93,6 +93,7 @@ _sig = {
     "frkc2_bruss_rho_bound": (C.c_int, [C.POINTER(frkc2_bruss_problem), _P, _P, _P, _P, C.c_size_t, _P]),
     "frkc2_bruss_step": (C.c_int, [_P, C.POINTER(frkc2_bruss_problem), C.c_double, C.c_int, C.c_double, _P, _P,
                                    _P, C.c_size_t, C.POINTER(frkc2_tuning), _P]),
+    "frkc2_fma_probe": (C.c_int, [C.c_int, C.c_int, C.c_int, _P, _P]),
     "frkc2_status_string": (C.c_char_p, [C.c_int]),
     "frkc2_launch_count": (C.c_longlong, []),
 }
@@ -400,6 +401,12 @@ def frkc2_bruss_step(plan: Plan, prob: frkc2_bruss_problem, dt: float, nsteps: i
                                  _ptr(ws), ws.numel() * ws.element_size(),
                                  C.byref(tune) if tune is not None else None, _stream_ptr(stream)),
            "frkc2_bruss_step")
+
+
+def frkc2_fma_probe(precision: str, blocks: int, iters: int, out, stream=None):
+    """FMA throughput probe (blocks x 256 threads x iters x 8 FMAs); the caller times it."""
+    _check(_lib.frkc2_fma_probe(PRECISION[precision], int(blocks), int(iters), _ptr(out), _stream_ptr(stream)),
+           "frkc2_fma_probe")
 
 
 def library_path() -> str:
