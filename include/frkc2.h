@@ -280,8 +280,8 @@ frkc2_status frkc2_step_adaptive(frkc2_plan_t plan, const frkc2_problem* prob, d
  * (every GPU that loads the library holds it until the process exits).  The call allocates
  * nothing: no cudaMalloc, no cudaFree, no allocating library routine.
  *   - Problems whose workspace (frkc2_workspace_size) exceeds the array are rejected with
- *     FRKC2_ENOMEM before any work is queued (e.g. FP64 2D grids up to about 590^2 cells,
- *     FP32 2D grids up to about 830^2 cells).
+ *     FRKC2_ENOMEM before any work is queued (e.g. FP64 2D grids up to about 510^2 cells,
+ *     FP32 2D grids up to about 720^2 cells).
  *   - Every call looks up the array's device address on the current device
  *     (cudaGetSymbolAddress, which allocates nothing).  The first call on a device may load
  *     the library's device code: make that first call before any stream capture.

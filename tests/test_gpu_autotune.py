@@ -31,6 +31,8 @@ def test_autotune_step_fp32_and_cache(tmp_path, monkeypatch):
     assert torch.equal(u, u_before)  # the tuner works on a scratch copy
     assert len(times) >= 5
     assert min(times.values()) <= 1.2 * times[json.dumps(dict(k=1, tile=[0, 0, 0], kernel=2))]
+    # the wavefront pass is among the candidates of a 512-wide FP32 grid, and runs
+    assert any(json.loads(k)["kernel"] == 7 for k in times)
     cached = json.load(open(tmp_path / "tune.json"))
     assert len(cached) == 1
     again, t2 = AT.autotune_step(plan, pr, u, dt, nsteps=2)
