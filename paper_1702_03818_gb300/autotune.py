@@ -132,38 +132,37 @@ def autotune_batch(plans, probs, dt, nsteps, u, reps: int = 2):
     """
     prec = probs[0].precision
     if prec == F.FP32:  # register-tiled 64 x 64 regions: the tile follows from k
-        ks, tiles = (4, 6, 8, 10), ((0, 0, 0),)
-    else:
-        ks, tiles = (1, 2, 4), ((64, 32, 1), (64, 16, 1), (32, 32, 1))
+        cands = [F.make_tuning(k=k) for k in (4, 6, 8, 10)]
+    else:  # streaming items (k = 1) by rows per tile, and the shared-memory tile pass
+        cands = [F.make_tuning(k=1, tile=(0, r, 1)) for r in (64, 128, 256)]
+        cands += [F.make_tuning(k=k, tile=t, kernel=1) for k in (1, 2) for t in ((64, 16, 1), (32, 32, 1))]
     scratch = [t.clone() for t in u]
     times = {}
     best, best_ms = None, float("inf")
-    for k in ks:
-        for tile in tiles:
-            t = F.make_tuning(k=k, tile=tile)
-            try:
-                ws = torch.empty(F.frkc2_batch_workspace_size(plans, probs, nsteps, t), dtype=torch.uint8,
-                                 device=u[0].device)
-                F.frkc2_workspace_reset(ws)
-                for a, b in zip(scratch, u):
-                    a.copy_(b)
-                F.frkc2_batch_prepare(plans, probs, dt, nsteps, scratch, ws, t)
-            except F.Frkc2Error:
-                continue
-            ms = []
-            for _ in range(reps + 1):
-                for a, b in zip(scratch, u):
-                    a.copy_(b)
-                e0 = torch.cuda.Event(enable_timing=True)
-                e1 = torch.cuda.Event(enable_timing=True)
-                e0.record()
-                F.frkc2_batch_launch(ws)
-                e1.record()
-                e1.synchronize()
-                ms.append(e0.elapsed_time(e1))
-            m = sorted(ms[1:])[len(ms[1:]) // 2]
-            times[json.dumps(_tuning_dict(t))] = m
-            if m < best_ms:
-                best, best_ms = t, m
-            del ws
+    for t in cands:
+        try:
+            ws = torch.empty(F.frkc2_batch_workspace_size(plans, probs, nsteps, t), dtype=torch.uint8,
+                             device=u[0].device)
+            F.frkc2_workspace_reset(ws)
+            for a, b in zip(scratch, u):
+                a.copy_(b)
+            F.frkc2_batch_prepare(plans, probs, dt, nsteps, scratch, ws, t)
+        except F.Frkc2Error:
+            continue
+        ms = []
+        for _ in range(reps + 1):
+            for a, b in zip(scratch, u):
+                a.copy_(b)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            F.frkc2_batch_launch(ws)
+            e1.record()
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        m = sorted(ms[1:])[len(ms[1:]) // 2]
+        times[json.dumps(_tuning_dict(t))] = m
+        if m < best_ms:
+            best, best_ms = t, m
+        del ws
     return best, times

@@ -16,8 +16,11 @@
 // State buffers are rewritten by other CTAs within the launch, so state loads bypass L1
 // (ld.global.cg); a finished tile is published with a device-scope fence before its counter
 // increment.  FP32 items run the register-tiled 64 x 64 region of the single-problem FP32
-// pass (tb2d_region.cuh: tile 64 - 2k, k-cell recomputed halo); FP64 and MIXED items run a
-// k-stage shared-memory tile pass.
+// pass (tb2d_region.cuh: tile 64 - 2k, k-cell recomputed halo).  FP64 and MIXED items with one
+// stage per pass (the default) run the streaming body of the single-problem pass on a tile of
+// 31 columns and a block of rows split among the CTA's warps -- interleaved complex state,
+// face pairs, every neighbour difference formed once: 16 FP64 instructions per cell-stage;
+// with k > 1 (or kernel 1) they run a k-stage shared-memory tile pass.
 #include <algorithm>
 #include <cmath>
 #include <mutex>
@@ -47,6 +50,7 @@ struct BProb {
   int s, passes_per_step, total_passes, extra_copy;
   const void* fx;
   const void* fy;
+  const void* fen;     // face pairs (east, north) [ny + 1][nx + 1] for the streaming items
   void* u;
   void* ua;
   void* va;
@@ -57,6 +61,7 @@ struct BProb {
 
 struct BHeader {
   int nprob, nrounds, bc, tx, ty, k, fault_inject;
+  int stream_rows;               // > 0: FP64 / MIXED streaming items of 31 columns x this many rows
   long long total_items;
   long long wait_limit;
   const BProb* probs;            // sorted by total passes, largest first
@@ -104,6 +109,136 @@ __device__ __forceinline__ void pass_buffers(const BProb& P, int r, const void*&
     Uout = P.u;
     Vout = nullptr;
   }
+}
+
+constexpr int BS_COLS = 31;  // output columns of a streaming item (lane 0 is the west halo)
+
+template <class T> struct BVec2;
+template <> struct BVec2<double> { using type = double2; };
+template <> struct BVec2<float> { using type = float2; };
+
+// One stage (one pass of k = 1) of a streaming item: column chunk cw (output columns
+// 31 cw .. 31 cw + 30, lane 0 reading the column to their west), rows [r0, r1) split evenly
+// among the warps, each warp walking up its rows with the south difference and face carried
+// in registers and east / west differences shared by shuffles (the single-problem streaming
+// pass's arithmetic).  The state comes interleaved (in_real: the real part only) and goes out
+// interleaved (out_real: the real part only); state loads go through L2 (other CTAs of the
+// launch wrote them).  Returns true if a stored real part is not finite (out_real only).
+template <class S, class A, bool PERIODIC>
+__device__ __forceinline__ bool stream_item(const BProb& P, int cw, int r0, int r1, const void* in, bool in_real,
+                                            void* out, bool out_real, S ca, S cb) {
+  using S2 = typename BVec2<S>::type;
+  using A2 = typename BVec2<A>::type;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = BT_THREADS / 32;
+  const int nx = P.nx, ny = P.ny;
+  const int per = (r1 - r0 + nwarps - 1) / nwarps;
+  const int y0 = r0 + warp * per, y1 = min(y0 + per, r1);
+  bool bad = false;
+  if (y0 >= y1) return false;  // warp-uniform
+  const A2* __restrict__ FEN = static_cast<const A2*>(P.fen);
+  const S* Ur = static_cast<const S*>(in);
+  const S2* Wi = static_cast<const S2*>(in);
+  S* Uo = static_cast<S*>(out);
+  S2* Wo = static_cast<S2*>(out);
+  const int x = cw * BS_COLS + lane - 1;
+  int xr, xeast;
+  bool xin, eastin;
+  if (PERIODIC) {
+    xr = x < 0 ? x + nx : (x >= nx ? x - nx : x);
+    xin = true;
+    xeast = xr + 1 == nx ? 0 : xr + 1;
+    eastin = true;
+  } else {
+    xr = x;
+    xin = x >= 0 && x < nx;
+    xeast = x + 1;
+    eastin = xeast >= 0 && xeast < nx;
+  }
+  const bool has_faces = PERIODIC || (x >= -1 && x < nx);
+  const int fcol = (PERIODIC ? xr : x) + 1;
+  const bool out_ok = lane >= 1 && x >= 0 && x < nx;
+  auto load = [&](int yy, int xx, bool inx) -> S2 {
+    S2 w;
+    w.x = S(0);
+    w.y = S(0);
+    int yw = yy;
+    if (PERIODIC) {
+      if (yw < 0) yw += ny;
+      while (yw >= ny) yw -= ny;
+    } else if (!(inx && yy >= 0 && yy < ny)) {
+      return w;
+    }
+    const size_t g = size_t(yw) * nx + xx;
+    if (in_real)
+      w.x = __ldcg(Ur + g);
+    else
+      w = __ldcg(Wi + g);
+    return w;
+  };
+  auto faces = [&](int yy) -> A2 {
+    A2 f;
+    f.x = A(0);
+    f.y = A(0);
+    if (PERIODIC) {
+      if (yy < 0) yy += ny;
+      while (yy >= ny) yy -= ny;
+    } else if (yy >= ny) {
+      return f;
+    }
+    if (!has_faces) return f;
+    return __ldg(FEN + size_t(yy + 1) * (nx + 1) + fcol);
+  };
+  S2 Wc = load(y0, xr, xin);
+  A dSU, dSV, ks;
+  {
+    const S2 Ws = load(y0 - 1, xr, xin);
+    ks = faces(y0 - 1).y;
+    dSU = A(Wc.x - Ws.x);
+    dSV = A(Wc.y - Ws.y);
+  }
+  S2 Wn = load(y0 + 1, xr, xin);
+  A2 f = faces(y0);
+  S2 Wen = lane == 31 ? load(y0, xeast, eastin) : Wc;
+  for (int y = y0; y < y1; ++y) {
+    const S2 Wnn = load(y + 2, xr, xin);
+    const A2 fnext = faces(y + 1);
+    const S2 Wenn = lane == 31 ? load(y + 1, xeast, eastin) : Wn;
+    S Ue = __shfl_down_sync(0xffffffffu, Wc.x, 1);
+    S Ve = __shfl_down_sync(0xffffffffu, Wc.y, 1);
+    if (lane == 31) {
+      Ue = Wen.x;
+      Ve = Wen.y;
+    }
+    const A dEU = A(Ue - Wc.x), dEV = A(Ve - Wc.y);
+    const A dNU = A(Wn.x - Wc.x), dNV = A(Wn.y - Wc.y);
+    const A dWU = __shfl_up_sync(0xffffffffu, dEU, 1);
+    const A dWV = __shfl_up_sync(0xffffffffu, dEV, 1);
+    const A kw = __shfl_up_sync(0xffffffffu, f.x, 1);
+    const A fU = f.y * dNU - ks * dSU - kw * dWU + f.x * dEU;
+    const A fV = f.y * dNV - ks * dSV - kw * dWV + f.x * dEV;
+    const S un = Wc.x + ca * S(fU) - cb * S(fV);
+    const S vn = Wc.y + ca * S(fV) + cb * S(fU);
+    if (out_ok) {
+      const size_t g = size_t(y) * nx + x;
+      if (out_real) {
+        Uo[g] = un;
+        bad |= !isfinite(double(un));
+      } else {
+        S2 w;
+        w.x = un;
+        w.y = vn;
+        Wo[g] = w;
+      }
+    }
+    dSU = dNU;
+    dSV = dNV;
+    ks = f.y;
+    Wc = Wn;
+    Wn = Wnn;
+    f = fnext;
+    Wen = Wenn;
+  }
+  return bad;
 }
 
 // FP32 items hold a 4 x 4 block of cells per thread in registers: two CTAs per SM
@@ -200,6 +335,15 @@ __global__ void __launch_bounds__(BT_THREADS, bt_min_blocks<S, A>()) k_batched(c
                    : tb2d_region<false, true>(rsh, P.nx, P.ny, h.k, kq, x0, y0, Uin, Vin, Uout, Vout,
                                               static_cast<const float*>(P.fx), static_cast<const float*>(P.fy), coef,
                                               Vout == nullptr);
+      if (bad) atomicOr(h.status, ST_NONFINITE);
+    } else if (h.stream_rows > 0) {
+      // one stage: real input at a step's first stage, real output at its last
+      const int q = s_round < P.total_passes ? s_round % P.passes_per_step : 0;
+      const S ca = S(P.coef[2 * l0]), cb = S(P.coef[2 * l0 + 1]);
+      const int r0 = tyi * h.stream_rows, r1 = min(r0 + h.stream_rows, P.ny);
+      const bool in_real = q == 0, out_real = q == P.passes_per_step - 1;
+      const bool bad = periodic ? stream_item<S, A, true>(P, txi, r0, r1, Uin_v, in_real, Uout_v, out_real, ca, cb)
+                                : stream_item<S, A, false>(P, txi, r0, r1, Uin_v, in_real, Uout_v, out_real, ca, cb);
       if (bad) atomicOr(h.status, ST_NONFINITE);
     } else {
       const S* Uin = static_cast<const S*>(Uin_v);
@@ -322,10 +466,16 @@ struct BatchPlanHost {
   long long total_items;
 };
 
-// dynamic shared memory of an item: none for the FP32 register-tiled regions, the k-halo tile
-// of state ping-pong buffers and face conductivities otherwise
-size_t batch_smem(int precision, int tx, int ty, int k) {
-  if (precision == FRKC2_FP32) return 0;
+// FP64 / MIXED batches with one stage per pass run streaming items unless kernel 1 (the shared-
+// memory tile pass) is asked for
+bool batch_streaming(int precision, int k, const frkc2_tuning* tune) {
+  return precision != FRKC2_FP32 && k == 1 && !(tune && tune->kernel == 1);
+}
+
+// dynamic shared memory of an item: none for the FP32 register-tiled regions and the streaming
+// items, the k-halo tile of state ping-pong buffers and face conductivities otherwise
+size_t batch_smem(int precision, int tx, int ty, int k, bool streaming = false) {
+  if (precision == FRKC2_FP32 || streaming) return 0;
   return size_t(tx + 2 * k) * (ty + 2 * k) * (4 * state_bytes(precision) + 2 * arith_bytes(precision));
 }
 
@@ -341,15 +491,18 @@ frkc2_status batch_geometry(int nprob, const frkc2_plan_t* plans, const frkc2_pr
     if (probs[i].precision == FRKC2_DFLOAT) return FRKC2_EUNSUPPORTED;
     if (probs[i].precision != p0.precision || probs[i].bc != p0.bc) return FRKC2_EINVAL;
   }
-  int k = (tune && tune->k) ? tune->k : (p0.precision == FRKC2_FP32 ? 6 : 2);
+  int k = (tune && tune->k) ? tune->k : (p0.precision == FRKC2_FP32 ? 6 : 1);
   int tx = (tune && tune->tile_x) ? tune->tile_x : 64;
   int ty = (tune && tune->tile_y) ? tune->tile_y : 16;
   if (k < 1 || k > KMAX || tx < 1 || ty < 1) return FRKC2_EINVAL;
   if (p0.precision == FRKC2_FP32) {  // register-tiled regions: the tile is the region minus its halo
     if (2 * k >= RT_R) return FRKC2_EINVAL;
     tx = ty = RT_R - 2 * k;
+  } else if (batch_streaming(p0.precision, k, tune)) {  // streaming items: 31 columns x a row block
+    tx = BS_COLS;
+    ty = (tune && tune->tile_y) ? tune->tile_y : 128;
   }
-  if (batch_smem(p0.precision, tx, ty, k) > 200 * 1024) return FRKC2_EINVAL;
+  if (batch_smem(p0.precision, tx, ty, k, batch_streaming(p0.precision, k, tune)) > 200 * 1024) return FRKC2_EINVAL;
   *k_out = k;
   *tx_out = tx;
   *ty_out = ty;
@@ -423,9 +576,11 @@ frkc2_status batch_plan(int nprob, const frkc2_plan_t* plans, const frkc2_proble
   B.counter_bytes = 16 + sizeof(unsigned) * size_t(nprob);
   off += align256(B.counter_bytes);
   B.off_faces = off;
+  const bool streaming = batch_streaming(probs[0].precision, k, tune);
   for (int r = 0; r < nprob; ++r) {
     const BProb& P = B.probs[r];
     off += align256(size_t(P.ny) * (P.nx + 1) * AB) + align256(size_t(P.ny + 1) * P.nx * AB);
+    if (streaming) off += align256(size_t(P.ny + 1) * (P.nx + 1) * 2 * AB);  // face pairs
   }
   B.off_states = off;
   for (int r = 0; r < nprob; ++r) {
@@ -489,6 +644,7 @@ frkc2_status frkc2_batch_prepare(int nprob, const frkc2_plan_t* plans, const frk
   char* base = static_cast<char*>(ws);
   const int prec = probs[0].precision;
   const size_t SB = state_bytes(prec), AB = arith_bytes(prec);
+  const bool streaming = batch_streaming(prec, k, tune);
   // per-problem pointers and face conductivities
   size_t fo = B.off_faces, so = B.off_states;
   for (int r = 0; r < nprob; ++r) {
@@ -500,6 +656,12 @@ frkc2_status frkc2_batch_prepare(int nprob, const frkc2_plan_t* plans, const frk
     fo += align256(size_t(P.ny + 1) * P.nx * AB);
     P.fx = fx;
     P.fy = fy;
+    P.fen = nullptr;
+    if (streaming) {
+      void* fen = base + fo;
+      fo += align256(size_t(P.ny + 1) * (P.nx + 1) * 2 * AB);
+      P.fen = fen;
+    }
     const size_t sb = align256(size_t(P.nx) * P.ny * SB);
     P.ua = base + so;
     P.va = base + so + sb;
@@ -509,6 +671,8 @@ frkc2_status frkc2_batch_prepare(int nprob, const frkc2_plan_t* plans, const frk
     P.u = u[i];
     P.coef = reinterpret_cast<const double*>(base + B.off_coef) + B.coef_off[r];
     if (launch_faces(probs[i], fx, fy, nullptr, st) != cudaSuccess) return FRKC2_ECUDA;
+    if (streaming && launch_face_pairs(probs[i], fx, fy, const_cast<void*>(P.fen), st) != cudaSuccess)
+      return FRKC2_ECUDA;
   }
   BHeader h{};
   h.nprob = nprob;
@@ -517,6 +681,7 @@ frkc2_status frkc2_batch_prepare(int nprob, const frkc2_plan_t* plans, const frk
   h.tx = tx;
   h.ty = ty;
   h.k = k;
+  h.stream_rows = streaming ? ty : 0;
   h.fault_inject = tune ? tune->fault_inject : 0;
   h.total_items = B.total_items;
   h.wait_limit = (tune && tune->wait_limit > 0) ? tune->wait_limit : DEFAULT_WAIT_LIMIT;
@@ -540,7 +705,7 @@ frkc2_status frkc2_batch_prepare(int nprob, const frkc2_plan_t* plans, const frk
   if (cudaStreamSynchronize(st) != cudaSuccess) return FRKC2_ECUDA;
   LaunchCfg cfg{};
   cfg.precision = prec;
-  cfg.smem = batch_smem(prec, tx, ty, k);
+  cfg.smem = batch_smem(prec, tx, ty, k, streaming);
   cudaError_t e = prec == FRKC2_FP64 ? set_smem<double, double>(cfg.smem)
                                      : (prec == FRKC2_FP32 ? set_smem<float, float>(cfg.smem) : set_smem<double, float>(cfg.smem));
   if (e != cudaSuccess) return FRKC2_ECUDA;

@@ -63,6 +63,30 @@ def test_batched_matches_oracle(prec, bc):
         assert err < TOL[prec], (it["u"].shape, it["s"], it["nsteps"], err)
 
 
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+@pytest.mark.parametrize("bc", ["periodic", "dirichlet"])
+@pytest.mark.parametrize("rows", [0, 7])
+def test_batched_streaming_items_match_oracle(prec, bc, rows):
+    """FP64 / MIXED batches with one stage per pass (the default) run the streaming body on
+    tiles of 31 columns x a row block split among the warps (128 rows by default; 7 makes
+    blocks smaller than the warp count): every item against the oracle, grid norm and every
+    element, over ragged grids of 5 .. 150 cells a side and 1 .. 3 steps."""
+    items = make_batch(prec, bc, SPECS, seed0=1300)
+    plans = [F.frkc2_plan(it["s"]) for it in items]
+    tune = F.make_tuning(tile=(0, rows, 0)) if rows else None
+    nst = [it["nsteps"] for it in items]
+    ws = torch.empty(F.frkc2_batch_workspace_size(plans, [it["pr"] for it in items], nst, tune),
+                     dtype=torch.uint8, device="cuda")
+    F.frkc2_workspace_reset(ws)
+    F.frkc2_step_batched(plans, [it["pr"] for it in items], [it["dt"] for it in items], nst,
+                         [it["u"] for it in items], ws, tune)
+    assert F.frkc2_workspace_status(ws) == F.OK
+    refs = oracle_results(items, prec)
+    for it, ref in zip(items, refs):
+        err = rel_err(it["u"].double().cpu().numpy(), ref)
+        assert err < TOL[prec], (it["u"].shape, it["s"], it["nsteps"], err)
+
+
 def test_batched_cuda_graph_replay():
     prec = "fp32"
     items = make_batch(prec, "periodic", SPECS[:5], seed0=950)
@@ -156,7 +180,7 @@ def test_batched_64_problems_large_s_matches_oracle(prec):
         plans = [F.frkc2_plan(it["s"]) for it in items]
     probs = [it["pr"] for it in items]
     nst = [it["nsteps"] for it in items]
-    tune = F.make_tuning(k=8 if prec == "fp32" else 2)
+    tune = F.make_tuning(k=8) if prec == "fp32" else None  # FP64: the streaming items
     ws = torch.empty(F.frkc2_batch_workspace_size(plans, probs, nst, tune), dtype=torch.uint8, device="cuda")
     F.frkc2_workspace_reset(ws)
     F.frkc2_step_batched(plans, probs, [it["dt"] for it in items], nst, [it["u"] for it in items], ws, tune)
