@@ -285,7 +285,7 @@ def batched2d(F):
                      "plans": ("precision policy (Lebedev-Finogenov order), largest predicted FP32 error "
                                f"{max(a[2] for a in auto.values()):.2e}" if prec == "fp32" else "the paper's order"),
                      "workspace_gb": ws.numel() / 1e9,
-                     "tuning": {"k": tune.k, "tile": [tune.tile_x, tune.tile_y]}, "autotune_ms": tt}
+                     "tuning": {"k": tune.k, "tile": [tune.tile_x, tune.tile_y, tune.tile_z]}, "autotune_ms": tt}
         del ws, g
     return {"workload": "batched2d: 512 var-kappa 2D problems, n~U{64..1024}, s~{16..256}, 10 steps, one persistent launch (CUDA graph)",
             "metric": "cell-stage/s", "value": res["fp32"]["value"], "unit": UNIT, "precisions": res}

@@ -46,7 +46,8 @@ constexpr long long DEFAULT_WAIT_LIMIT = 1ll << 22;
 
 struct BProb {
   int nx, ny;
-  int tiles_x, ntiles;
+  int tiles_x, ntiles;   // tiles per row of tiles; work items per pass
+  int tiles_total;       // tiles per pass (an FP32 item covers up to `group` consecutive tiles)
   int s, passes_per_step, total_passes, extra_copy;
   const void* fx;
   const void* fy;
@@ -62,6 +63,7 @@ struct BProb {
 struct BHeader {
   int nprob, nrounds, bc, tx, ty, k, fault_inject;
   int stream_rows;               // > 0: FP64 / MIXED streaming items of 31 columns x this many rows
+  int group;                     // FP32: consecutive tiles of one pass per work item
   long long total_items;
   long long wait_limit;
   const BProb* probs;            // sorted by total passes, largest first
@@ -323,18 +325,25 @@ __global__ void __launch_bounds__(BT_THREADS, bt_min_blocks<S, A>()) k_batched(c
         ca = float(cf[2 * j]);
         cb = float(cf[2 * j + 1]);
       };
-      const int x0 = txi * h.tx - h.k, y0 = tyi * h.ty - h.k;
       const float* Uin = static_cast<const float*>(Uin_v);
       const float* Vin = static_cast<const float*>(Vin_v);
       float* Uout = static_cast<float*>(Uout_v);
       float* Vout = static_cast<float*>(Vout_v);
-      const bool bad =
-          periodic ? tb2d_region<true, true>(rsh, P.nx, P.ny, h.k, kq, x0, y0, Uin, Vin, Uout, Vout,
-                                             static_cast<const float*>(P.fx), static_cast<const float*>(P.fy), coef,
-                                             Vout == nullptr)
-                   : tb2d_region<false, true>(rsh, P.nx, P.ny, h.k, kq, x0, y0, Uin, Vin, Uout, Vout,
-                                              static_cast<const float*>(P.fx), static_cast<const float*>(P.fy), coef,
-                                              Vout == nullptr);
+      bool bad = false;
+      // the item's tiles: consecutive tiles of the pass, one region after another
+      for (int g = 0; g < h.group; ++g) {
+        const int tile = s_tile * h.group + g;
+        if (tile >= P.tiles_total) break;  // block-uniform
+        const int ty_i = tile / P.tiles_x, tx_i = tile - ty_i * P.tiles_x;
+        const int x0 = tx_i * h.tx - h.k, y0 = ty_i * h.ty - h.k;
+        bad |= periodic ? tb2d_region<true, true>(rsh, P.nx, P.ny, h.k, kq, x0, y0, Uin, Vin, Uout, Vout,
+                                                  static_cast<const float*>(P.fx), static_cast<const float*>(P.fy),
+                                                  coef, Vout == nullptr)
+                        : tb2d_region<false, true>(rsh, P.nx, P.ny, h.k, kq, x0, y0, Uin, Vin, Uout, Vout,
+                                                   static_cast<const float*>(P.fx), static_cast<const float*>(P.fy),
+                                                   coef, Vout == nullptr);
+        __syncthreads();  // the region's shared exchange buffers are reused by the next tile
+      }
       if (bad) atomicOr(h.status, ST_NONFINITE);
     } else if (h.stream_rows > 0) {
       // one stage: real input at a step's first stage, real output at its last
@@ -466,6 +475,14 @@ struct BatchPlanHost {
   long long total_items;
 };
 
+// FP32 items: consecutive 64 x 64 regions of one pass per work item (tune->tile_z; default 4),
+// which spreads the per-item hand-over (ticket, decode, dependency check, completion fence)
+// over several regions
+int batch_group(int precision, const frkc2_tuning* tune) {
+  if (precision != FRKC2_FP32) return 1;
+  return (tune && tune->tile_z) ? tune->tile_z : 4;
+}
+
 // FP64 / MIXED batches with one stage per pass run streaming items unless kernel 1 (the shared-
 // memory tile pass) is asked for
 bool batch_streaming(int precision, int k, const frkc2_tuning* tune) {
@@ -514,6 +531,8 @@ frkc2_status batch_plan(int nprob, const frkc2_plan_t* plans, const frkc2_proble
   frkc2_status v = batch_geometry(nprob, plans, probs, nsteps, tune, &k, &tx, &ty);
   if (v != FRKC2_OK) return v;
   const size_t SB = state_bytes(probs[0].precision), AB = arith_bytes(probs[0].precision);
+  const int group = batch_group(probs[0].precision, tune);
+  if (group < 1 || group > 64) return FRKC2_EINVAL;
   std::vector<int> T(nprob);
   for (int i = 0; i < nprob; ++i) {
     const int P = (plans[i]->s + k - 1) / k;
@@ -533,7 +552,8 @@ frkc2_status batch_plan(int nprob, const frkc2_plan_t* plans, const frkc2_proble
     P.nx = int(p.n[0]);
     P.ny = int(p.n[1]);
     P.tiles_x = (P.nx + tx - 1) / tx;
-    P.ntiles = P.tiles_x * ((P.ny + ty - 1) / ty);
+    P.tiles_total = P.tiles_x * ((P.ny + ty - 1) / ty);
+    P.ntiles = (P.tiles_total + group - 1) / group;
     P.s = plans[i]->s;
     P.passes_per_step = (P.s + k - 1) / k;
     P.total_passes = T[i];
@@ -682,6 +702,7 @@ frkc2_status frkc2_batch_prepare(int nprob, const frkc2_plan_t* plans, const frk
   h.ty = ty;
   h.k = k;
   h.stream_rows = streaming ? ty : 0;
+  h.group = batch_group(prec, tune);
   h.fault_inject = tune ? tune->fault_inject : 0;
   h.total_items = B.total_items;
   h.wait_limit = (tune && tune->wait_limit > 0) ? tune->wait_limit : DEFAULT_WAIT_LIMIT;

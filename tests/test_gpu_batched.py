@@ -87,6 +87,24 @@ def test_batched_streaming_items_match_oracle(prec, bc, rows):
         assert err < TOL[prec], (it["u"].shape, it["s"], it["nsteps"], err)
 
 
+@pytest.mark.parametrize("group", [1, 3])
+def test_batched_fp32_regions_per_item(group):
+    """FP32 items covering `group` consecutive 64 x 64 regions of one pass (the default is 4,
+    used by the other tests): the same results as the oracle on ragged grids."""
+    items = make_batch("fp32", "periodic", SPECS, seed0=1500)
+    plans = [F.frkc2_plan(it["s"]) for it in items]
+    tune = F.make_tuning(k=6, tile=(0, 0, group))
+    nst = [it["nsteps"] for it in items]
+    ws = torch.empty(F.frkc2_batch_workspace_size(plans, [it["pr"] for it in items], nst, tune),
+                     dtype=torch.uint8, device="cuda")
+    F.frkc2_workspace_reset(ws)
+    F.frkc2_step_batched(plans, [it["pr"] for it in items], [it["dt"] for it in items], nst,
+                         [it["u"] for it in items], ws, tune)
+    assert F.frkc2_workspace_status(ws) == F.OK
+    for it, ref in zip(items, oracle_results(items, "fp32")):
+        assert rel_err(it["u"].double().cpu().numpy(), ref) < TOL["fp32"]
+
+
 def test_batched_cuda_graph_replay():
     prec = "fp32"
     items = make_batch(prec, "periodic", SPECS[:5], seed0=950)
