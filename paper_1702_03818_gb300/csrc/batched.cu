@@ -508,7 +508,7 @@ frkc2_status batch_geometry(int nprob, const frkc2_plan_t* plans, const frkc2_pr
     if (probs[i].precision == FRKC2_DFLOAT) return FRKC2_EUNSUPPORTED;
     if (probs[i].precision != p0.precision || probs[i].bc != p0.bc) return FRKC2_EINVAL;
   }
-  int k = (tune && tune->k) ? tune->k : (p0.precision == FRKC2_FP32 ? 6 : 1);
+  int k = (tune && tune->k) ? tune->k : (p0.precision == FRKC2_FP32 ? 8 : 1);
   int tx = (tune && tune->tile_x) ? tune->tile_x : 64;
   int ty = (tune && tune->tile_y) ? tune->tile_y : 16;
   if (k < 1 || k > KMAX || tx < 1 || ty < 1) return FRKC2_EINVAL;
