@@ -64,7 +64,10 @@ def _rel(a, b):
     return float(np.linalg.norm((a - b).ravel()) / np.linalg.norm(b.ravel()))
 
 
-def heat1d(F):
+def heat1d(F, sweep: bool = True):
+    """The 1D heat workload (N = 256 Dirichlet, s = 16, 87 steps) with the library's default
+    whole-job kernel in FP64 and FP32, and (sweep) the kernel's cluster size, stages per halo
+    exchange and threads per CTA; each against the FP64 default run."""
     torch = _torch()
     cfg = I.CONFIGS["heat1d"]
     u0, _, dx = I.heat1d_u0(cfg["n"], 8, cfg["seed"])
@@ -73,20 +76,41 @@ def heat1d(F):
     beta = plan.info()["beta"]
     nsteps = int(np.ceil(cfg["t_end"] / (0.9 * beta * dx * dx / 4.0)))
     dt = cfg["t_end"] / nsteps
-    pr = F.make_problem(1, (cfg["n"],), dx, "dirichlet", "const", "fp64", kappa_c=1.0)
-    ws = torch.empty(F.frkc2_workspace_size(pr), dtype=torch.uint8, device="cuda")
-    u0d = torch.as_tensor(u0, device="cuda")
-    u = u0d.clone()
-
-    def job():
-        u.copy_(u0d)
-        F.frkc2_step(plan, pr, dt, nsteps, 0.0, u, ws)
-
-    med, _ = _timed(job, 3, 5)
     cs = cfg["n"] * s * nsteps
-    return {"workload": "heat1d: 1D heat N=256 Dirichlet, s=16, 87 steps, FP64", "metric": "cell-stage/s",
-            "value": cs / (med / 1e3), "unit": UNIT, "ms_per_job": med, "nsteps": nsteps,
-            "kernel": "1D whole-job cluster kernel (one launch for all 87 x 16 stages)"}
+
+    def run(prec, tune=None):
+        pr = F.make_problem(1, (cfg["n"],), dx, "dirichlet", "const", prec, kappa_c=1.0)
+        ws = torch.empty(F.frkc2_workspace_size(pr), dtype=torch.uint8, device="cuda")
+        u0d = torch.as_tensor(u0, dtype=_dt(torch)[prec][0], device="cuda")
+        u = u0d.clone()
+
+        def job():
+            u.copy_(u0d)
+            F.frkc2_step(plan, pr, dt, nsteps, 0.0, u, ws, tune)
+
+        med, _ = _timed(job, 3, 5)
+        return med, u.double().cpu().numpy()
+
+    ms64, ref = run("fp64")
+    ms32, u32 = run("fp32")
+    out = {"workload": "heat1d: 1D heat N=256 Dirichlet, s=16, 87 steps, FP64", "metric": "cell-stage/s",
+           "value": cs / (ms64 / 1e3), "unit": UNIT, "ms_per_job": ms64, "nsteps": nsteps,
+           "fp32": {"ms_per_job": ms32, "value": cs / (ms32 / 1e3), "rel_l2_vs_fp64": _rel(u32, ref)},
+           "kernel": "1D whole-job cluster kernel (one launch for all 87 x 16 stages)"}
+    if sweep:
+        rows = {}
+        for prec in ("fp64", "fp32"):
+            for cl in (1, 2, 4, 8):
+                for kx in ((0,) if cl == 1 else (1, 4, 8, 16)):
+                    for th in (32, 64, 128, 256):
+                        tune = F.make_tuning(k=kx, kernel=6, tile=(cl, th, 0))
+                        try:
+                            ms, u = run(prec, tune)
+                        except F.Frkc2Error:
+                            continue
+                        rows[f"{prec}_cl{cl}_k{kx}_t{th}"] = {"ms_per_job": ms, "rel_l2_vs_fp64": _rel(u, ref)}
+        out["sweep"] = rows
+    return out
 
 
 def nonlinear3d(F, n=None):
@@ -383,12 +407,13 @@ def precision(F):
 
 def peaks(F):
     """FMA throughput of the FP64 and FP32 pipes (frkc2_fma_probe: 8 independent FMA chains per
-    thread, 152 x 8 CTAs of 256 threads), against the unit-count figures the rooflines use:
-    152 SMs x 2 FP64 FMA per clock and x 128 FP32 FMA per clock at 2.07 GHz."""
+    thread, 152 x 8 CTAs of 256 threads; FP32 also as packed two-lane FMAs), against the
+    unit-count figures the rooflines use: 152 SMs x 2 FP64 FMA per clock and x 128 FP32 FMA per
+    clock at 2.07 GHz."""
     torch = _torch()
     blocks = 152 * 8
     out = {}
-    for prec, iters, units in (("fp64", 4096, 2), ("fp32", 65536, 128)):
+    for prec, iters, units in (("fp64", 4096, 2), ("fp32", 65536, 128), ("fp32x2", 65536, 128)):
         buf = torch.empty(blocks * 256, dtype=torch.float64 if prec == "fp64" else torch.float32, device="cuda")
 
         def job():
@@ -549,6 +574,17 @@ def profile_case(F, name: str):
         for _ in range(2):
             u = torch.as_tensor(u0, dtype=torch.float32, device="cuda")
             F.frkc2_step(plan, pr, dt, 1, 0.0, u, ws, F.make_tuning(kernel=7))
+    elif name in ("small1d", "small1d_fp32"):  # the 1D heat job (N = 256), the default whole-job kernel
+        cfg = I.CONFIGS["heat1d"]
+        u0, _, dx = I.heat1d_u0(cfg["n"], 8, cfg["seed"])
+        plan = F.frkc2_plan(cfg["s"])
+        nsteps = int(np.ceil(cfg["t_end"] / (0.9 * plan.info()["beta"] * dx * dx / 4.0)))
+        prec = "fp32" if name.endswith("fp32") else "fp64"
+        pr = F.make_problem(1, (cfg["n"],), dx, "dirichlet", "const", prec, kappa_c=1.0)
+        ws = torch.empty(F.frkc2_workspace_size(pr), dtype=torch.uint8, device="cuda")
+        for _ in range(2):
+            u = torch.as_tensor(u0, dtype=torch.float32 if prec == "fp32" else torch.float64, device="cuda")
+            F.frkc2_step(plan, pr, cfg["t_end"] / nsteps, nsteps, 0.0, u, ws)
     elif name == "tb2d":  # FP32 temporally blocked pass, 4096^2, k = 8
         n, s = 4096, 16
         u0 = I.smooth_unit((n, n), 128.0, 3819)

@@ -91,8 +91,9 @@ typedef struct {
 typedef struct {
   int k;             /* stages per pass (temporal blocking), 1..16; 0 = library default       */
   int tile_x;        /* output tile per CTA along x, y, z; 0 = library default (kernel 6:
-                        tile_x = CTAs in the cluster, 1..8; kernel 7: tile_y = rows per CTA,
-                        0 = one wave of CTAs)                                                */
+                        tile_x = CTAs in the cluster, 1..8, k = stages per halo exchange
+                        between them, 1..16, tile_y = threads per CTA; kernel 7: tile_y =
+                        rows per CTA, 0 = one wave of CTAs)                                  */
   int tile_y;
   int tile_z;
   int kernel;        /* 0 = library choice, 1 = generic shared-memory tile kernel,
@@ -400,7 +401,9 @@ frkc2_status frkc2_bruss_step(frkc2_plan_t plan, const frkc2_bruss_problem* prob
  * rooflines are stated against.  Launches `blocks` CTAs of 256 threads, each thread running
  * `iters` rounds of 8 independent FMA chains (FMAs = blocks * 256 * iters * 8) and writing one
  * value to out (device array of blocks * 256 elements of the precision).  The caller times it.
- *   precision : FRKC2_FP64 or FRKC2_FP32.                                                    */
+ *   precision : FRKC2_FP64, FRKC2_FP32 (scalar FMAs), or FRKC2_FP32 | FRKC2_PROBE_PACKED (the
+ *               same FMAs as packed two-lane FP32 instructions: 4 chains of float pairs).  */
+#define FRKC2_PROBE_PACKED 16
 frkc2_status frkc2_fma_probe(int precision, int blocks, int iters, void* out, void* stream);
 
 /* Short text for a status code (static storage).                                          */

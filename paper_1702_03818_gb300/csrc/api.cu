@@ -298,9 +298,10 @@ frkc2_status frkc2_step(frkc2_plan_t plan, const frkc2_problem* prob, double dt,
   a.status = reinterpret_cast<unsigned*>(base + L.status);
 
   if (use_small1d) {  // the whole job in one cluster launch
-    const int cl = tune ? tune->tile_x : 0;  // kernel 6: CTAs in the cluster (0: library choice)
-    return launch_small1d(p, *plan, dt, nsteps, u, base + L.fx, a.status, st, cl) == cudaSuccess ? FRKC2_OK
-                                                                                                 : FRKC2_ECUDA;
+    // kernel 6: CTAs in the cluster, stages per halo exchange, threads per CTA (0: library choice)
+    const int cl = tune ? tune->tile_x : 0, kx = tune ? tune->k : 0, th = tune ? tune->tile_y : 0;
+    const cudaError_t e = launch_small1d(p, *plan, dt, nsteps, u, base + L.fx, a.status, st, cl, kx, th);
+    return e == cudaSuccess ? FRKC2_OK : e == cudaErrorInvalidValue ? FRKC2_EINVAL : FRKC2_ECUDA;
   }
   const void* curU = u;
   const void* curV = nullptr;

@@ -105,7 +105,8 @@ cudaError_t launch_faces_wf(const frkc2_problem& p, const void* fx, const void* 
 cudaError_t launch_pass_wf2d(const frkc2_problem& p, const PassArgs& a, const void* faces_wf, int chunk_rows,
                              bool in_real, bool out_real, cudaStream_t st, bool overlap_previous);
 cudaError_t launch_small1d(const frkc2_problem& p, const frkc2_plan_s& plan, double dt, int nsteps, void* u,
-                           const void* fx, unsigned* status, cudaStream_t st, int cluster);
+                           const void* fx, unsigned* status, cudaStream_t st, int cluster, int stages_per_exchange,
+                           int threads_per_cta);
 cudaError_t launch_pass_stream3d(const frkc2_problem& p, const PassArgs& a, cudaStream_t st);
 cudaError_t launch_pass_tb2d_df(const frkc2_problem& p, const PassArgs& a, cudaStream_t st, bool overlap_previous);
 cudaError_t launch_pass_stream2d_df(const frkc2_problem& p, const PassArgs& a, const void* fen, cudaStream_t st);

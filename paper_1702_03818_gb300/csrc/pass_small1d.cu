@@ -2,16 +2,21 @@
 // thread-block cluster, the state never leaving the chip.
 //
 // The N cells are split into CL contiguous chunks, one per CTA of a cluster of CL <= 8 CTAs
-// (co-scheduled by the hardware); thread t of a CTA holds R consecutive cells of its chunk in
-// registers (complex state and the R + 1 face conductivities around them) for the whole job.
-// Per stage each thread publishes its first and last cell in shared memory (double-buffered
-// by stage parity), the cluster meets at one hardware barrier, and each thread reads the
-// neighbour cell beyond either end from the adjacent thread -- or, at a chunk end, from the
-// adjacent CTA's shared memory through the cluster's distributed shared memory.  The stage
-// shares each neighbour difference d_i = W_i - W_{i-1} between the two cells of face i:
-// f_i = kappa_{i+1} d_{i+1} - kappa_i d_i, then W_i += dt a_l f_i / dx^2 (Sec. 3, Eq. 13):
-// 10 floating-point instructions per cell-stage.  At the end of each step the state is Re W^L.
-// The stage coefficients of the whole plan (up to 1024 stages) travel in the parameter block.
+// (co-scheduled by the hardware).  A CTA holds its chunk extended by H halo cells on each side
+// (H = 0 for a Dirichlet grid in one CTA); thread t holds R consecutive cells of the extended
+// chunk in registers (complex state and the R + 1 face conductivities around them) for the
+// whole job, R a compile-time 1, 2, 4 or 8, the cells past the extended chunk's end zero and
+// never updated (as are Dirichlet cells outside the grid).  Per stage each thread takes the
+// neighbour cells beyond its ends from the adjacent lanes by shuffles; only the warps' end
+// lanes go through shared memory, at one CTA barrier (none when the CTA is one warp).  The
+// halo cells at the ends of the extended chunk go stale one cell per stage; every H stages the
+// CTAs refresh them from their neighbours' edge cells (a periodic grid in one CTA from its own)
+// through the cluster's distributed shared memory, at one cluster barrier.  The stage shares
+// each neighbour difference d_i = W_i - W_{i-1} between the two cells of face i:
+// f_i = kappa_{i+1} d_{i+1} - kappa_i d_i, then W_i += dt a_l f_i / dx^2 (Sec. 3, Eq. 13): 10
+// floating-point instructions per cell-stage, with no product contracted into an add, so every
+// launch shape gives the same bits.  At the end of each step the state is Re W^L.  The stage
+// coefficients of the whole plan (up to 1024 stages) are copied once to shared memory.
 #include <algorithm>
 #include <memory>
 
@@ -27,8 +32,10 @@ namespace {
 
 constexpr int S1_MAXS = 1024;
 constexpr int S1_RMAX = 8;      // cells per thread
-constexpr int S1_TMAX = 256;    // threads per CTA
+constexpr int S1_TMAX = 512;    // threads per CTA
+constexpr int S1_WMAX = S1_TMAX / 32;
 constexpr int S1_CMAX = 8;      // CTAs per cluster (portable size)
+constexpr int S1_HMAX = KMAX;   // halo cells per side (stages per halo exchange)
 
 template <class T> struct V2o;
 template <> struct V2o<double> { using type = double2; };
@@ -39,117 +46,166 @@ struct Small1dArgs {
   const void* fx;        // face conductivities, N + 1 (face i between cells i - 1 and i)
   unsigned* status;
   int n, nsteps, s;
-  int R;                 // cells per thread
+  int H;                 // halo cells per side and stages per halo exchange (0: none)
   double ca[S1_MAXS];    // dt Re a_l / dx^2
   double cb[S1_MAXS];    // dt Im a_l / dx^2
 };
 
+// products that are never contracted into a neighbouring add: every cell position of every
+// launch shape then rounds the same way, so all shapes give the same bits
+__device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
+
 __device__ __forceinline__ bool bad1(double v) { return (__double2hiint(v) & 0x7ff00000) == 0x7ff00000; }
 __device__ __forceinline__ bool bad1(float v) { return (__float_as_uint(v) & 0x7f800000u) == 0x7f800000u; }
 
-template <class S, class A, bool PERIODIC>
-__global__ void __launch_bounds__(S1_TMAX) k_small1d(const Small1dArgs a) {
+template <class S, class A, bool PERIODIC, int R>
+__global__ void __launch_bounds__(S1_TMAX, 1) k_small1d(const Small1dArgs a) {
   using S2 = typename V2o<S>::type;
-  __shared__ S2 edge_lo[2][S1_TMAX];  // each thread's first cell, by stage parity
-  __shared__ S2 edge_hi[2][S1_TMAX];  // its last cell
+  __shared__ S2 wlo[2][S1_WMAX];      // each warp's first cell (lane 0), by stage parity
+  __shared__ S2 whi[2][S1_WMAX];      // its last cell (lane 31)
+  __shared__ S2 own_lo[2][S1_HMAX];   // the chunk's first H cells, by exchange parity
+  __shared__ S2 own_hi[2][S1_HMAX];   // its last H cells
+  __shared__ S cs[2][S1_MAXS];        // the stage coefficients (ca, cb)
   cg::cluster_group cluster = cg::this_cluster();
   const int CL = int(cluster.num_blocks());
   const int c = int(cluster.block_rank());
-  const int t = threadIdx.x;
-  const int n = a.n, R = a.R;
-  // chunk of this CTA and of the previous one (for the index of its last occupied thread)
+  const int t = threadIdx.x, nt = blockDim.x, lane = t & 31, wid = t >> 5, nw = nt >> 5;
+  const int n = a.n, H = a.H;
   const int c0 = int((long long)c * n / CL), c1 = int((long long)(c + 1) * n / CL);
   const int cp = (c + CL - 1) % CL, cn = (c + 1) % CL;
-  const int p0 = int((long long)cp * n / CL), p1 = int((long long)(cp + 1) * n / CL);
-  const int prev_last = (p1 - p0 - 1) / R;  // occupied thread holding the previous chunk's end
-  const int lo = c0 + t * R, hi = min(lo + R, c1);
-  const int m = max(0, hi - lo);  // cells held by this thread
+  const int E = (c1 - c0) + 2 * H;          // cells of the extended chunk, from global c0 - H
+  const int lo = t * R;
   const S* __restrict__ U0 = static_cast<const S*>(a.u);
   const A* __restrict__ FX = static_cast<const A*>(a.fx);
+  auto wrapn = [n](int g) { return g < 0 ? g + n : (g >= n ? g - n : g); };  // |g| < 2n here
 
-  S U[S1_RMAX], V[S1_RMAX];
-  A kf[S1_RMAX + 1];  // faces lo .. lo + m
+  S U[R], V[R];
+  A kf[R + 1];           // faces west of the held cells, and east of the last
+  unsigned live = 0;     // bit i: held cell i is updated (in the extended chunk and the grid)
 #pragma unroll
-  for (int i = 0; i < S1_RMAX; ++i) {
-    U[i] = i < m ? U0[lo + i] : S(0);
+  for (int i = 0; i < R; ++i) {
+    const int e = lo + i, g = c0 - H + e;
+    const bool in = e < E && (PERIODIC || (g >= 0 && g < n));
+    if (in) live |= 1u << i;
+    U[i] = in ? U0[PERIODIC ? wrapn(g) : g] : S(0);
     V[i] = S(0);
   }
 #pragma unroll
-  for (int i = 0; i <= S1_RMAX; ++i) kf[i] = i <= m && m > 0 ? FX[lo + i] : A(0);
+  for (int i = 0; i <= R; ++i) {
+    const int e = lo + i, g = c0 - H + e;  // face g lies between cells g - 1 and g
+    A v = A(0);
+    if (e <= E) {
+      if (PERIODIC)
+        v = FX[wrapn(g)];
+      else if (g >= 0 && g <= n)
+        v = FX[g];
+    }
+    kf[i] = v;
+  }
+  for (int l = t; l < a.s; l += nt) {
+    cs[0][l] = S(a.ca[l]);
+    cs[1][l] = S(a.cb[l]);
+  }
   cluster.sync();  // every CTA of the cluster is running before any remote access
 
   bool bad = false;
-  int par = 0;
+  int par = 0, xpar = 0, since = 0;  // stages since the last halo exchange (the halo starts exact)
   for (int step = 0; step < a.nsteps; ++step) {
     for (int l = 0; l < a.s; ++l, par ^= 1) {
-      if (m > 0) {
-        S2 e;
-        e.x = U[0];
-        e.y = V[0];
-        edge_lo[par][t] = e;
-        // the last held cell, selected without a run-time register index (which would move
-        // the arrays to local memory)
+      if (H > 0 && since == H) {
+        // halo exchange: the chunk's own first and last H cells out, the neighbours' in
 #pragma unroll
-        for (int i = 1; i < S1_RMAX; ++i) {
-          e.x = i < m ? U[i] : e.x;
-          e.y = i < m ? V[i] : e.y;
+        for (int i = 0; i < R; ++i) {
+          const int e = lo + i;
+          S2 v;
+          v.x = U[i];
+          v.y = V[i];
+          if (e >= H && e < 2 * H) own_lo[xpar][e - H] = v;
+          if (e >= E - 2 * H && e < E - H) own_hi[xpar][e - (E - 2 * H)] = v;
         }
-        edge_hi[par][t] = e;
-      }
-      cluster.sync();
-      if (m > 0) {
-        // west neighbour of the first cell, east neighbour of the last cell
-        S2 w, ea;
-        w.x = w.y = ea.x = ea.y = S(0);
-        if (lo > c0) {
-          w = edge_hi[par][t - 1];
-        } else if (PERIODIC || c > 0) {
-          const S2* rem = cluster.map_shared_rank(&edge_hi[par][0], cp);
-          w = rem[prev_last];
-        }
-        if (hi < c1) {
-          ea = edge_lo[par][t + 1];
-        } else if (PERIODIC || c < CL - 1) {
-          const S2* rem = cluster.map_shared_rank(&edge_lo[par][0], cn);
-          ea = rem[0];
-        }
-        const S ca = S(a.ca[l]), cb = S(a.cb[l]);
-        // d across the thread's first face, then cell by cell
-        A dU = A(U[0] - w.x), dV = A(V[0] - w.y);
+        cluster.sync();
+        const S2* rlo = cluster.map_shared_rank(&own_hi[xpar][0], cp);  // global cells c0 - H .. c0 - 1
+        const S2* rhi = cluster.map_shared_rank(&own_lo[xpar][0], cn);  // global cells c1 .. c1 + H - 1
 #pragma unroll
-        for (int i = 0; i < S1_RMAX; ++i) {
-          if (i < m) {
-            const int in = i + 1 < S1_RMAX ? i + 1 : i;  // a compile-time index inside the array
-            const S nU = i + 1 < m ? U[in] : ea.x;
-            const S nV = i + 1 < m ? V[in] : ea.y;
-            const A eU = A(nU - U[i]), eV = A(nV - V[i]);
-            const A fU = kf[i + 1] * eU - kf[i] * dU;
-            const A fV = kf[i + 1] * eV - kf[i] * dV;
-            U[i] = U[i] + ca * S(fU) - cb * S(fV);
-            V[i] = V[i] + ca * S(fV) + cb * S(fU);
-            dU = eU;
-            dV = eV;
+        for (int i = 0; i < R; ++i) {
+          const int e = lo + i;
+          if (live & (1u << i)) {
+            if (e < H) {
+              const S2 v = rlo[e];
+              U[i] = v.x;
+              V[i] = v.y;
+            } else if (e >= E - H) {
+              const S2 v = rhi[e - (E - H)];
+              U[i] = v.x;
+              V[i] = v.y;
+            }
           }
         }
-        if (l == a.s - 1) {  // step output: the real part
-#pragma unroll
-          for (int i = 0; i < S1_RMAX; ++i) V[i] = S(0);
-        }
+        xpar ^= 1;
+        since = 0;
       }
+      // west neighbour of the first cell, east neighbour of the last: the adjacent lanes; at a
+      // warp's ends the adjacent warps' end lanes through shared memory; beyond the extended
+      // chunk's ends zero (a stale halo's neighbour, or a Dirichlet ghost)
+      S wU = __shfl_up_sync(0xffffffffu, U[R - 1], 1), wV = __shfl_up_sync(0xffffffffu, V[R - 1], 1);
+      S eU = __shfl_down_sync(0xffffffffu, U[0], 1), eV = __shfl_down_sync(0xffffffffu, V[0], 1);
+      if (nw > 1) {
+        if (lane == 0) wlo[par][wid] = S2{U[0], V[0]};
+        if (lane == 31) whi[par][wid] = S2{U[R - 1], V[R - 1]};
+        __syncthreads();
+        if (lane == 0) {
+          const S2 v = wid > 0 ? whi[par][wid - 1] : S2{S(0), S(0)};
+          wU = v.x;
+          wV = v.y;
+        }
+        if (lane == 31) {
+          const S2 v = wid < nw - 1 ? wlo[par][wid + 1] : S2{S(0), S(0)};
+          eU = v.x;
+          eV = v.y;
+        }
+      } else {
+        if (lane == 0) wU = wV = S(0);
+        if (lane == 31) eU = eV = S(0);
+      }
+      const S ca = cs[0][l], cb = cs[1][l];
+      // d across the thread's first face, then cell by cell
+      A dU = A(U[0] - wU), dV = A(V[0] - wV);
+#pragma unroll
+      for (int i = 0; i < R; ++i) {
+        const S nU = i + 1 < R ? U[i + 1 < R ? i + 1 : i] : eU;
+        const S nV = i + 1 < R ? V[i + 1 < R ? i + 1 : i] : eV;
+        const A xU = A(nU - U[i]), xV = A(nV - V[i]);
+        const A fU = fma(kf[i + 1], xU, -mul_rn(kf[i], dU));
+        const A fV = fma(kf[i + 1], xV, -mul_rn(kf[i], dV));
+        if (live & (1u << i)) {
+          U[i] = fma(-cb, S(fV), fma(ca, S(fU), U[i]));
+          V[i] = fma(cb, S(fU), fma(ca, S(fV), V[i]));
+        }
+        dU = xU;
+        dV = xV;
+      }
+      if (l == a.s - 1) {  // step output: the real part
+#pragma unroll
+        for (int i = 0; i < R; ++i) V[i] = S(0);
+      }
+      ++since;
     }
   }
   cluster.sync();  // no CTA leaves while another may still read its shared memory
 #pragma unroll
-  for (int i = 0; i < S1_RMAX; ++i)
-    if (i < m) {
-      static_cast<S*>(a.u)[lo + i] = U[i];
+  for (int i = 0; i < R; ++i) {
+    const int e = lo + i;
+    if (e >= H && e < E - H) {
+      static_cast<S*>(a.u)[c0 - H + e] = U[i];
       bad |= bad1(U[i]);
     }
+  }
   if (bad) atomicOr(a.status, ST_NONFINITE);
 }
 
-template <class S, class A, bool PERIODIC>
-cudaError_t launch_t(const Small1dArgs& a, int CL, int threads, cudaStream_t st) {
+template <class S, class A, bool PERIODIC, int R>
+cudaError_t launch_r(const Small1dArgs& a, int CL, int threads, cudaStream_t st) {
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(CL, 1, 1);
   cfg.blockDim = dim3(threads, 1, 1);
@@ -162,34 +218,61 @@ cudaError_t launch_t(const Small1dArgs& a, int CL, int threads, cudaStream_t st)
   attr[0].val.clusterDim.z = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  const cudaError_t e = cudaLaunchKernelEx(&cfg, k_small1d<S, A, PERIODIC>, a);
+  const cudaError_t e = cudaLaunchKernelEx(&cfg, k_small1d<S, A, PERIODIC, R>, a);
   count_launch();
   return e;
+}
+
+template <class S, class A, bool PERIODIC>
+cudaError_t launch_t(const Small1dArgs& a, int CL, int threads, int R, cudaStream_t st) {
+  switch (R) {
+    case 1: return launch_r<S, A, PERIODIC, 1>(a, CL, threads, st);
+    case 2: return launch_r<S, A, PERIODIC, 2>(a, CL, threads, st);
+    case 4: return launch_r<S, A, PERIODIC, 4>(a, CL, threads, st);
+    case 8: return launch_r<S, A, PERIODIC, 8>(a, CL, threads, st);
+    default: return cudaErrorInvalidValue;
+  }
 }
 
 }  // namespace
 
 bool small1d_supported(const frkc2_problem& p, int s) {
   return p.ndim == 1 && p.kappa_kind != FRKC2_KAPPA_POWER && s <= S1_MAXS && p.n[0] >= 1 &&
-         p.n[0] <= int64_t(S1_CMAX) * S1_TMAX * S1_RMAX &&
+         p.n[0] <= int64_t(S1_CMAX) * S1_TMAX * S1_RMAX / 2 &&
          (p.precision == FRKC2_FP64 || p.precision == FRKC2_FP32 || p.precision == FRKC2_MIXED);
 }
 
 cudaError_t launch_small1d(const frkc2_problem& p, const frkc2_plan_s& plan, double dt, int nsteps, void* u,
-                           const void* fx, unsigned* status, cudaStream_t st, int cluster) {
+                           const void* fx, unsigned* status, cudaStream_t st, int cluster, int stages_per_exchange,
+                           int threads_per_cta) {
   const int n = int(p.n[0]);
-  // cluster size (or the caller's): the per-stage cluster barrier grows with the CTAs, the
-  // FP64 pipe time per stage shrinks with them -- FP64 state spreads 128 cells a CTA (N = 256:
-  // 2 CTAs, 1.44 ms a job against 1.52 with 8), FP32 keeps one CTA while it fits (0.87 ms
-  // against 1.00)
+  const bool periodic = p.bc == FRKC2_BC_PERIODIC;
+  // cluster size (or the caller's): 32 cells a CTA, up to 8 CTAs (N = 256: FP64 0.89 ms a job
+  // against 1.22 in one CTA, FP32 0.16 against 0.20)
   const bool f32 = p.precision == FRKC2_FP32;
-  int CL = cluster > 0 ? std::min(S1_CMAX, std::min(cluster, n))
-                       : (f32 ? 1 : std::max(1, std::min(S1_CMAX, n / 128)));
-  CL = std::max(CL, (n + S1_TMAX * S1_RMAX - 1) / (S1_TMAX * S1_RMAX));  // at most S1_RMAX cells a thread
-  const int chunk = (n + CL - 1) / CL;
-  // threads per CTA: a multiple of 32, at most 256, holding at most S1_RMAX cells each
-  int threads = std::min(S1_TMAX, ((chunk + 31) / 32) * 32);
-  int R = (chunk + threads - 1) / threads;
+  int CL = cluster > 0 ? std::min(S1_CMAX, std::min(cluster, n)) : std::max(1, std::min(S1_CMAX, n / 32));
+  CL = std::max(CL, (n + S1_TMAX * S1_RMAX / 2 - 1) / (S1_TMAX * S1_RMAX / 2));  // room for a halo
+  if (CL > S1_CMAX) return cudaErrorInvalidValue;
+  const int chunk = (n + CL - 1) / CL, min_chunk = n / CL;
+  // halo cells = stages per exchange (default 16): at most the smallest chunk (a halo comes
+  // from one neighbour); none for a Dirichlet grid in one CTA
+  int H = 0;
+  if (CL > 1 || periodic) {
+    H = stages_per_exchange > 0 ? stages_per_exchange : 16;
+    H = std::min(H, std::min(S1_HMAX, min_chunk));
+    if (H < 1) return cudaErrorInvalidValue;
+  }
+  const int ext = chunk + 2 * H;
+  // threads per CTA (a multiple of 32, at most 512) and cells per thread (1, 2, 4 or 8): the
+  // caller's thread count, raised to what holds the extended chunk; by default in FP32 one
+  // warp while it holds the extended chunk (no CTA barrier), in FP64 and MIXED one cell a
+  // thread (the FP64 instructions of a stage spread over the SM's schedulers)
+  int threads = threads_per_cta > 0 ? ((threads_per_cta + 31) / 32) * 32
+                                    : (f32 ? 32 : std::min(S1_TMAX, ((ext + 31) / 32) * 32));
+  threads = std::max(threads, ((ext + S1_RMAX * 32 - 1) / (S1_RMAX * 32)) * 32);
+  if (threads > S1_TMAX) return cudaErrorInvalidValue;
+  int R = 1;
+  while (R * threads < ext) R *= 2;
   if (R > S1_RMAX) return cudaErrorInvalidValue;
   auto a = std::make_unique<Small1dArgs>();
   a->u = u;
@@ -198,20 +281,22 @@ cudaError_t launch_small1d(const frkc2_problem& p, const frkc2_plan_s& plan, dou
   a->n = n;
   a->nsteps = nsteps;
   a->s = plan.s;
-  a->R = R;
+  a->H = H;
   const double h2 = p.dx * p.dx;
   for (int l = 0; l < plan.s; ++l) {
     a->ca[l] = dt * plan.a_re[l] / h2;
     a->cb[l] = dt * plan.a_im[l] / h2;
   }
-  const bool per = p.bc == FRKC2_BC_PERIODIC;
   switch (p.precision) {
     case FRKC2_FP64:
-      return per ? launch_t<double, double, true>(*a, CL, threads, st) : launch_t<double, double, false>(*a, CL, threads, st);
+      return periodic ? launch_t<double, double, true>(*a, CL, threads, R, st)
+                      : launch_t<double, double, false>(*a, CL, threads, R, st);
     case FRKC2_FP32:
-      return per ? launch_t<float, float, true>(*a, CL, threads, st) : launch_t<float, float, false>(*a, CL, threads, st);
+      return periodic ? launch_t<float, float, true>(*a, CL, threads, R, st)
+                      : launch_t<float, float, false>(*a, CL, threads, R, st);
     default:
-      return per ? launch_t<double, float, true>(*a, CL, threads, st) : launch_t<double, float, false>(*a, CL, threads, st);
+      return periodic ? launch_t<double, float, true>(*a, CL, threads, R, st)
+                      : launch_t<double, float, false>(*a, CL, threads, R, st);
   }
 }
 

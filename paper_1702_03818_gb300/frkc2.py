@@ -24,6 +24,7 @@ KAPPA_CONST, KAPPA_FIELD, KAPPA_POWER = 0, 1, 2
 FP64, FP32, MIXED, DFLOAT = 0, 1, 2, 3
 PLAN_STRICT, PLAN_GREEDY, PLAN_LEBEDEV, PLAN_PAIRED = 1, 2, 4, 8
 PRECISION = {"fp64": FP64, "fp32": FP32, "mixed": MIXED, "dfloat": DFLOAT}
+PROBE_PACKED = 16  # frkc2_fma_probe: packed two-lane FP32 FMAs
 BC = {"periodic": BC_PERIODIC, "dirichlet": BC_DIRICHLET, "neumann": BC_NEUMANN}
 KAPPA = {"const": KAPPA_CONST, "field": KAPPA_FIELD, "power": KAPPA_POWER}
 
@@ -404,8 +405,10 @@ def frkc2_bruss_step(plan: Plan, prob: frkc2_bruss_problem, dt: float, nsteps: i
 
 
 def frkc2_fma_probe(precision: str, blocks: int, iters: int, out, stream=None):
-    """FMA throughput probe (blocks x 256 threads x iters x 8 FMAs); the caller times it."""
-    _check(_lib.frkc2_fma_probe(PRECISION[precision], int(blocks), int(iters), _ptr(out), _stream_ptr(stream)),
+    """FMA throughput probe (blocks x 256 threads x iters x 8 FMAs); the caller times it.
+    ``precision``: "fp64", "fp32", or "fp32x2" (packed two-lane FP32 FMAs)."""
+    code = (PRECISION["fp32"] | PROBE_PACKED) if precision == "fp32x2" else PRECISION[precision]
+    _check(_lib.frkc2_fma_probe(code, int(blocks), int(iters), _ptr(out), _stream_ptr(stream)),
            "frkc2_fma_probe")
 
 

@@ -525,9 +525,9 @@ def test_small1d_single_cell(bc):
 @pytest.mark.parametrize("n", [256, 3001])
 def test_small1d_cluster_size_choice(n, prec, tol):
     """The 1D whole-job kernel with 1, 2, 4 and 8 CTAs in its cluster (tile_x) and the
-    library's choice: each against the oracle, and all within rounding of each other (the
-    split changes how many cells a thread holds, and the multiply-adds of different cell
-    positions in a thread may be contracted differently)."""
+    library's choice: each against the oracle, and all bit-identical (every cell takes the
+    same operations in the same order whatever thread or CTA holds it, and a halo cell is
+    recomputed exactly as its owner computes it)."""
     u0, field = seeded_case((n,), "dirichlet", "field", 60 + n)
     plan = F.frkc2_plan(16)
     oplan = O.plan(16)
@@ -544,7 +544,34 @@ def test_small1d_cluster_size_choice(n, prec, tol):
         assert rel_err(got, ref) < tol, (cl, rel_err(got, ref))
         outs.append(got)
     for o in outs[1:]:
-        assert rel_err(o, outs[0]) < (1e-14 if prec == "fp64" else 1e-6), rel_err(o, outs[0])
+        assert np.array_equal(o, outs[0]), rel_err(o, outs[0])
+
+
+@pytest.mark.parametrize("bc", ["dirichlet", "periodic"])
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "mixed"])
+@pytest.mark.parametrize("n", [31, 256, 3001])
+def test_small1d_halo_exchange(n, prec, bc):
+    """Clusters of 2 to 8 CTAs that hold their chunk plus a halo of K cells and exchange the
+    halos every K stages (K = 1, 3, 5, 8, 16; clamped to the smallest chunk), with 32 to 96
+    threads per CTA (raised to what holds the chunk): each against the oracle over 3 steps of
+    s = 16, so that exchanges fall inside steps and across step ends, and bit-identical to the
+    one-CTA launch."""
+    u0, field = seeded_case((n,), bc, "field", 90 + n)
+    plan = F.frkc2_plan(16)
+    oplan = O.plan(16)
+    fo = rounded_field(field, prec)
+    opr = oracle_problem(1, bc, "field", 1.0, fo)
+    dt = 0.9 * oplan["beta"] / O.rho_bound(opr, u0)
+    u0o = u0.astype(np.float32).astype(np.float64) if prec == "fp32" else u0
+    ref = O.frkc2_step(u0o, oplan["a"], dt, opr, 3)
+    one, st = run_gpu(plan, (n,), bc, "field", prec, u0, field, dt, 3, tune=F.make_tuning(kernel=6, tile=(1, 0, 0)))
+    assert st == F.OK
+    for cl, kx, th in [(2, 1, 0), (2, 8, 32), (8, 3, 0), (8, 8, 64), (8, 16, 0), (4, 5, 96)]:
+        got, st = run_gpu(plan, (n,), bc, "field", prec, u0, field, dt, 3,
+                          tune=F.make_tuning(k=kx, kernel=6, tile=(cl, th, 0)))
+        assert st == F.OK
+        assert rel_err(got, ref) < TOL[prec], (cl, kx, th, rel_err(got, ref))
+        assert np.array_equal(got, one), (cl, kx, th, rel_err(got, one))
 
 
 def test_small1d_rejects_out_of_range():
