@@ -148,11 +148,13 @@ def test_nonfinite_latched(kernel):
     assert st == F.ENONFINITE
 
 
-def test_barrier_wait_runs_out_and_context_survives():
-    """fault_inject: the first grid barrier waits for a count nothing reaches; every CTA gives
-    up after wait_limit polls, the launch returns and FRKC2_ETIMEOUT is latched.  The next
-    call on the same device then runs normally."""
-    shape = (64, 64)
+@pytest.mark.parametrize("shape", [(64, 64), (1, 257)], ids=["neighbour-flags", "grid-barrier"])
+def test_barrier_wait_runs_out_and_context_survives(shape):
+    """fault_inject: the first wait between stages (on the neighbour CTAs' stage flags, or on
+    the grid barrier where a CTA's stencil reaches too many CTAs: one row of 257 cells over
+    152 CTAs) waits for a count nothing reaches; every CTA gives up after wait_limit polls,
+    the launch returns and FRKC2_ETIMEOUT is latched.  The next call on the same device then
+    runs normally."""
     v0, w0 = state(shape, "periodic", 5)
     plan = F.frkc2_plan(8)
     dt = 1e-4

@@ -187,11 +187,13 @@ def test_paired_plan_matches_oracle(L):
 
 
 def test_bruss_workspace_size_and_validation_on_host():
+    # status words, the stage flags of up to 8192 CTAs (8 bytes each), then 8 state planes
+    head = 256 + 8192 * 8
     p = F.make_bruss_problem((200, 120), precision="fp64")
     plane = ((200 * 120 * 8 + 255) // 256) * 256
-    assert F.frkc2_bruss_workspace_size(p) == 256 + 8 * plane
+    assert F.frkc2_bruss_workspace_size(p) == head + 8 * plane
     p32 = F.make_bruss_problem(64, precision="fp32")
-    assert F.frkc2_bruss_workspace_size(p32) == 256 + 8 * (64 * 64 * 4)
+    assert F.frkc2_bruss_workspace_size(p32) == head + 8 * (64 * 64 * 4)
     for bad, st in [(dict(bc="dirichlet"), F.EINVAL), (dict(precision="mixed"), F.EUNSUPPORTED),
                     (dict(D=-1.0), F.EINVAL), (dict(dx=0.0), F.EINVAL)]:
         kw = dict(n=32)
