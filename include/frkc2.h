@@ -371,7 +371,8 @@ typedef struct {
 } frkc2_bruss_problem;
 
 /* Workspace bytes for frkc2_bruss_step and frkc2_bruss_rho_bound: 256 bytes of status and
- * barrier words, then two complex stage states (4 planes of nx*ny values each).            */
+ * barrier words, 64 KB of per-CTA stage flags, then two complex stage states (4 planes of
+ * nx*ny values each).                                                                      */
 frkc2_status frkc2_bruss_workspace_size(const frkc2_bruss_problem* prob, size_t* bytes);
 
 /* Gershgorin bound on the spectral radius of the Jacobian of f at the real state (v, w):
@@ -385,12 +386,13 @@ frkc2_status frkc2_bruss_rho_bound(const frkc2_bruss_problem* prob, const void* 
 /* Advances (v, w) by nsteps FRKC2 steps of size dt (in place; v and w distinct device arrays
  * of the problem's precision).  rho > 0: dt*rho <= beta is checked (FRKC2_EUNSTABLE).
  * tune->kernel: 0 or 1 = one persistent cooperative launch for every stage of every step,
- * the CTAs meeting at a device-wide barrier between stages (a plan of more than 1024 stages
- * takes one launch per 1024 stages of each step); 2 = one launch per stage.  The barrier
- * waits are bounded by tune->wait_limit polls (0 = 2^22); on expiry FRKC2_ETIMEOUT is latched
- * in the workspace and the launch returns early (the state is then unspecified).
- * tune->fault_inject = 1 (testing only, persistent form) makes the first barrier wait for a
- * count that nothing reaches.  A non-finite value in a step's output latches FRKC2_ENONFINITE.
+ * each CTA waiting between stages for the CTAs whose cells its stencil reads (per-CTA stage
+ * flags), or for FP64 stages of more than 2048 cells a CTA at a device-wide barrier (a plan of
+ * more than 1024 stages takes one launch per 1024 stages of each step); 2 = one launch per
+ * stage.  The waits are bounded by tune->wait_limit polls (0 = 2^22); on expiry FRKC2_ETIMEOUT
+ * is latched in the workspace and the launch returns early (the state is then unspecified).
+ * tune->fault_inject = 1 (testing only, persistent form) makes the first wait between stages
+ * wait for a count that nothing reaches.  A non-finite value in a step's output latches FRKC2_ENONFINITE.
  * Memory: 4 state reads and writes per cell-stage (32 bytes in FP32, 64 in FP64).          */
 frkc2_status frkc2_bruss_step(frkc2_plan_t plan, const frkc2_bruss_problem* prob, double dt,
                               int nsteps, double rho, void* v, void* w, void* ws,
