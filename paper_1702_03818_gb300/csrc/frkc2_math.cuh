@@ -3,6 +3,8 @@
 
 #include <cuda_runtime.h>
 
+#include <type_traits>
+
 namespace frkc2 {
 
 // Principal square root of x + i y (branch cut on the negative real axis; the sign of a
@@ -13,17 +15,29 @@ namespace frkc2 {
 // |y| / (2t) = |y| q / 2.  On GB300's narrow FP64 pipe this is about half the cost of hypot,
 // sqrt and a division.  (m is formed without rescaling: |w| below ~1e-154 or above ~1e154
 // in FP64 (1e-19 / 1e19 in FP32) loses accuracy, far outside the states of a diffusion run.)
+// Reciprocal square root: CUDA's rsqrt in FP64; in FP32 the hardware approximation with
+// subnormal inputs flushed to zero (rsqrt.approx.ftz: the same accuracy for normal inputs,
+// without the subnormal handling; csqrt_principal keeps its inputs normal).
+__device__ __forceinline__ double rsqrt_n(double a) { return rsqrt(a); }
+__device__ __forceinline__ float rsqrt_n(float a) {
+  float r;
+  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(a));
+  return r;
+}
+
 template <class T>
 __device__ __forceinline__ void csqrt_principal(T x, T y, T& rr, T& ri) {
   const T m = x * x + y * y;
-  if (m == T(0)) {
+  // w = 0, or in FP32 a modulus below ~1e-19 (m subnormal, which rsqrt.approx.ftz would take
+  // as zero): sqrt(w) taken as (0, y)
+  if (m == T(0) || (std::is_same<T, float>::value && m < T(1.17549435e-38f))) {
     rr = T(0);
     ri = y;
     return;
   }
-  const T r = m * rsqrt(m);
+  const T r = m * rsqrt_n(m);
   const T a = (r + fabs(x)) * T(0.5);
-  const T q = rsqrt(a);
+  const T q = rsqrt_n(a);
   const T t = a * q;
   const T h = T(0.5) * fabs(y) * q;
   if (x >= T(0)) {
