@@ -304,7 +304,36 @@ def batched2d(F):
             v = u0s[i].clone()
             F.frkc2_step(pl[i], probs[i], dts[i], nsteps, 0.0, v, wsi)
             errs.append(_rel(us[i].double().cpu().numpy(), v.double().cpu().numpy()))
+        # the same 512 problems one frkc2_step call after another on one stream (the library's
+        # default kernel for each, one workspace reused), timed the same way
+        wsmax = max(F.frkc2_workspace_size(pr) for pr in probs)
+        wss = torch.empty(wsmax, dtype=torch.uint8, device="cuda")
+        vs = [u0.clone() for u0 in u0s]
+
+        def sequential():
+            for i in range(len(specs)):
+                F.frkc2_step(pl[i], probs[i], dts[i], nsteps, 0.0, vs[i], wss)
+
+        sequential()  # warm-up: first-call launch configuration queries
+        torch.cuda.synchronize()
+        sms = []
+        for it in range(2):
+            for v, u0 in zip(vs, u0s):
+                v.copy_(u0)
+            flush.zero_()
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            sequential()
+            e1.record()
+            e1.synchronize()
+            sms.append(e0.elapsed_time(e1))
+        seq_ms = float(min(sms))
+        del wss, vs
         res[prec] = {"value": cs / (np.median(ms) / 1e3), "ms_per_launch": float(np.median(ms)),
+                     "sequential_single_problem": {"ms": seq_ms, "value": cs / (seq_ms / 1e3),
+                                                   "batched_speedup": seq_ms / float(np.median(ms))},
                      "cell_stages": cs, "max_rel_l2_vs_single_problem_path": max(errs),
                      "plans": ("precision policy (Lebedev-Finogenov order), largest predicted FP32 error "
                                f"{max(a[2] for a in auto.values()):.2e}" if prec == "fp32" else "the paper's order"),
