@@ -32,9 +32,10 @@ array, same shape as the state).  State arrays use numpy order, last axis = x.
 
 Parity status: every function here is pinned by ``tests/test_oracle_pins.py`` except the
 greedy ordering itself (``order_greedy``): the paper's coefficient table is not available,
-so the permutation it produces is checked only through invariants (it is a permutation, the
-product is unchanged, the realised Q meets the paper's bound) -- parity unpinned for the
-exact greedy order.  ``order_lebedev`` is pinned by the lower bound it attains.
+so the permutation it produces is checked through invariants (it is a permutation, the
+product is unchanged, the realised Q meets the paper's bound) and, for L = 6 and 8, by brute
+force (it attains the smallest Q of all L! orderings) -- parity unpinned for the exact greedy
+order of larger plans.  ``order_lebedev`` is pinned by the lower bound it attains.
 """
 from __future__ import annotations
 
