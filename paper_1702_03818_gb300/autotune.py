@@ -71,6 +71,11 @@ def candidates(prob) -> list:
         for k in (1, 2):
             c += [F.make_tuning(k=k, tile=t, kernel=1) for t in ((32, 4, 4), (32, 8, 2), (64, 4, 2), (16, 8, 4))]
     else:
+        if int(prob.n[0]) <= 16384 and prob.kappa_kind != F.KAPPA_POWER:
+            # the 1D whole-job kernel: CTAs in the cluster, stages per halo exchange, threads
+            c.append(F.make_tuning(kernel=6))
+            c += [F.make_tuning(k=k, tile=(cl, th, 0), kernel=6)
+                  for cl in (1, 2, 4, 8) for k in (8, 16) for th in (32, 64, 128) if cl > 1 or k == 16]
         c += [F.make_tuning(k=k, tile=(t, 1, 1), kernel=1) for k in (4, 8, 16) for t in (256, 1024)]
     return c
 

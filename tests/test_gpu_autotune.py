@@ -46,6 +46,39 @@ def test_autotune_step_fp32_and_cache(tmp_path, monkeypatch):
     assert rel_err(a.double().cpu().numpy(), b.double().cpu().numpy()) < 1e-4
 
 
+@pytest.mark.parametrize("bc", ["dirichlet", "periodic"])
+def test_autotune_step_1d_whole_job_kernel(tmp_path, monkeypatch, bc):
+    """A 1D problem: the whole-job kernel's cluster sizes, halo exchange periods and thread
+    counts are among the candidates and run; the choice matches the oracle, and every
+    whole-job shape gives the library default's bits."""
+    from paper_1702_03818_gb300 import autotune as AT
+
+    monkeypatch.setenv("FRKC2_TUNE_CACHE", str(tmp_path / "tune.json"))
+    n, s, nsteps = 1000, 16, 3
+    u0, field = seeded_case((n,), bc, "field", 73)
+    plan = F.frkc2_plan(s)
+    kt = torch.as_tensor(field, dtype=torch.float64, device="cuda")
+    pr = F.make_problem(1, (n,), 1.0, bc, "field", "fp64", kappa_field=kt)
+    opr = oracle_problem(1, bc, "field", 1.0, field)
+    dt = 0.9 * O.beta(s) / O.rho_bound(opr, u0)
+    u = torch.as_tensor(u0, dtype=torch.float64, device="cuda")
+    best, times = AT.autotune_step(plan, pr, u, dt, nsteps=nsteps, use_cache=False)
+    k6 = [json.loads(k) for k in times if json.loads(k)["kernel"] == 6]
+    assert len(k6) >= 10
+    ref = O.frkc2_step(u0, O.plan(s)["a"], dt, opr, nsteps)
+    outs = {}
+    for t in [best] + [F.make_tuning(k=d["k"], tile=tuple(d["tile"]), kernel=6) for d in k6]:
+        ws = torch.empty(F.frkc2_workspace_size(pr, t), dtype=torch.uint8, device="cuda")
+        v = u.clone()
+        F.frkc2_step(plan, pr, dt, nsteps, 0.0, v, ws, t)
+        got = v.cpu().numpy()
+        assert rel_err(got, ref) < 1e-11
+        if t.kernel == 6:
+            outs[(t.k, t.tile_x, t.tile_y)] = got
+    first = next(iter(outs.values()))
+    assert all(np.array_equal(o, first) for o in outs.values())
+
+
 def test_autotune_batch_runs():
     from paper_1702_03818_gb300 import autotune as AT
 
