@@ -89,6 +89,27 @@ def test_persistent_equals_per_stage_launches(prec):
     assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
 
 
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("n", [1024, 2048])
+def test_persistent_waits_at_size(n, prec):
+    """Large grids, where the persistent launch's CTAs own thousands of cells: at 1024^2 they
+    wait on their neighbours' stage flags, at 2048^2 in FP64 at the grid barrier (FP32 keeps the
+    flags).  Bit-identical to one launch per stage, and at 1024^2 FP64 equal to the oracle."""
+    shape = (n, n)
+    v0, w0 = state(shape, "periodic", 11)
+    v0, w0 = rounded(v0, prec), rounded(w0, prec)
+    plan = F.frkc2_plan(16)
+    pr = BR.problem(shape, dx=1.0 / n)
+    dt = 0.8 * F.frkc2_plan_info(plan)["beta"] / BR.rho_bound(v0, w0, pr)
+    a = run_gpu(plan, shape, "periodic", prec, v0, w0, dt, 1, kernel=1)
+    b = run_gpu(plan, shape, "periodic", prec, v0, w0, dt, 1, kernel=2)
+    assert a[2] == F.OK and b[2] == F.OK
+    assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+    if n == 1024 and prec == "fp64":
+        rv, rw = BR.frkc2_step(v0, w0, O.plan(16)["a"], dt, pr, 1)
+        assert rel_err(a[0], rv) < 1e-11 and rel_err(a[1], rw) < 1e-11
+
+
 def test_more_than_1024_stages_chunked_launches():
     """A 2048-stage plan takes two persistent launches per step; same result as per stage and
     as the oracle on the plan's own step sizes."""
