@@ -42,7 +42,9 @@ typedef enum {
   FRKC2_ECUDA = 5,        /* a CUDA runtime call failed (launch, copy, device query)        */
   FRKC2_ETIMEOUT = 6,     /* a bounded device wait expired (latched in the workspace)       */
   FRKC2_ENONFINITE = 7,   /* a step produced NaN or Inf (latched in the workspace)          */
-  FRKC2_EUNSUPPORTED = 8  /* valid request that this build does not implement               */
+  FRKC2_EUNSUPPORTED = 8, /* valid request that this build does not implement               */
+  FRKC2_EBOUNDS = 9       /* bounds-checking build only: a kernel's index fell outside its
+                             array and the access was skipped (latched in the workspace)   */
 } frkc2_status;
 
 /* NEUMANN (zero flux: the ghost cell repeats its boundary cell) is taken by the Brusselator
@@ -206,8 +208,8 @@ frkc2_status frkc2_workspace_size(const frkc2_problem* prob, const frkc2_tuning*
 /* Clears the status word of a workspace (asynchronous, on stream).                         */
 frkc2_status frkc2_workspace_reset(void* ws, void* stream);
 
-/* Synchronises stream, reads the status word and returns FRKC2_OK, FRKC2_ENONFINITE or
- * FRKC2_ETIMEOUT (the first condition latched).                                            */
+/* Synchronises stream, reads the status word and returns FRKC2_OK, FRKC2_EBOUNDS (only the
+ * bounds-checking build latches it), FRKC2_ENONFINITE or FRKC2_ETIMEOUT, in that priority. */
 frkc2_status frkc2_workspace_status(const void* ws, void* stream);
 
 /* ---- Forward step (Sec. 3, Eq. 13) ------------------------------------------------------

@@ -43,12 +43,16 @@ def _compile(nvcc, src, obj, extra):
     return r.stderr
 
 
-def build(verbose: bool = False, ptxas_info: bool = False) -> str:
-    """Compile and link the library; returns its path."""
+def build(verbose: bool = False, ptxas_info: bool = False, debug: bool = False) -> str:
+    """Compile and link the library; returns its path.  debug=True builds the bounds-checking
+    library ``libfrkc2_debug.so`` (-DFRKC2_DEBUG_BOUNDS: kernel indices checked against their
+    arrays), loaded by the binding when FRKC2_DEBUG_BOUNDS=1."""
     nvcc = _nvcc()
-    objdir = os.path.join(OUTDIR, "obj")
+    objdir = os.path.join(OUTDIR, "obj_debug" if debug else "obj")
     os.makedirs(objdir, exist_ok=True)
     extra = ["-Xptxas", "-v"] if ptxas_info else []
+    if debug:
+        extra.append("-DFRKC2_DEBUG_BOUNDS")
     srcs = sources()
     objs = [os.path.join(objdir, os.path.basename(s) + ".o") for s in srcs]
     with cf.ThreadPoolExecutor(max_workers=min(len(srcs), os.cpu_count() or 4)) as ex:
@@ -57,7 +61,7 @@ def build(verbose: bool = False, ptxas_info: bool = False) -> str:
         for s, log in zip(srcs, logs):
             if log.strip():
                 print(f"--- {os.path.basename(s)}\n{log}", file=sys.stderr)
-    out = os.path.join(OUTDIR, LIBNAME)
+    out = os.path.join(OUTDIR, "libfrkc2_debug.so" if debug else LIBNAME)
     tmp = out + ".tmp"
     r = subprocess.run([nvcc, *ARCH, "-shared", "-o", tmp, *objs], capture_output=True, text=True)
     if r.returncode != 0:
@@ -67,4 +71,4 @@ def build(verbose: bool = False, ptxas_info: bool = False) -> str:
 
 
 if __name__ == "__main__":
-    print(build(verbose="-v" in sys.argv, ptxas_info="--ptxas" in sys.argv))
+    print(build(verbose="-v" in sys.argv, ptxas_info="--ptxas" in sys.argv, debug="--debug" in sys.argv))

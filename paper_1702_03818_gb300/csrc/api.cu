@@ -152,6 +152,7 @@ frkc2_status frkc2_workspace_status(const void* ws, void* stream) {
   if (cudaMemcpyAsync(&st, ws, sizeof(unsigned), cudaMemcpyDeviceToHost, s) != cudaSuccess)
     return FRKC2_ECUDA;
   if (cudaStreamSynchronize(s) != cudaSuccess) return FRKC2_ECUDA;
+  if (st & ST_BOUNDS) return FRKC2_EBOUNDS;
   if (st & ST_NONFINITE) return FRKC2_ENONFINITE;
   if (st & ST_TIMEOUT) return FRKC2_ETIMEOUT;
   return FRKC2_OK;

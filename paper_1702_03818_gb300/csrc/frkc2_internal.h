@@ -26,6 +26,19 @@ namespace frkc2 {
 constexpr int KMAX = 16;                 // most stages in one pass
 constexpr unsigned ST_NONFINITE = 1u;    // status word bits
 constexpr unsigned ST_TIMEOUT = 2u;
+constexpr unsigned ST_BOUNDS = 4u;       // bounds-checking build: an index left its array
+
+// Index checks of the bounds-checking build (FRKC2_DEBUG_BOUNDS, libfrkc2_debug.so): false
+// and ST_BOUNDS latched in *status when ok is false, the caller then skipping the access.  In
+// the normal build it is the constant true and the check compiles away.
+#ifdef FRKC2_DEBUG_BOUNDS
+__device__ __forceinline__ bool in_bounds(bool ok, unsigned* status) {
+  if (!ok) atomicOr(status, ST_BOUNDS);
+  return ok;
+}
+#else
+__device__ __forceinline__ constexpr bool in_bounds(bool, unsigned*) { return true; }
+#endif
 
 // state layouts a pass reads or writes (the streaming pass honours them; the tile kernels
 // always use planar U, V)

@@ -60,6 +60,10 @@ __global__ void __launch_bounds__(GEN_THREADS) k_pass_generic(const PassArgs p) 
   const A* __restrict__ FZ = static_cast<const A*>(p.fz);
   const int tid = threadIdx.x;
 
+  // array sizes, for the bounds-checking build's index checks
+  const size_t ncell = size_t(p.nz) * p.ny * p.nx;
+  const size_t nfx = size_t(p.nz) * p.ny * (p.nx + 1), nfy = size_t(p.nz) * (p.ny + 1) * p.nx;
+  const size_t nfz = size_t(p.nz + 1) * p.ny * p.nx;
   // ---- load the region: state, and the low-side face of every region cell ----
   for (int z = 0; z < RZ; ++z) {
     for (int idx = tid; idx < plane; idx += GEN_THREADS) {
@@ -71,30 +75,43 @@ __global__ void __launch_bounds__(GEN_THREADS) k_pass_generic(const PassArgs p) 
       if (periodic) {
         const int wx = wrap_idx(gx, p.nx), wy = wrap_idx(gy, p.ny), wz = wrap_idx(gz, p.nz);
         const size_t g = (size_t(wz) * p.ny + wy) * p.nx + wx;
-        uu = Uin[g];
-        if (Vin) vv = Vin[g];
-        if (hat) hb[i] = Hin[g];
-        if (!POWER) {
-          a0 = FX[(size_t(wz) * p.ny + wy) * (p.nx + 1) + wx];
-          if (p.ndim >= 2) a1 = FY[(size_t(wz) * (p.ny + 1) + wy) * p.nx + wx];
-          if (p.ndim >= 3) a2 = FZ[(size_t(wz) * p.ny + wy) * p.nx + wx];
-        }
-      } else {
-        const bool inx = gx >= 0 && gx < p.nx, iny = gy >= 0 && gy < p.ny, inz = gz >= 0 && gz < p.nz;
-        if (inx && iny && inz) {
-          const size_t g = (size_t(gz) * p.ny + gy) * p.nx + gx;
+        if (in_bounds(g < ncell, p.status)) {
           uu = Uin[g];
           if (Vin) vv = Vin[g];
           if (hat) hb[i] = Hin[g];
-        } else if (hat) {
-          hb[i] = S(0);
         }
         if (!POWER) {
-          if (iny && inz && gx >= 0 && gx <= p.nx) a0 = FX[(size_t(gz) * p.ny + gy) * (p.nx + 1) + gx];
-          if (p.ndim >= 2 && inx && inz && gy >= 0 && gy <= p.ny)
-            a1 = FY[(size_t(gz) * (p.ny + 1) + gy) * p.nx + gx];
-          if (p.ndim >= 3 && inx && iny && gz >= 0 && gz <= p.nz)
-            a2 = FZ[(size_t(gz) * p.ny + gy) * p.nx + gx];
+          const size_t f0 = (size_t(wz) * p.ny + wy) * (p.nx + 1) + wx;
+          const size_t f1 = (size_t(wz) * (p.ny + 1) + wy) * p.nx + wx;
+          const size_t f2 = (size_t(wz) * p.ny + wy) * p.nx + wx;
+          if (in_bounds(f0 < nfx, p.status)) a0 = FX[f0];
+          if (p.ndim >= 2 && in_bounds(f1 < nfy, p.status)) a1 = FY[f1];
+          if (p.ndim >= 3 && in_bounds(f2 < nfz, p.status)) a2 = FZ[f2];
+        }
+      } else {
+        const bool inx = gx >= 0 && gx < p.nx, iny = gy >= 0 && gy < p.ny, inz = gz >= 0 && gz < p.nz;
+        if (hat) hb[i] = S(0);
+        if (inx && iny && inz) {
+          const size_t g = (size_t(gz) * p.ny + gy) * p.nx + gx;
+          if (in_bounds(g < ncell, p.status)) {
+            uu = Uin[g];
+            if (Vin) vv = Vin[g];
+            if (hat) hb[i] = Hin[g];
+          }
+        }
+        if (!POWER) {
+          if (iny && inz && gx >= 0 && gx <= p.nx) {
+            const size_t f0 = (size_t(gz) * p.ny + gy) * (p.nx + 1) + gx;
+            if (in_bounds(f0 < nfx, p.status)) a0 = FX[f0];
+          }
+          if (p.ndim >= 2 && inx && inz && gy >= 0 && gy <= p.ny) {
+            const size_t f1 = (size_t(gz) * (p.ny + 1) + gy) * p.nx + gx;
+            if (in_bounds(f1 < nfy, p.status)) a1 = FY[f1];
+          }
+          if (p.ndim >= 3 && inx && iny && gz >= 0 && gz <= p.nz) {
+            const size_t f2 = (size_t(gz) * p.ny + gy) * p.nx + gx;
+            if (in_bounds(f2 < nfz, p.status)) a2 = FZ[f2];
+          }
         }
       }
       ub[0][i] = uu;
@@ -199,6 +216,7 @@ __global__ void __launch_bounds__(GEN_THREADS) k_pass_generic(const PassArgs p) 
       const int y = idx / ex, x = idx - y * ex;
       const int i = (z + p.hz) * plane + (y + p.hy) * RX + (x + p.hx);
       const size_t g = (size_t(oz + z) * p.ny + (oy + y)) * p.nx + (ox + x);
+      if (!in_bounds(g < size_t(p.nz) * p.ny * p.nx, p.status)) continue;
       const S uu = uf[i];
       Uout[g] = uu;
       if (Vout) Vout[g] = vf[i];

@@ -88,7 +88,8 @@ __global__ void __launch_bounds__(S1_TMAX, 1) k_small1d(const Small1dArgs a) {
     const int e = lo + i, g = c0 - H + e;
     const bool in = e < E && (PERIODIC || (g >= 0 && g < n));
     if (in) live |= 1u << i;
-    U[i] = in ? U0[PERIODIC ? wrapn(g) : g] : S(0);
+    const int gi = PERIODIC ? wrapn(g) : g;
+    U[i] = in && in_bounds(gi >= 0 && gi < n, a.status) ? U0[gi] : S(0);
     V[i] = S(0);
   }
 #pragma unroll
@@ -96,10 +97,8 @@ __global__ void __launch_bounds__(S1_TMAX, 1) k_small1d(const Small1dArgs a) {
     const int e = lo + i, g = c0 - H + e;  // face g lies between cells g - 1 and g
     A v = A(0);
     if (e <= E) {
-      if (PERIODIC)
-        v = FX[wrapn(g)];
-      else if (g >= 0 && g <= n)
-        v = FX[g];
+      const int fi = PERIODIC ? wrapn(g) : g;
+      if ((PERIODIC || (g >= 0 && g <= n)) && in_bounds(fi >= 0 && fi <= n, a.status)) v = FX[fi];
     }
     kf[i] = v;
   }
@@ -121,8 +120,9 @@ __global__ void __launch_bounds__(S1_TMAX, 1) k_small1d(const Small1dArgs a) {
           S2 v;
           v.x = U[i];
           v.y = V[i];
-          if (e >= H && e < 2 * H) own_lo[xpar][e - H] = v;
-          if (e >= E - 2 * H && e < E - H) own_hi[xpar][e - (E - 2 * H)] = v;
+          if (e >= H && e < 2 * H && in_bounds(e - H < S1_HMAX, a.status)) own_lo[xpar][e - H] = v;
+          if (e >= E - 2 * H && e < E - H && in_bounds(e - (E - 2 * H) < S1_HMAX, a.status))
+            own_hi[xpar][e - (E - 2 * H)] = v;
         }
         cluster.sync();
         const S2* rlo = cluster.map_shared_rank(&own_hi[xpar][0], cp);  // global cells c0 - H .. c0 - 1
@@ -196,7 +196,7 @@ __global__ void __launch_bounds__(S1_TMAX, 1) k_small1d(const Small1dArgs a) {
 #pragma unroll
   for (int i = 0; i < R; ++i) {
     const int e = lo + i;
-    if (e >= H && e < E - H) {
+    if (e >= H && e < E - H && in_bounds(c0 - H + e >= 0 && c0 - H + e < n, a.status)) {
       static_cast<S*>(a.u)[c0 - H + e] = U[i];
       bad |= bad1(U[i]);
     }

@@ -129,6 +129,7 @@ __global__ void __launch_bounds__(ST_THREADS, ST_MIN_BLOCKS)
         return w;
       }
       const size_t g = size_t(yw) * nx + xx;
+      if (!in_bounds(g < size_t(nx) * ny, p.status)) return w;
       if (in_mode == PASS_IO_COMPLEX) {
         w = __ldg(Wi + g);
       } else {
@@ -149,7 +150,9 @@ __global__ void __launch_bounds__(ST_THREADS, ST_MIN_BLOCKS)
         return f;  // face pairs exist for rows -1 .. ny-1
       }
       if (!has_faces) return f;
-      return __ldg(FEN + size_t(yy + 1) * (nx + 1) + fcol);
+      const size_t fi = size_t(yy + 1) * (nx + 1) + fcol;
+      if (!in_bounds(fi < size_t(ny + 1) * (nx + 1), p.status)) return f;
+      return __ldg(FEN + fi);
     };
 
     // prime the stream: row y0, and the difference across the south face of row y0 (the
@@ -203,7 +206,7 @@ __global__ void __launch_bounds__(ST_THREADS, ST_MIN_BLOCKS)
       const A fV = f.y * dNV - ks * dSV - kw * dWV + f.x * dEV;
       const S un = Wc.x + ca * S(fU) - cb * S(fV);
       const S vn = Wc.y + ca * S(fV) + cb * S(fU);
-      if (out_ok) {
+      if (out_ok && in_bounds(size_t(y) * nx + x < size_t(nx) * ny, p.status)) {
         const size_t g = size_t(y) * nx + x;
         if (out_mode == PASS_IO_COMPLEX) {
           S2 w;

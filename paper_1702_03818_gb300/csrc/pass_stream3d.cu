@@ -95,10 +95,14 @@ __global__ void __launch_bounds__(S3_THREADS) k_stream3d(const PassArgs p, int z
       return w;
     }
     const size_t g = size_t(zz) * plane + col;
+    if (!in_bounds(g < size_t(nz) * plane, p.status)) return w;
     w.x = __ldg(Ur + g);
     if (in_mode == PASS_IO_PLANAR) w.y = __ldg(Vr + g);
     return w;
   };
+  // face array sizes, for the bounds-checking build's index checks
+  const size_t nfx = size_t(nz) * ny * (nx + 1), nfy = size_t(nz) * (ny + 1) * nx, nfz = size_t(nz + 1) * ny * nx;
+  auto ldf = [&](const A* F, size_t i, size_t n) -> A { return in_bounds(i < n, p.status) ? __ldg(F + i) : A(0); };
   auto kap = [&](S2 w) -> A2 {
     A2 k;
     if constexpr (P25)
@@ -109,19 +113,19 @@ __global__ void __launch_bounds__(S3_THREADS) k_stream3d(const PassArgs p, int z
   };
   // face conductivities (FIELD / CONST): east (x face x+1), north (y face y+1), up (z face z+1)
   auto face_e = [&](int z) -> A {
-    if (PERIODIC) return __ldg(FX + (size_t(wrap3(z, nz)) * ny + yr) * (nx + 1) + xr + 1);
+    if (PERIODIC) return ldf(FX, (size_t(wrap3(z, nz)) * ny + yr) * (nx + 1) + xr + 1, nfx);
     if (z < 0 || z >= nz || gy < 0 || gy >= ny || gx < -1 || gx >= nx) return A(0);
-    return __ldg(FX + (size_t(z) * ny + gy) * (nx + 1) + gx + 1);
+    return ldf(FX, (size_t(z) * ny + gy) * (nx + 1) + gx + 1, nfx);
   };
   auto face_n = [&](int z) -> A {
-    if (PERIODIC) return __ldg(FY + (size_t(wrap3(z, nz)) * (ny + 1) + yr + 1) * nx + xr);
+    if (PERIODIC) return ldf(FY, (size_t(wrap3(z, nz)) * (ny + 1) + yr + 1) * nx + xr, nfy);
     if (z < 0 || z >= nz || gx < 0 || gx >= nx || gy < -1 || gy >= ny) return A(0);
-    return __ldg(FY + (size_t(z) * (ny + 1) + gy + 1) * nx + gx);
+    return ldf(FY, (size_t(z) * (ny + 1) + gy + 1) * nx + gx, nfy);
   };
   auto face_u = [&](int z) -> A {  // z face z+1, above cell z
-    if (PERIODIC) return __ldg(FZ + (size_t(wrap3(z, nz) + 1) * ny + yr) * nx + xr);
+    if (PERIODIC) return ldf(FZ, (size_t(wrap3(z, nz) + 1) * ny + yr) * nx + xr, nfz);
     if (!colin || z < -1 || z >= nz) return A(0);
-    return __ldg(FZ + (size_t(z + 1) * ny + gy) * nx + gx);
+    return ldf(FZ, (size_t(z + 1) * ny + gy) * nx + gx, nfz);
   };
   // complex flux kappa_f * d with kappa_f real (FIELD) or complex (kappa(u))
   auto flux = [&](A2 kf, A dr, A di) -> A2 {
@@ -204,7 +208,7 @@ __global__ void __launch_bounds__(S3_THREADS) k_stream3d(const PassArgs p, int z
     Fw.y = __shfl_up_sync(0xffffffffu, Fe.y, 1);
     const A fR = ((Fe.x - Fw.x) + (Fn.x - Fs.x)) + (Fu.x - Fd.x);
     const A fI = ((Fe.y - Fw.y) + (Fn.y - Fs.y)) + (Fu.y - Fd.y);
-    if (out_ok) {
+    if (out_ok && in_bounds(size_t(z) * plane + col < size_t(nz) * plane, p.status)) {
       const size_t g = size_t(z) * plane + col;
       const S un = Wc.x + ca * S(fR) - cb * S(fI);
       Uo[g] = un;

@@ -86,12 +86,18 @@ __global__ void __launch_bounds__(RT_THREADS, FRKC2_TBR_MIN_BLOCKS) k_tb2d_reg(c
     for (int c = 0; c < 5; ++c) {
       if (r < 4) {
         float v = 0.f;
-        if (PERIODIC || (yin[r] && gxc[c] >= 0 && gxc[c] <= nx)) v = FX[size_t(gyr[r]) * (nx + 1) + gxc[c]];
+        if (PERIODIC || (yin[r] && gxc[c] >= 0 && gxc[c] <= nx)) {
+          const size_t fi = size_t(gyr[r]) * (nx + 1) + gxc[c];
+          if (in_bounds(fi < size_t(ny) * (nx + 1), p.status)) v = FX[fi];
+        }
         fx[r][c] = v;
       }
       if (c < 4) {
         float v = 0.f;
-        if (PERIODIC || (xin[c] && gyr[r] >= 0 && gyr[r] <= ny)) v = FY[size_t(gyr[r]) * nx + gxc[c]];
+        if (PERIODIC || (xin[c] && gyr[r] >= 0 && gyr[r] <= ny)) {
+          const size_t fi = size_t(gyr[r]) * nx + gxc[c];
+          if (in_bounds(fi < size_t(ny + 1) * nx, p.status)) v = FY[fi];
+        }
         fy[r][c] = v;
         if (r < 4 && xin[c] && yin[r]) inside |= 1u << (4 * r + c);
       }
@@ -113,8 +119,10 @@ __global__ void __launch_bounds__(RT_THREADS, FRKC2_TBR_MIN_BLOCKS) k_tb2d_reg(c
       float uu = 0.f, vv = 0.f;
       if (PERIODIC || (inside & (1u << (4 * r + c)))) {
         const size_t g = size_t(gyr[r]) * nx + gxc[c];
-        uu = Uin[g];
-        if (Vin) vv = Vin[g];
+        if (in_bounds(g < size_t(nx) * ny, p.status)) {
+          uu = Uin[g];
+          if (Vin) vv = Vin[g];
+        }
       }
       if (c & 1) {
         U2[r][c >> 1].y = uu;
@@ -214,6 +222,7 @@ __global__ void __launch_bounds__(RT_THREADS, FRKC2_TBR_MIN_BLOCKS) k_tb2d_reg(c
       const int gx = x0 + rx;
       if (rx < k || rx >= RT_R - k || gx >= nx) continue;
       const size_t g = size_t(gy) * nx + gx;
+      if (!in_bounds(g < size_t(nx) * ny, p.status)) continue;
       const float uu = (c & 1) ? U2[r][c >> 1].y : U2[r][c >> 1].x;
       Uo[g] = uu;
       if (Vo) Vo[g] = (c & 1) ? V2[r][c >> 1].y : V2[r][c >> 1].x;

@@ -210,8 +210,16 @@ __global__ void __launch_bounds__(WF_NW * 32, 2) k_wf2d(const WfArgs p) {
     const float2* fbase = p.faces + size_t((PERIODIC ? sy : row) + 1) * p.pitch_f + 2;
 #pragma unroll
     for (int i = 0; i < 2; ++i) {
-      if (srow && ss.len[i] > 0) bulk_load(dst + ss.off[i] * es, sbase + size_t(ss.g[i]) * es, ss.len[i] * es, bar);
-      if (frow && fs.len[i] > 0) bulk_load(dst + SB + fs.off[i] * 8, fbase + fs.g[i], fs.len[i] * 8, bar);
+      // (a bounds-checking build skips a copy that leaves its array; the row's wait then runs
+      // out and latches its timeout as well)
+      if (srow && ss.len[i] > 0 &&
+          in_bounds(sy >= 0 && sy < ny && ss.g[i] >= 0 && ss.g[i] + ss.len[i] <= nx, p.status))
+        bulk_load(dst + ss.off[i] * es, sbase + size_t(ss.g[i]) * es, ss.len[i] * es, bar);
+      if (frow && fs.len[i] > 0 &&
+          in_bounds((PERIODIC ? sy : row) + 1 >= 0 && (PERIODIC ? sy : row) + 1 <= ny && fs.g[i] + 2 >= 0 &&
+                        fs.g[i] + 2 + fs.len[i] <= p.pitch_f,
+                    p.status))
+        bulk_load(dst + SB + fs.off[i] * 8, fbase + fs.g[i], fs.len[i] * 8, bar);
     }
   };
   if (tid == 0)
@@ -326,7 +334,7 @@ __global__ void __launch_bounds__(WF_NW * 32, 2) k_wf2d(const WfArgs p) {
     }
     // the pass output: level K's row t - K, rows [y0, y1) of the chunk
     const int r = t - K;
-    if (r >= y0 && ocol) {
+    if (r >= y0 && ocol && in_bounds(size_t(r) * nx + (xs + cx) + 2 <= size_t(nx) * ny, p.status)) {
       const Cells o = cur[K];
       const size_t g = size_t(r) * nx + (xs + cx);
       if (out_real)

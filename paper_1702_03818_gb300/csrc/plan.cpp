@@ -384,6 +384,7 @@ const char* frkc2_status_string(frkc2_status st) {
     case FRKC2_ETIMEOUT: return "bounded device wait expired";
     case FRKC2_ENONFINITE: return "non-finite value in a step's output";
     case FRKC2_EUNSUPPORTED: return "not supported by this build";
+    case FRKC2_EBOUNDS: return "bounds-checking build: a device index fell outside its array";
   }
   return "unknown status";
 }

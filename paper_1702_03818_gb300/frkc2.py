@@ -13,12 +13,17 @@ import os
 
 import numpy as np
 
-_LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_lib", "libfrkc2.so")
+# FRKC2_DEBUG_BOUNDS=1 loads the bounds-checking build (every kernel index checked against
+# its array, a violation latched as EBOUNDS and the access skipped)
+_DEBUG = os.environ.get("FRKC2_DEBUG_BOUNDS", "0") not in ("", "0")
+_LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_lib",
+                         "libfrkc2_debug.so" if _DEBUG else "libfrkc2.so")
 if not os.path.exists(_LIB_PATH):
-    raise ImportError(f"FRKC2 CUDA library not built ({_LIB_PATH}); run paper_1702_03818_gb300.build")
+    raise ImportError(f"FRKC2 CUDA library not built ({_LIB_PATH}); run paper_1702_03818_gb300.build"
+                      + (" with debug=True" if _DEBUG else ""))
 _lib = C.CDLL(_LIB_PATH)
 
-OK, EINVAL, EUNSTABLE, EPLAN, ENOMEM, ECUDA, ETIMEOUT, ENONFINITE, EUNSUPPORTED = range(9)
+OK, EINVAL, EUNSTABLE, EPLAN, ENOMEM, ECUDA, ETIMEOUT, ENONFINITE, EUNSUPPORTED, EBOUNDS = range(10)
 BC_PERIODIC, BC_DIRICHLET, BC_NEUMANN = 0, 1, 2
 KAPPA_CONST, KAPPA_FIELD, KAPPA_POWER = 0, 1, 2
 FP64, FP32, MIXED, DFLOAT = 0, 1, 2, 3

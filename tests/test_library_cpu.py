@@ -30,6 +30,21 @@ def test_library_exports_every_declared_symbol():
     assert set(syms) <= set(F.EXPORTED)
 
 
+def test_bounds_checking_build_exports_every_declared_symbol():
+    """The bounds-checking library (-DFRKC2_DEBUG_BOUNDS) builds and exports the same ABI."""
+    import ctypes
+    import shutil
+
+    from paper_1702_03818_gb300 import build as B
+
+    if not (shutil.which("nvcc") or os.path.exists("/usr/local/cuda/bin/nvcc")):
+        pytest.skip("no nvcc")
+    lib = ctypes.CDLL(B.build(debug=True))
+    missing = [s for s in declared_symbols() if not hasattr(lib, s)]
+    assert not missing, missing
+    assert lib.frkc2_status_string(9) is not None
+
+
 @pytest.mark.parametrize("L", [2, 4, 8, 16, 32, 64, 100, 128])
 def test_plan_matches_oracle(L):
     lib = F.frkc2_plan(L).info()
@@ -141,7 +156,7 @@ def test_step_rejects_unstable_dt_and_small_workspace_before_gpu_work():
 
 
 def test_status_strings():
-    for st in range(9):
+    for st in range(10):
         assert F.frkc2_status_string(st)
     assert "unknown" in F.frkc2_status_string(99)
 
