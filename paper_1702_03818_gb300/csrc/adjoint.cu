@@ -404,6 +404,60 @@ bool run_segment(const AdjCtx& C, int j) {
   return true;
 }
 
+// Segment j without a tape (FP32 register-tiled path): the forward passes of frkc2_step from
+// checkpoint j to checkpoint j + 1, planar (U, V) ping-pong buffers in the tape area (the
+// segments before the last leave no tape the backward reads: it recomputes each from its
+// checkpoint).
+bool run_segment_plain_tb(const AdjCtx& C, int j) {
+  const frkc2_problem& p = *C.p;
+  PassArgs a{};
+  a.ndim = 2;
+  a.bc = p.bc;
+  a.nx = int(p.n[0]);
+  a.ny = int(p.n[1]);
+  a.nz = 1;
+  a.fx = C.base + C.L.fx;
+  a.fy = C.base + C.L.fy;
+  a.kc = p.kappa_c;
+  a.kp = p.kappa_p;
+  a.status = reinterpret_cast<unsigned*>(C.base + C.L.status);
+  char* ua = C.tape(0, 0);
+  char* va = ua + C.slot;
+  char* ub = C.tape(0, 1);
+  char* vb = ub + C.slot;
+  const void* curU = C.ckpt(j);
+  const void* curV = nullptr;
+  const int n0 = j * C.c, m = std::min(C.c, C.nsteps - n0);
+  const int k = C.tbk, npass = (C.s + k - 1) / k;
+  for (int q = 0; q < m; ++q)
+    for (int ps = 0; ps < npass; ++ps) {
+      const int l0 = ps * k, kq = std::min(k, C.s - l0);
+      const bool last = ps == npass - 1;
+      void* outU = (last && q == m - 1) ? static_cast<void*>(C.ckpt(j + 1)) : (curU == ua ? ub : ua);
+      void* outV = last ? nullptr : (curV == va ? vb : va);
+      a.k = kq;
+      a.hx = kq;
+      a.hy = kq;
+      a.U_in = curU;
+      a.V_in = curV;
+      a.U_out = outU;
+      a.V_out = outV;
+      a.check_finite = last ? 1 : 0;
+      for (int jj = 0; jj < kq; ++jj) {
+        a.ca[jj] = C.dt * C.plan->a_re[l0 + jj] / C.h2;
+        a.cb[jj] = C.dt * C.plan->a_im[l0 + jj] / C.h2;
+        a.caf[jj] = float(a.ca[jj]);
+        a.cbf[jj] = float(a.cb[jj]);
+      }
+      a.in_mode = curV ? PASS_IO_PLANAR : PASS_IO_REAL;
+      a.out_mode = outV ? PASS_IO_PLANAR : PASS_IO_REAL;
+      if (launch_pass_tb2d(p, a, C.st, q > 0 || ps > 0) != cudaSuccess) return false;
+      curU = outU;
+      curV = outV;
+    }
+  return true;
+}
+
 frkc2_status adj_forward(const AdjCtx& C, const void* u0) {
   const frkc2_problem& p = *C.p;
   if (p.kappa_kind != FRKC2_KAPPA_POWER) {
@@ -412,8 +466,10 @@ frkc2_status adj_forward(const AdjCtx& C, const void* u0) {
       return FRKC2_ECUDA;
   }
   if (cudaMemcpyAsync(C.ckpt(0), u0, C.N * C.SB, cudaMemcpyDeviceToDevice, C.st) != cudaSuccess) return FRKC2_ECUDA;
+  // the last segment's tape stays for the backward; in FP32 the segments before it run the
+  // forward passes alone (the tape passes write 8 bytes per cell-stage more)
   for (int j = 0; j < C.L.nseg; ++j)
-    if (!run_segment(C, j)) return FRKC2_ECUDA;
+    if (!(C.tb && j + 1 < C.L.nseg && C.s >= 2 ? run_segment_plain_tb(C, j) : run_segment(C, j))) return FRKC2_ECUDA;
   return FRKC2_OK;
 }
 
