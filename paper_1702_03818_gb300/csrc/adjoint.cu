@@ -619,6 +619,7 @@ frkc2_status frkc2_adjoint_workspace_size(const frkc2_plan_t plan, const frkc2_p
 frkc2_status frkc2_adjoint_forward(frkc2_plan_t plan, const frkc2_problem* prob, double dt, int nsteps,
                                    int ckpt_every, const void* u0, void* uT, void* ws, size_t ws_bytes,
                                    void* stream) {
+  const frkc2::NvtxRange call_range("frkc2_adjoint_forward");
   if (!u0) return FRKC2_EINVAL;
   AdjCtx C;
   frkc2_status v = adj_setup(C, plan, prob, dt, nsteps, ckpt_every, ws, ws_bytes, stream);
@@ -633,6 +634,7 @@ frkc2_status frkc2_adjoint_forward(frkc2_plan_t plan, const frkc2_problem* prob,
 frkc2_status frkc2_adjoint_backward(frkc2_plan_t plan, const frkc2_problem* prob, double dt, int nsteps,
                                     int ckpt_every, const void* g, void* dJdu0, void* dJdkappa, void* ws,
                                     size_t ws_bytes, void* stream) {
+  const frkc2::NvtxRange call_range("frkc2_adjoint_backward");
   if (!g || !dJdu0) return FRKC2_EINVAL;
   if (dJdkappa && (!prob || prob->kappa_kind != FRKC2_KAPPA_FIELD)) return FRKC2_EINVAL;
   AdjCtx C;
@@ -644,6 +646,7 @@ frkc2_status frkc2_adjoint_backward(frkc2_plan_t plan, const frkc2_problem* prob
 frkc2_status frkc2_adjoint(frkc2_plan_t plan, const frkc2_problem* prob, double dt, int nsteps, int ckpt_every,
                            const void* u0, const void* g, void* dJdu0, void* dJdkappa, void* ws, size_t ws_bytes,
                            void* stream) {
+  const frkc2::NvtxRange call_range("frkc2_adjoint");
   if (!u0 || !g || !dJdu0) return FRKC2_EINVAL;
   if (dJdkappa && (!prob || prob->kappa_kind != FRKC2_KAPPA_FIELD)) return FRKC2_EINVAL;
   AdjCtx C;

@@ -4,7 +4,6 @@
 #include <cstring>
 
 #include <cuda_runtime.h>
-#include <nvtx3/nvToolsExt.h>
 
 #include "frkc2.h"
 #include "frkc2_internal.h"
@@ -13,13 +12,6 @@ namespace frkc2 {
 
 static thread_local long long g_launches = 0;
 
-// NVTX range for the enclosing scope (host timeline: a call, a step; no cost without a tool)
-struct NvtxRange {
-  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
-  ~NvtxRange() { nvtxRangePop(); }
-  NvtxRange(const NvtxRange&) = delete;
-  NvtxRange& operator=(const NvtxRange&) = delete;
-};
 void count_launch(int n) { g_launches += n; }
 
 size_t state_bytes(int precision) { return precision == FRKC2_FP32 ? 4 : 8; }
@@ -313,6 +305,7 @@ frkc2_status frkc2_step(frkc2_plan_t plan, const frkc2_problem* prob, double dt,
     for (int n = 0; n < nsteps; ++n) {
       const NvtxRange step_range("frkc2 step");
       for (int q = 0; q < npair; ++q) {
+        const NvtxRange pass_range("frkc2 pass");
         const bool last = n == nsteps - 1 && q == npair - 1;
         void* out = (last && curU != u) ? u : (curU == ua ? ub : ua);
         const double al = plan->a_re[2 * q], be = plan->a_im[2 * q];
@@ -339,6 +332,7 @@ frkc2_status frkc2_step(frkc2_plan_t plan, const frkc2_problem* prob, double dt,
     for (int n = 0; n < nsteps; ++n) {
       const NvtxRange step_range("frkc2 step");
       for (int q = 0; q < npass; ++q) {
+        const NvtxRange pass_range("frkc2 pass");
         const int l0 = q * k, kq = std::min(k, s - l0);
         const bool first = q == 0, last = q == npass - 1;
         void* outW = (curU == ua) ? ub : ua;
@@ -376,6 +370,7 @@ frkc2_status frkc2_step(frkc2_plan_t plan, const frkc2_problem* prob, double dt,
     for (int n = 0; n < nsteps; ++n) {
       const NvtxRange step_range("frkc2 step");
       for (int q = 0; q < npass; ++q) {
+        const NvtxRange pass_range("frkc2 pass");
         const int l0 = q * k, kq = std::min(k, s - l0);
         const bool first = q == 0, last = q == npass - 1;
         void* outW = (curU == ua) ? ub : ua;
@@ -409,6 +404,7 @@ frkc2_status frkc2_step(frkc2_plan_t plan, const frkc2_problem* prob, double dt,
     for (int n = 0; n < nsteps; ++n) {
       const NvtxRange step_range("frkc2 step");
       for (int l = 0; l < s; ++l) {
+        const NvtxRange pass_range("frkc2 pass");
         const bool first = l == 0, last = l == s - 1;
         a.U_in = first ? u : curU;
         a.V_in = nullptr;
@@ -433,6 +429,7 @@ frkc2_status frkc2_step(frkc2_plan_t plan, const frkc2_problem* prob, double dt,
   for (int n = 0; n < nsteps; ++n) {
       const NvtxRange step_range("frkc2 step");
     for (int q = 0; q < npass; ++q) {
+      const NvtxRange pass_range("frkc2 pass");
       const int l0 = q * k;
       const int kq = std::min(k, s - l0);
       const bool last = q == npass - 1;
@@ -492,6 +489,7 @@ frkc2_status frkc2_adaptive_workspace_size(const frkc2_problem* prob, const frkc
 frkc2_status frkc2_step_adaptive(frkc2_plan_t plan, const frkc2_problem* prob, double t_end, double tol,
                                  double dt0, double rho, void* u, void* ws, size_t ws_bytes,
                                  const frkc2_tuning* tune, frkc2_adaptive_stats* stats, void* stream) {
+  const frkc2::NvtxRange call_range("frkc2_step_adaptive");
   if (!plan || !u || !ws || !(t_end > 0.0) || !(tol > 0.0) || !(dt0 > 0.0)) return FRKC2_EINVAL;
   const frkc2_status v = validate_problem(prob);
   if (v != FRKC2_OK) return v;

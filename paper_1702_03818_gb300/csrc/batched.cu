@@ -741,6 +741,7 @@ frkc2_status frkc2_batch_prepare(int nprob, const frkc2_plan_t* plans, const frk
 }
 
 frkc2_status frkc2_batch_launch(void* ws, void* stream) {
+  const frkc2::NvtxRange call_range("frkc2_batch_launch");
   if (!ws) return FRKC2_EINVAL;
   LaunchCfg cfg;
   {

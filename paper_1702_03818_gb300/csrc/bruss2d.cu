@@ -518,6 +518,7 @@ frkc2_status frkc2_bruss_rho_bound(const frkc2_bruss_problem* prob, const void* 
 
 frkc2_status frkc2_bruss_step(frkc2_plan_t plan, const frkc2_bruss_problem* prob, double dt, int nsteps, double rho,
                               void* v, void* w, void* ws, size_t ws_bytes, const frkc2_tuning* tune, void* stream) {
+  const frkc2::NvtxRange call_range("frkc2_bruss_step");
   if (!plan || !v || !w || !ws || nsteps < 0) return FRKC2_EINVAL;
   const frkc2_status vs = validate(prob);
   if (vs != FRKC2_OK) return vs;

@@ -6,6 +6,7 @@
 #include <vector>
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include "frkc2.h"
 
@@ -22,6 +23,15 @@ struct frkc2_plan_s {
 };
 
 namespace frkc2 {
+
+// NVTX range for the enclosing scope (host timeline: a call, a step, a pass; no cost without a
+// tool attached)
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 constexpr int KMAX = 16;                 // most stages in one pass
 constexpr unsigned ST_NONFINITE = 1u;    // status word bits

@@ -33,6 +33,7 @@ using namespace frkc2;
 
 extern "C" frkc2_status frkc2_stages(frkc2_plan_t plan, const frkc2_problem* prob, double dt, int l0, int l1,
                                      void* w, void* ws, size_t ws_bytes, void* stream) {
+  const frkc2::NvtxRange call_range("frkc2_stages");
   if (!plan || !w || !ws) return FRKC2_EINVAL;
   const frkc2_status v = validate_problem(prob);
   if (v != FRKC2_OK) return v;
