@@ -57,7 +57,7 @@ def _timed(fn, warmup=2, reps=3, flush=None):
 
 def _dt(torch):
     return {"fp64": (torch.float64, torch.float64), "fp32": (torch.float32, torch.float32),
-            "mixed": (torch.float64, torch.float32)}
+            "mixed": (torch.float64, torch.float32), "dfloat": (torch.float64, torch.float32)}
 
 
 def _rel(a, b):
@@ -245,7 +245,8 @@ def batched2d(F):
     auto = {sv: F.frkc2_plan_auto(sv, probe, nsteps, 1e-4) for sv in plans}
     assert all(a[1] == "fp32" for a in auto.values()), {sv: a[1] for sv, a in auto.items()}
     res = {}
-    for prec in ("fp32", "fp64"):
+    finals = {}
+    for prec in ("fp32", "fp64", "dfloat"):
         sd, kd = _dt(torch)[prec]
         probs, us, u0s, dts, pl = [], [], [], [], []
         for p, (u, k) in zip(specs, fields):
@@ -296,6 +297,7 @@ def batched2d(F):
             if it >= 1:
                 ms.append(e0.elapsed_time(e1))
         assert F.frkc2_workspace_status(ws) == F.OK
+        finals[prec] = [u.double() for u in us]
         cs = sum(p["n"] ** 2 * p["s"] * nsteps for p in specs)
         # consistency: three problems against the single-problem path
         errs = []
@@ -340,6 +342,11 @@ def batched2d(F):
                      "workspace_gb": ws.numel() / 1e9,
                      "tuning": {"k": tune.k, "tile": [tune.tile_x, tune.tile_y, tune.tile_z]}, "autotune_ms": tt}
         del ws, g
+    # every item of the FP32 and DFLOAT launches against the FP64 launch's result
+    for prec in ("fp32", "dfloat"):
+        res[prec]["max_rel_l2_vs_fp64_batch"] = max(
+            float(torch.linalg.norm(a - b) / torch.linalg.norm(b)) for a, b in zip(finals[prec], finals["fp64"]))
+    del finals
     return {"workload": "batched2d: 512 var-kappa 2D problems, n~U{64..1024}, s~{16..256}, 10 steps, one persistent launch (CUDA graph)",
             "metric": "cell-stage/s", "value": res["fp32"]["value"], "unit": UNIT, "precisions": res}
 

@@ -337,11 +337,12 @@ frkc2_status frkc2_adjoint_backward(frkc2_plan_t plan, const frkc2_problem* prob
  * previous pass of its problem is done.  frkc2_batch_prepare writes the problem table
  * into the workspace (host-to-device copies on stream); frkc2_batch_launch only resets the
  * counters and launches, so it can be captured in a CUDA graph and replayed.
- * Work items: FP32 problems run register-tiled 64 x 64 regions of k stages (tile 64 - 2k,
- * default k = 8, the fastest on a mixed batch), tune->tile_z consecutive regions of one pass
- * per item (default 4); FP64 / MIXED problems with k = 1 (the default) run the single-stage streaming
- * body on tiles of 31 columns x tune->tile_y rows (default 128), with k > 1 or kernel = 1 a
- * k-stage shared-memory tile of tune->tile_x x tune->tile_y.
+ * Work items: FP32 and DFLOAT problems run register-tiled 64 x 64 regions of k stages (tile
+ * 64 - 2k, default k = 8, the fastest on a mixed batch; DFLOAT with float-pair state),
+ * tune->tile_z consecutive regions of one pass per item (default 4); FP64 / MIXED problems
+ * with k = 1 (the default), and DFLOAT with k = 1, run the single-stage streaming body on
+ * tiles of 31 columns x tune->tile_y rows (default 128); FP64 / MIXED with k > 1 or kernel = 1
+ * a k-stage shared-memory tile of tune->tile_x x tune->tile_y (DFLOAT: FRKC2_EUNSUPPORTED).
  *   plans, probs, dt, nsteps, u : host arrays of nprob entries (u[i] device pointers).    */
 frkc2_status frkc2_batch_workspace_size(int nprob, const frkc2_plan_t* plans,
                                         const frkc2_problem* probs, const int* nsteps,

@@ -138,6 +138,9 @@ def autotune_batch(plans, probs, dt, nsteps, u, reps: int = 2):
     prec = probs[0].precision
     if prec == F.FP32:  # register-tiled 64 x 64 regions: the tile follows from k
         cands = [F.make_tuning(k=k, tile=(0, 0, g)) for k in (6, 8, 10) for g in (1, 4, 8, 16)]
+    elif prec == F.DFLOAT:  # float-pair regions, or streaming items of one stage
+        cands = [F.make_tuning(k=k, tile=(0, 0, g)) for k in (6, 8, 10) for g in (1, 4, 8)]
+        cands += [F.make_tuning(k=1, tile=(0, r, 1)) for r in (128, 256)]
     else:  # streaming items (k = 1) by rows per tile, and the shared-memory tile pass
         cands = [F.make_tuning(k=1, tile=(0, r, 1)) for r in (64, 128, 256)]
         cands += [F.make_tuning(k=k, tile=t, kernel=1) for k in (1, 2) for t in ((64, 16, 1), (32, 32, 1))]

@@ -16,7 +16,10 @@
 // State buffers are rewritten by other CTAs within the launch, so state loads bypass L1
 // (ld.global.cg); a finished tile is published with a device-scope fence before its counter
 // increment.  FP32 items run the register-tiled 64 x 64 region of the single-problem FP32
-// pass (tb2d_region.cuh: tile 64 - 2k, k-cell recomputed halo).  FP64 and MIXED items with one
+// pass (tb2d_region.cuh: tile 64 - 2k, k-cell recomputed halo), DFLOAT items the float-pair
+// region of the single-problem DFLOAT pass (tb2d_df_region.cuh) or, with one stage per pass,
+// a float-pair streaming body; each region is a call of its own, not inlined into the item
+// loop, so that it keeps the register budget it has in the single-problem pass.  FP64 and MIXED items with one
 // stage per pass (the default) run the streaming body of the single-problem pass on a tile of
 // 31 columns and a block of rows split among the CTA's warps -- interleaved complex state,
 // face pairs, every neighbour difference formed once: 16 FP64 instructions per cell-stage;
@@ -33,6 +36,7 @@
 
 #include "frkc2.h"
 #include "frkc2_internal.h"
+#include "tb2d_df_region.cuh"
 #include "tb2d_region.cuh"
 
 namespace frkc2 {
@@ -243,10 +247,172 @@ __device__ __forceinline__ bool stream_item(const BProb& P, int cw, int r0, int 
   return bad;
 }
 
+// The kernel instantiations of DFLOAT batches (the state is the float pair below): one for the
+// register-tiled region items, one for the streaming items (their register budgets differ).
+template <bool PERIODIC>
+struct DFloatRegions {};
+struct DFloatStream {};
+template <class S> struct is_df_regions : std::false_type {};
+template <bool P> struct is_df_regions<DFloatRegions<P>> : std::true_type {
+  static constexpr bool periodic = P;
+};
+
+// (h, l) + d as a renormalised float pair (Knuth's TwoSum, then a fast renormalisation)
+__device__ __forceinline__ void bdf_add(float& h, float& l, float d) {
+  const float s = h + d;
+  const float bb = s - h;
+  const float e = (h - (s - bb)) + (d - bb);
+  const float t = l + e;
+  const float hi = s + t;
+  l = t - (hi - s);
+  h = hi;
+}
+
+// One stage of a DFLOAT streaming item: the layout of stream_item with the state as float
+// pairs, (U hi, U lo, V hi, V lo) in one float4 a cell, float faces and float arithmetic
+// (the single-problem DFLOAT pass's stage).  IN_REAL: the step's first stage, reading the
+// double real state and splitting it; OUT_REAL: its last, writing hi + lo as a double (template
+// arguments, so the stages between hold no double arithmetic).
+template <bool PERIODIC, bool IN_REAL, bool OUT_REAL>
+__device__ __forceinline__ bool stream_item_df(const BProb& P, int cw, int r0, int r1, const void* in, void* out,
+                                               float ca, float cb) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = BT_THREADS / 32;
+  const int nx = P.nx, ny = P.ny;
+  const int per = (r1 - r0 + nwarps - 1) / nwarps;
+  const int y0 = r0 + warp * per, y1 = min(y0 + per, r1);
+  bool bad = false;
+  if (y0 >= y1) return false;  // warp-uniform
+  const float2* __restrict__ FEN = static_cast<const float2*>(P.fen);
+  const double* Ur = static_cast<const double*>(in);
+  const float4* Wi = static_cast<const float4*>(in);
+  double* Uo = static_cast<double*>(out);
+  float4* Wo = static_cast<float4*>(out);
+  const int x = cw * BS_COLS + lane - 1;
+  int xr, xeast;
+  bool xin, eastin;
+  if (PERIODIC) {
+    xr = x < 0 ? x + nx : (x >= nx ? x - nx : x);
+    xin = true;
+    xeast = xr + 1 == nx ? 0 : xr + 1;
+    eastin = true;
+  } else {
+    xr = x;
+    xin = x >= 0 && x < nx;
+    xeast = x + 1;
+    eastin = xeast >= 0 && xeast < nx;
+  }
+  const bool has_faces = PERIODIC || (x >= -1 && x < nx);
+  const int fcol = (PERIODIC ? xr : x) + 1;
+  const bool out_ok = lane >= 1 && x >= 0 && x < nx;
+  auto load = [&](int yy, int xx, bool inx) -> float4 {
+    int yw = yy;
+    if (PERIODIC) {
+      if (yw < 0) yw += ny;
+      while (yw >= ny) yw -= ny;
+    } else if (!(inx && yy >= 0 && yy < ny)) {
+      return make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    const size_t g = size_t(yw) * nx + xx;
+    if (IN_REAL) {
+      const double u = __ldcg(Ur + g);
+      const float hi = __double2float_rn(u);
+      return make_float4(hi, __double2float_rn(u - double(hi)), 0.f, 0.f);
+    }
+    return __ldcg(Wi + g);
+  };
+  auto faces = [&](int yy) -> float2 {
+    if (PERIODIC) {
+      if (yy < 0) yy += ny;
+      while (yy >= ny) yy -= ny;
+    } else if (yy >= ny) {
+      return make_float2(0.f, 0.f);
+    }
+    if (!has_faces) return make_float2(0.f, 0.f);
+    return __ldg(FEN + size_t(yy + 1) * (nx + 1) + fcol);
+  };
+  auto diff = [](float ah, float al, float bh, float bl) -> float { return (ah - bh) + (al - bl); };
+  float4 Wc = load(y0, xr, xin);
+  float dSU, dSV, ks;
+  {
+    const float4 Ws = load(y0 - 1, xr, xin);
+    ks = faces(y0 - 1).y;
+    dSU = diff(Wc.x, Wc.y, Ws.x, Ws.y);
+    dSV = diff(Wc.z, Wc.w, Ws.z, Ws.w);
+  }
+  float4 Wn = load(y0 + 1, xr, xin);
+  float2 f = faces(y0);
+  float4 Wen = lane == 31 ? load(y0, xeast, eastin) : Wc;
+  for (int y = y0; y < y1; ++y) {
+    const float4 Wnn = load(y + 2, xr, xin);
+    const float2 fnext = faces(y + 1);
+    const float4 Wenn = lane == 31 ? load(y + 1, xeast, eastin) : Wn;
+    float4 We;
+    We.x = __shfl_down_sync(0xffffffffu, Wc.x, 1);
+    We.y = __shfl_down_sync(0xffffffffu, Wc.y, 1);
+    We.z = __shfl_down_sync(0xffffffffu, Wc.z, 1);
+    We.w = __shfl_down_sync(0xffffffffu, Wc.w, 1);
+    if (lane == 31) We = Wen;
+    const float dEU = diff(We.x, We.y, Wc.x, Wc.y), dEV = diff(We.z, We.w, Wc.z, Wc.w);
+    const float dNU = diff(Wn.x, Wn.y, Wc.x, Wc.y), dNV = diff(Wn.z, Wn.w, Wc.z, Wc.w);
+    const float dWU = __shfl_up_sync(0xffffffffu, dEU, 1);
+    const float dWV = __shfl_up_sync(0xffffffffu, dEV, 1);
+    const float kw = __shfl_up_sync(0xffffffffu, f.x, 1);
+    const float fU = f.y * dNU - ks * dSU - kw * dWU + f.x * dEU;
+    const float fV = f.y * dNV - ks * dSV - kw * dWV + f.x * dEV;
+    float uh = Wc.x, ul = Wc.y, vh = Wc.z, vl = Wc.w;
+    bdf_add(uh, ul, ca * fU - cb * fV);
+    bdf_add(vh, vl, ca * fV + cb * fU);
+    if (out_ok) {
+      const size_t g = size_t(y) * nx + x;
+      if (OUT_REAL) {
+        const double un = double(uh) + double(ul);
+        Uo[g] = un;
+        bad |= (__double2hiint(un) & 0x7ff00000) == 0x7ff00000;
+      } else {
+        Wo[g] = make_float4(uh, ul, vh, vl);
+      }
+    }
+    dSU = dNU;
+    dSV = dNV;
+    ks = f.y;
+    Wc = Wn;
+    Wn = Wnn;
+    f = fnext;
+    Wen = Wenn;
+  }
+  return bad;
+}
+
+// One DFLOAT region as a call of its own (not inlined), so that each of its variants gets the
+// register budget it has in the single-problem pass instead of sharing one with the item loop.
+template <bool PERIODIC, bool IN_REAL, bool OUT_REAL>
+__device__ __noinline__ bool df_region_call(DfShared& sh, int nx, int ny, int k, int kq, int x0, int y0,
+                                            const void* in, void* out, const float* FX, const float* FY,
+                                            const double* cf) {
+  auto coef = [&](int j, float& ca, float& cb) {
+    ca = float(cf[2 * j]);
+    cb = float(cf[2 * j + 1]);
+  };
+  return tb2d_df_region<PERIODIC, IN_REAL, OUT_REAL, true>(sh, nx, ny, k, kq, x0, y0, in, out, FX, FY, coef, true,
+                                                          [] {});
+}
+
+// One FP32 region as a call of its own (not inlined), for the same reason.
+template <bool PERIODIC>
+__device__ __noinline__ bool fp32_region_call(RegionShared& sh, int nx, int ny, int k, int kq, int x0, int y0,
+                                              const float* Uin, const float* Vin, float* Uout, float* Vout,
+                                              const float* FX, const float* FY, const double* cf) {
+  auto coef = [&](int j, float& ca, float& cb) {
+    ca = float(cf[2 * j]);
+    cb = float(cf[2 * j + 1]);
+  };
+  return tb2d_region<PERIODIC, true>(sh, nx, ny, k, kq, x0, y0, Uin, Vin, Uout, Vout, FX, FY, coef, Vout == nullptr);
+}
+
 // FP32 items hold a 4 x 4 block of cells per thread in registers: two CTAs per SM
 template <class S, class A>
 constexpr int bt_min_blocks() {
-  return std::is_same<S, float>::value && std::is_same<A, float>::value ? 2 : 1;
+  return (std::is_same<S, float>::value && std::is_same<A, float>::value) || is_df_regions<S>::value ? 2 : 1;
 }
 
 template <class S, class A>
@@ -318,13 +484,62 @@ __global__ void __launch_bounds__(BT_THREADS, bt_min_blocks<S, A>()) k_batched(c
     int l0, kq;
     pass_buffers(P, s_round, Uin_v, Vin_v, Uout_v, Vout_v, l0, kq, h.k);
     const int tyi = s_tile / P.tiles_x, txi = s_tile - tyi * P.tiles_x;
-    if constexpr (std::is_same<S, float>::value && std::is_same<A, float>::value) {
-      __shared__ RegionShared rsh;
+    if constexpr (is_df_regions<S>::value) {
+      // DFLOAT float-pair register-tiled regions of k stages: real input at a step's first
+      // pass, real output at its last
+      constexpr bool PER = is_df_regions<S>::periodic;
+      const int q = s_round < P.total_passes ? s_round % P.passes_per_step : 0;
+      const bool in_real = q == 0, out_real = q == P.passes_per_step - 1;
+      bool bad = false;
+      DfShared& dsh = *reinterpret_cast<DfShared*>(smem);
       const double* cf = P.coef + 2 * l0;
-      auto coef = [&](int j, float& ca, float& cb) {
-        ca = float(cf[2 * j]);
-        cb = float(cf[2 * j + 1]);
-      };
+      const float* FXp = static_cast<const float*>(P.fx);
+      const float* FYp = static_cast<const float*>(P.fy);
+      for (int g = 0; g < h.group; ++g) {
+        const int tile = s_tile * h.group + g;
+        if (tile >= P.tiles_total) break;  // block-uniform
+        const int ty_i = tile / P.tiles_x, tx_i = tile - ty_i * P.tiles_x;
+        const int x0 = tx_i * h.tx - h.k, y0 = ty_i * h.ty - h.k;
+        auto region = [&](auto inr, auto outr) {
+          return df_region_call<PER, decltype(inr)::value, decltype(outr)::value>(dsh, P.nx, P.ny, h.k, kq, x0, y0,
+                                                                                  Uin_v, Uout_v, FXp, FYp, cf);
+        };
+        using T_ = std::true_type;
+        using F_ = std::false_type;
+        bad |= in_real ? (out_real ? region(T_{}, T_{}) : region(T_{}, F_{}))
+                       : (out_real ? region(F_{}, T_{}) : region(F_{}, F_{}));
+        __syncthreads();  // the region's shared buffers are reused by the next tile
+      }
+      if (bad) atomicOr(h.status, ST_NONFINITE);
+    } else if constexpr (std::is_same<S, DFloatStream>::value) {
+      // DFLOAT streaming items of one stage
+      const int q = s_round < P.total_passes ? s_round % P.passes_per_step : 0;
+      const bool in_real = q == 0, out_real = q == P.passes_per_step - 1;
+      bool bad = false;
+      const float ca = float(P.coef[2 * l0]), cb = float(P.coef[2 * l0 + 1]);
+      const int r0 = tyi * h.stream_rows, r1 = min(r0 + h.stream_rows, P.ny);
+      if (periodic) {
+        if (in_real && out_real)
+          bad = stream_item_df<true, true, true>(P, txi, r0, r1, Uin_v, Uout_v, ca, cb);
+        else if (in_real)
+          bad = stream_item_df<true, true, false>(P, txi, r0, r1, Uin_v, Uout_v, ca, cb);
+        else if (out_real)
+          bad = stream_item_df<true, false, true>(P, txi, r0, r1, Uin_v, Uout_v, ca, cb);
+        else
+          bad = stream_item_df<true, false, false>(P, txi, r0, r1, Uin_v, Uout_v, ca, cb);
+      } else {
+        if (in_real && out_real)
+          bad = stream_item_df<false, true, true>(P, txi, r0, r1, Uin_v, Uout_v, ca, cb);
+        else if (in_real)
+          bad = stream_item_df<false, true, false>(P, txi, r0, r1, Uin_v, Uout_v, ca, cb);
+        else if (out_real)
+          bad = stream_item_df<false, false, true>(P, txi, r0, r1, Uin_v, Uout_v, ca, cb);
+        else
+          bad = stream_item_df<false, false, false>(P, txi, r0, r1, Uin_v, Uout_v, ca, cb);
+      }
+      if (bad) atomicOr(h.status, ST_NONFINITE);
+    } else if constexpr (std::is_same<S, float>::value && std::is_same<A, float>::value) {
+      __shared__ RegionShared rsh;
       const float* Uin = static_cast<const float*>(Uin_v);
       const float* Vin = static_cast<const float*>(Vin_v);
       float* Uout = static_cast<float*>(Uout_v);
@@ -336,12 +551,12 @@ __global__ void __launch_bounds__(BT_THREADS, bt_min_blocks<S, A>()) k_batched(c
         if (tile >= P.tiles_total) break;  // block-uniform
         const int ty_i = tile / P.tiles_x, tx_i = tile - ty_i * P.tiles_x;
         const int x0 = tx_i * h.tx - h.k, y0 = ty_i * h.ty - h.k;
-        bad |= periodic ? tb2d_region<true, true>(rsh, P.nx, P.ny, h.k, kq, x0, y0, Uin, Vin, Uout, Vout,
+        bad |= periodic ? fp32_region_call<true>(rsh, P.nx, P.ny, h.k, kq, x0, y0, Uin, Vin, Uout, Vout,
+                                                 static_cast<const float*>(P.fx), static_cast<const float*>(P.fy),
+                                                 P.coef + 2 * l0)
+                        : fp32_region_call<false>(rsh, P.nx, P.ny, h.k, kq, x0, y0, Uin, Vin, Uout, Vout,
                                                   static_cast<const float*>(P.fx), static_cast<const float*>(P.fy),
-                                                  coef, Vout == nullptr)
-                        : tb2d_region<false, true>(rsh, P.nx, P.ny, h.k, kq, x0, y0, Uin, Vin, Uout, Vout,
-                                                   static_cast<const float*>(P.fx), static_cast<const float*>(P.fy),
-                                                   coef, Vout == nullptr);
+                                                  P.coef + 2 * l0);
         __syncthreads();  // the region's shared exchange buffers are reused by the next tile
       }
       if (bad) atomicOr(h.status, ST_NONFINITE);
@@ -453,6 +668,8 @@ __global__ void __launch_bounds__(BT_THREADS, bt_min_blocks<S, A>()) k_batched(c
 
 struct LaunchCfg {
   int precision;
+  bool df_stream;  // DFLOAT streaming items (else DFLOAT region items)
+  bool periodic;
   size_t smem;
   int grid;
   void* counters;
@@ -475,11 +692,12 @@ struct BatchPlanHost {
   long long total_items;
 };
 
-// FP32 items: consecutive 64 x 64 regions of one pass per work item (tune->tile_z; default 4),
+// FP32 and DFLOAT region items: consecutive 64 x 64 regions of one pass per work item
+// (tune->tile_z; default 4),
 // which spreads the per-item hand-over (ticket, decode, dependency check, completion fence)
 // over several regions
-int batch_group(int precision, const frkc2_tuning* tune) {
-  if (precision != FRKC2_FP32) return 1;
+int batch_group(int precision, const frkc2_tuning* tune, bool streaming) {
+  if (streaming || (precision != FRKC2_FP32 && precision != FRKC2_DFLOAT)) return 1;
   return (tune && tune->tile_z) ? tune->tile_z : 4;
 }
 
@@ -493,6 +711,7 @@ bool batch_streaming(int precision, int k, const frkc2_tuning* tune) {
 // items, the k-halo tile of state ping-pong buffers and face conductivities otherwise
 size_t batch_smem(int precision, int tx, int ty, int k, bool streaming = false) {
   if (precision == FRKC2_FP32 || streaming) return 0;
+  if (precision == FRKC2_DFLOAT) return sizeof(DfShared);  // the float-pair regions
   return size_t(tx + 2 * k) * (ty + 2 * k) * (4 * state_bytes(precision) + 2 * arith_bytes(precision));
 }
 
@@ -505,14 +724,16 @@ frkc2_status batch_geometry(int nprob, const frkc2_plan_t* plans, const frkc2_pr
     if (v != FRKC2_OK) return v;
     if (!plans[i] || nsteps[i] < 1) return FRKC2_EINVAL;
     if (probs[i].ndim != 2 || probs[i].kappa_kind == FRKC2_KAPPA_POWER) return FRKC2_EUNSUPPORTED;
-    if (probs[i].precision == FRKC2_DFLOAT) return FRKC2_EUNSUPPORTED;
     if (probs[i].precision != p0.precision || probs[i].bc != p0.bc) return FRKC2_EINVAL;
   }
-  int k = (tune && tune->k) ? tune->k : (p0.precision == FRKC2_FP32 ? 8 : 1);
+  const bool regions = p0.precision == FRKC2_FP32 || p0.precision == FRKC2_DFLOAT;
+  int k = (tune && tune->k) ? tune->k : (regions ? 8 : 1);
+  // DFLOAT items: float-pair regions, or streaming items with one stage per pass; no tile pass
+  if (p0.precision == FRKC2_DFLOAT && tune && tune->kernel == 1) return FRKC2_EUNSUPPORTED;
   int tx = (tune && tune->tile_x) ? tune->tile_x : 64;
   int ty = (tune && tune->tile_y) ? tune->tile_y : 16;
   if (k < 1 || k > KMAX || tx < 1 || ty < 1) return FRKC2_EINVAL;
-  if (p0.precision == FRKC2_FP32) {  // register-tiled regions: the tile is the region minus its halo
+  if (regions && !batch_streaming(p0.precision, k, tune)) {  // register-tiled regions: region minus halo
     if (2 * k >= RT_R) return FRKC2_EINVAL;
     tx = ty = RT_R - 2 * k;
   } else if (batch_streaming(p0.precision, k, tune)) {  // streaming items: 31 columns x a row block
@@ -531,7 +752,7 @@ frkc2_status batch_plan(int nprob, const frkc2_plan_t* plans, const frkc2_proble
   frkc2_status v = batch_geometry(nprob, plans, probs, nsteps, tune, &k, &tx, &ty);
   if (v != FRKC2_OK) return v;
   const size_t SB = state_bytes(probs[0].precision), AB = arith_bytes(probs[0].precision);
-  const int group = batch_group(probs[0].precision, tune);
+  const int group = batch_group(probs[0].precision, tune, batch_streaming(probs[0].precision, k, tune));
   if (group < 1 || group > 64) return FRKC2_EINVAL;
   std::vector<int> T(nprob);
   for (int i = 0; i < nprob; ++i) {
@@ -611,7 +832,7 @@ frkc2_status batch_plan(int nprob, const frkc2_plan_t* plans, const frkc2_proble
   return FRKC2_OK;
 }
 
-int persistent_grid(int precision, size_t smem) {
+int persistent_grid(int precision, size_t smem, bool df_stream) {
   int dev = 0, sms = 152, per = 1;
   if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   cudaError_t e;
@@ -619,6 +840,10 @@ int persistent_grid(int precision, size_t smem) {
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_batched<double, double>, BT_THREADS, smem);
   else if (precision == FRKC2_FP32)
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_batched<float, float>, BT_THREADS, smem);
+  else if (precision == FRKC2_DFLOAT && df_stream)
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_batched<DFloatStream, float>, BT_THREADS, smem);
+  else if (precision == FRKC2_DFLOAT)  // the periodic and Dirichlet instantiations share their budget
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_batched<DFloatRegions<true>, float>, BT_THREADS, smem);
   else
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_batched<double, float>, BT_THREADS, smem);
   if (e != cudaSuccess || per < 1) per = 1;
@@ -702,7 +927,7 @@ frkc2_status frkc2_batch_prepare(int nprob, const frkc2_plan_t* plans, const frk
   h.ty = ty;
   h.k = k;
   h.stream_rows = streaming ? ty : 0;
-  h.group = batch_group(prec, tune);
+  h.group = batch_group(prec, tune, streaming);
   h.fault_inject = tune ? tune->fault_inject : 0;
   h.total_items = B.total_items;
   h.wait_limit = (tune && tune->wait_limit > 0) ? tune->wait_limit : DEFAULT_WAIT_LIMIT;
@@ -727,10 +952,21 @@ frkc2_status frkc2_batch_prepare(int nprob, const frkc2_plan_t* plans, const frk
   LaunchCfg cfg{};
   cfg.precision = prec;
   cfg.smem = batch_smem(prec, tx, ty, k, streaming);
-  cudaError_t e = prec == FRKC2_FP64 ? set_smem<double, double>(cfg.smem)
-                                     : (prec == FRKC2_FP32 ? set_smem<float, float>(cfg.smem) : set_smem<double, float>(cfg.smem));
+  cfg.df_stream = prec == FRKC2_DFLOAT && streaming;
+  cfg.periodic = probs[0].bc == FRKC2_BC_PERIODIC;
+  cudaError_t e;
+  if (prec == FRKC2_FP64)
+    e = set_smem<double, double>(cfg.smem);
+  else if (prec == FRKC2_FP32)
+    e = set_smem<float, float>(cfg.smem);
+  else if (cfg.df_stream)
+    e = set_smem<DFloatStream, float>(cfg.smem);
+  else if (prec == FRKC2_DFLOAT)
+    e = cfg.periodic ? set_smem<DFloatRegions<true>, float>(cfg.smem) : set_smem<DFloatRegions<false>, float>(cfg.smem);
+  else
+    e = set_smem<double, float>(cfg.smem);
   if (e != cudaSuccess) return FRKC2_ECUDA;
-  cfg.grid = persistent_grid(prec, cfg.smem);
+  cfg.grid = persistent_grid(prec, cfg.smem, cfg.df_stream);
   if (cfg.grid > B.total_items) cfg.grid = int(B.total_items);
   cfg.counters = base + B.off_counters;
   cfg.counter_bytes = B.counter_bytes;
@@ -755,6 +991,14 @@ frkc2_status frkc2_batch_launch(void* ws, void* stream) {
   switch (cfg.precision) {
     case FRKC2_FP64: k_batched<double, double><<<cfg.grid, BT_THREADS, cfg.smem, st>>>(cfg.header); break;
     case FRKC2_FP32: k_batched<float, float><<<cfg.grid, BT_THREADS, cfg.smem, st>>>(cfg.header); break;
+    case FRKC2_DFLOAT:
+      if (cfg.df_stream)
+        k_batched<DFloatStream, float><<<cfg.grid, BT_THREADS, cfg.smem, st>>>(cfg.header);
+      else if (cfg.periodic)
+        k_batched<DFloatRegions<true>, float><<<cfg.grid, BT_THREADS, cfg.smem, st>>>(cfg.header);
+      else
+        k_batched<DFloatRegions<false>, float><<<cfg.grid, BT_THREADS, cfg.smem, st>>>(cfg.header);
+      break;
     default: k_batched<double, float><<<cfg.grid, BT_THREADS, cfg.smem, st>>>(cfg.header); break;
   }
   count_launch();

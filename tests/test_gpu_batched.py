@@ -11,9 +11,9 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 F = pytest.importorskip("paper_1702_03818_gb300.frkc2")
 
-DT = {"fp64": torch.float64, "fp32": torch.float32, "mixed": torch.float64}
-KDT = {"fp64": torch.float64, "fp32": torch.float32, "mixed": torch.float32}
-TOL = {"fp64": 1e-11, "fp32": 1e-4, "mixed": 1e-6}
+DT = {"fp64": torch.float64, "fp32": torch.float32, "mixed": torch.float64, "dfloat": torch.float64}
+KDT = {"fp64": torch.float64, "fp32": torch.float32, "mixed": torch.float32, "dfloat": torch.float32}
+TOL = {"fp64": 1e-11, "fp32": 1e-4, "mixed": 1e-6, "dfloat": 1e-6}
 
 
 def make_batch(prec, bc, specs, seed0=900):
@@ -63,17 +63,20 @@ def test_batched_matches_oracle(prec, bc):
         assert err < TOL[prec], (it["u"].shape, it["s"], it["nsteps"], err)
 
 
-@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+@pytest.mark.parametrize("prec", ["fp64", "mixed", "dfloat"])
 @pytest.mark.parametrize("bc", ["periodic", "dirichlet"])
 @pytest.mark.parametrize("rows", [0, 7])
 def test_batched_streaming_items_match_oracle(prec, bc, rows):
-    """FP64 / MIXED batches with one stage per pass (the default) run the streaming body on
-    tiles of 31 columns x a row block split among the warps (128 rows by default; 7 makes
-    blocks smaller than the warp count): every item against the oracle, grid norm and every
-    element, over ragged grids of 5 .. 150 cells a side and 1 .. 3 steps."""
+    """FP64 / MIXED / DFLOAT batches with one stage per pass (the default) run the streaming
+    body on tiles of 31 columns x a row block split among the warps (128 rows by default; 7
+    makes blocks smaller than the warp count); DFLOAT holds the stage states as float pairs.
+    Every item against the oracle, grid norm and every element, over ragged grids of 5 .. 150
+    cells a side and 1 .. 3 steps."""
     items = make_batch(prec, bc, SPECS, seed0=1300)
     plans = [F.frkc2_plan(it["s"]) for it in items]
     tune = F.make_tuning(tile=(0, rows, 0)) if rows else None
+    if prec == "dfloat":  # its default is the float-pair regions; one stage a pass streams
+        tune = F.make_tuning(k=1, tile=(0, rows, 0))
     nst = [it["nsteps"] for it in items]
     ws = torch.empty(F.frkc2_batch_workspace_size(plans, [it["pr"] for it in items], nst, tune),
                      dtype=torch.uint8, device="cuda")
@@ -85,6 +88,29 @@ def test_batched_streaming_items_match_oracle(prec, bc, rows):
     for it, ref in zip(items, refs):
         err = rel_err(it["u"].double().cpu().numpy(), ref)
         assert err < TOL[prec], (it["u"].shape, it["s"], it["nsteps"], err)
+
+
+@pytest.mark.parametrize("bc", ["periodic", "dirichlet"])
+@pytest.mark.parametrize("k,group", [(8, 4), (6, 1), (4, 3)])
+def test_batched_dfloat_regions_match_oracle(bc, k, group):
+    """DFLOAT batches with k stages per pass (8 by default) run the float-pair register-tiled
+    64 x 64 regions of the single-problem DFLOAT pass, `group` consecutive regions per item:
+    every item against the oracle over ragged grids and 1 .. 3 steps (s = 8 .. 32: passes of
+    fewer than k stages at a step's end, single-pass steps)."""
+    items = make_batch("dfloat", bc, SPECS, seed0=1700)
+    plans = [F.frkc2_plan(it["s"]) for it in items]
+    tune = F.make_tuning(k=k, tile=(0, 0, group))
+    nst = [it["nsteps"] for it in items]
+    ws = torch.empty(F.frkc2_batch_workspace_size(plans, [it["pr"] for it in items], nst, tune),
+                     dtype=torch.uint8, device="cuda")
+    F.frkc2_workspace_reset(ws)
+    F.frkc2_step_batched(plans, [it["pr"] for it in items], [it["dt"] for it in items], nst,
+                         [it["u"] for it in items], ws, tune)
+    assert F.frkc2_workspace_status(ws) == F.OK
+    refs = oracle_results(items, "dfloat")
+    for it, ref in zip(items, refs):
+        err = rel_err(it["u"].double().cpu().numpy(), ref)
+        assert err < TOL["dfloat"], (it["u"].shape, it["s"], it["nsteps"], err)
 
 
 @pytest.mark.parametrize("group", [1, 3])
@@ -176,13 +202,14 @@ def test_batched_rejects_mixed_kinds():
     assert e.value.status == F.EUNSUPPORTED
 
 
-@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "dfloat"])
 def test_batched_64_problems_large_s_matches_oracle(prec):
     """64 uneven problems with s from {16, 64, 128, 256} (every problem above the FP32 threshold
-    of the paper's order in the FP32 batch), one persistent launch.  FP64 items run the paper's
-    plans; FP32 items the plans the precision policy gives linear problems (the Lebedev-
-    Finogenov order, FP32 within 1e-4 at these s).  Each item against the oracle with its own
-    stage order, grid norm and every element."""
+    of the paper's order in the FP32 batch), one persistent launch.  FP64 and DFLOAT items run
+    the paper's plans (DFLOAT: the float-pair state that keeps those plans within reach where
+    FP32 does not); FP32 items the plans the precision policy gives linear problems (the
+    Lebedev-Finogenov order, FP32 within 1e-4 at these s).  Each item against the oracle with
+    its own stage order, grid norm and every element."""
     from helpers import oracle_map
 
     rng = np.random.default_rng(6464)
@@ -198,7 +225,7 @@ def test_batched_64_problems_large_s_matches_oracle(prec):
         plans = [F.frkc2_plan(it["s"]) for it in items]
     probs = [it["pr"] for it in items]
     nst = [it["nsteps"] for it in items]
-    tune = F.make_tuning(k=8) if prec == "fp32" else None  # FP64: the streaming items
+    tune = F.make_tuning(k=8) if prec == "fp32" else None  # FP64: streaming items, DFLOAT: regions (k = 8)
     ws = torch.empty(F.frkc2_batch_workspace_size(plans, probs, nst, tune), dtype=torch.uint8, device="cuda")
     F.frkc2_workspace_reset(ws)
     F.frkc2_step_batched(plans, probs, [it["dt"] for it in items], nst, [it["u"] for it in items], ws, tune)
@@ -211,6 +238,17 @@ def test_batched_64_problems_large_s_matches_oracle(prec):
         u0 = it["u0"].astype(np.float32).astype(np.float64) if prec == "fp32" else it["u0"]
         jobs.append((u0, a, it["dt"], it["opr"], it["nsteps"]))
     refs = oracle_map(jobs)
-    for it, ref in zip(items, refs):
+    errs = []
+    for it, p, ref in zip(items, plans, refs):
         err = rel_err(it["u"].double().cpu().numpy(), ref)
-        assert err < TOL[prec], (it["u"].shape, it["s"], it["nsteps"], err)
+        errs.append(err)
+        tol = TOL[prec]
+        if prec == "dfloat":
+            # float flux arithmetic under the paper's order: the library's precision model
+            # forecasts the DFLOAT error from the order's rounding gain (8e-6 at s = 128 and
+            # 4e-5 at s = 256 over 2 steps); below s = 128 it stays under the 1e-6 class
+            name, forecast = F.frkc2_precision_policy(p, it["pr"], it["nsteps"], 1e-4)
+            if name == "dfloat":
+                tol = max(tol, forecast)
+        assert err < tol, (it["u"].shape, it["s"], it["nsteps"], err, tol)
+    print(prec, "largest error", max(errs))

@@ -247,7 +247,8 @@ def test_bruss_step_rejects_before_gpu_work():
 
 
 def test_dfloat_precision_validation_on_host():
-    """DFLOAT (float-pair state) exists for 2D FIELD / CONST problems and frkc2_step only."""
+    """DFLOAT (float-pair state) exists for 2D FIELD / CONST problems, frkc2_step and the
+    batched launch (its float-pair regions or streaming items, not the shared-memory tile)."""
     p2 = F.make_problem(2, (64, 48), 1.0, "periodic", "const", "dfloat")
     pm = F.make_problem(2, (64, 48), 1.0, "periodic", "const", "mixed")
     assert F.frkc2_workspace_size(p2) == F.frkc2_workspace_size(pm)
@@ -264,8 +265,10 @@ def test_dfloat_precision_validation_on_host():
     with pytest.raises(F.Frkc2Error) as e:
         F.frkc2_adaptive_workspace_size(p2)
     assert e.value.status == F.EUNSUPPORTED
+    assert F.frkc2_batch_workspace_size([plan], [p2], [1]) > 0
+    assert F.frkc2_batch_workspace_size([plan], [p2], [1], F.make_tuning(k=1)) > 0
     with pytest.raises(F.Frkc2Error) as e:
-        F.frkc2_batch_workspace_size([plan], [p2], [1])
+        F.frkc2_batch_workspace_size([plan], [p2], [1], F.make_tuning(k=2, kernel=1))
     assert e.value.status == F.EUNSUPPORTED
     p_bad = F.make_problem(2, (8, 8), 1.0, "periodic", "const", 4)
     with pytest.raises(F.Frkc2Error) as e:
