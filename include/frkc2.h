@@ -107,10 +107,12 @@ typedef struct {
                         stage levels in flight, rows staged in shared memory by TMA bulk
                         copies (n[0] a multiple of 4 and >= 256, u 16-byte aligned, every
                         pass of 1, 2, 4, 6, 8, 10 or 12 stages; the FP32 2D default there)  */
-  long long wait_limit; /* batched launch: polls a device wait makes before it gives up and
-                        latches FRKC2_ETIMEOUT (0 = library default, 2^22 polls)           */
-  int fault_inject;  /* batched launch, testing only: 1 = the first dependent work item waits
-                        on a counter nothing advances, so the wait must run out             */
+  long long wait_limit; /* batched launch and kernel 7 (its waits on the TMA row copies):
+                        polls a device wait makes before it gives up and latches
+                        FRKC2_ETIMEOUT (0 = library default, 2^22 polls)                    */
+  int fault_inject;  /* testing only: 1 = in the batched launch the first dependent work
+                        item waits on a counter nothing advances; in kernel 7 (passes of
+                        k = 8) the first pass leaves one row uncopied; either wait must run out */
 } frkc2_tuning;
 
 /* ---- Plan (host, FP64) --------------------------------------------------------------

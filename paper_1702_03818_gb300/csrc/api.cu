@@ -385,7 +385,9 @@ frkc2_status frkc2_step(frkc2_plan_t plan, const frkc2_problem* prob, double dt,
           a.caf[j] = float(dt * plan->a_re[l0 + j] / h2);
           a.cbf[j] = float(dt * plan->a_im[l0 + j] / h2);
         }
-        if (launch_pass_wf2d(p, a, base + L.fen, chunk_rows, first, last, st, n > 0 || q > 0) != cudaSuccess)
+        if (launch_pass_wf2d(p, a, base + L.fen, chunk_rows, first, last, st, n > 0 || q > 0,
+                             tune ? tune->wait_limit : 0, tune && n == 0 && q == 0 ? tune->fault_inject : 0) !=
+            cudaSuccess)
           return FRKC2_ECUDA;
         curU = outU;
       }

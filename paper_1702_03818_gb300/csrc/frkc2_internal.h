@@ -126,7 +126,8 @@ cudaError_t launch_faces_wf(const frkc2_problem& p, const void* fx, const void* 
 // chunk_rows: rows per CTA (0 = one wave of two CTAs per SM); in_real / out_real: the pass reads
 // / writes the real state (float [ny][nx]) instead of interleaved (U, V) float2 [ny][nx]
 cudaError_t launch_pass_wf2d(const frkc2_problem& p, const PassArgs& a, const void* faces_wf, int chunk_rows,
-                             bool in_real, bool out_real, cudaStream_t st, bool overlap_previous);
+                             bool in_real, bool out_real, cudaStream_t st, bool overlap_previous,
+                             long long wait_limit = 0, int fault_inject = 0);
 cudaError_t launch_small1d(const frkc2_problem& p, const frkc2_plan_s& plan, double dt, int nsteps, void* u,
                            const void* fx, unsigned* status, cudaStream_t st, int cluster, int stages_per_exchange,
                            int threads_per_cta);

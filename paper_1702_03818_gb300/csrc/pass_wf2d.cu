@@ -142,7 +142,10 @@ struct Cells {
   float2 c0, c1;  // (U, V) of the thread's two cells
 };
 
-template <int K, bool PERIODIC>
+// FAULT (testing only, one instantiation): the chunk's first row is never copied, so every
+// thread's bounded wait on it must run out.  A template argument, since even a test outside
+// the loop measurably changed the normal kernel.
+template <int K, bool PERIODIC, bool FAULT = false>
 __global__ void __launch_bounds__(WF_NW * 32, 2) k_wf2d(const WfArgs p) {
   constexpr int NW = WF_NW;
   constexpr int CW = 64 * NW;                       // computed columns of the strip
@@ -223,7 +226,8 @@ __global__ void __launch_bounds__(WF_NW * 32, 2) k_wf2d(const WfArgs p) {
     }
   };
   if (tid == 0)
-    for (int r = t0; r < min(t0 + L, te + 1); ++r) issue(r, r - t0);
+    for (int r = t0; r < min(t0 + L, te + 1); ++r)
+      if (!(FAULT && r == t0)) issue(r, r - t0);
 
   // Dirichlet: which of the thread's columns lie in the grid
   const int gx0 = xs + cx;
@@ -420,9 +424,9 @@ struct WfResidency {
   int sms, per_sm;
 };
 
-template <int K, bool PERIODIC>
+template <int K, bool PERIODIC, bool FAULT = false>
 cudaError_t launch_k(WfArgs a, cudaStream_t st, bool overlap_previous, int chunk_rows) {
-  const auto kern = k_wf2d<K, PERIODIC>;
+  const auto kern = k_wf2d<K, PERIODIC, FAULT>;
   const size_t smem = smem_bytes(K);
   static const WfResidency res = [kern, smem] {
     WfResidency r{cudaSuccess, 152, 1};
@@ -457,7 +461,12 @@ cudaError_t launch_k(WfArgs a, cudaStream_t st, bool overlap_previous, int chunk
 }
 
 template <int K>
-cudaError_t launch_bc(const WfArgs& a, bool periodic, cudaStream_t st, bool ov, int chunk_rows) {
+cudaError_t launch_bc(const WfArgs& a, bool periodic, cudaStream_t st, bool ov, int chunk_rows, int fault) {
+  if (fault) {  // the fault-injecting instantiation exists for k = 8 only
+    if constexpr (K == 8)
+      return periodic ? launch_k<K, true, true>(a, st, ov, chunk_rows) : launch_k<K, false, true>(a, st, ov, chunk_rows);
+    return cudaErrorInvalidValue;
+  }
   return periodic ? launch_k<K, true>(a, st, ov, chunk_rows) : launch_k<K, false>(a, st, ov, chunk_rows);
 }
 
@@ -502,7 +511,8 @@ cudaError_t launch_faces_wf(const frkc2_problem& p, const void* fx, const void* 
 }
 
 cudaError_t launch_pass_wf2d(const frkc2_problem& p, const PassArgs& a, const void* faces_wf, int chunk_rows,
-                             bool in_real, bool out_real, cudaStream_t st, bool overlap_previous) {
+                             bool in_real, bool out_real, cudaStream_t st, bool overlap_previous, long long wait_limit,
+                             int fault_inject) {
   (void)p;
   WfArgs w{};
   w.nx = a.nx;
@@ -518,20 +528,20 @@ cudaError_t launch_pass_wf2d(const frkc2_problem& p, const PassArgs& a, const vo
   w.faces = static_cast<const float2*>(faces_wf);
   w.status = a.status;
   w.check_finite = a.check_finite;
-  w.wait_limit = 1ll << 22;
+  w.wait_limit = wait_limit > 0 ? wait_limit : 1ll << 22;
   for (int j = 0; j < a.k; ++j) {
     w.ca[j] = a.caf[j];
     w.cb[j] = a.cbf[j];
   }
   const bool periodic = a.bc == FRKC2_BC_PERIODIC;
   switch (a.k) {
-    case 1: return launch_bc<1>(w, periodic, st, overlap_previous, chunk_rows);
-    case 2: return launch_bc<2>(w, periodic, st, overlap_previous, chunk_rows);
-    case 4: return launch_bc<4>(w, periodic, st, overlap_previous, chunk_rows);
-    case 6: return launch_bc<6>(w, periodic, st, overlap_previous, chunk_rows);
-    case 8: return launch_bc<8>(w, periodic, st, overlap_previous, chunk_rows);
-    case 10: return launch_bc<10>(w, periodic, st, overlap_previous, chunk_rows);
-    case 12: return launch_bc<12>(w, periodic, st, overlap_previous, chunk_rows);
+    case 1: return launch_bc<1>(w, periodic, st, overlap_previous, chunk_rows, fault_inject);
+    case 2: return launch_bc<2>(w, periodic, st, overlap_previous, chunk_rows, fault_inject);
+    case 4: return launch_bc<4>(w, periodic, st, overlap_previous, chunk_rows, fault_inject);
+    case 6: return launch_bc<6>(w, periodic, st, overlap_previous, chunk_rows, fault_inject);
+    case 8: return launch_bc<8>(w, periodic, st, overlap_previous, chunk_rows, fault_inject);
+    case 10: return launch_bc<10>(w, periodic, st, overlap_previous, chunk_rows, fault_inject);
+    case 12: return launch_bc<12>(w, periodic, st, overlap_previous, chunk_rows, fault_inject);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -253,6 +253,33 @@ def test_step_parity_fp32_wavefront(case):
         assert rel_err(got, reg) < TOL["fp32"], rel_err(got, reg)  # two roundings of the same stages
 
 
+def test_wavefront_row_wait_runs_out_and_context_survives():
+    """fault_inject on kernel 7: the first pass leaves one row's TMA copies unissued, so every
+    thread's bounded wait on that row's mbarrier runs out (wait_limit polls); the CTAs wait
+    (bounded) for their copies in flight and return, FRKC2_ETIMEOUT is latched, and the next
+    call on the same device matches the oracle."""
+    shape = (40, 256)
+    u0, field = seeded_case(shape, "periodic", "field", 8)
+    s = 16
+    plan = F.frkc2_plan(s)
+    kt = dev(field, torch.float32)
+    pr = lib_problem(shape, "periodic", "field", "fp32", 1.0, kt, 1.0)
+    fo = field.astype(np.float32).astype(np.float64)
+    opr = oracle_problem(2, "periodic", "field", 1.0, fo)
+    dt = 0.9 * O.beta(s) / O.rho_bound(opr)
+    ws = torch.empty(F.frkc2_workspace_size(pr), dtype=torch.uint8, device="cuda")
+    F.frkc2_workspace_reset(ws)
+    u = dev(u0, torch.float32)
+    F.frkc2_step(plan, pr, dt, 2, 0.0, u, ws, F.make_tuning(k=8, kernel=7, wait_limit=2000, fault_inject=1))
+    assert F.frkc2_workspace_status(ws) == F.ETIMEOUT
+    F.frkc2_workspace_reset(ws)
+    u = dev(u0, torch.float32)
+    F.frkc2_step(plan, pr, dt, 2, 0.0, u, ws, F.make_tuning(k=8, kernel=7))
+    assert F.frkc2_workspace_status(ws) == F.OK
+    ref = O.frkc2_step(u0.astype(np.float32).astype(np.float64), O.plan(s)["a"], dt, opr, 2)
+    assert rel_err(u.double().cpu().numpy(), ref) < TOL["fp32"]
+
+
 def test_wavefront_launches_and_rejects_unsupported():
     """Kernel 7 on an FP32 2D problem with nx a multiple of 4 and at least 256: one face set-up
     kernel for the call, one for the wavefront layout, then one launch per pass; other widths,
