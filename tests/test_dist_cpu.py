@@ -109,18 +109,19 @@ def _slab_worker(rank, world, port, q, ny, nx, s, nsteps, halo, m):
         dist.destroy_process_group()
 
 
-@pytest.mark.parametrize("ny,halo,m", [(24, 4, 4), (23, 5, 3)])
-def test_two_gloo_ranks_slab_steps_equal_the_whole_grid(ny, halo, m):
-    """Two ranks, each holding half of a periodic grid's rows plus `halo` rows each side, run 2
-    FRKC2 steps of s = 8 stages exchanging halos before every group of m stages; the interior
-    rows equal the oracle's step on the whole grid bit for bit, the conductivity's halo rows
-    equal the global rows they stand for, and the schedule is ceil(s / m) groups per step."""
+@pytest.mark.parametrize("world,ny,halo,m", [(2, 24, 4, 4), (2, 23, 5, 3), (3, 31, 4, 4), (4, 26, 3, 2)])
+def test_gloo_ranks_slab_steps_equal_the_whole_grid(world, ny, halo, m):
+    """2 to 4 ranks, each holding its slab of a periodic grid's rows (uneven heights where ny
+    does not divide) plus `halo` rows each side, run 2 FRKC2 steps of s = 8 stages exchanging
+    halos before every group of m stages; the interior rows equal the oracle's step on the
+    whole grid bit for bit, the conductivity's halo rows equal the global rows they stand for,
+    and the schedule is ceil(s / m) groups per step."""
     import numpy as np
 
     import frkc2_inputs as I
     from oracle import frkc2_oracle as O
 
-    world, nx, s, nsteps = 2, 10, 8, 2
+    nx, s, nsteps = 10, 8, 2
     port = _free_port()
     ctx = mp.get_context("spawn")
     q = ctx.Queue()
@@ -138,7 +139,7 @@ def test_two_gloo_ranks_slab_steps_equal_the_whole_grid(ny, halo, m):
     dt = 0.9 * O.beta(s) / O.rho_bound(pr)
     ref = O.frkc2_step(u0, O.plan(s)["a"], dt, pr, nsteps)
     got = np.concatenate([r[3] for r in res])
-    assert [(r[1], r[2]) for r in res] == [(0, ny // 2), (ny // 2, ny)]
+    assert [(r[1], r[2]) for r in res] == [(q * ny // world, (q + 1) * ny // world) for q in range(world)]
     assert all(r[4] for r in res)
     groups = -(-s // m)
     assert all(r[5] == groups * nsteps for r in res)
