@@ -135,6 +135,133 @@ def damped_step_sizes(L: int, nu0: float):
     return a, mu
 
 
+# ----------------------------------------------------------------------------------------
+# The rank-N polynomial (Sec. 2, Eq. 7 with N = 4): a sum of Chebyshev polynomials
+# ----------------------------------------------------------------------------------------
+
+
+def _cheb_deriv_at_one(j: int, n: int) -> float:
+    """n-th derivative of the Chebyshev polynomial T_j at x = 1: prod_{m<n} (j^2 - m^2)/(2m+1).
+
+    (The classical identity obtained from the Chebyshev differential equation
+    (1 - x^2) T'' - x T' + j^2 T = 0 differentiated n times and taken at x = 1.)
+    """
+    p = 1.0
+    for m in range(n):
+        p *= (j * j - m * m) / (2.0 * m + 1.0)
+    return p
+
+
+def chebsum_coefficients(N: int, M: int, alpha_: float) -> np.ndarray:
+    """Coefficients d_0..d_N of B(z) = d_0 + 2 sum_{k=1}^N d_k T_{kM}(x), x = 1 + z/(M^2 alpha).
+
+    Reading of Eq. 7: the argument of the Chebyshev polynomials is the shifted variable
+    x = 1 + z/(M^2 alpha_M), the map under which the step sizes of Eq. 8 are
+    a_l = 1/(M^2 alpha_M (1 - zeta_l)) for the roots zeta_l in x.  The d_k solve the N + 1
+    linear order conditions of Eq. 5, R(0) = 1 and R^(n)(0) = 1 for n = 1..N, where
+    d^n/dz^n T_j(x(z)) at z = 0 is T_j^(n)(1) / (M^2 alpha)^n.
+    """
+    A = np.zeros((N + 1, N + 1))
+    A[0, 0] = 1.0
+    A[0, 1:] = 2.0
+    for n in range(1, N + 1):
+        for k in range(1, N + 1):
+            A[n, k] = 2.0 * _cheb_deriv_at_one(k * M, n) / (M * M * alpha_) ** n
+    return np.linalg.solve(A, np.ones(N + 1))
+
+
+def _chebsum_Q(d: np.ndarray) -> np.ndarray:
+    """Chebyshev series of Q(y) = d_0 + 2 sum_k d_k T_k(y): since T_{kM} = T_k(T_M), B = Q(T_M(x))."""
+    c = 2.0 * np.asarray(d, dtype=np.float64)
+    c[0] = d[0]
+    return c
+
+
+def _max_abs_Q(d: np.ndarray) -> float:
+    """max |Q(y)| over [-1, 1] from the end point y = -1 and the real critical points inside.
+
+    Q(1) = R(0) = 1 holds by the first order condition and Q'(1) = alpha > 0 there, so the
+    end point y = 1 is left out (it would only contribute its rounding error).
+    """
+    from numpy.polynomial import chebyshev as C
+
+    c = _chebsum_Q(d)
+    cand = [-1.0]
+    for r in C.chebroots(C.chebder(c)):
+        if abs(r.imag) <= 1e-12 * max(1.0, abs(r.real)) and -1.0 < r.real < 1.0:
+            cand.append(float(r.real))
+    return float(np.max(np.abs(C.chebval(np.array(cand), c))))
+
+
+def chebsum_alpha(N: int, M: int) -> float:
+    """alpha_M of the rank-N polynomial: the largest alpha whose order-condition polynomial is
+    bounded, |R(z)| <= 1 on [-2 M^2 alpha, 0] (Eq. 6).
+
+    Reading: T_M maps x in [-1, 1] onto [-1, 1], so the bound on z in [-2 M^2 alpha, 0] is
+    |Q(y)| <= 1 on y in [-1, 1]; alpha is found by bisection on that test (the feasible alphas
+    form an interval from 0).  For N = 2 this gives the closed form 4 (1 - 1/L^2) / 3 with
+    d_1 = 0; for L = N (M = 1) B is the degree-N Taylor polynomial of e^z.
+    """
+    lo, hi = 0.25, 4.0
+    if _max_abs_Q(chebsum_coefficients(N, M, lo)) > 1.0:
+        raise ValueError("lower bisection bracket not feasible")
+    for _ in range(200):
+        mid = 0.5 * (lo + hi)
+        if mid in (lo, hi):
+            break
+        if _max_abs_Q(chebsum_coefficients(N, M, mid)) <= 1.0:
+            lo = mid
+        else:
+            hi = mid
+    return lo
+
+
+def chebsum_beta(N: int, M: int) -> float:
+    """Real stability extent of the rank-N polynomial: beta = 2 M^2 alpha_M (x = -1)."""
+    return 2.0 * M * M * chebsum_alpha(N, M)
+
+
+def chebsum_roots(N: int, M: int) -> np.ndarray:
+    """The L = N M roots zeta of B in x, in the root order used for the stage ordering.
+
+    Q(y) has N roots y_i (numpy's companion-matrix root finder); T_M(x) = y_i has the M
+    solutions x = cos((arccos y_i + 2 pi k) / M), k = 0..M-1.  Reading of the root order:
+    the roots with Im zeta > 0 sorted by decreasing Re zeta are zeta_0..zeta_{L/2-1}, and
+    zeta_{L-1-j} = conj(zeta_j) exactly -- for N = 2 this is the order of ``roots``.  Q has
+    real coefficients and, for N = 2 and 4, no real roots, so no zeta is real.
+    """
+    from numpy.polynomial import chebyshev as C
+
+    L = N * M
+    al = chebsum_alpha(N, M)
+    ys = C.chebroots(_chebsum_Q(chebsum_coefficients(N, M, al)))
+    xs = []
+    for y in ys.astype(np.complex128):
+        th = np.arccos(y)
+        for k in range(M):
+            xs.append(np.cos((th + 2.0 * np.pi * k) / M))
+    xs = np.array(xs)
+    upper = xs[xs.imag > 0.0]
+    if len(upper) != L // 2:
+        raise ValueError("roots not in conjugate pairs off the real axis")
+    upper = upper[np.argsort(-upper.real, kind="stable")]
+    z = np.empty(L, dtype=np.complex128)
+    z[: L // 2] = upper
+    z[L // 2:] = np.conj(upper[::-1])
+    return z
+
+
+def chebsum_step_sizes(N: int, M: int) -> np.ndarray:
+    """Step sizes a_l = 1/(M^2 alpha_M (1 - zeta_l)) of the rank-N polynomial (Eq. 8), in root
+    order; the second member of each conjugate pair is the exact conjugate of the first."""
+    L = N * M
+    al = chebsum_alpha(N, M)
+    a = 1.0 / (M * M * al * (1.0 - chebsum_roots(N, M)))
+    for j in range(L // 2):
+        a[L - 1 - j] = np.conj(a[j])
+    return a
+
+
 def stability_extent(a, guess: float) -> float:
     """Largest x with |R(-x)| <= 1 near ``guess`` (bisection on the last crossing, Eq. 6)."""
     def absR(x):
@@ -288,7 +415,7 @@ def frkc2_step_paired(u0, a, T, prob, nsteps: int = 1):
 
 
 def plan(L: int, samples: int | None = None, q_points: int | None = None, n_max: int = 10,
-         bound: float = 10.0, method: str = "auto", nu0: float = 0.0) -> dict:
+         bound: float = 10.0, method: str = "auto", nu0: float = 0.0, N: int = 2) -> dict:
     """Ordered FRKC2 step sizes for L stages (Sec. 2.2, the n-loop).
 
     ``greedy``: the ordering of Eq. 12 is repeated with n = 1, 2, ... until the realised Q is
@@ -302,8 +429,18 @@ def plan(L: int, samples: int | None = None, q_points: int | None = None, n_max:
     bound (the smaller realised Q is kept).
     ``paired``: ``order_paired`` (conjugates adjacent, for real-arithmetic pair stages).
     ``nu0`` > 0 uses the damped step sizes of Sec. 2.1, with beta found by bisection.
+    ``N`` = 4 takes the step sizes and extent of the rank-4 polynomial (``chebsum_step_sizes``,
+    ``chebsum_beta``, L = 4M; undamped only).  Reading for ``auto`` there: the Lebedev-Finogenov
+    order first at every L (on the rank-4 roots its realised Q is about 0.1 L^2, close to the
+    largest single factor, where the greedy reaches a few L^2), the greedy n-loop only if it
+    misses the bound.
     """
-    if nu0 > 0.0:
+    if N not in (2, 4) or (N == 4 and (L % 4 or nu0 > 0.0)):
+        raise ValueError("N = 2, or N = 4 with L a multiple of 4 and no damping")
+    if N == 4:
+        a = chebsum_step_sizes(4, L // 4)
+        b = chebsum_beta(4, L // 4)
+    elif nu0 > 0.0:
         a, _ = damped_step_sizes(L, nu0)
         b = stability_extent(a, (1.0 - nu0 / 2.0) * beta(L))
     else:
@@ -323,8 +460,8 @@ def plan(L: int, samples: int | None = None, q_points: int | None = None, n_max:
     if method == "paired":
         consider(order_paired(L), 0)
         return best
-    run_greedy = method == "greedy" or (method == "auto" and L <= 256)
-    if method == "lebedev" or (method == "auto" and L > 256):
+    run_greedy = method == "greedy" or (method == "auto" and L <= 256 and N == 2)
+    if method == "lebedev" or (method == "auto" and (L > 256 or N == 4)):
         q = consider(order_lebedev(L), 0)
         if method == "auto" and q > bound * L * L:
             run_greedy = True

@@ -895,3 +895,125 @@ def test_rounding_gain_closed_forms():
     assert abs(O.rounding_gain(a, b, P) ** 2 / want - 1.0) < 1e-12
     a16 = O.plan(16)["a"]
     assert abs(O.rounding_gain(a16[::-1], O.beta(16)) / O.rounding_gain(a16, O.beta(16)) - 1.0) > 1e-3
+
+
+# --------------------------------------------------------------------------------------
+# Rank-4 polynomial (Sec. 2, Eq. 7 with N = 4; order conditions Eq. 5, bound Eq. 6)
+# --------------------------------------------------------------------------------------
+
+
+def _taylor_coeffs(a):
+    c = np.array([1.0 + 0j])
+    for al in a:
+        c = np.convolve(c, np.array([1.0, al]))
+    return c
+
+
+def test_rank4_at_L4_is_the_rk4_taylor_polynomial():
+    """L = N = 4 (M = 1): degree 4 and five order conditions leave only the Taylor polynomial
+    1 + z + z^2/2 + z^3/6 + z^4/24, whose real stability boundary is the real root of
+    1 + z/2 + z^2/6 + z^3/24 = 0 (numpy.roots; textbook value 2.78529)."""
+    c = _taylor_coeffs(O.chebsum_step_sizes(4, 1))
+    assert np.allclose(c, [1.0, 1.0, 0.5, 1.0 / 6.0, 1.0 / 24.0], rtol=0, atol=1e-14)
+    r = np.roots([1.0 / 24.0, 1.0 / 6.0, 0.5, 1.0])
+    x = -float(r[np.argmin(np.abs(r.imag))].real)
+    assert abs(O.chebsum_beta(4, 1) - x) < 1e-12 * x
+    assert abs(x - 2.78529) < 1e-5
+
+
+@pytest.mark.parametrize("M", [1, 2, 4, 8, 32])
+def test_rank_n_construction_at_N2_gives_the_frkc2_polynomial(M):
+    """The rank-N route (order conditions for d, largest bounded alpha, roots through
+    T_M(x) = y) at N = 2 reproduces alpha = 4(1 - 1/L^2)/3, d_1 = 0 and the FRKC2 roots."""
+    L = 2 * M
+    al = O.chebsum_alpha(2, M)
+    assert abs(al - 4.0 * (1.0 - 1.0 / L ** 2) / 3.0) < 1e-14
+    d = O.chebsum_coefficients(2, M, al)
+    assert abs(d[1]) < 1e-12 and abs(d[0] - (1.0 - al / 4.0)) < 1e-14 and abs(d[2] - al / 8.0) < 1e-14
+    assert np.max(np.abs(O.chebsum_roots(2, M) - O.roots(L))) < 1e-13
+
+
+@pytest.mark.parametrize("L", [8, 16, 64, 256])
+def test_rank4_order_conditions_exactly_fourth(L):
+    """prod (1 + a_l z) = e^z + O(z^5): e_n n! = 1 for n <= 4 (Eq. 5), but not for n = 5."""
+    c = _taylor_coeffs(O.chebsum_step_sizes(4, L // 4))
+    fac = np.array([1.0, 1.0, 2.0, 6.0, 24.0, 120.0])
+    err = np.abs(c[:6] * fac - 1.0)
+    assert np.all(err[:5] < 1e-11), err
+    assert err[5] > 0.05
+
+
+@pytest.mark.parametrize("L", [8, 32, 128])
+def test_rank4_product_equals_chebyshev_sum(L):
+    """The roots reproduce B = d_0 + 2 sum d_k T_{kM}(1 + z/(M^2 alpha)), the T_j taken from
+    numpy's Chebyshev basis, at real and complex z."""
+    M = L // 4
+    al = O.chebsum_alpha(4, M)
+    d = O.chebsum_coefficients(4, M, al)
+    a = O.chebsum_step_sizes(4, M)
+    rng = np.random.default_rng(L)
+    b = O.chebsum_beta(4, M)
+    z = -b * rng.random(40) + 1j * 0.05 * b * rng.standard_normal(40)
+    x = 1.0 + z / (M * M * al)
+    B = d[0] + 2.0 * sum(d[k] * C.Chebyshev.basis(k * M)(x) for k in range(1, 5))
+    Rp = R_product(z, a)
+    assert np.max(np.abs(Rp - B)) < 1e-9 * max(1.0, np.max(np.abs(B)))
+
+
+@pytest.mark.parametrize("L", [8, 16, 64])
+def test_rank4_bounded_on_extent_and_alpha_maximal(L):
+    """|R| <= 1 on [-beta, 0] (dense grid, product form); the order-condition polynomial for an
+    alpha 1e-6 larger leaves the bound, 1e-6 smaller stays inside (Eq. 6)."""
+    M = L // 4
+    a = O.chebsum_step_sizes(4, M)
+    b = O.chebsum_beta(4, M)
+    x = -b * np.linspace(0.0, 1.0, 40001)
+    assert np.max(np.abs(R_product(x, a))) <= 1.0 + 1e-10
+    al = O.chebsum_alpha(4, M)
+    y = np.cos(np.linspace(0.0, np.pi, 200001))
+
+    def qmax(alpha_):
+        d = O.chebsum_coefficients(4, M, alpha_)
+        c = 2.0 * d
+        c[0] = d[0]
+        return np.max(np.abs(C.chebval(y, c)))
+
+    assert qmax(al * (1 + 1e-6)) > 1.0 + 1e-9
+    assert qmax(al * (1 - 1e-6)) <= 1.0
+
+
+@pytest.mark.parametrize("L", [8, 64])
+def test_rank4_conjugate_pairs_positive_real_part(L):
+    a = O.chebsum_step_sizes(4, L // 4)
+    assert np.array_equal(a[::-1], np.conj(a))
+    assert np.all(a.real > 0) and np.all(np.abs(a.imag) > 0)
+    assert abs(a.sum() - 1.0) < 1e-13
+
+
+def test_rank4_fourth_order_against_expm():
+    """A rank-4 plan converges at order 4 to expm on a variable-kappa periodic problem (the
+    rank-2 plan, same problem, at order 2)."""
+    scipy_linalg = pytest.importorskip("scipy.linalg")
+    rng = np.random.default_rng(3)
+    shape = (8, 8)
+    pr = _prob(2, "periodic", "field", 1.0, np.exp(0.5 * rng.standard_normal(shape)))
+    A = dense(pr, shape)
+    u0 = rng.random(shape)
+    t_end = 2.0
+    ref = scipy_linalg.expm(t_end * A) @ u0.ravel()
+    a = O.plan(16, N=4)["a"]
+    errs = [np.linalg.norm(O.frkc2_step(u0, a, t_end / m, pr, m).ravel() - ref) for m in (16, 32, 64)]
+    slope = np.log2(errs[0] / errs[1]), np.log2(errs[1] / errs[2])
+    assert all(3.8 < s < 4.2 for s in slope), slope
+
+
+@pytest.mark.parametrize("L", [16, 64, 256])
+def test_rank4_plan_Q_near_single_factor_bound(L):
+    """The rank-4 plan meets 10 L^2 with a realised Q within 1.3x of the largest single factor
+    max |1 + a_l x| (a lower bound for every ordering, Eq. 10)."""
+    p = O.plan(L, N=4)
+    x = -p["beta"] * np.linspace(0.0, 1.0, 16 * L + 1)
+    single = np.max(np.abs(1.0 + np.outer(p["a"], x)))
+    assert p["Q"] <= 10.0 * L * L
+    assert single <= p["Q"] * (1 + 1e-12) <= 1.3 * single
+    assert sorted(p["order"]) == list(range(L))
