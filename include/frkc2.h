@@ -71,8 +71,15 @@ enum { FRKC2_FP64 = 0, FRKC2_FP32 = 1, FRKC2_MIXED = 2, FRKC2_DFLOAT = 3 };
  * that 2D fixed-conductivity steps apply each pair to the real state in real arithmetic
  * (w' = w + 2 T Re(a) f(w) + T^2 |a|^2 f(f(w)), exact for a linear f): about half the
  * arithmetic and memory traffic of two complex stages, at an internal amplification
- * Q of about 0.12 L^4 instead of about L^2. */
-enum { FRKC2_PLAN_STRICT = 1, FRKC2_PLAN_GREEDY = 2, FRKC2_PLAN_LEBEDEV = 4, FRKC2_PLAN_PAIRED = 8 };
+ * Q of about 0.12 L^4 instead of about L^2.  ORDER4 takes the step sizes of the rank-4
+ * polynomial (Eq. 7 with N = 4): fourth order on linear problems (frkc2_plan). */
+enum {
+  FRKC2_PLAN_STRICT = 1,
+  FRKC2_PLAN_GREEDY = 2,
+  FRKC2_PLAN_LEBEDEV = 4,
+  FRKC2_PLAN_PAIRED = 8,
+  FRKC2_PLAN_ORDER4 = 16
+};
 
 typedef struct frkc2_plan_s* frkc2_plan_t;
 
@@ -135,6 +142,16 @@ typedef struct {
  *   flags : FRKC2_PLAN_STRICT makes an unmet Q bound an error (FRKC2_EPLAN); otherwise the
  *           ordering with the smallest realised Q is kept.  FRKC2_PLAN_GREEDY or
  *           FRKC2_PLAN_LEBEDEV use that ordering alone (both together: FRKC2_EINVAL).
+ *           FRKC2_PLAN_ORDER4: the rank-4 polynomial of Eq. 7 (N = 4, s = 4M, s a multiple
+ *           of 4, else FRKC2_EINVAL; nu0 > 0 gives FRKC2_EUNSUPPORTED), read as
+ *           B = d_0 + 2 sum_{k=1}^4 d_k T_{kM}(1 + z/(M^2 alpha)) with the d_k from the order
+ *           conditions R^(n)(0) = 1, n <= 4 (Eq. 5), and alpha the largest value keeping
+ *           |R| <= 1 on [-2 M^2 alpha, 0] (bisection); beta = 2 M^2 alpha (about 0.254 s^2;
+ *           2.785 at s = 4, where B is the Taylor polynomial of e^z).  The step sizes are
+ *           a_l = 1/(M^2 alpha (1 - zeta_l)) (Eq. 8) for the 4M roots zeta_l in conjugate
+ *           pairs.  Ordering: Lebedev-Finogenov first at every s (realised Q about 0.1 s^2),
+ *           the greedy n-loop only if that misses 10 s^2.  The steps of frkc2_step with such
+ *           a plan are fourth order for linear f (second order for kappa(u)).
  *   out   : receives a new plan; release it with frkc2_plan_destroy.
  * Cost: the greedy is O(s^3) host work (tens of ms at s = 64, about 1 s at s = 256); the
  * Lebedev-Finogenov order costs O(s^2) (about 0.2 s at s = 1024).                          */

@@ -90,6 +90,170 @@ std::vector<cplx> damped_steps(int L, double nu0) {
   return a;
 }
 
+// ---- Rank-N polynomial (Eq. 7 with N = 4): B(z) = d_0 + 2 sum_{k=1}^N d_k T_{kM}(x),
+// x = 1 + z/(M^2 alpha), L = N M.  With T_{kM} = T_k(T_M), B(z) = Q(T_M(x)) for the degree-N
+// Chebyshev series Q(y) = d_0 + 2 sum d_k T_k(y).
+
+// n-th derivative of T_j at 1: prod_{m<n} (j^2 - m^2)/(2m+1).
+double cheb_deriv_at_one(int j, int n) {
+  double p = 1.0;
+  for (int m = 0; m < n; ++m) p *= (double(j) * j - double(m) * m) / (2.0 * m + 1.0);
+  return p;
+}
+
+constexpr int RANK_MAX = 4;
+
+// d_0..d_N from the linear order conditions R(0) = 1, R^(n)(0) = 1 (Eq. 5), by Gaussian
+// elimination with partial pivoting.  Returns false on a singular system.
+bool chebsum_d(int N, int M, double al, double* d) {
+  double A[RANK_MAX + 1][RANK_MAX + 2];
+  for (int n = 0; n <= N; ++n) {
+    for (int k = 0; k <= N; ++k) {
+      if (n == 0)
+        A[n][k] = k == 0 ? 1.0 : 2.0;
+      else
+        A[n][k] = k == 0 ? 0.0 : 2.0 * cheb_deriv_at_one(k * M, n) / std::pow(double(M) * M * al, n);
+    }
+    A[n][N + 1] = 1.0;
+  }
+  for (int c = 0; c <= N; ++c) {
+    int piv = c;
+    for (int r = c + 1; r <= N; ++r)
+      if (std::abs(A[r][c]) > std::abs(A[piv][c])) piv = r;
+    if (A[piv][c] == 0.0) return false;
+    if (piv != c)
+      for (int k = 0; k <= N + 1; ++k) std::swap(A[c][k], A[piv][k]);
+    for (int r = 0; r <= N; ++r) {
+      if (r == c) continue;
+      const double f = A[r][c] / A[c][c];
+      for (int k = c; k <= N + 1; ++k) A[r][k] -= f * A[c][k];
+    }
+  }
+  for (int k = 0; k <= N; ++k) d[k] = A[k][N + 1] / A[k][k];
+  return true;
+}
+
+// Monomial coefficients q[0..N] of Q(y), from T_0 = 1, T_1 = y, T_{k+1} = 2y T_k - T_{k-1}.
+void chebsum_monomial(int N, const double* d, double* q) {
+  double T[RANK_MAX + 1][RANK_MAX + 1] = {};
+  T[0][0] = 1.0;
+  if (N >= 1) T[1][1] = 1.0;
+  for (int k = 1; k < N; ++k)
+    for (int i = 0; i <= N; ++i) T[k + 1][i] = (i > 0 ? 2.0 * T[k][i - 1] : 0.0) - T[k - 1][i];
+  for (int i = 0; i <= N; ++i) {
+    q[i] = d[0] * T[0][i];
+    for (int k = 1; k <= N; ++k) q[i] += 2.0 * d[k] * T[k][i];
+  }
+}
+
+// All complex roots of sum_{i<=n} c[i] y^i (c[n] != 0, n <= RANK_MAX) by the Aberth-Ehrlich
+// simultaneous iteration from points on a circle, then Newton steps on each root.
+std::vector<cplx> poly_roots(int n, const double* c) {
+  auto P = [&](cplx y, cplx* dp) {
+    cplx p = c[n], q = 0.0;
+    for (int i = n - 1; i >= 0; --i) {
+      q = q * y + p;
+      p = p * y + c[i];
+    }
+    *dp = q;
+    return p;
+  };
+  double rad = 0.0;
+  for (int i = 0; i < n; ++i) rad = std::max(rad, std::pow(std::abs(c[i] / c[n]), 1.0 / (n - i)));
+  rad = std::max(rad, 1e-3);
+  std::vector<cplx> z(n);
+  for (int i = 0; i < n; ++i) z[i] = std::polar(rad, 2.0 * M_PI * (i + 0.25) / n);
+  for (int it = 0; it < 500; ++it) {
+    double moved = 0.0;
+    for (int i = 0; i < n; ++i) {
+      cplx dp;
+      const cplx p = P(z[i], &dp);
+      if (p == 0.0) continue;
+      const cplx ratio = p / dp;
+      cplx s = 0.0;
+      for (int j = 0; j < n; ++j)
+        if (j != i) s += 1.0 / (z[i] - z[j]);
+      const cplx w = ratio / (1.0 - ratio * s);
+      z[i] -= w;
+      moved = std::max(moved, std::abs(w) / std::max(1.0, std::abs(z[i])));
+    }
+    if (moved < 1e-17) break;
+  }
+  for (cplx& y : z)
+    for (int it = 0; it < 3; ++it) {
+      cplx dp;
+      const cplx p = P(y, &dp);
+      if (dp == 0.0) break;
+      y -= p / dp;
+    }
+  return z;
+}
+
+// max |Q(y)| on [-1, 1] from y = -1 and the real critical points inside (Q(1) = R(0) = 1 with
+// Q'(1) = alpha > 0, so y = 1 is left out).
+double chebsum_max_abs_Q(int N, const double* d) {
+  double q[RANK_MAX + 1], dq[RANK_MAX];
+  chebsum_monomial(N, d, q);
+  for (int i = 1; i <= N; ++i) dq[i - 1] = double(i) * q[i];
+  auto Qv = [&](double y) {
+    double p = q[N];
+    for (int i = N - 1; i >= 0; --i) p = p * y + q[i];
+    return p;
+  };
+  double m = std::abs(Qv(-1.0));
+  for (const cplx& r : poly_roots(N - 1, dq))
+    if (std::abs(r.imag()) <= 1e-12 * std::max(1.0, std::abs(r.real())) && r.real() > -1.0 &&
+        r.real() < 1.0)
+      m = std::max(m, std::abs(Qv(r.real())));
+  return m;
+}
+
+// alpha_M: the largest alpha with |Q| <= 1 on [-1, 1] (Eq. 6), by bisection; the feasible
+// alphas form an interval from 0.  N = 2 gives 4(1 - 1/L^2)/3 (d_1 = 0).
+double chebsum_alpha(int N, int M) {
+  double lo = 0.25, hi = 4.0, d[RANK_MAX + 1];
+  for (int it = 0; it < 200; ++it) {
+    const double mid = 0.5 * (lo + hi);
+    if (mid == lo || mid == hi) break;
+    if (chebsum_d(N, M, mid, d) && chebsum_max_abs_Q(N, d) <= 1.0)
+      lo = mid;
+    else
+      hi = mid;
+  }
+  return lo;
+}
+
+// Step sizes a_l = 1/(M^2 alpha (1 - zeta_l)) of the rank-N polynomial in root order: the
+// roots of T_M(x) = y_i for the N roots y_i of Q are x = cos((arccos y_i + 2 pi k)/M),
+// k = 0..M-1; those with Im x > 0 sorted by decreasing Re x are zeta_0..zeta_{L/2-1} and
+// zeta_{L-1-j} = conj(zeta_j).  Returns an empty vector if the roots are not in conjugate
+// pairs off the real axis.
+std::vector<cplx> chebsum_steps(int N, int M, double* beta_out) {
+  const int L = N * M;
+  const double al = chebsum_alpha(N, M);
+  double d[RANK_MAX + 1], q[RANK_MAX + 1];
+  if (!chebsum_d(N, M, al, d)) return {};
+  chebsum_monomial(N, d, q);
+  std::vector<cplx> upper;
+  for (const cplx& y : poly_roots(N, q)) {
+    const cplx th = std::acos(y);
+    for (int k = 0; k < M; ++k) {
+      const cplx x = std::cos((th + 2.0 * M_PI * double(k)) / double(M));
+      if (x.imag() > 0.0) upper.push_back(x);
+    }
+  }
+  if (int(upper.size()) != L / 2) return {};
+  std::stable_sort(upper.begin(), upper.end(),
+                   [](const cplx& u, const cplx& v) { return u.real() > v.real(); });
+  std::vector<cplx> a(L);
+  for (int j = 0; j < L / 2; ++j) {
+    a[j] = 1.0 / (double(M) * M * al * (1.0 - upper[j]));
+    a[L - 1 - j] = std::conj(a[j]);
+  }
+  *beta_out = 2.0 * double(M) * M * al;
+  return a;
+}
+
 // Largest x with |R(-x)| <= 1 near `guess` (bisection on the last crossing of |R| = 1).
 double stability_extent(const std::vector<cplx>& a, double guess) {
   auto absR = [&](double x) {
@@ -279,8 +443,18 @@ frkc2_status frkc2_plan(int s, double nu, unsigned flags, frkc2_plan_t* out) {
   if (!(nu >= 0.0 && nu < 0.9)) return FRKC2_EINVAL;
   *out = nullptr;
   const int L = s;
-  const std::vector<cplx> a = nu > 0.0 ? damped_steps(L, nu) : root_order_steps(L);
-  const double beta = nu > 0.0 ? stability_extent(a, (1.0 - 0.5 * nu) * poly_beta(L)) : poly_beta(L);
+  const bool order4 = flags & FRKC2_PLAN_ORDER4;
+  if (order4 && (L % 4)) return FRKC2_EINVAL;
+  if (order4 && nu > 0.0) return FRKC2_EUNSUPPORTED;
+  double beta = 0.0;
+  std::vector<cplx> a;
+  if (order4) {
+    a = chebsum_steps(4, L / 4, &beta);
+    if (a.empty()) return FRKC2_EPLAN;
+  } else {
+    a = nu > 0.0 ? damped_steps(L, nu) : root_order_steps(L);
+    beta = nu > 0.0 ? stability_extent(a, (1.0 - 0.5 * nu) * poly_beta(L)) : poly_beta(L);
+  }
   const int S = 16 * L, P = 16 * L, n_max = 10;
   const double bound = 10.0 * double(L) * double(L);
   std::vector<int> best_order;
@@ -301,8 +475,10 @@ frkc2_status frkc2_plan(int s, double nu, unsigned flags, frkc2_plan_t* out) {
   const bool paired = flags & FRKC2_PLAN_PAIRED;
   if (int(force_greedy) + int(force_lebedev) + int(paired) > 1) return FRKC2_EINVAL;
   if (paired) consider(order_paired(L), 0);
-  bool run_greedy = !paired && (force_greedy || (!force_lebedev && L <= 256));
-  if (!paired && (force_lebedev || (!force_greedy && L > 256))) {
+  // rank-4 plans take the Lebedev-Finogenov order first at every s: on those roots its
+  // realised Q is about 0.1 s^2 where the greedy reaches a few s^2
+  bool run_greedy = !paired && (force_greedy || (!force_lebedev && L <= 256 && !order4));
+  if (!paired && (force_lebedev || (!force_greedy && (L > 256 || order4)))) {
     const double q = consider(order_lebedev(L), 0);
     if (!force_lebedev && q > bound) run_greedy = true;
   }

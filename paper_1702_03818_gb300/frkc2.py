@@ -27,7 +27,7 @@ OK, EINVAL, EUNSTABLE, EPLAN, ENOMEM, ECUDA, ETIMEOUT, ENONFINITE, EUNSUPPORTED,
 BC_PERIODIC, BC_DIRICHLET, BC_NEUMANN = 0, 1, 2
 KAPPA_CONST, KAPPA_FIELD, KAPPA_POWER = 0, 1, 2
 FP64, FP32, MIXED, DFLOAT = 0, 1, 2, 3
-PLAN_STRICT, PLAN_GREEDY, PLAN_LEBEDEV, PLAN_PAIRED = 1, 2, 4, 8
+PLAN_STRICT, PLAN_GREEDY, PLAN_LEBEDEV, PLAN_PAIRED, PLAN_ORDER4 = 1, 2, 4, 8, 16
 PRECISION = {"fp64": FP64, "fp32": FP32, "mixed": MIXED, "dfloat": DFLOAT}
 PROBE_PACKED = 16  # frkc2_fma_probe: packed two-lane FP32 FMAs
 BC = {"periodic": BC_PERIODIC, "dirichlet": BC_DIRICHLET, "neumann": BC_NEUMANN}

@@ -1,0 +1,102 @@
+"""GPU parity of frkc2_step with rank-4 plans (FRKC2_PLAN_ORDER4: the N = 4 polynomial of
+Eq. 7, fourth order on linear problems) against the FP64 oracle, and the fourth order itself
+measured through the CUDA path on a Fourier mode with a closed-form solution.
+
+The kernels are the FRKC2 stage kernels; only the step sizes and the extent change, so each
+case runs the kernel the library picks for it (or the one the tuning names) on the rank-4
+step sizes.  Tolerances as for the rank-2 plans (relative error against the FP64 oracle).
+"""
+import numpy as np
+import pytest
+
+from oracle import frkc2_oracle as O
+from helpers import oracle_problem, rel_err, seeded_case
+from test_gpu_forward import F, rounded_field, run_gpu, torch, dev, lib_problem
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"fp64": 1e-11, "fp32": 1e-4, "mixed": 1e-6, "dfloat": 1e-6}
+
+CASES = [
+    # shape, bc, kappa, s, nsteps, tuning (kernel, k)
+    ((100, 77), "periodic", "field", 16, 2, (0, 0)),     # 2D default kernels
+    ((70, 130), "dirichlet", "field", 32, 2, (1, 3)),    # generic tiles, k = 3 (ragged last pass)
+    ((64, 64), "periodic", "const", 64, 1, (0, 0)),
+    ((260, 300), "dirichlet", "field", 32, 2, (0, 0)),   # FP32: the wavefront pass (nx = 300)
+    ((1000,), "periodic", "field", 64, 2, (0, 0)),       # 1D whole-job cluster kernel
+    ((12, 10, 14), "dirichlet", "field", 16, 1, (0, 0)),  # 3D
+    ((34, 20), "periodic", "power", 16, 2, (0, 0)),      # kappa(u): generic tiles
+]
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "mixed", "dfloat"])
+@pytest.mark.parametrize("case", CASES, ids=lambda c: f"{'x'.join(map(str, c[0]))}-{c[1]}-{c[2]}-s{c[3]}")
+def test_rank4_step_parity(case, prec):
+    shape, bc, kappa, s, nsteps, (kernel, k) = case
+    if prec == "dfloat" and (len(shape) != 2 or kappa == "power" or kernel == 1):
+        pytest.skip("DFLOAT covers 2D fixed-conductivity steps on kernels 2 and 3")
+    u0, field = seeded_case(shape, bc, kappa, 700 + s)
+    oplan = O.plan(s, N=4)
+    plan = F.frkc2_plan(s, flags=F.PLAN_ORDER4)
+    assert np.array_equal(plan.info()["order"], oplan["order"])
+    fo = rounded_field(field, prec)
+    opr = oracle_problem(len(shape), bc, kappa, 1.0, fo)
+    dt = 0.9 * oplan["beta"] / O.rho_bound(opr, u0)
+    u0g = u0.astype(np.float32).astype(np.float64) if prec == "fp32" else u0
+    ref = O.frkc2_step(u0g, oplan["a"], dt, opr, nsteps)
+    tune = F.make_tuning(k=k, kernel=kernel) if (kernel or k) else None
+    got, st = run_gpu(plan, shape, bc, kappa, prec, u0, field, dt, nsteps, tune=tune)
+    assert st == F.OK
+    assert rel_err(got, ref) < TOL[prec], rel_err(got, ref)
+
+
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-11), ("fp32", 5e-4)])
+def test_rank4_paired_real_pairs(prec, tol):
+    """A rank-4 plan with its conjugates adjacent runs on the real pair kernel (kernel 4)."""
+    shape, bc, kappa, s = (90, 70), "periodic", "field", 16
+    u0, field = seeded_case(shape, bc, kappa, 777)
+    oplan = O.plan(s, N=4, method="paired")
+    plan = F.frkc2_plan(s, flags=F.PLAN_ORDER4 | F.PLAN_PAIRED)
+    assert np.array_equal(plan.info()["order"], oplan["order"])
+    fo = rounded_field(field, prec)
+    opr = oracle_problem(2, bc, kappa, 1.0, fo)
+    dt = 0.9 * oplan["beta"] / O.rho_bound(opr, u0)
+    u0g = u0.astype(np.float32).astype(np.float64) if prec == "fp32" else u0
+    ref = O.frkc2_step(u0g, oplan["a"], dt, opr, 2)
+    got, st = run_gpu(plan, shape, bc, kappa, prec, u0, field, dt, 2, tune=F.make_tuning(kernel=4))
+    assert st == F.OK
+    assert rel_err(got, ref) < tol, rel_err(got, ref)
+
+
+def test_rank4_fourth_order_on_gpu_fourier_mode():
+    """u0 = sin(2 pi kx x / n) sin(2 pi ky y / n) on a periodic grid with constant kappa is an
+    eigenvector of f with lambda = -(4 kappa / dx^2)(sin^2(pi kx / n) + sin^2(pi ky / n)), so
+    the exact solution is e^{lambda t} u0.  Through the CUDA path (FP64) the rank-4 plan's
+    error falls 16x per halving of dt, the rank-2 plan's 4x."""
+    n, kx, ky, kap = 64, 1, 2, 1.0
+    dx = 1.0 / n
+    x = np.arange(n) / n
+    u0 = np.outer(np.sin(2 * np.pi * ky * x), np.sin(2 * np.pi * kx * x))
+    lam = -(4.0 * kap / dx ** 2) * (np.sin(np.pi * kx / n) ** 2 + np.sin(np.pi * ky / n) ** 2)
+    t_end = 8.0 / -lam
+    exact = np.exp(lam * t_end) * u0
+
+    def errors(plan):
+        out = []
+        for m in (32, 64, 128):
+            u = dev(u0, torch.float64)
+            pr = lib_problem((n, n), "periodic", "const", "fp64", dx, c=kap)
+            ws = torch.empty(F.frkc2_workspace_size(pr, None), dtype=torch.uint8, device="cuda")
+            F.frkc2_workspace_reset(ws)
+            F.frkc2_step(plan, pr, t_end / m, m, 0.0, u, ws, None)
+            assert F.frkc2_workspace_status(ws) == F.OK
+            out.append(np.linalg.norm(u.cpu().numpy() - exact) / np.linalg.norm(exact))
+        return np.array(out)
+
+    e4 = errors(F.frkc2_plan(16, flags=F.PLAN_ORDER4))
+    e2 = errors(F.frkc2_plan(16))
+    s4 = np.log2(e4[:-1] / e4[1:])
+    s2 = np.log2(e2[:-1] / e2[1:])
+    assert np.all((s4 > 3.9) & (s4 < 4.2)), (e4, s4)
+    assert np.all((s2 > 1.9) & (s2 < 2.2)), (e2, s2)
+    assert e4[-1] < 1e-3 * e2[-1]

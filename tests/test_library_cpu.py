@@ -319,3 +319,32 @@ def test_precision_policy_choices():
     for bad in [(0, 1e-4), (10, 0.0)]:
         with pytest.raises(F.Frkc2Error):
             F.frkc2_precision_policy(greedy, p2, *bad)
+
+
+@pytest.mark.parametrize("L", [4, 8, 12, 64, 256])
+def test_rank4_plan_matches_oracle(L):
+    """FRKC2_PLAN_ORDER4: the host plan's rank-4 step sizes, extent and stage order agree with
+    the oracle's (its own root finder and Chebyshev routines)."""
+    lib = F.frkc2_plan(L, flags=F.PLAN_ORDER4).info()
+    ora = O.plan(L, N=4)
+    assert np.array_equal(lib["order"], ora["order"])
+    assert np.max(np.abs(lib["a"] - ora["a"])) < 1e-13 * np.max(np.abs(ora["a"]))
+    assert abs(lib["beta"] / ora["beta"] - 1.0) < 1e-13
+    assert abs(lib["Q"] / ora["Q"] - 1.0) < 1e-9
+
+
+def test_rank4_plan_flags_and_errors():
+    for bad in (6, 10, 18):
+        with pytest.raises(F.Frkc2Error) as e:
+            F.frkc2_plan(bad, flags=F.PLAN_ORDER4)
+        assert e.value.status == F.EINVAL
+    with pytest.raises(F.Frkc2Error) as e:
+        F.frkc2_plan(16, nu=0.1, flags=F.PLAN_ORDER4)
+    assert e.value.status == F.EUNSUPPORTED
+    g = F.frkc2_plan(16, flags=F.PLAN_ORDER4 | F.PLAN_GREEDY).info()
+    go = O.plan(16, N=4, method="greedy")
+    assert np.array_equal(g["order"], go["order"])
+    p = F.frkc2_plan(16, flags=F.PLAN_ORDER4 | F.PLAN_PAIRED).info()
+    assert np.array_equal(p["a"][1::2], np.conj(p["a"][0::2]))
+    # a strict rank-4 plan meets 10 L^2 with room to spare
+    assert F.frkc2_plan(4096, flags=F.PLAN_ORDER4 | F.PLAN_STRICT).info()["Q"] < 0.2 * 4096 ** 2
