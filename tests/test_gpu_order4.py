@@ -100,3 +100,70 @@ def test_rank4_fourth_order_on_gpu_fourier_mode():
     assert np.all((s4 > 3.9) & (s4 < 4.2)), (e4, s4)
     assert np.all((s2 > 1.9) & (s2 < 2.2)), (e2, s2)
     assert e4[-1] < 1e-3 * e2[-1]
+
+
+def test_rank4_s4_step_is_classical_rk4():
+    """At s = 4 the rank-4 polynomial is the Taylor polynomial of e^z, so on a linear problem the
+    factorised step equals the classical RK4 step (the oracle's ``rk4``, its Butcher tableau,
+    not the stage loop) to rounding -- through the CUDA path, FP64, 2D and 1D."""
+    for shape, bc, kappa in [((48, 40), "periodic", "field"), ((300,), "dirichlet", "const")]:
+        u0, field = seeded_case(shape, bc, kappa, 4242)
+        opr = oracle_problem(len(shape), bc, kappa, 1.0, field)
+        plan = F.frkc2_plan(4, flags=F.PLAN_ORDER4)
+        dt = 0.9 * plan.info()["beta"] / O.rho_bound(opr, u0)
+        ref = O.rk4(u0, dt, opr, 3)
+        got, st = run_gpu(plan, shape, bc, kappa, "fp64", u0, field, dt, 3)
+        assert st == F.OK
+        assert rel_err(got, ref) < 1e-12, rel_err(got, ref)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_rank4_batched_matches_oracle(prec):
+    """Rank-4 plans of different s in one batched launch (streaming items in FP64, register-tiled
+    regions in FP32) against the oracle's rank-4 stage loop."""
+    specs = [(20, 33, 8, 2), (64, 64, 16, 1), (150, 97, 32, 2), (7, 5, 12, 3), (40, 128, 16, 1)]
+    dtp = {"fp64": torch.float64, "fp32": torch.float32}[prec]
+    items = []
+    for i, (ny, nx, s, nsteps) in enumerate(specs):
+        u0, field = seeded_case((ny, nx), "periodic", "field", 950 + 3 * i)
+        fo = rounded_field(field, prec)
+        opr = oracle_problem(2, "periodic", "field", 1.0, fo)
+        op = O.plan(s, N=4)
+        dt = 0.9 * op["beta"] / O.rho_bound(opr)
+        pr = F.make_problem(2, (nx, ny), 1.0, "periodic", "field", prec, kappa_field=dev(field, dtp))
+        u0g = u0.astype(np.float32).astype(np.float64) if prec == "fp32" else u0
+        items.append(dict(ref=O.frkc2_step(u0g, op["a"], dt, opr, nsteps), dt=dt, nsteps=nsteps, pr=pr,
+                          u=dev(u0, dtp), plan=F.frkc2_plan(s, flags=F.PLAN_ORDER4)))
+    plans = [it["plan"] for it in items]
+    probs = [it["pr"] for it in items]
+    nst = [it["nsteps"] for it in items]
+    ws = torch.empty(F.frkc2_batch_workspace_size(plans, probs, nst, None), dtype=torch.uint8, device="cuda")
+    F.frkc2_workspace_reset(ws)
+    F.frkc2_step_batched(plans, probs, [it["dt"] for it in items], nst, [it["u"] for it in items], ws, None)
+    assert F.frkc2_workspace_status(ws) == F.OK
+    for it in items:
+        err = rel_err(it["u"].double().cpu().numpy(), it["ref"])
+        assert err < TOL[prec], err
+
+
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-10), ("fp32", 2e-3)])
+def test_rank4_adjoint_matches_oracle(prec, tol):
+    """The discrete adjoint of a rank-4 step loop (state and kappa gradients) against the
+    oracle's full-tape adjoint on the same rank-4 step sizes."""
+    from test_gpu_adjoint import gpu_adjoint
+
+    shape, bc, kappa, s, nsteps, ckpt = (48, 40), "periodic", "field", 16, 4, 2
+    u0, field = seeded_case(shape, bc, kappa, 515)
+    fo = rounded_field(field, prec)
+    u0o = u0 if prec != "fp32" else u0.astype(np.float32).astype(np.float64)
+    opr = oracle_problem(2, bc, kappa, 1.0, fo)
+    oplan = O.plan(s, N=4)
+    plan = F.frkc2_plan(s, flags=F.PLAN_ORDER4)
+    dt = 0.8 * oplan["beta"] / O.rho_bound(opr, u0o)
+    g = np.random.default_rng(8).standard_normal(shape)
+    if prec == "fp32":
+        g = g.astype(np.float32).astype(np.float64)
+    ref_u, ref_k = O.frkc2_adjoint(u0o, oplan["a"], dt, opr, nsteps, g)
+    du, dk = gpu_adjoint(plan, shape, bc, kappa, prec, u0, field, dt, nsteps, ckpt, g)
+    assert rel_err(du, ref_u) < tol, rel_err(du, ref_u)
+    assert rel_err(dk, ref_k) < tol, rel_err(dk, ref_k)

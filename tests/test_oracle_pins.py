@@ -1017,3 +1017,16 @@ def test_rank4_plan_Q_near_single_factor_bound(L):
     assert p["Q"] <= 10.0 * L * L
     assert single <= p["Q"] * (1 + 1e-12) <= 1.3 * single
     assert sorted(p["order"]) == list(range(L))
+
+
+def test_rank4_s4_step_equals_rk4_step():
+    """On a linear problem the 4-stage rank-4 factorised step and the classical RK4 tableau
+    (``rk4``) are the same map."""
+    rng = np.random.default_rng(11)
+    shape = (12, 10)
+    pr = _prob(2, "dirichlet", "field", 1.0, np.exp(0.5 * rng.standard_normal(shape)))
+    u0 = rng.random(shape)
+    T = 0.9 * O.chebsum_beta(4, 1) / O.rho_bound(pr)
+    a = O.plan(4, N=4)["a"]
+    ref = O.rk4(u0, T, pr, 3)
+    assert np.max(np.abs(O.frkc2_step(u0, a, T, pr, 3) - ref)) < 1e-14 * np.max(np.abs(ref))
