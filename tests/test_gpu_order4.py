@@ -167,3 +167,25 @@ def test_rank4_adjoint_matches_oracle(prec, tol):
     du, dk = gpu_adjoint(plan, shape, bc, kappa, prec, u0, field, dt, nsteps, ckpt, g)
     assert rel_err(du, ref_u) < tol, rel_err(du, ref_u)
     assert rel_err(dk, ref_k) < tol, rel_err(dk, ref_k)
+
+
+def test_rank4_adaptive_matches_oracle_controller():
+    """Error-controlled integration (Sec. 3, Eqs. 14-16) with a rank-4 plan: the embedded
+    first-order solution and the controller are those of the rank-2 plans; the GPU takes the
+    oracle's accepted and rejected steps and ends on its state."""
+    shape, bc, kappa, s, t_end, tol = (48, 40), "periodic", "field", 16, 40.0, 1e-5
+    u0, field = seeded_case(shape, bc, kappa, 716)
+    opr = oracle_problem(2, bc, kappa, 1.0, field)
+    rho = O.rho_bound(opr)
+    oplan = O.plan(s, N=4)
+    dt0 = oplan["beta"] / rho
+    ref, st_ref = O.frkc2_adaptive(u0, oplan["a"], oplan["beta"], opr, t_end, tol, dt0, rho=rho)
+    plan = F.frkc2_plan(s, flags=F.PLAN_ORDER4)
+    pr = lib_problem(shape, bc, kappa, "fp64", 1.0, dev(field, torch.float64))
+    ws = torch.empty(F.frkc2_adaptive_workspace_size(pr), dtype=torch.uint8, device="cuda")
+    u = dev(u0, torch.float64)
+    st = F.frkc2_step_adaptive(plan, pr, t_end, tol, dt0, rho, u, ws)
+    assert abs(st["t"] - t_end) < 1e-9 * t_end
+    assert (st["accepted"], st["rejected"]) == (st_ref["accepted"], st_ref["rejected"])
+    assert st_ref["accepted"] >= 2
+    assert rel_err(u.cpu().numpy(), ref) < 1e-10
