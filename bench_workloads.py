@@ -588,8 +588,69 @@ def bruss2d(F, hbm_peak_gbs: float = 6787.2):
             "kernel": "k_bruss2d: persistent cooperative launch, grid barrier between stages"}
 
 
+def order4(F):
+    """Work against accuracy for the rank-2 and rank-4 polynomials (Eq. 7, N = 2 and 4) on one
+    smooth Fourier mode of a 2048^2 periodic constant-kappa grid, whose exact solution is
+    e^{lambda t} u0: s = 64 plans of both ranks at 1, 2, 4 and 8 times their fewest stable steps
+    (dt = 0.9 beta / rho) to t with lambda t = -2, each run timed (CUDA events) and compared with
+    the closed form.  Reported: time, cell-stage/s and relative L2 error per run, the observed
+    order, and the time each rank needs for a relative error of 1e-8 (interpolated in log-log)."""
+    torch = _torch()
+    n, s, kx, ky = 2048, 64, 3, 5
+    dx = 1.0 / n
+    x = np.arange(n) / n
+    u0 = np.outer(np.sin(2 * np.pi * ky * x), np.sin(2 * np.pi * kx * x))
+    lam = -(4.0 / dx ** 2) * (np.sin(np.pi * kx / n) ** 2 + np.sin(np.pi * ky / n) ** 2)
+    t_end = 2.0 / -lam
+    exact = np.exp(lam * t_end) * u0
+    pr = F.make_problem(2, (n, n), dx, "periodic", "const", "fp64", kappa_c=1.0)
+    rho = torch.zeros(1, dtype=torch.float64, device="cuda")
+    F.frkc2_rho_bound(pr, None, rho)
+    ws = torch.empty(F.frkc2_workspace_size(pr), dtype=torch.uint8, device="cuda")
+    out = {}
+    for name, flags in (("rank2", 0), ("rank4", F.PLAN_ORDER4)):
+        plan = F.frkc2_plan(s, flags=flags)
+        beta = plan.info()["beta"]
+        m0 = int(np.ceil(t_end * rho.item() / (0.9 * beta)))
+        runs = []
+        for f in (1, 2, 4, 8):
+            m = m0 * f
+            u = torch.as_tensor(u0, dtype=torch.float64, device="cuda")
+            u_init = u.clone()
+            F.frkc2_workspace_reset(ws)
+
+            def run():
+                u.copy_(u_init)
+                F.frkc2_step(plan, pr, t_end / m, m, rho.item(), u, ws)
+
+            ms, _ = _timed(run, warmup=1, reps=3)
+            err = _rel(u.cpu().numpy(), exact)
+            assert F.frkc2_workspace_status(ws) == F.OK
+            runs.append({"nsteps": m, "ms": ms, "cell_stage_per_s": n * n * s * m / (ms * 1e-3), "rel_err": err})
+        e = np.array([r["rel_err"] for r in runs])
+        t = np.array([r["ms"] for r in runs])
+        slope = np.log2(e[:-1] / e[1:]).tolist()
+        how = "interpolated"
+        if e.min() <= 1e-8 <= e.max():
+            i = int(np.argmax(e <= 1e-8))
+            w = (np.log(1e-8) - np.log(e[i - 1])) / (np.log(e[i]) - np.log(e[i - 1]))
+            ms_at = float(np.exp(np.log(t[i - 1]) + w * (np.log(t[i]) - np.log(t[i - 1]))))
+        elif e.max() < 1e-8:  # already below at the fewest stable steps
+            ms_at, how = float(t[0]), "fewest stable steps"
+        else:  # time grows as the steps, error falls as steps^-order: extend the last interval
+            ms_at = float(t[-1] * (e[-1] / 1e-8) ** (1.0 / slope[-1]))
+            how = "extrapolated with the last observed order"
+        out[name] = {"beta": beta, "fewest_stable_steps": m0, "runs": runs, "observed_order": slope,
+                     "ms_for_rel_err_1e-8": ms_at, "ms_for_rel_err_1e-8_from": how}
+    return {"workload": f"order4: 2048^2 periodic const-kappa Fourier mode ({kx},{ky}), s = {s}, lambda t = -2, "
+                        "FP64, exact solution e^(lambda t) u0",
+            "metric": "ms for relative L2 error 1e-8", "unit": "ms",
+            "value": {k: v["ms_for_rel_err_1e-8"] for k, v in out.items()}, "cases": out}
+
+
 WORKLOADS = {"peaks": peaks, "fp32passes": fp32passes, "heat1d": heat1d, "nonlinear3d": nonlinear3d, "adjoint2d": adjoint2d,
-             "batched2d": batched2d, "ssweep": ssweep, "bruss2d": bruss2d, "precision": precision}
+             "batched2d": batched2d, "ssweep": ssweep, "bruss2d": bruss2d, "precision": precision,
+             "order4": order4}
 
 
 def profile_case(F, name: str):
