@@ -189,3 +189,49 @@ def test_rank4_adaptive_matches_oracle_controller():
     assert (st["accepted"], st["rejected"]) == (st_ref["accepted"], st_ref["rejected"])
     assert st_ref["accepted"] >= 2
     assert rel_err(u.cpu().numpy(), ref) < 1e-10
+
+
+LARGE = [(1024, 256), (4096, 128)]  # (s, n): up to the largest stage count a plan accepts
+
+
+@pytest.fixture(scope="module")
+def large_refs():
+    from helpers import oracle_map
+
+    jobs, keys = [], []
+    for s, n in LARGE:
+        u0, field = seeded_case((n, n), "periodic", "field", 880 + n)
+        a = O.chebsum_step_sizes(4, s // 4)[O.order_lebedev(s)]
+        for prec in ("fp64", "fp32"):
+            fo = rounded_field(field, prec)
+            opr = oracle_problem(2, "periodic", "field", 1.0, fo)
+            u = u0.astype(np.float32).astype(np.float64) if prec == "fp32" else u0
+            jobs.append((u, a, 0.9 * O.chebsum_beta(4, s // 4) / O.rho_bound(opr), opr, 1))
+            keys.append((s, prec))
+    return dict(zip(keys, oracle_map(jobs)))
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("s,n", LARGE)
+def test_rank4_large_s_one_step_matches_oracle(large_refs, s, n, prec):
+    """Rank-4 plans at s = 1024 and 4096 (Lebedev-Finogenov order, rounding gain 4.8 and 6.5):
+    one long step against the whole-grid oracle, FP64 and FP32 (the FP32 state stays within
+    1e-4 at every s, unlike the paper's order of the rank-2 polynomial)."""
+    u0, field = seeded_case((n, n), "periodic", "field", 880 + n)
+    plan = F.frkc2_plan(s, flags=F.PLAN_ORDER4)
+    assert np.array_equal(plan.info()["order"], O.order_lebedev(s))
+    a_o = O.chebsum_step_sizes(4, s // 4)[O.order_lebedev(s)]
+    assert np.max(np.abs(plan.info()["a"] - a_o) / np.abs(a_o)) < 1e-9
+    opr = oracle_problem(2, "periodic", "field", 1.0, rounded_field(field, prec))
+    dt = 0.9 * plan.info()["beta"] / O.rho_bound(opr)
+    got, st = run_gpu(plan, (n, n), "periodic", "field", prec, u0, field, dt, 1)
+    assert st == F.OK
+    ref = large_refs[(s, prec)]
+    if prec == "fp64":
+        assert rel_err(got, ref) < 1e-11, rel_err(got, ref)
+        m = ref.mean()
+        from helpers import rel_l2
+
+        assert rel_l2(got - m, ref - m) < 1e-9
+    else:
+        assert rel_err(got, ref) < 1e-4, rel_err(got, ref)
