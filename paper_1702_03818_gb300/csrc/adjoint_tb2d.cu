@@ -156,13 +156,16 @@ __global__ void __launch_bounds__(RT_THREADS, 2) k_tape_tb2d(const AdjTbArgs a) 
   asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
   asm volatile("griddepcontrol.wait;" ::: "memory");
   const RegionIdx R = region_idx<PERIODIC>(nx, ny, k, x0, y0, tx, ty);
-  float fx[4][5];
+  // x faces 0..3 of each row; face 4 (the east face of cell 3) is the east thread's face 0, taken
+  // by shuffle where it is used (the region's east column of threads gets its own face 0 there,
+  // which only reaches halo cells: a wrong edge face spreads one cell per stage, nst <= k)
+  float fx[4][4];
   float2 FY2[5][2];
 #pragma unroll
   for (int r = 0; r < 5; ++r) {
     if (r < 4)
 #pragma unroll
-      for (int c = 0; c < 5; ++c) fx[r][c] = face_x<PERIODIC>(R, a.fx, nx, r, c);
+      for (int c = 0; c < 4; ++c) fx[r][c] = face_x<PERIODIC>(R, a.fx, nx, r, c);
 #pragma unroll
     for (int h = 0; h < 2; ++h)
       FY2[r][h] = make_float2(face_y<PERIODIC>(R, a.fy, nx, ny, r, 2 * h), face_y<PERIODIC>(R, a.fy, nx, ny, r, 2 * h + 1));
@@ -220,14 +223,15 @@ __global__ void __launch_bounds__(RT_THREADS, 2) k_tape_tb2d(const AdjTbArgs a) 
         dxU[c] = u[c + 1] - u[c];
         dxV[c] = v[c + 1] - v[c];
       }
+      const float kx[5] = {fx[r][0], fx[r][1], fx[r][2], fx[r][3], __shfl_down_sync(0xffffffffu, fx[r][0], 1, 16)};
       float2 fU[2], fV[2];
 #pragma unroll
       for (int h = 0; h < 2; ++h) {
         const int c = 2 * h;
-        fU[h].x = fx[r][c + 1] * dxU[c + 1] - fx[r][c] * dxU[c];
-        fU[h].y = fx[r][c + 2] * dxU[c + 2] - fx[r][c + 1] * dxU[c + 1];
-        fV[h].x = fx[r][c + 1] * dxV[c + 1] - fx[r][c] * dxV[c];
-        fV[h].y = fx[r][c + 2] * dxV[c + 2] - fx[r][c + 1] * dxV[c + 1];
+        fU[h].x = kx[c + 1] * dxU[c + 1] - kx[c] * dxU[c];
+        fU[h].y = kx[c + 2] * dxU[c + 2] - kx[c + 1] * dxU[c + 1];
+        fV[h].x = kx[c + 1] * dxV[c + 1] - kx[c] * dxV[c];
+        fV[h].y = kx[c + 2] * dxV[c + 2] - kx[c + 1] * dxV[c + 1];
       }
 #pragma unroll
       for (int h = 0; h < 2; ++h) {
@@ -327,13 +331,10 @@ __global__ void __launch_bounds__(RT_THREADS, 2) k_adjrev_tb2d(const AdjTbArgs a
     sh.fy4[r][tid] = make_float4(face_y<PERIODIC>(R, a.fy, nx, ny, r, 0), face_y<PERIODIC>(R, a.fy, nx, ny, r, 1),
                                  face_y<PERIODIC>(R, a.fy, nx, ny, r, 2), face_y<PERIODIC>(R, a.fy, nx, ny, r, 3));
   }
-  // the faces beyond the thread's own cells, kept in registers: x face 4 of each row and the
-  // y faces of row 4
-  float kxe[4];
-#pragma unroll
-  for (int r = 0; r < 4; ++r) kxe[r] = face_x<PERIODIC>(R, a.fx, nx, r, 4);
-  const float4 kyn = make_float4(face_y<PERIODIC>(R, a.fy, nx, ny, 4, 0), face_y<PERIODIC>(R, a.fy, nx, ny, 4, 1),
-                                 face_y<PERIODIC>(R, a.fy, nx, ny, 4, 2), face_y<PERIODIC>(R, a.fy, nx, ny, 4, 3));
+  // the faces beyond the thread's own cells (x face 4 of each row, the y faces of row 4) are
+  // the east thread's x face 0 and the north thread's row-0 y faces, read from shared memory;
+  // the region's east column and north row of threads take 0 there, which only reaches halo
+  // cells (a wrong face at the region's edge spreads one cell per stage, at most nst <= k)
   // Dirichlet: a boundary face gives all of its sensitivity to its interior cell
   unsigned bE = 0, bW = 0, bN = 0, bS = 0;
   if (!PERIODIC) {
@@ -453,7 +454,7 @@ __global__ void __launch_bounds__(RT_THREADS, 2) k_adjrev_tb2d(const AdjTbArgs a
         dY[c] = ly[c + 1] - ly[c];
       }
       const float4 k4 = sh.fx4[r][tid];
-      const float kx[5] = {k4.x, k4.y, k4.z, k4.w, kxe[r]};
+      const float kx[5] = {k4.x, k4.y, k4.z, k4.w, tx < 15 ? sh.fx4[r][tid + 1].x : 0.f};
       float2 fX[2], fY[2];
 #pragma unroll
       for (int h = 0; h < 2; ++h) {
@@ -469,7 +470,7 @@ __global__ void __launch_bounds__(RT_THREADS, 2) k_adjrev_tb2d(const AdjTbArgs a
       for (int c = 0; c < 4; ++c) ge[c] = dX[c + 1] * (yx[c + 1] - yx[c]) + dY[c + 1] * (yy[c + 1] - yy[c]);
       const float gw0 = __shfl_up_sync(0xffffffffu, ge[3], 1, 16);
       const float4 ks4 = sh.fy4[r][tid];
-      const float4 kn4 = r < 3 ? sh.fy4[r + 1 < 4 ? r + 1 : 3][tid] : kyn;
+      const float4 kn4 = r < 3 ? sh.fy4[r + 1 < 4 ? r + 1 : 3][tid] : (ty < 15 ? sh.fy4[0][tid + 16] : z4);
       float2 gn2[2];
 #pragma unroll
       for (int h = 0; h < 2; ++h) {
