@@ -348,3 +348,24 @@ def test_rank4_plan_flags_and_errors():
     assert np.array_equal(p["a"][1::2], np.conj(p["a"][0::2]))
     # a strict rank-4 plan meets 10 L^2 with room to spare
     assert F.frkc2_plan(4096, flags=F.PLAN_ORDER4 | F.PLAN_STRICT).info()["Q"] < 0.2 * 4096 ** 2
+
+
+def test_degenerate_inputs_on_host():
+    """An empty grid is refused; zero steps succeed without touching the buffers (the addresses
+    here are never dereferenced); negative step counts are refused."""
+    for n in [(0, 5), (5, 0), (0,)]:
+        with pytest.raises(F.Frkc2Error) as e:
+            F.frkc2_workspace_size(F.make_problem(len(n), n, 1.0, "periodic", "const", "fp64", kappa_c=1.0))
+        assert e.value.status == F.EINVAL
+    plan = F.frkc2_plan(16)
+    p = F.make_problem(2, (64, 64), 1.0, "periodic", "const", "fp64", kappa_c=1.0)
+    need = F.frkc2_workspace_size(p)
+    u = _FakeBuf(1 << 20, 64 * 64 * 8)
+    ws = _FakeBuf(1 << 30, need)
+    F.frkc2_step(plan, p, 1.0, 0, 0.0, u, ws, stream=0)
+    with pytest.raises(F.Frkc2Error) as e:
+        F.frkc2_step(plan, p, 1.0, -1, 0.0, u, ws, stream=0)
+    assert e.value.status == F.EINVAL
+    with pytest.raises(F.Frkc2Error) as e:
+        F.frkc2_step(plan, p, float("nan"), 1, 0.0, u, ws, stream=0)
+    assert e.value.status == F.EINVAL
