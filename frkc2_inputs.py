@@ -72,9 +72,12 @@ def grf_torch(n: int, ell: float, seed: int, device="cuda"):
 
 
 def smooth_unit(shape, ell: float, seed: int) -> np.ndarray:
-    """Smooth random field rescaled to the interval [0, 1]."""
+    """Smooth random field rescaled to the interval [0, 1] (a constant field, e.g. one cell,
+    becomes 1/2 everywhere)."""
     g = grf(shape, ell, seed)
     lo, hi = g.min(), g.max()
+    if not hi > lo:
+        return np.full(np.shape(g), 0.5)
     return (g - lo) / (hi - lo)
 
 

@@ -35,6 +35,13 @@ CASES = [
     ((3001,), "dirichlet", "field", "fp64", 16, 3, dict(k=8, tile=(8, 0, 0), kernel=6)),  # 1D cluster
     ((3001,), "periodic", "field", "fp32", 16, 3, dict(k=5, tile=(4, 64, 0), kernel=6)),
 ]
+# grids of one or two cells along an axis, with the library's default kernel for each (the
+# 2D streaming pass, the FP32 register regions, the 1D cluster kernel, the 3D z-streaming
+# pass) and the shared-memory tiles
+CASES += [(shape, bc, "field", prec, 8, 2, dict())
+          for shape in [(1, 1), (2, 2), (1, 3), (1,), (2,), (1, 1, 1), (2, 1, 3)]
+          for bc in ("periodic", "dirichlet") for prec in ("fp64", "fp32")]
+CASES += [((2, 3), bc, "field", "fp64", 8, 2, dict(k=2, kernel=1)) for bc in ("periodic", "dirichlet")]
 
 out = []
 for shape, bc, kappa, prec, s, nsteps, tk in CASES:

@@ -2,7 +2,8 @@
 the main pass kernels -- the 2D streaming pass, the wavefront pass's row copies and stores,
 the register regions, the shared-memory tiles, the 3D z-streaming pass and the 1D cluster
 kernel -- is checked against its array before the access.  On ragged grids of both boundary
-kinds no check fires (no EBOUNDS latched) and every result still matches the oracle."""
+kinds, and on grids of one or two cells along an axis, no check fires (no EBOUNDS latched) and
+every result still matches the oracle."""
 import json
 import os
 import subprocess
@@ -27,7 +28,7 @@ def test_bounds_checking_build_parity():
                        capture_output=True, text=True, timeout=900)
     assert r.returncode == 0, r.stderr[-3000:]
     cases = json.loads(r.stdout.strip().splitlines()[-1])
-    assert len(cases) == 12
+    assert len(cases) == 12 + 7 * 2 * 2 + 2
     for c in cases:
         assert c["status"] == 0, c  # 9 would be FRKC2_EBOUNDS
         assert c["err"] < c["tol"], c
