@@ -777,6 +777,20 @@ def profile_case(F, name: str):
         for _ in range(2):
             u = torch.as_tensor(u0, device="cuda")
             F.frkc2_step(plan, pr, dt, 1, 0.0, u, ws, t)
+    elif name == "paired":  # FP64 real pair stages (PAIRED plan), 2048^2 var-kappa, s = 16, 1 step
+        n, s = 2048, 16
+        u0 = I.smooth_unit((n, n), 64.0, 3819)
+        k = I.kappa_field((n, n), 3818)
+        plan = F.frkc2_plan(s, flags=F.PLAN_PAIRED)
+        kt = torch.as_tensor(k, dtype=torch.float64, device="cuda")
+        pr = F.make_problem(2, (n, n), 1.0, "periodic", "field", "fp64", kappa_field=kt)
+        rho = torch.zeros(1, dtype=torch.float64, device="cuda")
+        F.frkc2_rho_bound(pr, None, rho)
+        dt = 0.9 * plan.info()["beta"] / rho.item()
+        ws = torch.empty(F.frkc2_workspace_size(pr), dtype=torch.uint8, device="cuda")
+        for _ in range(2):
+            u = torch.as_tensor(u0, device="cuda")
+            F.frkc2_step(plan, pr, dt, 1, 0.0, u, ws, F.make_tuning(kernel=4))
     elif name == "bruss":  # FP64 Brusselator persistent launch, 2048^2, s = 16, 1 step
         n, s = 2048, 16
         v0, w0 = I.bruss_u0(n, n, 1.0 / n)
