@@ -552,6 +552,19 @@ def test_lebedev_order_reaches_single_factor_lower_bound(L):
     assert q < GOLD["Q_optimal_factor"]["value"] * L * L
 
 
+@pytest.mark.parametrize("L", [6, 10, 12, 24, 48, 96, 100, 192, 320])
+def test_lebedev_order_within_paper_bound_for_every_even_L(L):
+    """For L not a power of two the Lebedev-Finogenov order no longer attains the single-factor
+    bound, but its realised Q stays inside the paper's 10 L^2 (Sec. 2.2, Fig. 3) -- the
+    library takes this order for every L above 256 (e.g. 320, 384, 1000)."""
+    a = O.step_sizes(L)[O.order_lebedev(L)]
+    b = O.beta(L)
+    x = -b * np.linspace(0.0, 1.0, 8 * L + 1)
+    single = float(np.max(np.abs(1.0 + np.outer(a, x))))
+    q = O.realised_Q(a, b, 8 * L)
+    assert single * (1 - 1e-12) <= q <= 10.0 * L * L
+
+
 def test_lebedev_permutation_recursion():
     assert O.lebedev_permutation(1) == [0]
     assert O.lebedev_permutation(2) == [0, 1]
