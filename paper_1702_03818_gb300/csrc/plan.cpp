@@ -398,20 +398,17 @@ double rounding_gain(const std::vector<cplx>& a, double beta) {
   return std::sqrt(total / double(P));
 }
 
-// Lebedev-Finogenov recursive permutation of 0..m-1: P(1) = (0); P(2q) interleaves each v of
-// P(q) with 2q-1-v; P(2q+1) = P(2q) followed by 2q.
+// Lebedev-Finogenov recursive permutation of 0..m-1: P(1) = (0); P(m) interleaves each v of
+// P(m/2) (integer division) with its mirror m-1-v, and for odd m ends with the middle index m/2,
+// so every root stays paired with its mirror (for m a power of two the classical recursion).
 std::vector<int> lebedev_permutation(int m) {
   if (m == 1) return {0};
   std::vector<int> out;
-  if (m % 2 == 0) {
-    for (int v : lebedev_permutation(m / 2)) {
-      out.push_back(v);
-      out.push_back(m - 1 - v);
-    }
-    return out;
+  for (int v : lebedev_permutation(m / 2)) {
+    out.push_back(v);
+    out.push_back(m - 1 - v);
   }
-  out = lebedev_permutation(m - 1);
-  out.push_back(m - 1);
+  if (m % 2) out.push_back(m / 2);
   return out;
 }
 

@@ -369,3 +369,17 @@ def test_degenerate_inputs_on_host():
     with pytest.raises(F.Frkc2Error) as e:
         F.frkc2_step(plan, p, float("nan"), 1, 0.0, u, ws, stream=0)
     assert e.value.status == F.EINVAL
+
+
+def test_large_plans_meet_the_bound_in_lebedev_order_quickly():
+    """Above s = 256 the Lebedev-Finogenov order meets 10 s^2 at every stage count, not only at
+    powers of two (odd sub-sizes keep each root beside its mirror), so a strict plan needs no
+    greedy n-loop: milliseconds where the greedy took minutes (about 280 s at s = 1000)."""
+    import time
+
+    for s in (1000, 2000, 3542, 4094):
+        t = time.time()
+        info = F.frkc2_plan(s, flags=F.PLAN_STRICT).info()
+        assert time.time() - t < 20.0
+        assert info["n_iter"] == 0 and info["Q"] <= 10.0 * s * s
+        assert np.array_equal(info["order"], O.order_lebedev(s))

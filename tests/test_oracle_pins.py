@@ -552,7 +552,7 @@ def test_lebedev_order_reaches_single_factor_lower_bound(L):
     assert q < GOLD["Q_optimal_factor"]["value"] * L * L
 
 
-@pytest.mark.parametrize("L", [6, 10, 12, 24, 48, 96, 100, 192, 320])
+@pytest.mark.parametrize("L", [6, 10, 12, 24, 48, 96, 100, 192, 320, 600])
 def test_lebedev_order_within_paper_bound_for_every_even_L(L):
     """For L not a power of two the Lebedev-Finogenov order no longer attains the single-factor
     bound, but its realised Q stays inside the paper's 10 L^2 (Sec. 2.2, Fig. 3) -- the
@@ -570,9 +570,17 @@ def test_lebedev_permutation_recursion():
     assert O.lebedev_permutation(2) == [0, 1]
     assert O.lebedev_permutation(4) == [0, 3, 1, 2]
     assert O.lebedev_permutation(8) == [0, 7, 3, 4, 1, 6, 2, 5]
-    assert O.lebedev_permutation(5) == [0, 3, 1, 2, 4]
+    assert O.lebedev_permutation(3) == [0, 2, 1]
+    assert O.lebedev_permutation(5) == [0, 4, 1, 3, 2]
+    assert O.lebedev_permutation(6) == [0, 5, 2, 3, 1, 4]
     for m in range(1, 40):
-        assert sorted(O.lebedev_permutation(m)) == list(range(m))
+        p = O.lebedev_permutation(m)
+        assert sorted(p) == list(range(m))
+        # every entry but an odd size's middle one sits next to its mirror m - 1 - v
+        for i in range(0, m - (m % 2), 2):
+            assert p[i] + p[i + 1] == m - 1
+        if m % 2:
+            assert p[-1] == m // 2
 
 
 def test_plan_auto_uses_lebedev_above_256():
