@@ -135,7 +135,9 @@ typedef struct {
  * next to its mirror about the middle, with the middle one of an odd block last: realised Q
  * at most 4.7 L^2 for every s tried up to 4096), with the greedy n-loop as well if that
  * order misses 10 L^2; the smaller realised Q wins.
- *   s     : number of stages, even, 2..4096.
+ *   s     : number of stages, even, 2..16384.  Above 4096 the Lebedev-Finogenov order is the
+ *           only one (FRKC2_PLAN_GREEDY gives FRKC2_EINVAL there: the greedy's table would
+ *           take 16 s^2 doubles of host memory).
  *   nu    : damping nu0 of Sec. 2.1, 0 <= nu0 < 0.9 (nu = nu0/2 with N = 2).  nu0 > 0 uses
  *           a_l = (1 - mu_l)/((1 - nu) M^2 alpha (1 - (1 - 2 mu_l) zeta_l)) with mu_l = mu on
  *           the roots of T_M = +i c and conj(mu) on their conjugates, mu found by Newton-

@@ -435,8 +435,12 @@ std::vector<int> order_paired(int L) {
 
 extern "C" {
 
+// Largest stage count of a plan, and of a plan that may run the greedy ordering (its table of
+// log-factors holds 16 s^2 doubles: 2 GB at s = 4096).
+constexpr int S_MAX = 16384, S_GREEDY_MAX = 4096;
+
 frkc2_status frkc2_plan(int s, double nu, unsigned flags, frkc2_plan_t* out) {
-  if (!out || s < 2 || s > 4096 || (s & 1)) return FRKC2_EINVAL;
+  if (!out || s < 2 || s > S_MAX || (s & 1)) return FRKC2_EINVAL;
   if (!(nu >= 0.0 && nu < 0.9)) return FRKC2_EINVAL;
   *out = nullptr;
   const int L = s;
@@ -471,13 +475,14 @@ frkc2_status frkc2_plan(int s, double nu, unsigned flags, frkc2_plan_t* out) {
   const bool force_greedy = flags & FRKC2_PLAN_GREEDY, force_lebedev = flags & FRKC2_PLAN_LEBEDEV;
   const bool paired = flags & FRKC2_PLAN_PAIRED;
   if (int(force_greedy) + int(force_lebedev) + int(paired) > 1) return FRKC2_EINVAL;
+  if (force_greedy && L > S_GREEDY_MAX) return FRKC2_EINVAL;
   if (paired) consider(order_paired(L), 0);
   // rank-4 plans take the Lebedev-Finogenov order first at every s: on those roots its
   // realised Q is about 0.1 s^2 where the greedy reaches a few s^2
   bool run_greedy = !paired && (force_greedy || (!force_lebedev && L <= 256 && !order4));
   if (!paired && (force_lebedev || (!force_greedy && (L > 256 || order4)))) {
     const double q = consider(order_lebedev(L), 0);
-    if (!force_lebedev && q > bound) run_greedy = true;
+    if (!force_lebedev && q > bound && L <= S_GREEDY_MAX) run_greedy = true;
   }
   if (run_greedy) {
     for (int n = 1; n <= n_max; ++n)
@@ -507,7 +512,7 @@ frkc2_status frkc2_plan(int s, double nu, unsigned flags, frkc2_plan_t* out) {
 
 frkc2_status frkc2_plan_from_steps(int s, const double* a_re, const double* a_im,
                                    frkc2_plan_t* out) {
-  if (!out || !a_re || !a_im || s < 2 || s > 4096 || (s & 1)) return FRKC2_EINVAL;
+  if (!out || !a_re || !a_im || s < 2 || s > S_MAX || (s & 1)) return FRKC2_EINVAL;
   *out = nullptr;
   frkc2_plan_s* p = new (std::nothrow) frkc2_plan_s;
   if (!p) return FRKC2_EINVAL;

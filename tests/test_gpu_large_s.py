@@ -80,3 +80,31 @@ def test_large_s_one_step_matches_oracle(refs, prec, s, order):
         err = rel_err(got, ref)
         assert err < tol, (err, pred)
         assert rel_l2(got, ref) < 2.0 * pred, (rel_l2(got, ref), pred)  # the policy's forecast holds
+
+
+def test_ten_thousand_stages_keep_seven_digits():
+    """The paper's 10^4 stages (Sec. 2.2: internal stability with about 7 of 16 digits kept at
+    accelerations above 6000): one FP64 step of s = 10000 in the Lebedev-Finogenov order on a
+    64^2 periodic var-kappa grid against the oracle's literal complex stages in the same order."""
+    n, s = 64, 10000
+    u0 = I.smooth_unit((n, n), 8.0, 4041)
+    kap = I.kappa_field((n, n), 4042, ell=4.0)
+    plan = F.frkc2_plan(s)
+    assert np.array_equal(plan.info()["order"], O.order_lebedev(s))
+    a_o = O.step_sizes(s)[O.order_lebedev(s)]
+    opr = oracle_problem(2, "periodic", "field", 1.0, kap)
+    dt = 0.9 * O.beta(s) / O.rho_bound(opr)
+    ref = O.frkc2_step(u0, a_o, dt, opr, 1)
+    pr = F.make_problem(2, (n, n), 1.0, "periodic", "field", "fp64",
+                        kappa_field=torch.as_tensor(kap, device="cuda"))
+    ws = torch.empty(F.frkc2_workspace_size(pr), dtype=torch.uint8, device="cuda")
+    F.frkc2_workspace_reset(ws)
+    u = torch.as_tensor(u0, device="cuda")
+    F.frkc2_step(plan, pr, dt, 1, 0.0, u, ws)
+    assert F.frkc2_workspace_status(ws) == F.OK
+    got = u.cpu().numpy()
+    m = ref.mean()
+    print("s = 10000 FP64 against the oracle: rel", rel_err(got, ref), "deviation from the mean",
+          rel_l2(got - m, ref - m))
+    assert rel_err(got, ref) < 1e-7
+    assert rel_l2(got - m, ref - m) < 1e-7

@@ -383,3 +383,16 @@ def test_large_plans_meet_the_bound_in_lebedev_order_quickly():
         assert time.time() - t < 20.0
         assert info["n_iter"] == 0 and info["Q"] <= 10.0 * s * s
         assert np.array_equal(info["order"], O.order_lebedev(s))
+
+
+def test_plans_up_to_16384_stages():
+    """s up to 16384 (the paper's 10^4 stages, Sec. 2.2): the Lebedev-Finogenov order alone,
+    within the 10 s^2 bound; a forced greedy above 4096 and s above 16384 are refused."""
+    info = F.frkc2_plan(10000, flags=F.PLAN_STRICT).info()
+    assert info["Q"] <= 10.0 * 1e8 and info["n_iter"] == 0
+    assert np.array_equal(info["order"], O.order_lebedev(10000))
+    assert info["beta"] / 10000 > 6000  # acceleration over 6000 (Sec. 1)
+    for bad, flags in [(16386, 0), (5000, F.PLAN_GREEDY)]:
+        with pytest.raises(F.Frkc2Error) as e:
+            F.frkc2_plan(bad, flags=flags)
+        assert e.value.status == F.EINVAL
