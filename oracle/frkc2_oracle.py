@@ -11,7 +11,9 @@ silent or garbled the reading taken is stated in the docstring ("Reading:").
 Contents
 --------
 * stability polynomial and step sizes (Sec. 2, Eqs. 5-8): ``alpha``, ``beta``, ``roots``,
-  ``step_sizes``;
+  ``step_sizes``; the damped step sizes of Sec. 2.1 (``damped_step_sizes``); the rank-N
+  Chebyshev-sum polynomial of Eq. 7 (``chebsum_coefficients``, ``chebsum_alpha``,
+  ``chebsum_beta``, ``chebsum_roots``, ``chebsum_step_sizes``; N = 4 is the fourth-order plan);
 * internal stability (Sec. 2.2, Eqs. 10-12): ``realised_Q`` (brute force over all
   sub-sequences), ``rounding_gain`` (the partial products applied to rounding errors),
   ``order_greedy``, ``order_lebedev`` and ``plan`` (the n-loop);
