@@ -177,7 +177,7 @@ std::vector<cplx> poly_roots(int n, const double* c) {
       z[i] -= w;
       moved = std::max(moved, std::abs(w) / std::max(1.0, std::abs(z[i])));
     }
-    if (moved < 1e-17) break;
+    if (moved < 1e-15) break;  // converged to rounding; Newton steps polish below
   }
   for (cplx& y : z)
     for (int it = 0; it < 3; ++it) {
